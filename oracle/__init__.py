@@ -1,0 +1,325 @@
+"""CPU oracle for the layered-graph planner (GTMP, straight-line local planner).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``, never by the library.  It shares no
+code with the CUDA path: the per-edge work lives in ``gtmp_oracle.c`` (plain C,
+FP64, OpenMP over edges), the graph search below is plain numpy in FP64.
+
+What it computes (Sec. III-A/B, Sec. IV-B and Alg. 1 of the paper): for
+layers V_0 = {q0}, V_1..V_L (the samples), V_{L+1} = {qg}, every edge between
+adjacent layers gets a tri-state label from the straight-line checker and the
+cost ||v - u||; the backward value iteration
+    J_{L+1}(qg) = 0,  J_l(u) = min_v c(u, v) + J_{l+1}(v)
+(absent edges cost +inf) gives the cost-to-go of every vertex and a minimiser
+sigma_l(u) (first index among equal values); following sigma from q0 gives one
+minimum-cost chain.  Edges whose label is "ambiguous" (a waypoint within
++-eps of contact) are resolved both ways: ambiguous -> free gives V_lo,
+ambiguous -> collide gives V_hi; any correct checker's optimum lies between.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+FREE, COLLIDE, AMBIGUOUS = 0, 1, 2
+TAG_UNIFORM, TAG_INFORMED, TAG_COIN = 1, 2, 3
+EPS_DEFAULT = 1e-6
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = ctypes.CDLL(path)
+        _declare(_lib)
+    return _lib
+
+
+class OrcScene(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("dof", ctypes.c_int32),
+        ("dh", ctypes.POINTER(ctypes.c_double)),
+        ("spl", ctypes.c_int32),
+        ("link_sph", ctypes.POINTER(ctypes.c_double)),
+        ("point_radius", ctypes.c_double),
+        ("n_s", ctypes.c_int32), ("spheres", ctypes.POINTER(ctypes.c_double)),
+        ("n_b", ctypes.c_int32), ("boxes", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class OrcEllipsoid(ctypes.Structure):
+    _fields_ = [("centre", ctypes.c_float * 64), ("axis", ctypes.c_float * 64),
+                ("r1", ctypes.c_float), ("r2", ctypes.c_float), ("cmin", ctypes.c_float)]
+
+
+_P = ctypes.POINTER
+_u32p, _f32p, _f64p, _i8p = _P(ctypes.c_uint32), _P(ctypes.c_float), _P(ctypes.c_double), _P(ctypes.c_int8)
+
+
+def _declare(L):
+    L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+    L.orc_sample_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, _f32p, _f32p, _f32p]
+    L.orc_num_robot_spheres.argtypes = [_P(OrcScene)]
+    L.orc_num_robot_spheres.restype = ctypes.c_int
+    L.orc_fk_spheres.argtypes = [_P(OrcScene), _f64p, _f64p]
+    L.orc_config_margin.argtypes = [_P(OrcScene), _f64p]
+    L.orc_config_margin.restype = ctypes.c_double
+    L.orc_config_labels.argtypes = [_P(OrcScene), ctypes.c_int, _f32p, ctypes.c_double, _i8p, _f64p]
+    L.orc_edge_label.argtypes = [_P(OrcScene), _f32p, _f32p, ctypes.c_int, ctypes.c_double]
+    L.orc_edge_label.restype = ctypes.c_int
+    L.orc_edge_length.argtypes = [ctypes.c_int, _f32p, _f32p]
+    L.orc_edge_length.restype = ctypes.c_double
+    L.orc_edge_block.argtypes = [_P(OrcScene), _f32p, ctypes.c_int, _f32p, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_double, _i8p, _f64p]
+    L.orc_edge_margins.argtypes = [_P(OrcScene), _f32p, _f32p, ctypes.c_int, _f64p]
+    L.orc_informed_params.argtypes = [ctypes.c_int, _f32p, _f32p, ctypes.c_float, _P(OrcEllipsoid)]
+    L.orc_informed_attempt.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_int, _P(OrcEllipsoid), _f32p, _f32p, _f32p]
+    L.orc_informed_attempt.restype = ctypes.c_int
+    L.orc_expand_layers.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    _f32p, _f32p, _f32p, _f32p, ctypes.c_float, ctypes.c_int, _f32p]
+    L.orc_expand_layers.restype = ctypes.c_int
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _c32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Philox and uniform layer sampling
+# ---------------------------------------------------------------------------
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_ptr(c, _u32p), _ptr(k, _u32p), _ptr(out, _u32p))
+    return out
+
+
+def sample_uniform(seed: int, restart: int, L: int, M: int, q_lo, q_hi) -> np.ndarray:
+    """Alg. 1 uniform layer samples, float32 [L][M][dof]."""
+    lo, hi = _c32(q_lo), _c32(q_hi)
+    dof = lo.shape[0]
+    Q = np.zeros((L, M, dof), np.float32)
+    lib().orc_sample_uniform(seed, restart, L, M, dof, _ptr(lo, _f32p), _ptr(hi, _f32p), _ptr(Q, _f32p))
+    return Q
+
+
+# ---------------------------------------------------------------------------
+# Scene marshalling and geometry
+# ---------------------------------------------------------------------------
+
+class _SceneHandle:
+    """Keeps the FP64 copies alive while the C struct points at them."""
+
+    def __init__(self, scene):
+        r = scene.robot
+        self.dh = _c64(r.dh)
+        self.link = _c64(r.link_spheres) if r.link_spheres.size else np.zeros(4)
+        self.spheres = _c64(scene.spheres) if scene.spheres.size else np.zeros(4)
+        self.boxes = _c64(scene.boxes) if scene.boxes.size else np.zeros(6)
+        self.s = OrcScene(int(r.kind), int(r.dof), _ptr(self.dh, _f64p), int(r.spheres_per_link),
+                          _ptr(self.link, _f64p), float(r.point_radius),
+                          int(scene.spheres.shape[0]), _ptr(self.spheres, _f64p),
+                          int(scene.boxes.shape[0]), _ptr(self.boxes, _f64p))
+        self.ref = ctypes.byref(self.s)
+        self.dof = int(r.dof)
+
+
+def fk_spheres(scene, q) -> np.ndarray:
+    h = _SceneHandle(scene)
+    S = lib().orc_num_robot_spheres(h.ref)
+    out = np.zeros((S, 4))
+    qq = _c64(q)
+    lib().orc_fk_spheres(h.ref, _ptr(qq, _f64p), _ptr(out, _f64p))
+    return out
+
+
+def config_margin(scene, q) -> float:
+    h = _SceneHandle(scene)
+    qq = _c64(q)
+    return lib().orc_config_margin(h.ref, _ptr(qq, _f64p))
+
+
+def config_labels(scene, Q, eps=EPS_DEFAULT):
+    """Tri-state labels and margins of configurations Q[n][dof] (float32)."""
+    h = _SceneHandle(scene)
+    q = _c32(Q).reshape(-1, h.dof)
+    n = q.shape[0]
+    labels = np.zeros(n, np.int8)
+    margins = np.zeros(n)
+    lib().orc_config_labels(h.ref, n, _ptr(q, _f32p), eps, _ptr(labels, _i8p), _ptr(margins, _f64p))
+    return labels, margins
+
+
+def config_free(scene, Q, eps=EPS_DEFAULT):
+    labels, _ = config_labels(scene, Q, eps)
+    return labels == FREE
+
+
+def edge_block(scene, A, B, H: int, eps=EPS_DEFAULT, max_len=math.inf):
+    """Labels int8 [na][nb] and FP64 costs of every edge A[a] -> B[b]."""
+    h = _SceneHandle(scene)
+    A = _c32(A).reshape(-1, h.dof)
+    B = _c32(B).reshape(-1, h.dof)
+    labels = np.zeros((A.shape[0], B.shape[0]), np.int8)
+    costs = np.zeros((A.shape[0], B.shape[0]))
+    lib().orc_edge_block(h.ref, _ptr(A, _f32p), A.shape[0], _ptr(B, _f32p), B.shape[0], H, eps, max_len,
+                         _ptr(labels, _i8p), _ptr(costs, _f64p))
+    return labels, costs
+
+
+def edge_margins(scene, u, v, H: int) -> np.ndarray:
+    h = _SceneHandle(scene)
+    u, v = _c32(u), _c32(v)
+    out = np.zeros(H)
+    lib().orc_edge_margins(h.ref, _ptr(u, _f32p), _ptr(v, _f32p), H, _ptr(out, _f64p))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Informed sampling and expand-samples (AO-GTMP)
+# ---------------------------------------------------------------------------
+
+def informed_params(q0, qg, c: float):
+    q0, qg = _c32(q0), _c32(qg)
+    e = OrcEllipsoid()
+    lib().orc_informed_params(q0.shape[0], _ptr(q0, _f32p), _ptr(qg, _f32p), np.float32(c), ctypes.byref(e))
+    d = q0.shape[0]
+    return dict(centre=np.array(e.centre[:d], np.float32), axis=np.array(e.axis[:d], np.float32),
+                r1=np.float32(e.r1), r2=np.float32(e.r2), cmin=np.float32(e.cmin), _raw=e)
+
+
+def informed_attempt(seed, i, l, attempt, params, q_lo, q_hi):
+    lo, hi = _c32(q_lo), _c32(q_hi)
+    x = np.zeros(lo.shape[0], np.float32)
+    ok = lib().orc_informed_attempt(seed, i, l, attempt, lo.shape[0], ctypes.byref(params["_raw"]),
+                                    _ptr(lo, _f32p), _ptr(hi, _f32p), _ptr(x, _f32p))
+    return bool(ok), x
+
+
+def expand_layers(seed, Q_old, M_new, q0, qg, q_lo, q_hi, c_best, max_attempts=1 << 16):
+    """expand-samples of Alg. 1: returns (status, Q float32 [L][M_new][dof])."""
+    Q_old = _c32(Q_old)
+    L, M_old, dof = Q_old.shape
+    Q = np.zeros((L, M_new, dof), np.float32)
+    Q[:, :M_old] = Q_old
+    lo, hi, a, b = _c32(q_lo), _c32(q_hi), _c32(q0), _c32(qg)
+    st = lib().orc_expand_layers(seed, L, M_old, M_new, dof, _ptr(lo, _f32p), _ptr(hi, _f32p), _ptr(a, _f32p),
+                                 _ptr(b, _f32p), np.float32(c_best), max_attempts, _ptr(Q, _f32p))
+    return st, Q
+
+
+# ---------------------------------------------------------------------------
+# Graph search on the layered DAG (Sec. IV-B; Alg. 1 gtmp)
+# ---------------------------------------------------------------------------
+
+def layer_vertices(Q, q0, qg):
+    """Vertex sets V_0 = {q0}, V_1..V_L = Q[0..L-1], V_{L+1} = {qg}."""
+    return [_c32(q0)[None, :]] + [_c32(Q[l]) for l in range(Q.shape[0])] + [_c32(qg)[None, :]]
+
+
+def realize_edges(scene, verts, H, eps=EPS_DEFAULT, max_len=math.inf):
+    """Labels and costs of every transition l -> l+1, l = 0..L."""
+    return [edge_block(scene, verts[l], verts[l + 1], H, eps, max_len) for l in range(len(verts) - 1)]
+
+
+def value_iteration(edges, ambiguous_free: bool):
+    """Backward pass J_l(u) = min_v c(u,v) + J_{l+1}(v); returns V, sigma, second.
+
+    V[l] float64 [n_l], sigma[l] int64 [n_l] (-1 if no finite candidate),
+    second[l] = the second smallest candidate value (over distinct v).
+    """
+    n_layers = len(edges) + 1
+    V = [None] * n_layers
+    sigma = [None] * n_layers
+    second = [None] * n_layers
+    V[-1] = np.zeros(edges[-1][0].shape[1])
+    sigma[-1] = np.full(V[-1].shape, -1)
+    second[-1] = np.full(V[-1].shape, np.inf)
+    for l in range(len(edges) - 1, -1, -1):
+        labels, costs = edges[l]
+        ok = (labels == FREE) | ((labels == AMBIGUOUS) if ambiguous_free else False)
+        cand = np.where(ok, costs + V[l + 1][None, :], np.inf)
+        arg = np.argmin(cand, axis=1)                      # first index among equal minima
+        best = cand[np.arange(cand.shape[0]), arg]
+        if cand.shape[1] > 1:
+            part = np.sort(cand, axis=1)
+            sec = part[:, 1]
+        else:
+            sec = np.full(cand.shape[0], np.inf)
+        V[l] = best
+        sigma[l] = np.where(np.isfinite(best), arg, -1)
+        second[l] = sec
+    return V, sigma, second
+
+
+def extract_path(sigma):
+    """Follow the minimisers from q0: one index per sample layer 1..L (-1 if infeasible)."""
+    L = len(sigma) - 2
+    path = np.full(L, -1, np.int64)
+    i = 0
+    if sigma[0][0] < 0:
+        return path
+    for l in range(0, L):
+        i = sigma[l][i]
+        path[l] = i
+    return path
+
+
+@dataclass
+class Solution:
+    V_lo: list
+    V_hi: list
+    sigma: list
+    second: list
+    path: np.ndarray
+    cost_lo: float
+    cost_hi: float
+    edges: list
+    verts: list
+
+
+def solve(scene, Q, H: int, eps=EPS_DEFAULT, max_len=math.inf) -> Solution:
+    """gtmp of Alg. 1 for given samples Q float32 [L][M][dof]."""
+    verts = layer_vertices(Q, scene.q_start, scene.q_goal)
+    edges = realize_edges(scene, verts, H, eps, max_len)
+    V_lo, sig_lo, sec_lo = value_iteration(edges, ambiguous_free=True)
+    V_hi, _, _ = value_iteration(edges, ambiguous_free=False)
+    path = extract_path(sig_lo)
+    return Solution(V_lo, V_hi, sig_lo, sec_lo, path, float(V_lo[0][0]), float(V_hi[0][0]), edges, verts)
+
+
+def path_cost(scene, Q, path, H: int):
+    """FP64 cost of the chain q0 -> Q[l][path[l]] -> qg and its worst waypoint margin."""
+    verts = [_c32(scene.q_start)] + [_c32(Q[l, int(path[l])]) for l in range(Q.shape[0])] + [_c32(scene.q_goal)]
+    total = 0.0
+    worst = math.inf
+    for a, b in zip(verts[:-1], verts[1:]):
+        total += lib().orc_edge_length(a.shape[0], _ptr(a, _f32p), _ptr(b, _f32p))
+        worst = min(worst, float(edge_margins(scene, a, b, H).min()))
+    return total, worst
+
+
+def anytime(scene, seed, R, L, M, H, eps=EPS_DEFAULT):
+    """anytime-gtmp of Alg. 1 with R restarts (single class): per-restart solutions."""
+    return [solve(scene, sample_uniform(seed, r, L, M, scene.robot.q_lo, scene.robot.q_hi), H, eps)
+            for r in range(R)]

@@ -1,0 +1,453 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against a published value, a closed form, an
+invariant, brute force, or an independent library routine, chosen so that a
+plausible slip (a dropped term, a wrong sign or index, a transposed operand)
+fails at least one of them.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.sparse import csr_matrix
+from scipy.sparse.csgraph import dijkstra
+
+import oracle
+from paper_2608_25830_b300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors
+# ---------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_uniform_samples_are_uniform_in_box():
+    lo = np.array([-math.pi, -1.0, 0.25], np.float32)
+    hi = np.array([math.pi, 3.0, 0.5], np.float32)
+    Q = oracle.sample_uniform(7, 3, 2, 4000, lo, hi)
+    assert Q.dtype == np.float32 and Q.shape == (2, 4000, 3)
+    for k in range(3):
+        x = Q[..., k].ravel().astype(np.float64)
+        assert x.min() >= lo[k] and x.max() < hi[k]
+        p = stats.kstest((x - lo[k]) / (hi[k] - lo[k]), "uniform").pvalue
+        assert p > 1e-4, (k, p)
+    # layers, restarts and seeds give different streams; same arguments repeat exactly
+    assert not np.array_equal(Q[0], Q[1])
+    assert not np.array_equal(Q, oracle.sample_uniform(7, 4, 2, 4000, lo, hi))
+    assert not np.array_equal(Q, oracle.sample_uniform(8, 3, 2, 4000, lo, hi))
+    assert np.array_equal(Q, oracle.sample_uniform(7, 3, 2, 4000, lo, hi))
+    # coordinates within one vertex are not copies of each other
+    assert np.corrcoef(Q[0, :, 0], Q[0, :, 1])[0, 1] ** 2 < 0.01
+
+
+# ---------------------------------------------------------------------------
+# Forward kinematics: closed forms of simple chains
+# ---------------------------------------------------------------------------
+
+def _robot(dh, link_sph):
+    dh = np.asarray(dh, np.float32)
+    dof = dh.shape[0]
+    return scenes.Robot(scenes.ROBOT_DH_ARM, dof, dh, np.asarray(link_sph, np.float32),
+                        np.full(dof, -math.pi, np.float32), np.full(dof, math.pi, np.float32))
+
+
+def _empty_scene(robot):
+    return scenes.Scene(robot, np.zeros((0, 4), np.float32), np.zeros((0, 6), np.float32),
+                        np.zeros(robot.dof, np.float32), np.zeros(robot.dof, np.float32))
+
+
+def test_fk_planar_chain_closed_form():
+    a = [0.3, 0.2, 0.1]
+    dh = [[0.0, ai, 0.0, 0.0] for ai in a]
+    origin_sph = np.zeros((3, 1, 4))
+    origin_sph[:, 0, 3] = 0.01
+    sc = _empty_scene(_robot(dh, origin_sph))
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        q = rng.uniform(-math.pi, math.pi, 3)
+        got = oracle.fk_spheres(sc, q)
+        phi = np.cumsum(q)
+        x = np.cumsum(np.array(a, np.float32).astype(np.float64) * np.cos(phi))
+        y = np.cumsum(np.array(a, np.float32).astype(np.float64) * np.sin(phi))
+        np.testing.assert_allclose(got[:, 0], x, atol=1e-12)
+        np.testing.assert_allclose(got[:, 1], y, atol=1e-12)
+        np.testing.assert_allclose(got[:, 2], 0.0, atol=1e-12)
+        np.testing.assert_allclose(got[:, 3], 0.01, rtol=1e-6)
+
+
+def test_fk_twisted_two_link_closed_form():
+    # link 1 twisted by +pi/2: o1 = (a1 c1, a1 s1, d1),
+    # o2 - o1 = (a2 c2 c1 + d2 s1, a2 c2 s1 - d2 c1, a2 s2)   (worked out by hand)
+    a1, d1, a2, d2 = 0.25, 0.05, 0.2, 0.07
+    dh = [[d1, a1, math.pi / 2, 0.0], [d2, a2, 0.0, 0.0]]
+    sph = np.zeros((2, 1, 4))
+    sph[:, 0, 3] = 0.02
+    rob = _robot(dh, sph)
+    a1, d1, a2, d2 = (float(np.float32(v)) for v in (a1, d1, a2, d2))
+    sc = _empty_scene(rob)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        q1, q2 = rng.uniform(-math.pi, math.pi, 2)
+        got = oracle.fk_spheres(sc, [q1, q2])
+        c1, s1, c2, s2 = math.cos(q1), math.sin(q1), math.cos(q2), math.sin(q2)
+        o1 = np.array([a1 * c1, a1 * s1, d1])
+        o2 = o1 + np.array([a2 * c2 * c1 + d2 * s1, a2 * c2 * s1 - d2 * c1, a2 * s2])
+        np.testing.assert_allclose(got[0, :3], o1, atol=1e-7)   # float32 pi/2 twist: 4e-8 off exact
+        np.testing.assert_allclose(got[1, :3], o2, atol=1e-7)
+
+
+def test_fk_generated_arm_spheres_lie_on_link_segments():
+    """Generated link spheres sit at fixed fractions of the segment between frame origins."""
+    rob = scenes.dh_arm(3, 7)
+    origin = rob.link_spheres.copy()
+    origin[:, :, :3] = 0.0                       # same robot with spheres at the frame origins
+    frames = _empty_scene(scenes.Robot(rob.kind, rob.dof, rob.dh, origin[:, :1], rob.q_lo, rob.q_hi))
+    sc = _empty_scene(rob)
+    fr = (np.arange(4) + 0.5) / 4
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        q = rng.uniform(-math.pi, math.pi, 7)
+        o = np.vstack([np.zeros(3), oracle.fk_spheres(frames, q)[:, :3]])
+        s = oracle.fk_spheres(sc, q)[:, :3].reshape(7, 4, 3)
+        for i in range(7):
+            expect = o[i][None, :] + fr[:, None] * (o[i + 1] - o[i])[None, :]
+            np.testing.assert_allclose(s[i], expect, atol=2e-7)
+            # rigid-motion invariant: |o_i - o_{i-1}| = sqrt(a^2 + d^2)
+            d, a = float(rob.dh[i, 0]), float(rob.dh[i, 1])
+            assert abs(np.linalg.norm(o[i + 1] - o[i]) - math.hypot(a, d)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Collision margins: hand cases with known distances
+# ---------------------------------------------------------------------------
+
+def _point_scene(spheres=(), boxes=(), radius=0.0, dof=3):
+    rob = scenes.Robot(scenes.ROBOT_POINT, dof, np.zeros((dof, 4), np.float32), np.zeros((dof, 0, 4), np.float32),
+                       np.full(dof, -2, np.float32), np.full(dof, 2, np.float32), radius)
+    return scenes.Scene(rob, np.asarray(spheres, np.float32).reshape(-1, 4), np.asarray(boxes, np.float32).reshape(-1, 6),
+                        np.zeros(dof, np.float32), np.zeros(dof, np.float32))
+
+
+def test_margin_sphere_cases():
+    sc = _point_scene(spheres=[(0.5, 0.0, 0.0, 0.25)], radius=0.125)
+    assert oracle.config_margin(sc, [0.0, 0.0, 0.0]) == pytest.approx(0.5 - 0.25 - 0.125, abs=1e-15)
+    assert oracle.config_margin(sc, [0.125, 0.0, 0.0]) == pytest.approx(0.0, abs=1e-15)       # tangent
+    assert oracle.config_margin(sc, [0.5, 0.0, 0.0]) == pytest.approx(-0.375, abs=1e-15)      # centred
+    assert oracle.config_margin(sc, [0.5, 3.0, 4.0]) == pytest.approx(5.0 - 0.375, abs=1e-12)  # 3-4-5
+
+
+def test_margin_box_face_edge_corner_inside():
+    box = (0.0, 0.0, 0.0, 1.0, 2.0, 3.0)
+    sc = _point_scene(boxes=[box])
+    m = lambda q: oracle.config_margin(sc, q)
+    assert m([-0.5, 1.0, 1.0]) == pytest.approx(0.5)                      # face
+    assert m([-0.3, -0.4, 1.0]) == pytest.approx(0.5)                     # edge (3-4-5)
+    assert m([2.0, 4.0, 5.0]) == pytest.approx(3.0)                       # corner (1,2,2)
+    assert m([0.5, 1.0, 1.0]) == pytest.approx(-0.5)                      # inside: nearest face x
+    assert m([0.9, 1.0, 1.5]) == pytest.approx(-0.1)                      # inside: nearest face x=1
+    assert m([0.5, 1.9, 1.5]) == pytest.approx(-0.1)                      # inside: nearest face y=2
+    assert m([1.0, 1.0, 1.0]) == pytest.approx(0.0)                       # on the face
+    sc_r = _point_scene(boxes=[box], radius=0.25)
+    assert oracle.config_margin(sc_r, [-0.5, 1.0, 1.0]) == pytest.approx(0.25)
+
+
+def test_margin_brute_force_over_pairs():
+    rob = scenes.dh_arm(5, 6)
+    rng = np.random.default_rng(3)
+    sph, box = scenes.arm_obstacles(rng, 9)
+    sc = scenes.Scene(rob, sph, box, np.zeros(6, np.float32), np.zeros(6, np.float32))
+    for _ in range(5):
+        q = rng.uniform(-math.pi, math.pi, 6)
+        S = oracle.fk_spheres(sc, q)
+        best = math.inf
+        for c in S:
+            for o in sph.astype(np.float64):
+                best = min(best, np.linalg.norm(c[:3] - o[:3]) - o[3] - c[3])
+            for b in box.astype(np.float64):
+                # distance to the box by dense projection onto the box (outside) / faces (inside)
+                clamp = np.minimum(np.maximum(c[:3], b[:3]), b[3:])
+                if np.all(clamp == c[:3]):
+                    dist = -min(np.min(c[:3] - b[:3]), np.min(b[3:] - c[:3]))
+                else:
+                    dist = np.linalg.norm(c[:3] - clamp)
+                best = min(best, dist - c[3])
+        assert oracle.config_margin(sc, q) == pytest.approx(best, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Straight-line local planner: waypoint rule and tri-state labels
+# ---------------------------------------------------------------------------
+
+def test_edge_label_waypoints():
+    # disk of radius 0.2 at x = 0.5 on the segment (0,0) -> (1,0), H = 3 checks x = 0, 0.5, 1
+    sc = _point_scene(spheres=[(0.5, 0.0, 0.0, 0.2)], dof=2)
+    lab, cost = oracle.edge_block(sc, [[0.0, 0.0]], [[1.0, 0.0]], 3)
+    assert lab[0, 0] == oracle.COLLIDE and cost[0, 0] == 1.0
+    # a disk between waypoints is missed: the checker is the paper's discretised SEV
+    sc2 = _point_scene(spheres=[(0.25, 0.0, 0.0, 0.1)], dof=2)
+    lab, _ = oracle.edge_block(sc2, [[0.0, 0.0]], [[1.0, 0.0]], 3)
+    assert lab[0, 0] == oracle.FREE
+    lab, _ = oracle.edge_block(sc2, [[0.0, 0.0]], [[1.0, 0.0]], 5)   # t = 0.25 hits it
+    assert lab[0, 0] == oracle.COLLIDE
+    # tangent waypoint (distance exactly the radius) is ambiguous
+    sc3 = _point_scene(spheres=[(0.5, 0.25, 0.0, 0.25)], dof=2)
+    lab, _ = oracle.edge_block(sc3, [[0.0, 0.0]], [[1.0, 0.0]], 3)
+    assert lab[0, 0] == oracle.AMBIGUOUS
+    # edge-length limit removes the edge
+    lab, _ = oracle.edge_block(sc2, [[0.0, 0.0]], [[0.0, 1.0]], 3, max_len=0.5)
+    assert lab[0, 0] == oracle.COLLIDE
+    # endpoint in collision
+    lab, _ = oracle.edge_block(sc, [[0.5, 0.0]], [[0.5, 1.0]], 2)
+    assert lab[0, 0] == oracle.COLLIDE
+
+
+def test_edge_margins_match_config_margins():
+    a = scenes.arm_scene(1, 7, 12)
+    rng = np.random.default_rng(4)
+    u = rng.uniform(-3, 3, 7).astype(np.float32)
+    v = rng.uniform(-3, 3, 7).astype(np.float32)
+    H = 9
+    m = oracle.edge_margins(a, u, v, H)
+    assert m[0] == oracle.config_margin(a, u.astype(np.float64))
+    assert m[-1] == oracle.config_margin(a, v.astype(np.float64))
+    t = np.float32(4) / np.float32(8)           # t = 0.5 exactly: the midpoint waypoint
+    mid = (np.float64(t) * (v - u).astype(np.float64) + u).astype(np.float32)
+    assert m[4] == oracle.config_margin(a, mid.astype(np.float64))
+
+
+# ---------------------------------------------------------------------------
+# Graph search: brute force, Dijkstra, Alg. 1's Jacobi form, closed forms
+# ---------------------------------------------------------------------------
+
+def _small_problem(seed=0, M=4, L=3, n_obs=12):
+    sc = scenes.point2d_scene(seed, n_obs)
+    Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    return sc, Q
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_value_iteration_equals_brute_force(seed):
+    sc, Q = _small_problem(seed, M=4, L=3, n_obs=6 + seed)
+    H = 16
+    sol = oracle.solve(sc, Q, H)
+    verts = sol.verts
+    best, best_chain = math.inf, None
+    for chain in itertools.product(range(4), repeat=3):
+        idx = (0,) + chain + (0,)
+        total = 0.0
+        for l in range(4):
+            lab, cost = sol.edges[l]
+            if lab[idx[l], idx[l + 1]] != oracle.FREE:
+                total = math.inf
+                break
+            total += cost[idx[l], idx[l + 1]]
+        if total < best:
+            best, best_chain = total, chain
+    assert sol.cost_lo == pytest.approx(best, rel=1e-12) if math.isfinite(best) else math.isinf(sol.cost_lo)
+    if math.isfinite(best):
+        assert tuple(sol.path) == best_chain
+    else:
+        assert list(sol.path) == [-1, -1, -1]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_value_iteration_equals_dijkstra(seed):
+    sc, Q = _small_problem(seed, M=12, L=4, n_obs=10)
+    sol = oracle.solve(sc, Q, 16)
+    sizes = [len(v) for v in sol.verts]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    rows, cols, w = [], [], []
+    for l, (lab, cost) in enumerate(sol.edges):
+        a, b = np.nonzero(lab == oracle.FREE)
+        rows += list(off[l] + a)
+        cols += list(off[l + 1] + b)
+        w += list(cost[a, b])
+    n = off[-1]
+    G = csr_matrix((w, (rows, cols)), shape=(n, n))
+    dist = dijkstra(G, directed=True, indices=0)
+    assert dist[n - 1] == pytest.approx(sol.cost_lo, rel=1e-12) if math.isfinite(sol.cost_lo) else math.isinf(dist[n - 1])
+    # every vertex's cost-to-go equals its Dijkstra distance to the goal (reverse graph)
+    back = dijkstra(G.T.tocsr(), directed=True, indices=n - 1)
+    for l in range(len(sizes)):
+        np.testing.assert_allclose(sol.V_lo[l], back[off[l]:off[l + 1]], rtol=1e-12)
+
+
+def test_jacobi_form_of_algorithm1_matches_backward_pass():
+    """Alg. 1 initialises V_h to 0 and sweeps L+1 times; the result is the backward pass."""
+    sc, Q = _small_problem(2, M=8, L=5, n_obs=8)
+    sol = oracle.solve(sc, Q, 16)
+    L = Q.shape[0]
+    C = [np.where(lab == oracle.FREE, cost, np.inf) for lab, cost in sol.edges]
+    Vh = [np.zeros(Q.shape[1]) for _ in range(L)]       # V_h <- 0
+    Vg = np.zeros(1)
+    Vs = 0.0
+    for _ in range(L + 1):
+        new = [None] * L
+        new[L - 1] = np.min(C[L] + Vg[None, :], axis=1)
+        for m in range(L - 1):
+            new[m] = np.min(C[m + 1] + Vh[m + 1][None, :], axis=1)
+        Vs = float(np.min(C[0][0] + Vh[0]))
+        Vh = new
+    for m in range(L):
+        np.testing.assert_allclose(Vh[m], sol.V_lo[m + 1], rtol=1e-12)
+    assert Vs == pytest.approx(sol.cost_lo, rel=1e-12)
+
+
+def test_collinear_samples_give_straight_line_cost():
+    sc = _point_scene(dof=2)
+    sc.q_start = np.array([-0.5, -0.25], np.float32)
+    sc.q_goal = np.array([0.5, 0.25], np.float32)
+    L, M = 3, 5
+    rng = np.random.default_rng(0)
+    Q = rng.uniform(-1, 1, (L, M, 2)).astype(np.float32)
+    # plant one exactly collinear point per layer (t = 1/4, 1/2, 3/4 are exact in binary)
+    for l, t in enumerate([0.25, 0.5, 0.75]):
+        Q[l, (l * 2 + 1) % M] = sc.q_start + np.float32(t) * (sc.q_goal - sc.q_start)
+    sol = oracle.solve(sc, Q, 8)
+    assert sol.cost_lo == pytest.approx(math.hypot(1.0, 0.5), rel=1e-14)
+    assert list(sol.path) == [1, 3, 0]
+
+
+def test_infeasible_graph_reports_infinity_and_minus_one():
+    sc = _point_scene(spheres=[(0.0, 0.0, 0.0, 5.0)], dof=2)        # everything in collision
+    Q = oracle.sample_uniform(0, 0, 3, 4, [-1, -1], [1, 1])
+    sol = oracle.solve(sc, Q, 4)
+    assert math.isinf(sol.cost_lo) and math.isinf(sol.cost_hi)
+    assert list(sol.path) == [-1, -1, -1]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_returned_chain_is_free_and_costs_what_it_claims(seed):
+    a = scenes.arm_scene(seed, 6, 20)
+    a = scenes.pick_endpoints(a, lambda q: oracle.config_free(a, q))
+    Q = oracle.sample_uniform(seed, 0, 3, 24, a.robot.q_lo, a.robot.q_hi)
+    sol = oracle.solve(a, Q, 16)
+    straight = float(np.linalg.norm(a.q_goal.astype(np.float64) - a.q_start))
+    if math.isfinite(sol.cost_lo):
+        total, worst = oracle.path_cost(a, Q, sol.path, 16)
+        assert total == pytest.approx(sol.cost_lo, rel=1e-12)
+        assert worst > -oracle.EPS_DEFAULT
+        assert sol.cost_lo >= straight * (1 - 1e-12)
+    assert sol.cost_lo <= sol.cost_hi
+
+
+# ---------------------------------------------------------------------------
+# Informed sampling (X_f(c), Sec. IV-D) and expand-samples (Alg. 1)
+# ---------------------------------------------------------------------------
+
+def _informed_draws(d, c, n, lo=-50.0, hi=50.0, seed=11):
+    q0 = np.linspace(-1, 1, d).astype(np.float32)
+    qg = (q0[::-1] * 0.5 + 0.3).astype(np.float32)
+    par = oracle.informed_params(q0, qg, c)
+    xs = []
+    i = 0
+    while len(xs) < n:
+        for a in range(1 << 12):
+            ok, x = oracle.informed_attempt(seed, i, 0, a, par, np.full(d, lo), np.full(d, hi))
+            if ok:
+                xs.append(x)
+                break
+        i += 1
+    return q0, qg, par, np.array(xs, np.float64)
+
+
+@pytest.mark.parametrize("d", [2, 6])
+def test_informed_samples_in_ellipsoid_and_uniform(d):
+    q0 = np.linspace(-1, 1, d).astype(np.float32)
+    qg = (q0[::-1] * 0.5 + 0.3).astype(np.float32)
+    cmin = float(np.linalg.norm(qg.astype(np.float64) - q0))
+    c = 1.7 * cmin
+    q0, qg, par, X = _informed_draws(d, c, 1500)
+    s = np.linalg.norm(X - q0, axis=1) + np.linalg.norm(X - qg, axis=1)
+    assert np.all(s <= c * (1 + 1e-6))
+    # r1, r2 are the semi-axes of the informed set: foci distance c_min
+    assert par["r1"] == pytest.approx(c / 2, rel=1e-6)
+    assert par["r2"] == pytest.approx(math.sqrt(c * c - cmin * cmin) / 2, rel=1e-5)
+    # back to the unit ball: the radius of a uniform point of the d-ball has CDF rho^d
+    a = par["axis"].astype(np.float64)
+    Y = X - par["centre"].astype(np.float64)
+    along = Y @ a
+    perp = Y - along[:, None] * a[None, :]
+    Z = perp / float(par["r2"]) + (along / float(par["r1"]))[:, None] * a[None, :]
+    rho = np.linalg.norm(Z, axis=1)
+    assert rho.max() <= 1 + 1e-5
+    assert stats.kstest(rho ** d, "uniform").pvalue > 1e-4
+    # the direction along the major axis is symmetric and spans the whole axis
+    assert abs(np.mean(along)) < 0.1 * float(par["r1"])
+    assert np.max(np.abs(along)) > 0.8 * float(par["r1"])
+
+
+def test_informed_box_rejection_and_degenerate_bound():
+    d = 3
+    q0 = np.zeros(d, np.float32)
+    qg = np.array([1, 0, 0], np.float32)
+    par = oracle.informed_params(q0, qg, 3.0)
+    lo, hi = np.full(d, -0.5, np.float32), np.full(d, 0.5, np.float32)
+    hits = 0
+    for a in range(2000):
+        ok, x = oracle.informed_attempt(5, 0, 0, a, par, lo, hi)
+        if ok:
+            hits += 1
+            assert np.all(x >= lo) and np.all(x <= hi)
+    assert hits > 0
+    # c = c_min: the informed set collapses onto the segment q0 -> qg
+    par = oracle.informed_params(q0, qg, 1.0)
+    assert float(par["r2"]) == 0.0
+    for a in range(200):
+        ok, x = oracle.informed_attempt(5, 1, 0, a, par, np.full(d, -5, np.float32), np.full(d, 5, np.float32))
+        if ok:
+            assert abs(x[1]) == 0 and abs(x[2]) == 0 and -1e-6 <= x[0] <= 1 + 1e-6
+
+
+def test_expand_with_infinite_bound_is_the_uniform_stream():
+    lo, hi = np.full(4, -1, np.float32), np.full(4, 1, np.float32)
+    st, Q = oracle.expand_layers(9, np.zeros((3, 0, 4), np.float32), 16, np.zeros(4), np.ones(4) * 0.5, lo, hi, math.inf)
+    assert st == 0
+    np.testing.assert_array_equal(Q, oracle.sample_uniform(9, 0, 3, 16, lo, hi))
+
+
+def test_expand_keeps_old_samples_and_mixes_heuristic_midpoints():
+    d = 3
+    lo, hi = np.full(d, -2, np.float32), np.full(d, 2, np.float32)
+    q0 = np.array([-1, -1, 0], np.float32)
+    qg = np.array([1, 1, 0], np.float32)
+    _, Q0 = oracle.expand_layers(4, np.zeros((4, 0, d), np.float32), 32, q0, qg, lo, hi, math.inf)
+    c = 4.0
+    st, Q = oracle.expand_layers(4, Q0, 256, q0, qg, lo, hi, c)
+    assert st == 0
+    np.testing.assert_array_equal(Q[:, :32], Q0)
+    L = Q.shape[0]
+    n_mid = 0
+    n_new = 0
+    for l in range(L):
+        prev = q0[None, :] if l == 0 else Q0[l - 1]
+        nxt = qg[None, :] if l == L - 1 else Q0[l + 1]
+        for x in Q[l, 32:]:
+            n_new += 1
+            # brute force: is x the midpoint of some u in the previous layer and its nearest next-layer vertex?
+            is_mid = False
+            for u in prev:
+                j = int(np.argmin(((nxt.astype(np.float64) - u) ** 2).sum(1)))
+                if np.array_equal(x, (np.float32(0.5) * (u + nxt[j])).astype(np.float32)):
+                    is_mid = True
+                    break
+            if is_mid:
+                n_mid += 1
+            else:
+                s = np.linalg.norm(x.astype(np.float64) - q0) + np.linalg.norm(x.astype(np.float64) - qg)
+                assert s <= c * (1 + 1e-6)
+    # fair coin: about half of the new samples are heuristic midpoints
+    assert abs(n_mid / n_new - 0.5) < 0.08, n_mid / n_new
