@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Throughput of the fused GTMP planner on one B300 (or N, one process each).
+
+Workload (default): 7-DoF DH arm, 20 sphere + 10 box obstacles in a 1.5 m
+cube, M = 1024 samples per layer, L = 8 layers, H = 32 waypoints per edge,
+float32.  One step = one complete plan through the C ABI: Philox layer
+sampling, vertex labels, the L+1 fused edge + min-plus transitions and path
+extraction, i.e. H * (2M + (L-1) M^2) = 234,946,560 nominal waypoint checks.
+Every step plans a different sample set (seed = step); under torchrun every
+rank plans its own seeds (independent problems, weak scaling, no collective
+on the data path).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge-waypoint checks/sec and solves/sec (7-DoF, M=1024, L=8), surrogate/batched vs plain"
+
+
+def flops_per_waypoint(dof, spl, n_s, n_b, arm=True):
+    """FP32 arithmetic of one interior waypoint check as the kernel performs it.
+
+    add/sub/mul/div/sqrt count 1, fma counts 2; compares, min/max and the
+    sincosf calls count 0.  Waypoint: dof fma + 1 div.  FK per link: angle add
+    (1), new x and pre-twist y axes (2 x (3 mul + 3 fma) = 18), origin (6 fma =
+    12), twisted y and z axes (18), and spl sphere centres (9 fma = 18 each).
+    Per robot sphere: sphere obstacle 3 sub + 1 mul + 2 fma = 8, box 3 sub +
+    3 sub + 1 mul + 2 fma = 11.
+    """
+    interp = 2 * dof + 1
+    if arm:
+        fk = dof * (1 + 18 + 12 + 18 + 18 * spl)
+        spheres = dof * spl
+    else:
+        fk, spheres = 0, 1
+    return interp + fk + spheres * (8 * n_s + 11 * n_b)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_rows(sc, wl, budget_s, seed=0, max_rows=None):
+    """Run the oracle's edge realisation on whole rows of a middle transition
+    until budget_s has passed; return (edges, seconds, rows)."""
+    import oracle
+    M, L, H = wl["M"], wl["L"], wl["H"]
+    Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
+    mid = max(1, L // 2)
+    t0 = time.perf_counter()
+    rows = 0
+    while True:
+        oracle.edge_block(sc, verts[mid][rows:rows + 1], verts[mid + 1], H)
+        rows += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or rows >= M or (max_rows and rows >= max_rows):
+            return rows * M, el, rows
+
+
+def oracle_free_fn(sc):
+    import oracle
+    return lambda q: oracle.config_free(sc, q)
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2608_25830_b300 import scenes
+    if wl["kind"] == "point2d":
+        sc = scenes.point2d_scene(wl["seed"], wl["n_obs"])
+    else:
+        base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
+        sc = scenes.pick_endpoints(base, oracle_free_fn(base))
+    per_step = args.ref_budget
+    for _ in range(args.warmup):
+        oracle_rows(sc, wl, per_step / 4, max_rows=1)
+    edges = 0
+    secs = 0.0
+    rows = 0
+    for s in range(args.steps):
+        e, t, r = oracle_rows(sc, wl, per_step, seed=s)
+        edges += e
+        secs += t
+        rows += r
+    checks = edges * wl["H"]
+    nominal_edges = 2 * wl["M"] + (wl["L"] - 1) * wl["M"] ** 2
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    value = checks / secs
+    sample = (f"{rows} rows x {wl['M']} edges of a middle transition (H={wl['H']}), "
+              f"{args.steps} steps of ~{per_step:.0f} s, extrapolated per check")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "solves_per_s": edges / secs / nominal_edges,
+        "config": {"workload": args.workload, "M": wl["M"], "L": wl["L"], "H": wl["H"], "dof": wl.get("dof", 2),
+                   "obstacles": wl["n_obs"], "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "checks/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "checks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9 or not f[1].isdigit():
+                    continue
+                sm.append(int(f[1]))
+                mx.append(int(f[2]))
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2608_25830_b300 import binding, scenes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    M, L, H = wl["M"], wl["L"], wl["H"]
+    # scene: endpoints chosen by the GPU's own exact checker
+    if wl["kind"] == "point2d":
+        sc = scenes.point2d_scene(wl["seed"], wl["n_obs"])
+    else:
+        base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
+        probe = binding.Planner(base.robot, 8, 1, 2, max_obstacles=64)
+        binding.gtmp_set_obstacles(probe.ctx, base.spheres, base.boxes)
+
+        def free_fn(q):
+            return (probe.label_configs(torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
+
+        sc = scenes.pick_endpoints(base, free_fn)
+        probe.close()
+    dof = sc.robot.dof
+    n_s, n_b = sc.spheres.shape[0], sc.boxes.shape[0]
+    nominal_edges = 2 * M + (L - 1) * M * M
+    nominal_checks = H * nominal_edges
+
+    p = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_EARLY_EXIT)
+    p.set_scene(sc)
+    path = torch.empty(L, dtype=torch.int32, device="cuda")
+    cost = torch.empty(1, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
+
+    def step(seed):
+        binding.gtmp_sample_layers(p.ctx, seed, M)
+        binding.gtmp_solve(p.ctx, path, cost)
+
+    seed0 = 1 + rank * 1_000_003
+    for s in range(args.warmup):
+        step(seed0 + 10_000 + s)
+    p.synchronize()
+
+    # --- device-resident timed region: K plans, L2 flushed between them
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    costs = []
+    binding.gtmp_profile_read(p.ctx)                 # reset counters
+    binding.gtmp_profile_enable(p.ctx, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            evs[s][0].record(stream)
+            step(seed0 + s)
+            evs[s][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    prof = binding.gtmp_profile_read(p.ctx)
+    binding.gtmp_profile_enable(p.ctx, False)
+    p.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    solves = args.steps * world
+    value = nominal_checks * solves / total_s
+    clocks = clk.summary()
+    last_cost = float(cost.cpu()[0])
+
+    # --- end to end through the public API, host buffers, copies inside the region
+    host_path = torch.empty(L, dtype=torch.int32, pin_memory=True)
+    host_cost = torch.empty(1, dtype=torch.float32, pin_memory=True)
+    h2d = (sc.spheres.size + sc.boxes.size + 2 * dof) * 4 + 8
+    d2h = L * 4 + 4
+
+    def e2e_step(seed):
+        binding.gtmp_set_obstacles(p.ctx, sc.spheres, sc.boxes)
+        binding.gtmp_set_endpoints(p.ctx, sc.q_start, sc.q_goal)
+        step(seed)
+        host_path.copy_(path, non_blocking=True)
+        host_cost.copy_(cost, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step(seed0 + 20_000)
+    e2e_s = 0.0
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step(seed0 + s)
+        e2e_s += time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = nominal_checks * solves / e2e_s
+
+    # --- roofline of the fused kernel in full-evaluation mode (data-independent FP32 work)
+    pf = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_FULL)
+    pf.set_scene(sc)
+    binding.gtmp_sample_layers(pf.ctx, seed0, M)
+    binding.gtmp_solve(pf.ctx, path, cost)
+    pf.synchronize()
+    binding.gtmp_profile_read(pf.ctx)
+    binding.gtmp_profile_enable(pf.ctx, True)
+    full_steps = max(1, min(3, args.steps))
+    for s in range(full_steps):
+        flush.zero_()
+        binding.gtmp_sample_layers(pf.ctx, seed0 + s, M)
+        binding.gtmp_solve(pf.ctx, path, cost)
+    fprof = binding.gtmp_profile_read(pf.ctx)
+    pf.close()
+    fpw = flops_per_waypoint(dof, sc.robot.spheres_per_link, n_s, n_b, wl["kind"] == "arm")
+    full_flops = fprof["fused_edges"] * (H - 2) * fpw
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = sms * 128 * 2 * 2.032e9 / 1e12
+    achieved = full_flops / (fprof["fused_ms"] / 1e3) / 1e12
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            edges, secs, rows = oracle_rows(sc, wl, args.cpu_budget)
+            cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+            cpu = {"value": edges * H / secs, "unit": "checks/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{rows} rows x {M} edges of transition {max(1, L // 2)} (H={H}) in {secs:.1f} s, "
+                             f"extrapolated per nominal check"}
+        out = {
+            "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene and samples)",
+            "solves_per_s": solves / total_s,
+            "config": {"workload": args.workload, "M": M, "L": L, "H": H, "dof": dof, "obstacles": [n_s, n_b],
+                       "eval_mode": "early_exit", "parallelism": f"replicas x{world}", "l2": "flushed between steps",
+                       "checks_per_solve": nominal_checks, "last_cost": last_cost},
+            "e2e": {"value": e2e_value, "unit": "checks/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(prof["launches"]),
+            "roofline": {"bound": "alu", "kernel": "fused_transition_kernel (full-evaluation mode)",
+                         "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": None, "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock)",
+                         "flops_per_waypoint": fpw,
+                         "fused_ms_per_solve": fprof["fused_ms"] / full_steps},
+            "fused_ms_per_solve_early_exit": prof["fused_ms"] / args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    p.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def main():
+    from paper_2608_25830_b300 import scenes
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="arm7_m1024_l8_h32", choices=sorted(scenes.WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=10.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = dict(scenes.WORKLOADS[args.workload])
+    if "M" not in wl:
+        raise SystemExit(f"{args.workload} is not a single-solve workload")
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * gtmp.h — C ABI of a B300 (sm_103a) planner for Global Tensor Motion Planning
+ * with the straight-line local planner, and its anytime policies.
+ *
+ * Paper: "Anytime Global Tensor Motion Planning" (Coumar, Le, Kingston).
+ * The planning problem (Sec. III): configuration space C ⊆ R^d (here a joint
+ * box), free space C_free (configurations whose robot spheres overlap no
+ * obstacle), start q0 and goal qg.  The layered graph (Sec. III-A): layers
+ * V_0 = {q0}, V_1..V_L of M sampled configurations each, V_{L+1} = {qg}; every
+ * pair of vertices in adjacent layers is a candidate edge.  The local planner
+ * (Sec. III-B; "SEV" of Sec. VI) realises edge (u, v) as the straight segment,
+ * checked at H waypoints t_k = k/(H-1), k = 0..H-1; a realised edge costs its
+ * length ||v - u|| (Sec. IV-A), an unrealised one +inf.  The graph search
+ * (Sec. IV-B, Alg. 1 gtmp) is the backward value iteration
+ *     J_{L+1}(qg) = 0,   J_l(u) = min_v c(u, v) + J_{l+1}(v)
+ * and the path is obtained by following the minimisers from q0.
+ * Anytime-GTMP (Sec. IV-C, Alg. 1 anytime-gtmp) repeats gtmp with fresh
+ * samples; AO-GTMP (Sec. IV-D, Alg. 1 ao-gtmp / expand-samples) grows the
+ * layers with informed and heuristic samples.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every function returns a gtmp_status; nothing throws across the ABI.
+ *    On failure gtmp_last_error(ctx) holds a one-line message.
+ *  - "host" pointers are read during the call and may be freed afterwards.
+ *    "device" pointers are CUDA device memory owned by the caller; they must
+ *    stay valid until the work enqueued by the call has completed.
+ *  - All GPU work is enqueued on the context's stream (asynchronous); results
+ *    in device buffers are valid after that stream has been synchronised
+ *    (gtmp_synchronize does that and reports device-side error flags).
+ *  - Floating-point data are IEEE float32, indices int32, row-major.
+ *  - A context is not thread-safe; independent contexts may be used from
+ *    different threads on different streams.
+ *  - An infeasible problem is not an error: the cost is +inf and every path
+ *    index is -1.
+ *  - Precision: samples and waypoint configurations are defined in float32
+ *    (the formulas below, correctly rounded); kinematics, distances, edge
+ *    costs and values are computed in float32.
+ */
+#ifndef GTMP_H
+#define GTMP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GTMP_API __attribute__((visibility("default")))
+#else
+#define GTMP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gtmp_ctx gtmp_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  GTMP_OK = 0,
+  GTMP_ERR_INVALID_ARG = 1, /* argument out of range, NULL, NaN/Inf input; nothing was enqueued */
+  GTMP_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  GTMP_ERR_OOM = 3,         /* device allocation failed */
+  GTMP_ERR_TIMEOUT = 4,     /* a bounded device-side wait or a bounded rejection sampler gave up */
+  GTMP_ERR_UNSUPPORTED = 5, /* valid request this build does not implement */
+  GTMP_ERR_NOT_READY = 6    /* a required earlier call is missing (e.g. solve before endpoints) */
+} gtmp_status;
+
+enum { GTMP_ROBOT_POINT = 0, GTMP_ROBOT_DH_ARM = 1 };
+
+/* Edge evaluation mode of the fused solver.  Both give the same result.
+ * EARLY_EXIT leaves an edge at its first colliding link and skips edges that
+ * cannot lie on a finite chain; FULL evaluates every interior waypoint of
+ * every candidate edge (data-independent work, used to measure the kernel). */
+enum { GTMP_EVAL_EARLY_EXIT = 0, GTMP_EVAL_FULL = 1 };
+
+/* Robot model (Sec. III: the map from a configuration to the robot's occupied
+ * space that defines C_free).
+ *  kind = GTMP_ROBOT_POINT: the configuration is the position of one sphere of
+ *         radius point_radius (dof 1..3; missing coordinates are 0).
+ *  kind = GTMP_ROBOT_DH_ARM: a serial arm in standard Denavit-Hartenberg form,
+ *         link transform A_i = Rz(q_i + theta_i) Tz(d_i) Tx(a_i) Rx(alpha_i),
+ *         base frame = world frame; link i carries spheres_per_link spheres
+ *         given in the frame of link i (radius > 0).
+ * All pointers are host pointers, copied by gtmp_create. */
+typedef struct {
+  int32_t kind;
+  int32_t dof;                 /* 1..16 */
+  const float* dh;             /* [dof][4]: d, a, alpha, theta_offset (arm; ignored for point) */
+  const float* link_spheres;   /* [dof][spheres_per_link][4]: x, y, z, r (arm) */
+  int32_t spheres_per_link;    /* 1..8 (arm) */
+  const float* q_lo;           /* [dof] joint-box lower bounds */
+  const float* q_hi;           /* [dof] joint-box upper bounds, > q_lo */
+  float point_radius;          /* point robot, >= 0 */
+} gtmp_robot;
+
+typedef struct {
+  int32_t M;            /* capacity: samples per layer (1..16384) */
+  int32_t L;            /* sample layers (1..64) */
+  int32_t H;            /* waypoints per edge including both endpoints (2..1024) */
+  int32_t R;            /* capacity: graphs solved together by gtmp_anytime (1..4096) */
+  int32_t max_obstacles;/* capacity: spheres + boxes accepted by gtmp_set_obstacles (0..4096) */
+  int32_t eval_mode;    /* GTMP_EVAL_EARLY_EXIT or GTMP_EVAL_FULL */
+  float max_edge_len;   /* edge-length limit l of Sec. III-B/IV-A; +INFINITY = none */
+} gtmp_params;
+
+/* Create a context on the current CUDA device; allocates all per-graph device
+ * memory for the given capacities.  cuda_stream is a cudaStream_t (NULL = the
+ * legacy default stream).  Source: problem statement of Sec. III. */
+GTMP_API gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void* cuda_stream, gtmp_ctx** out);
+
+/* Free a context (synchronises its stream first).  NULL is accepted. */
+GTMP_API gtmp_status gtmp_destroy(gtmp_ctx* ctx);
+
+/* Last error message of this context ("" if none); valid until the next call. */
+GTMP_API const char* gtmp_last_error(const gtmp_ctx* ctx);
+
+/* Short name of a status code. */
+GTMP_API const char* gtmp_status_string(gtmp_status s);
+
+/* Change the stream later calls enqueue on. */
+GTMP_API gtmp_status gtmp_set_stream(gtmp_ctx* ctx, void* cuda_stream);
+
+/* Wait for the context's stream; returns GTMP_ERR_TIMEOUT if a kernel raised
+ * a device-side error flag since the last call (the flag is then cleared). */
+GTMP_API gtmp_status gtmp_synchronize(gtmp_ctx* ctx);
+
+/* Obstacle region C_coll of Sec. III: spheres host [n_s][4] (centre x, y, z,
+ * radius) and axis-aligned boxes host [n_b][6] (lo x, y, z, hi x, y, z).
+ * Copied (the call returns after the copy).  n_s + n_b <= max_obstacles. */
+GTMP_API gtmp_status gtmp_set_obstacles(gtmp_ctx* ctx, const float* spheres, int32_t n_s, const float* boxes, int32_t n_b);
+
+/* Start q0 and goal qg (host [dof] each, inside the joint box).  Sec. III. */
+GTMP_API gtmp_status gtmp_set_endpoints(gtmp_ctx* ctx, const float* q_start, const float* q_goal);
+
+/* Alg. 1 "uniformly sample Q": M samples per layer (M <= capacity) for graph 0.
+ * Q[l][i][k] = fma(u, hi_k - lo_k, lo_k) in float32 with u = (w >> 8) * 2^-24,
+ * w = word k&3 of Philox4x32-10(counter = (i, l, restart, 1<<24 | k>>2),
+ * key = (seed lo 32 bits, seed hi 32 bits)), restart = 0 here; l is the
+ * 0-based sample layer.  Asynchronous. */
+GTMP_API gtmp_status gtmp_sample_layers(gtmp_ctx* ctx, uint64_t seed, int32_t M);
+
+/* Alg. 1 optional input Q: device [L][M][dof] float32 samples for graph 0. */
+GTMP_API gtmp_status gtmp_set_layers(gtmp_ctx* ctx, const float* dev_Q, int32_t M);
+
+/* Copy graph 0's current samples to device [L][M][dof]. */
+GTMP_API gtmp_status gtmp_get_layers(gtmp_ctx* ctx, float* dev_Q);
+
+/* Exact configuration checker (membership in C_coll, Sec. III): dev_q device
+ * [n][dof] float32 in, dev_labels device [n] uint8 out, 1 = in collision. */
+GTMP_API gtmp_status gtmp_label_configs(gtmp_ctx* ctx, const float* dev_q, int32_t n, uint8_t* dev_labels);
+
+/* gtmp of Alg. 1 on graph 0 with the fused edge + min-plus kernels (the edge
+ * costs C_l are never stored).  dev_path device [L] int32: index of the chosen
+ * vertex in each sample layer 1..L (-1 if infeasible); dev_cost device [1]
+ * float32: J_0(q0) (+inf if infeasible).  Ties in the minimisation are broken
+ * towards the smallest vertex index among exactly equal float32 values.
+ * Requires endpoints and samples.  Asynchronous. */
+GTMP_API gtmp_status gtmp_solve(gtmp_ctx* ctx, int32_t* dev_path, float* dev_cost);
+
+/* Values and minimisers of the last solve of graph g: dev_V device
+ * [L+2][M] float32 (row l = layer l; rows 0 and L+1 use column 0 only, other
+ * columns +inf), dev_sigma device [L+2][M] int32 (minimiser in layer l+1, -1
+ * if none or for the goal). */
+GTMP_API gtmp_status gtmp_get_values(gtmp_ctx* ctx, int32_t g, float* dev_V, int32_t* dev_sigma);
+
+/* Unfused variant of gtmp_solve (same result): step 1 writes every edge cost
+ * matrix C_l (float32, +inf = absent) into library-owned device memory,
+ * step 2 runs the min-plus sweep reading it back.  The first call allocates
+ * (2M + (L-1)M^2) floats (rows padded to a multiple of 4). */
+GTMP_API gtmp_status gtmp_solve_unfused(gtmp_ctx* ctx, int32_t* dev_path, float* dev_cost);
+
+/* Edge costs of one transition l -> l+1 (l = 0..L) of graph 0 as computed by
+ * the unfused step 1: dev_C device [n_l][n_{l+1}] float32, +inf = absent.
+ * Requires a previous gtmp_solve_unfused. */
+GTMP_API gtmp_status gtmp_get_edge_costs(gtmp_ctx* ctx, int32_t l, float* dev_C);
+
+/* anytime-gtmp of Alg. 1 (single class): `restarts` independent graphs
+ * (restart r uses Philox restart word r of gtmp_sample_layers' rule) solved
+ * in one batch of launches.  dev_paths device [restarts][L], dev_costs device
+ * [restarts], dev_best device [1] (restart with the lowest cost, first index
+ * on ties, -1 if all infeasible).  restarts <= R. */
+GTMP_API gtmp_status gtmp_anytime(gtmp_ctx* ctx, uint64_t seed, int32_t restarts, int32_t* dev_paths, float* dev_costs,
+                         int32_t* dev_best);
+
+/* One AO-GTMP stage (Alg. 1 ao-gtmp with expand-samples, Sec. IV-D) on
+ * graph 0: top every layer up from the current M to M_new samples, then
+ * solve; if the new cost is below *dev_best_cost, copy the path and cost into
+ * dev_best_path / dev_best_cost.  The informed set uses c_best = *dev_best_cost
+ * read on the device, so a sequence of stages needs no host round trip.
+ * New slot i of 0-based layer l:
+ *   c_best = +inf -> the uniform rule of gtmp_sample_layers (restart 0);
+ *   else coin = bit 0 of word 0 of Philox(i, l, 0, 3<<24); if heads, or the
+ *   graph had no samples yet: uniform in X_f(c_best) ∩ joint box, drawn by
+ *   rejection (attempt a: z_k = 2u - 1 from Philox(i, l, a, 2<<24 | k>>2),
+ *   accept if sum z_k^2 <= 1 and x = centre + r2 z + (r1 - r2)(a.z) a lies
+ *   in the box; at most 65536 attempts, else GTMP_ERR_TIMEOUT at the next
+ *   gtmp_synchronize); tails: midpoint of layer l-1 sample (word 1 mod M_old)
+ *   and its nearest layer l+1 sample.  Only samples present on entry are used.
+ * dev_stage_path device [L] and dev_stage_cost device [1] receive this
+ * stage's own solution. */
+GTMP_API gtmp_status aogtmp_expand(gtmp_ctx* ctx, uint64_t seed, int32_t M_new, int32_t* dev_stage_path,
+                          float* dev_stage_cost, int32_t* dev_best_path, float* dev_best_cost);
+
+/* Launch accounting and kernel timing (library instrumentation; the paper
+ * reports no such facility).  Every kernel the context enqueues increments
+ * `launches`.  While timing is enabled, CUDA events bracket each fused
+ * edge + min-plus launch on the context's stream; gtmp_profile_read
+ * synchronises the stream, sums those launches' durations and resets the
+ * counters.  The events add two event records per fused launch. */
+typedef struct {
+  int64_t launches;        /* kernels enqueued since the last read */
+  int64_t fused_launches;  /* fused edge + min-plus launches timed */
+  double fused_ms;         /* their summed device time (ms) */
+  double fused_edges;      /* candidate edges those launches processed */
+} gtmp_profile;
+
+GTMP_API gtmp_status gtmp_profile_enable(gtmp_ctx* ctx, int32_t enable);
+GTMP_API gtmp_status gtmp_profile_read(gtmp_ctx* ctx, gtmp_profile* out);
+
+/* Active samples per layer of graph 0 (after sample/set/expand). */
+GTMP_API gtmp_status gtmp_get_M(const gtmp_ctx* ctx, int32_t* M);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GTMP_H */

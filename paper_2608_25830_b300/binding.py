@@ -1,0 +1,327 @@
+"""Python binding of the C ABI in include/gtmp.h (argument marshalling only).
+
+Every function here forwards to the function of the same name in libgtmp.so:
+host arrays are passed as numpy float32 pointers, device buffers as the data
+pointers of CUDA torch tensors, and the stream as the current torch stream.
+No planning arithmetic happens in Python; if the shared library has not been
+built, importing the binding's loader raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import scenes
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libgtmp.so")
+
+GTMP_OK = 0
+STATUS = {0: "GTMP_OK", 1: "GTMP_ERR_INVALID_ARG", 2: "GTMP_ERR_CUDA", 3: "GTMP_ERR_OOM", 4: "GTMP_ERR_TIMEOUT",
+          5: "GTMP_ERR_UNSUPPORTED", 6: "GTMP_ERR_NOT_READY"}
+EVAL_EARLY_EXIT, EVAL_FULL = 0, 1
+ROBOT_POINT, ROBOT_DH_ARM = 0, 1
+
+
+class GtmpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GtmpRobot(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dof", ctypes.c_int32), ("dh", ctypes.POINTER(ctypes.c_float)),
+                ("link_spheres", ctypes.POINTER(ctypes.c_float)), ("spheres_per_link", ctypes.c_int32),
+                ("q_lo", ctypes.POINTER(ctypes.c_float)), ("q_hi", ctypes.POINTER(ctypes.c_float)),
+                ("point_radius", ctypes.c_float)]
+
+
+class GtmpParams(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("L", ctypes.c_int32), ("H", ctypes.c_int32), ("R", ctypes.c_int32),
+                ("max_obstacles", ctypes.c_int32), ("eval_mode", ctypes.c_int32), ("max_edge_len", ctypes.c_float)]
+
+
+class GtmpProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("fused_launches", ctypes.c_int64), ("fused_ms", ctypes.c_double),
+                ("fused_edges", ctypes.c_double)]
+
+
+_lib = None
+_vp, _i32, _u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+_fp = ctypes.POINTER(ctypes.c_float)
+
+_SIGNATURES = {
+    "gtmp_create": [ctypes.POINTER(GtmpRobot), ctypes.POINTER(GtmpParams), _vp, ctypes.POINTER(_vp)],
+    "gtmp_destroy": [_vp],
+    "gtmp_set_stream": [_vp, _vp],
+    "gtmp_synchronize": [_vp],
+    "gtmp_set_obstacles": [_vp, _fp, _i32, _fp, _i32],
+    "gtmp_set_endpoints": [_vp, _fp, _fp],
+    "gtmp_sample_layers": [_vp, _u64, _i32],
+    "gtmp_set_layers": [_vp, _vp, _i32],
+    "gtmp_get_layers": [_vp, _vp],
+    "gtmp_label_configs": [_vp, _vp, _i32, _vp],
+    "gtmp_solve": [_vp, _vp, _vp],
+    "gtmp_get_values": [_vp, _i32, _vp, _vp],
+    "gtmp_solve_unfused": [_vp, _vp, _vp],
+    "gtmp_get_edge_costs": [_vp, _i32, _vp],
+    "gtmp_anytime": [_vp, _u64, _i32, _vp, _vp, _vp],
+    "aogtmp_expand": [_vp, _u64, _i32, _vp, _vp, _vp, _vp],
+    "gtmp_get_M": [_vp, ctypes.POINTER(_i32)],
+    "gtmp_profile_enable": [_vp, _i32],
+    "gtmp_profile_read": [_vp, ctypes.POINTER(GtmpProfile)],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgtmp.so (built in-tree by paper_2608_25830_b300/build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                               f"g.build()'` (nvcc, sm_103a); there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.gtmp_last_error.argtypes = [_vp]
+        L.gtmp_last_error.restype = ctypes.c_char_p
+        L.gtmp_status_string.argtypes = [ctypes.c_int]
+        L.gtmp_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != GTMP_OK:
+        msg = lib().gtmp_last_error(ctx).decode() if ctx else ""
+        raise GtmpError(status, msg)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_fp)
+
+
+def _dev(t, dtype=None):
+    """Data pointer of a CUDA tensor (checked: device, contiguity, dtype)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if not t.is_contiguous():
+        raise ValueError("device buffer must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# the C calls, one by one
+# ---------------------------------------------------------------------------
+
+def robot_struct(robot: scenes.Robot):
+    keep = dict(dh=_f32(robot.dh).reshape(-1), sph=_f32(robot.link_spheres).reshape(-1) if robot.link_spheres.size
+                else np.zeros(4, np.float32), lo=_f32(robot.q_lo), hi=_f32(robot.q_hi))
+    s = GtmpRobot(robot.kind, robot.dof, _ptr(keep["dh"]), _ptr(keep["sph"]),
+                  robot.spheres_per_link if robot.kind == ROBOT_DH_ARM else 0,
+                  _ptr(keep["lo"]), _ptr(keep["hi"]), float(robot.point_radius))
+    return s, keep
+
+
+def gtmp_create(robot: scenes.Robot, M, L, H, R=1, max_obstacles=64, eval_mode=EVAL_EARLY_EXIT,
+                max_edge_len=math.inf, stream=None):
+    rs, keep = robot_struct(robot)
+    ps = GtmpParams(M, L, H, R, max_obstacles, eval_mode, max_edge_len)
+    out = _vp()
+    st = stream if stream is not None else _stream()
+    status = lib().gtmp_create(ctypes.byref(rs), ctypes.byref(ps), st, ctypes.byref(out))
+    if status != GTMP_OK:
+        raise GtmpError(status, "gtmp_create rejected its arguments or the device")
+    return out
+
+
+def gtmp_destroy(ctx):
+    _check(None, lib().gtmp_destroy(ctx))
+
+
+def gtmp_set_stream(ctx, stream=None):
+    _check(ctx, lib().gtmp_set_stream(ctx, stream if stream is not None else _stream()))
+
+
+def gtmp_synchronize(ctx):
+    _check(ctx, lib().gtmp_synchronize(ctx))
+
+
+def gtmp_set_obstacles(ctx, spheres, boxes):
+    s = _f32(spheres).reshape(-1, 4)
+    b = _f32(boxes).reshape(-1, 6)
+    _check(ctx, lib().gtmp_set_obstacles(ctx, _ptr(s), s.shape[0], _ptr(b), b.shape[0]))
+
+
+def gtmp_set_endpoints(ctx, q_start, q_goal):
+    a, b = _f32(q_start), _f32(q_goal)
+    _check(ctx, lib().gtmp_set_endpoints(ctx, _ptr(a), _ptr(b)))
+
+
+def gtmp_sample_layers(ctx, seed, M):
+    _check(ctx, lib().gtmp_sample_layers(ctx, seed, M))
+
+
+def gtmp_set_layers(ctx, dev_Q, M):
+    import torch
+    _check(ctx, lib().gtmp_set_layers(ctx, _dev(dev_Q, torch.float32), M))
+
+
+def gtmp_get_layers(ctx, dev_Q):
+    import torch
+    _check(ctx, lib().gtmp_get_layers(ctx, _dev(dev_Q, torch.float32)))
+
+
+def gtmp_label_configs(ctx, dev_q, dev_labels):
+    import torch
+    n = dev_q.shape[0]
+    _check(ctx, lib().gtmp_label_configs(ctx, _dev(dev_q, torch.float32), n, _dev(dev_labels, torch.uint8)))
+
+
+def gtmp_solve(ctx, dev_path, dev_cost):
+    import torch
+    _check(ctx, lib().gtmp_solve(ctx, _dev(dev_path, torch.int32), _dev(dev_cost, torch.float32)))
+
+
+def gtmp_get_values(ctx, g, dev_V, dev_sigma):
+    import torch
+    _check(ctx, lib().gtmp_get_values(ctx, g, _dev(dev_V, torch.float32), _dev(dev_sigma, torch.int32)))
+
+
+def gtmp_solve_unfused(ctx, dev_path, dev_cost):
+    import torch
+    _check(ctx, lib().gtmp_solve_unfused(ctx, _dev(dev_path, torch.int32), _dev(dev_cost, torch.float32)))
+
+
+def gtmp_get_edge_costs(ctx, l, dev_C):
+    import torch
+    _check(ctx, lib().gtmp_get_edge_costs(ctx, l, _dev(dev_C, torch.float32)))
+
+
+def gtmp_anytime(ctx, seed, restarts, dev_paths, dev_costs, dev_best):
+    import torch
+    _check(ctx, lib().gtmp_anytime(ctx, seed, restarts, _dev(dev_paths, torch.int32), _dev(dev_costs, torch.float32),
+                                   _dev(dev_best, torch.int32)))
+
+
+def aogtmp_expand(ctx, seed, M_new, dev_stage_path, dev_stage_cost, dev_best_path, dev_best_cost):
+    import torch
+    _check(ctx, lib().aogtmp_expand(ctx, seed, M_new, _dev(dev_stage_path, torch.int32),
+                                    _dev(dev_stage_cost, torch.float32), _dev(dev_best_path, torch.int32),
+                                    _dev(dev_best_cost, torch.float32)))
+
+
+def gtmp_profile_enable(ctx, enable=True):
+    _check(ctx, lib().gtmp_profile_enable(ctx, 1 if enable else 0))
+
+
+def gtmp_profile_read(ctx):
+    out = GtmpProfile()
+    _check(ctx, lib().gtmp_profile_read(ctx, ctypes.byref(out)))
+    return dict(launches=out.launches, fused_launches=out.fused_launches, fused_ms=out.fused_ms,
+                fused_edges=out.fused_edges)
+
+
+def gtmp_get_M(ctx):
+    m = _i32()
+    _check(ctx, lib().gtmp_get_M(ctx, ctypes.byref(m)))
+    return m.value
+
+
+# ---------------------------------------------------------------------------
+# A small object wrapper over the same calls
+# ---------------------------------------------------------------------------
+
+class Planner:
+    """One planning context (robot, capacities, obstacles, endpoints, layers)."""
+
+    def __init__(self, robot: scenes.Robot, M, L, H, R=1, max_obstacles=64, eval_mode=EVAL_EARLY_EXIT,
+                 max_edge_len=math.inf):
+        import torch
+        self.robot, self.M, self.L, self.H, self.R = robot, M, L, H, R
+        self.dev = torch.device("cuda")
+        self.ctx = gtmp_create(robot, M, L, H, R, max_obstacles, eval_mode, max_edge_len)
+
+    def close(self):
+        if self.ctx:
+            gtmp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_scene(self, scene: scenes.Scene):
+        gtmp_set_obstacles(self.ctx, scene.spheres, scene.boxes)
+        gtmp_set_endpoints(self.ctx, scene.q_start, scene.q_goal)
+
+    def sample_layers(self, seed, M=None):
+        gtmp_sample_layers(self.ctx, seed, M or self.M)
+
+    def set_layers(self, Q):
+        gtmp_set_layers(self.ctx, Q, Q.shape[1])
+
+    def get_layers(self):
+        import torch
+        Q = torch.empty((self.L, gtmp_get_M(self.ctx), self.robot.dof), dtype=torch.float32, device=self.dev)
+        gtmp_get_layers(self.ctx, Q)
+        return Q
+
+    def label_configs(self, q):
+        import torch
+        out = torch.empty(q.shape[0], dtype=torch.uint8, device=self.dev)
+        gtmp_label_configs(self.ctx, q.contiguous(), out)
+        return out
+
+    def solve(self, unfused=False):
+        import torch
+        path = torch.empty(self.L, dtype=torch.int32, device=self.dev)
+        cost = torch.empty(1, dtype=torch.float32, device=self.dev)
+        (gtmp_solve_unfused if unfused else gtmp_solve)(self.ctx, path, cost)
+        return path, cost
+
+    def values(self, g=0):
+        import torch
+        V = torch.empty((self.L + 2, gtmp_get_M(self.ctx)), dtype=torch.float32, device=self.dev)
+        S = torch.empty_like(V, dtype=torch.int32)
+        gtmp_get_values(self.ctx, g, V, S)
+        return V, S
+
+    def edge_costs(self, l):
+        import torch
+        m = gtmp_get_M(self.ctx)
+        rows = 1 if l == 0 else m
+        cols = 1 if l == self.L else m
+        C = torch.empty((rows, cols), dtype=torch.float32, device=self.dev)
+        gtmp_get_edge_costs(self.ctx, l, C)
+        return C
+
+    def anytime(self, seed, restarts):
+        import torch
+        paths = torch.empty((restarts, self.L), dtype=torch.int32, device=self.dev)
+        costs = torch.empty(restarts, dtype=torch.float32, device=self.dev)
+        best = torch.empty(1, dtype=torch.int32, device=self.dev)
+        gtmp_anytime(self.ctx, seed, restarts, paths, costs, best)
+        return paths, costs, best
+
+    def synchronize(self):
+        gtmp_synchronize(self.ctx)

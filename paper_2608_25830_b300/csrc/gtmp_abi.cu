@@ -1,0 +1,589 @@
+// C ABI of the layered-graph planner: argument checking, context memory, and
+// the launch sequences of gtmp / anytime-gtmp / ao-gtmp (Alg. 1).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gtmp.h"
+#include "gtmp_kernels.cuh"
+
+using namespace gtmp;
+
+struct gtmp_ctx {
+  int device = 0;
+  int num_sms = 148;
+  cudaStream_t stream = nullptr;
+  gtmp_params p{};
+  RobotDev rb{};
+  int variant = kVarArmGeneric;
+  int dof = 0, dp = 0;
+  float q_lo[kMaxDof] = {}, q_hi[kMaxDof] = {};
+  // device memory
+  float* Q = nullptr;
+  uint8_t* vflag = nullptr;
+  unsigned long long* keys = nullptr;
+  int* counters = nullptr;
+  int n_counters = 0;
+  float4* obs = nullptr;
+  int n_s = 0, n_b = 0;
+  int* err = nullptr;
+  float* C = nullptr;
+  std::vector<size_t> c_off;
+  std::vector<int> c_cs;
+  // state
+  bool have_endpoints = false;
+  int M_active = 0;
+  int fused_bps[2] = {1, 1};
+  std::string last_error;
+  // instrumentation
+  long long launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;  // (start, end) indices into ev_pool
+  double timed_edges = 0.0;
+};
+
+namespace {
+
+gtmp_status fail(gtmp_ctx* c, gtmp_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->last_error = buf;
+  }
+  return s;
+}
+
+#define CUDA_TRY(ctx, expr)                                                                              \
+  do {                                                                                                   \
+    cudaError_t e_ = (expr);                                                                             \
+    if (e_ != cudaSuccess)                                                                               \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? GTMP_ERR_OOM : GTMP_ERR_CUDA, "%s: %s", #expr, \
+                  cudaGetErrorString(e_));                                                               \
+  } while (0)
+
+bool finite_all(const float* v, size_t n) {
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(v[k])) return false;
+  return true;
+}
+
+GraphDev graph(gtmp_ctx* c, int R, int M) {
+  GraphDev g;
+  g.Q = c->Q;
+  g.vflag = c->vflag;
+  g.keys = c->keys;
+  g.R = R;
+  g.L = c->p.L;
+  g.M = M;
+  g.dp = c->dp;
+  g.H = c->p.H;
+  g.M_stride = c->p.M;
+  g.max_edge_len = c->p.max_edge_len;
+  return g;
+}
+
+SceneDev scene(gtmp_ctx* c) { return SceneDev{c->obs, c->n_s, c->n_b}; }
+
+// layer sizes and chunking of one transition
+void transition_shape(const GraphDev& g, int layer, int* rows, int* cols) {
+  *rows = layer_size(g, layer);
+  *cols = layer_size(g, layer + 1);
+}
+
+// count one enqueued kernel
+#define LAUNCHED(ctx, n) ((ctx)->launches += (n))
+
+cudaError_t event_at(gtmp_ctx* c, size_t slot, cudaEvent_t* out) {
+  while (c->ev_pool.size() <= slot) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    c->ev_pool.push_back(e);
+  }
+  *out = c->ev_pool[slot];
+  return cudaSuccess;
+}
+
+gtmp_status run_fused(gtmp_ctx* c, const GraphDev& g, int mode) {
+  const int bps = c->fused_bps[mode == GTMP_EVAL_FULL ? 1 : 0];
+  const int resident = c->num_sms * bps;
+  CUDA_TRY(c, launch_init_keys(g, c->counters, (g.L + 1) * g.R, c->stream));
+  CUDA_TRY(c, launch_vertex_labels(g, c->rb, c->variant, scene(c), c->stream));
+  LAUNCHED(c, 2);
+  for (int layer = g.L; layer >= 0; --layer) {
+    int rows, cols;
+    transition_shape(g, layer, &rows, &cols);
+    const long long edges = static_cast<long long>(rows) * cols;
+    int grid_x = resident / g.R;
+    if (grid_x < 1) grid_x = 1;
+    const long long warps = static_cast<long long>(grid_x) * 8;
+    long long chunk = edges / (warps * 8);
+    if (chunk < 1) chunk = 1;
+    if (chunk > 32) chunk = 32;
+    if (chunk > cols) chunk = cols;
+    const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
+    const long long useful_blocks = (n_chunks + 7) / 8;
+    if (grid_x > useful_blocks) grid_x = static_cast<int>(useful_blocks);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+      const size_t slot = c->ev_used.size() * 2;
+      CUDA_TRY(c, event_at(c, slot, &e0));
+      CUDA_TRY(c, event_at(c, slot + 1, &e1));
+      CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+    }
+    CUDA_TRY(c, launch_fused_transition(g, layer, c->rb, c->variant, scene(c), mode, c->counters + layer * g.R,
+                                        grid_x, static_cast<int>(chunk), c->err, c->stream));
+    LAUNCHED(c, 1);
+    if (c->timing) {
+      CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+      const size_t slot = c->ev_used.size() * 2;
+      c->ev_used.emplace_back(static_cast<int>(slot), static_cast<int>(slot + 1));
+      c->timed_edges += static_cast<double>(edges) * g.R;
+    }
+  }
+  return GTMP_OK;
+}
+
+gtmp_status check_ready(gtmp_ctx* c) {
+  if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "endpoints not set (gtmp_set_endpoints)");
+  if (c->M_active < 1) return fail(c, GTMP_ERR_NOT_READY, "no samples (gtmp_sample_layers / gtmp_set_layers)");
+  return GTMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gtmp_status_string(gtmp_status s) {
+  switch (s) {
+    case GTMP_OK: return "GTMP_OK";
+    case GTMP_ERR_INVALID_ARG: return "GTMP_ERR_INVALID_ARG";
+    case GTMP_ERR_CUDA: return "GTMP_ERR_CUDA";
+    case GTMP_ERR_OOM: return "GTMP_ERR_OOM";
+    case GTMP_ERR_TIMEOUT: return "GTMP_ERR_TIMEOUT";
+    case GTMP_ERR_UNSUPPORTED: return "GTMP_ERR_UNSUPPORTED";
+    case GTMP_ERR_NOT_READY: return "GTMP_ERR_NOT_READY";
+  }
+  return "GTMP_ERR_UNKNOWN";
+}
+
+const char* gtmp_last_error(const gtmp_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void* cuda_stream, gtmp_ctx** out) {
+  if (!out || !robot || !params) return GTMP_ERR_INVALID_ARG;
+  *out = nullptr;
+  // --- validate everything before touching the GPU
+  const gtmp_params& p = *params;
+  if (robot->kind != GTMP_ROBOT_POINT && robot->kind != GTMP_ROBOT_DH_ARM) return GTMP_ERR_INVALID_ARG;
+  if (robot->dof < 1 || robot->dof > kMaxDof) return GTMP_ERR_INVALID_ARG;
+  if (robot->kind == GTMP_ROBOT_POINT && robot->dof > 3) return GTMP_ERR_INVALID_ARG;
+  if (!robot->q_lo || !robot->q_hi) return GTMP_ERR_INVALID_ARG;
+  if (!finite_all(robot->q_lo, robot->dof) || !finite_all(robot->q_hi, robot->dof)) return GTMP_ERR_INVALID_ARG;
+  for (int k = 0; k < robot->dof; ++k)
+    if (!(robot->q_hi[k] > robot->q_lo[k])) return GTMP_ERR_INVALID_ARG;
+  if (robot->kind == GTMP_ROBOT_DH_ARM) {
+    if (!robot->dh || !robot->link_spheres) return GTMP_ERR_INVALID_ARG;
+    if (robot->spheres_per_link < 1 || robot->spheres_per_link > kMaxSpl) return GTMP_ERR_INVALID_ARG;
+    if (!finite_all(robot->dh, static_cast<size_t>(robot->dof) * 4)) return GTMP_ERR_INVALID_ARG;
+    const size_t ns = static_cast<size_t>(robot->dof) * robot->spheres_per_link;
+    if (!finite_all(robot->link_spheres, ns * 4)) return GTMP_ERR_INVALID_ARG;
+    for (size_t s = 0; s < ns; ++s)
+      if (!(robot->link_spheres[s * 4 + 3] > 0.0f)) return GTMP_ERR_INVALID_ARG;
+  } else if (!(robot->point_radius >= 0.0f) || !std::isfinite(robot->point_radius)) {
+    return GTMP_ERR_INVALID_ARG;
+  }
+  if (p.M < 1 || p.M > 16384 || p.L < 1 || p.L > 64 || p.H < 2 || p.H > 1024 || p.R < 1 || p.R > 4096 ||
+      p.max_obstacles < 0 || p.max_obstacles > 4096 ||
+      (p.eval_mode != GTMP_EVAL_EARLY_EXIT && p.eval_mode != GTMP_EVAL_FULL) || std::isnan(p.max_edge_len) ||
+      !(p.max_edge_len > 0.0f))
+    return GTMP_ERR_INVALID_ARG;
+  const size_t graph_vertices = static_cast<size_t>(p.R) * (p.L + 2) * p.M;
+  if (graph_vertices > (size_t(1) << 31)) return GTMP_ERR_INVALID_ARG;
+
+  gtmp_ctx* c = new gtmp_ctx();
+  c->p = p;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->dof = robot->dof;
+  // --- robot constants
+  RobotDev& rb = c->rb;
+  rb.kind = robot->kind;
+  rb.dof = robot->dof;
+  rb.point_radius = robot->point_radius;
+  for (int k = 0; k < robot->dof; ++k) {
+    c->q_lo[k] = robot->q_lo[k];
+    c->q_hi[k] = robot->q_hi[k];
+  }
+  if (robot->kind == GTMP_ROBOT_DH_ARM) {
+    rb.spl = robot->spheres_per_link;
+    bool uniform = true;
+    const float r0 = robot->link_spheres[3];
+    for (int i = 0; i < robot->dof; ++i) {
+      rb.d[i] = robot->dh[i * 4 + 0];
+      rb.a[i] = robot->dh[i * 4 + 1];
+      rb.ca[i] = cosf(robot->dh[i * 4 + 2]);
+      rb.sa[i] = sinf(robot->dh[i * 4 + 2]);
+      rb.toff[i] = robot->dh[i * 4 + 3];
+    }
+    // sphere table laid out [link][stride] with stride = 4 for the 4-sphere
+    // variants and kMaxSpl for the generic one
+    const bool four = robot->spheres_per_link == 4;
+    for (int i = 0; i < robot->dof; ++i)
+      for (int s = 0; s < robot->spheres_per_link; ++s) {
+        const float* ls = robot->link_spheres + (static_cast<size_t>(i) * robot->spheres_per_link + s) * 4;
+        if (ls[3] != r0) uniform = false;
+      }
+    rb.uniform_r = uniform ? 1 : 0;
+    rb.r_uniform = r0;
+    if (uniform && four && robot->dof == 6)
+      c->variant = kVarArm6x4;
+    else if (uniform && four && robot->dof == 7)
+      c->variant = kVarArm7x4;
+    else
+      c->variant = kVarArmGeneric;
+    const int stride = (c->variant == kVarArmGeneric) ? kMaxSpl : 4;
+    for (int i = 0; i < robot->dof; ++i)
+      for (int s = 0; s < robot->spheres_per_link; ++s) {
+        const float* ls = robot->link_spheres + (static_cast<size_t>(i) * robot->spheres_per_link + s) * 4;
+        rb.sph[i * stride + s] = make_float4(ls[0], ls[1], ls[2], ls[3]);
+      }
+    c->dp = 8;
+  } else {
+    rb.spl = 1;
+    rb.uniform_r = 1;
+    rb.r_uniform = robot->point_radius;
+    c->variant = kVarPoint;
+    c->dp = 4;
+  }
+  if (c->variant == kVarArmGeneric) c->dp = kMaxDof;  // generic kernels read kMaxDof padded floats
+  // --- device memory
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
+  };
+  alloc(reinterpret_cast<void**>(&c->Q), graph_vertices * c->dp * sizeof(float));
+  alloc(reinterpret_cast<void**>(&c->vflag), graph_vertices);
+  alloc(reinterpret_cast<void**>(&c->keys), graph_vertices * sizeof(unsigned long long));
+  c->n_counters = (p.L + 1) * p.R;
+  alloc(reinterpret_cast<void**>(&c->counters), static_cast<size_t>(c->n_counters) * sizeof(int));
+  alloc(reinterpret_cast<void**>(&c->obs), static_cast<size_t>(p.max_obstacles) * 2 * sizeof(float4));
+  alloc(reinterpret_cast<void**>(&c->err), sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->Q, 0, graph_vertices * c->dp * sizeof(float), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = configure_kernels(200 * 1024);
+  if (e == cudaSuccess) {
+    c->fused_bps[0] = fused_max_blocks_per_sm(c->variant, GTMP_EVAL_EARLY_EXIT);
+    c->fused_bps[1] = fused_max_blocks_per_sm(c->variant, GTMP_EVAL_FULL);
+    e = cudaStreamSynchronize(c->stream);
+  }
+  if (e != cudaSuccess) {
+    gtmp_status s = e == cudaErrorMemoryAllocation ? GTMP_ERR_OOM : GTMP_ERR_CUDA;
+    gtmp_destroy(c);
+    return s;
+  }
+  *out = c;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_destroy(gtmp_ctx* c) {
+  if (!c) return GTMP_OK;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->Q);
+  cudaFree(c->vflag);
+  cudaFree(c->keys);
+  cudaFree(c->counters);
+  cudaFree(c->obs);
+  cudaFree(c->err);
+  cudaFree(c->C);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_set_stream(gtmp_ctx* c, void* cuda_stream) {
+  if (!c) return GTMP_ERR_INVALID_ARG;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_synchronize(gtmp_ctx* c) {
+  if (!c) return GTMP_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  int err = 0;
+  CUDA_TRY(c, cudaMemcpy(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    CUDA_TRY(c, cudaMemset(c->err, 0, sizeof(int)));
+    return fail(c, GTMP_ERR_TIMEOUT, "device error flags 0x%x (1 = sampler exhausted, 2 = wait timed out)", err);
+  }
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_set_obstacles(gtmp_ctx* c, const float* spheres, int32_t n_s, const float* boxes, int32_t n_b) {
+  if (!c) return GTMP_ERR_INVALID_ARG;
+  if (n_s < 0 || n_b < 0 || n_s + n_b > c->p.max_obstacles)
+    return fail(c, GTMP_ERR_INVALID_ARG, "obstacle count %d + %d exceeds capacity %d", n_s, n_b, c->p.max_obstacles);
+  if ((n_s > 0 && !spheres) || (n_b > 0 && !boxes)) return fail(c, GTMP_ERR_INVALID_ARG, "NULL obstacle array");
+  if ((n_s > 0 && !finite_all(spheres, static_cast<size_t>(n_s) * 4)) ||
+      (n_b > 0 && !finite_all(boxes, static_cast<size_t>(n_b) * 6)))
+    return fail(c, GTMP_ERR_INVALID_ARG, "non-finite obstacle data");
+  std::vector<float4> host(static_cast<size_t>(n_s) + 2 * static_cast<size_t>(n_b));
+  for (int o = 0; o < n_s; ++o) {
+    const float* s = spheres + 4 * o;
+    if (!(s[3] >= 0.0f)) return fail(c, GTMP_ERR_INVALID_ARG, "negative sphere radius");
+    float w = s[3];
+    if (c->rb.uniform_r) {
+      const float rr = s[3] + c->rb.r_uniform;
+      w = rr * rr;  // inflated squared threshold
+    }
+    host[o] = make_float4(s[0], s[1], s[2], w);
+  }
+  for (int o = 0; o < n_b; ++o) {
+    const float* b = boxes + 6 * o;
+    for (int k = 0; k < 3; ++k)
+      if (!(b[3 + k] >= b[k])) return fail(c, GTMP_ERR_INVALID_ARG, "box with hi < lo");
+    const float cx = 0.5f * (b[0] + b[3]), cy = 0.5f * (b[1] + b[4]), cz = 0.5f * (b[2] + b[5]);
+    const float hx = 0.5f * (b[3] - b[0]), hy = 0.5f * (b[4] - b[1]), hz = 0.5f * (b[5] - b[2]);
+    host[n_s + 2 * o] = make_float4(cx, cy, cz, hx);
+    host[n_s + 2 * o + 1] = make_float4(hy, hz, 0.0f, 0.0f);
+  }
+  if (!host.empty())
+    CUDA_TRY(c, cudaMemcpyAsync(c->obs, host.data(), host.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
+  c->n_s = n_s;
+  c->n_b = n_b;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_set_endpoints(gtmp_ctx* c, const float* q_start, const float* q_goal) {
+  if (!c || !q_start || !q_goal) return fail(c, GTMP_ERR_INVALID_ARG, "NULL endpoint");
+  for (int k = 0; k < c->dof; ++k) {
+    if (!std::isfinite(q_start[k]) || !std::isfinite(q_goal[k]))
+      return fail(c, GTMP_ERR_INVALID_ARG, "non-finite endpoint");
+    if (q_start[k] < c->q_lo[k] || q_start[k] > c->q_hi[k] || q_goal[k] < c->q_lo[k] || q_goal[k] > c->q_hi[k])
+      return fail(c, GTMP_ERR_INVALID_ARG, "endpoint outside the joint box (coordinate %d)", k);
+  }
+  std::vector<float> s(static_cast<size_t>(c->p.R) * c->dp, 0.0f), g(s.size(), 0.0f);
+  for (int r = 0; r < c->p.R; ++r)
+    for (int k = 0; k < c->dof; ++k) {
+      s[static_cast<size_t>(r) * c->dp + k] = q_start[k];
+      g[static_cast<size_t>(r) * c->dp + k] = q_goal[k];
+    }
+  const size_t graph_stride = static_cast<size_t>(c->p.L + 2) * c->p.M * c->dp * sizeof(float);
+  const size_t row = c->dp * sizeof(float);
+  for (int which = 0; which < 2; ++which) {
+    const int layer = which == 0 ? 0 : c->p.L + 1;
+    float* dst = c->Q + static_cast<size_t>(layer) * c->p.M * c->dp;
+    CUDA_TRY(c, cudaMemcpy2DAsync(dst, graph_stride, which == 0 ? s.data() : g.data(), row, row, c->p.R,
+                                  cudaMemcpyHostToDevice, c->stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->have_endpoints = true;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_sample_layers(gtmp_ctx* c, uint64_t seed, int32_t M) {
+  if (!c) return GTMP_ERR_INVALID_ARG;
+  if (M < 1 || M > c->p.M) return fail(c, GTMP_ERR_INVALID_ARG, "M=%d outside 1..%d", M, c->p.M);
+  GraphDev g = graph(c, 1, M);
+  CUDA_TRY(c, launch_sample_uniform(g, c->q_lo, c->q_hi, c->dof, seed, 0, c->stream));
+  LAUNCHED(c, 1);
+  c->M_active = M;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_set_layers(gtmp_ctx* c, const float* dev_Q, int32_t M) {
+  if (!c || !dev_Q) return fail(c, GTMP_ERR_INVALID_ARG, "NULL samples");
+  if (M < 1 || M > c->p.M) return fail(c, GTMP_ERR_INVALID_ARG, "M=%d outside 1..%d", M, c->p.M);
+  GraphDev g = graph(c, 1, M);
+  CUDA_TRY(c, launch_pack_layers(g, const_cast<float*>(dev_Q), c->dof, 1, c->stream));
+  LAUNCHED(c, 1);
+  c->M_active = M;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_get_layers(gtmp_ctx* c, float* dev_Q) {
+  if (!c || !dev_Q) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
+  if (c->M_active < 1) return fail(c, GTMP_ERR_NOT_READY, "no samples");
+  GraphDev g = graph(c, 1, c->M_active);
+  CUDA_TRY(c, launch_pack_layers(g, dev_Q, c->dof, 0, c->stream));
+  LAUNCHED(c, 1);
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_profile_enable(gtmp_ctx* c, int32_t enable) {
+  if (!c) return GTMP_ERR_INVALID_ARG;
+  c->timing = enable != 0;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_profile_read(gtmp_ctx* c, gtmp_profile* out) {
+  if (!c || !out) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  double ms = 0.0;
+  for (const auto& pr : c->ev_used) {
+    float t = 0.0f;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev_pool[pr.first], c->ev_pool[pr.second]));
+    ms += t;
+  }
+  out->launches = c->launches;
+  out->fused_launches = static_cast<int64_t>(c->ev_used.size());
+  out->fused_ms = ms;
+  out->fused_edges = c->timed_edges;
+  c->launches = 0;
+  c->ev_used.clear();
+  c->timed_edges = 0.0;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_get_M(const gtmp_ctx* c, int32_t* M) {
+  if (!c || !M) return GTMP_ERR_INVALID_ARG;
+  *M = c->M_active;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_label_configs(gtmp_ctx* c, const float* dev_q, int32_t n, uint8_t* dev_labels) {
+  if (!c || n < 0 || (n > 0 && (!dev_q || !dev_labels))) return fail(c, GTMP_ERR_INVALID_ARG, "bad label request");
+  CUDA_TRY(c, launch_label_configs(dev_q, n, c->dof, c->rb, c->variant, scene(c), dev_labels, c->stream));
+  if (n > 0) LAUNCHED(c, 1);
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_solve(gtmp_ctx* c, int32_t* dev_path, float* dev_cost) {
+  if (!c || !dev_path || !dev_cost) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
+  gtmp_status s = check_ready(c);
+  if (s != GTMP_OK) return s;
+  GraphDev g = graph(c, 1, c->M_active);
+  if ((s = run_fused(c, g, c->p.eval_mode)) != GTMP_OK) return s;
+  CUDA_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, c->stream));
+  LAUNCHED(c, 1);
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_get_values(gtmp_ctx* c, int32_t gi, float* dev_V, int32_t* dev_sigma) {
+  if (!c || !dev_V || !dev_sigma || gi < 0 || gi >= c->p.R) return fail(c, GTMP_ERR_INVALID_ARG, "bad request");
+  GraphDev g = graph(c, 1, c->M_active);
+  // view graph gi as a one-graph batch
+  const size_t off = static_cast<size_t>(gi) * (c->p.L + 2) * c->p.M;
+  g.Q += off * c->dp;
+  g.vflag += off;
+  g.keys += off;
+  CUDA_TRY(c, launch_get_values(g, dev_V, dev_sigma, c->stream));
+  LAUNCHED(c, 1);
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_solve_unfused(gtmp_ctx* c, int32_t* dev_path, float* dev_cost) {
+  if (!c || !dev_path || !dev_cost) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
+  gtmp_status s = check_ready(c);
+  if (s != GTMP_OK) return s;
+  const int L = c->p.L;
+  if (!c->C) {
+    GraphDev cap = graph(c, 1, c->p.M);
+    size_t total = 0;
+    c->c_off.assign(L + 2, 0);
+    c->c_cs.assign(L + 1, 0);
+    for (int layer = 0; layer <= L; ++layer) {
+      int rows, cols;
+      transition_shape(cap, layer, &rows, &cols);
+      c->c_cs[layer] = ((cols + 3) / 4) * 4;
+      c->c_off[layer] = total;
+      total += static_cast<size_t>(rows) * c->c_cs[layer];
+    }
+    c->c_off[L + 1] = total;
+    CUDA_TRY(c, cudaMalloc(&c->C, total * sizeof(float)));
+  }
+  GraphDev g = graph(c, 1, c->M_active);
+  CUDA_TRY(c, launch_init_keys(g, c->counters, (L + 1), c->stream));
+  CUDA_TRY(c, launch_vertex_labels(g, c->rb, c->variant, scene(c), c->stream));
+  LAUNCHED(c, 2);
+  const int resident = c->num_sms * c->fused_bps[0];
+  // step 1: C_L first so that, when the matrices outgrow L2, step 2 reads each from HBM
+  for (int layer = L; layer >= 0; --layer) {
+    int rows, cols;
+    transition_shape(g, layer, &rows, &cols);
+    // the unfused step recomputes its own row stride for the active M
+    const int cs = ((cols + 3) / 4) * 4;
+    c->c_cs[layer] = cs;
+    const long long edges = static_cast<long long>(rows) * cols;
+    long long chunk = edges / (static_cast<long long>(resident) * 64);
+    if (chunk < 1) chunk = 1;
+    if (chunk > 32) chunk = 32;
+    if (chunk > cols) chunk = cols;
+    const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
+    int grid = resident;
+    if (grid > (n_chunks + 7) / 8) grid = static_cast<int>((n_chunks + 7) / 8);
+    CUDA_TRY(c, launch_edge_costs(g, layer, c->rb, c->variant, scene(c), c->C + c->c_off[layer], cs,
+                                  c->counters + layer, grid, static_cast<int>(chunk), c->err, c->stream));
+    LAUNCHED(c, 1);
+  }
+  // step 2: the min-plus sweep over the stored matrices
+  for (int layer = L; layer >= 0; --layer) {
+    int rows, cols;
+    transition_shape(g, layer, &rows, &cols);
+    int grid = (rows + 7) / 8;
+    if (grid > c->num_sms * 8) grid = c->num_sms * 8;
+    CUDA_TRY(c, launch_minplus(g, layer, c->C + c->c_off[layer], c->c_cs[layer], grid, c->stream));
+    LAUNCHED(c, 1);
+  }
+  CUDA_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, c->stream));
+  LAUNCHED(c, 1);
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_get_edge_costs(gtmp_ctx* c, int32_t l, float* dev_C) {
+  if (!c || !dev_C || l < 0 || l > c->p.L) return fail(c, GTMP_ERR_INVALID_ARG, "bad request");
+  if (!c->C) return fail(c, GTMP_ERR_NOT_READY, "no unfused solve yet");
+  GraphDev g = graph(c, 1, c->M_active);
+  int rows, cols;
+  transition_shape(g, l, &rows, &cols);
+  CUDA_TRY(c, cudaMemcpy2DAsync(dev_C, cols * sizeof(float), c->C + c->c_off[l], c->c_cs[l] * sizeof(float),
+                                cols * sizeof(float), rows, cudaMemcpyDeviceToDevice, c->stream));
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_anytime(gtmp_ctx* c, uint64_t seed, int32_t restarts, int32_t* dev_paths, float* dev_costs,
+                         int32_t* dev_best) {
+  if (!c || !dev_paths || !dev_costs || !dev_best) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
+  if (restarts < 1 || restarts > c->p.R)
+    return fail(c, GTMP_ERR_INVALID_ARG, "restarts=%d outside 1..%d", restarts, c->p.R);
+  if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "endpoints not set");
+  GraphDev g = graph(c, restarts, c->p.M);
+  CUDA_TRY(c, launch_sample_uniform(g, c->q_lo, c->q_hi, c->dof, seed, 0, c->stream));
+  LAUNCHED(c, 1);
+  c->M_active = c->p.M;
+  gtmp_status s = run_fused(c, g, c->p.eval_mode);
+  if (s != GTMP_OK) return s;
+  CUDA_TRY(c, launch_extract_paths(g, dev_paths, dev_costs, dev_best, c->stream));
+  LAUNCHED(c, 1);
+  return GTMP_OK;
+}
+
+gtmp_status aogtmp_expand(gtmp_ctx* c, uint64_t seed, int32_t M_new, int32_t* dev_stage_path, float* dev_stage_cost,
+                          int32_t* dev_best_path, float* dev_best_cost) {
+  if (!c || !dev_stage_path || !dev_stage_cost || !dev_best_path || !dev_best_cost)
+    return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
+  if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "endpoints not set");
+  const int M_old = c->M_active;
+  if (M_new < M_old || M_new < 1 || M_new > c->p.M)
+    return fail(c, GTMP_ERR_INVALID_ARG, "M_new=%d outside %d..%d", M_new, M_old, c->p.M);
+  GraphDev g = graph(c, 1, M_new);
+  CUDA_TRY(c, launch_expand(g, c->dof, c->q_lo, c->q_hi, seed, M_old, M_new, dev_best_cost, 1 << 16, c->err,
+                            c->stream));
+  if (M_new > M_old) LAUNCHED(c, 1);
+  c->M_active = M_new;
+  gtmp_status s = run_fused(c, g, c->p.eval_mode);
+  if (s != GTMP_OK) return s;
+  CUDA_TRY(c, launch_extract_paths(g, dev_stage_path, dev_stage_cost, nullptr, c->stream));
+  CUDA_TRY(c, launch_update_best(c->p.L, dev_stage_path, dev_stage_cost, dev_best_path, dev_best_cost, c->stream));
+  LAUNCHED(c, 2);
+  return GTMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+// Device-side building blocks of the layered-graph planner (sm_103a).
+//
+// * Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
+//   sample streams of the planner (Alg. 1 uniform layers; AO-GTMP informed /
+//   heuristic expansion).
+// * Forward kinematics of a DH serial arm into link collision spheres and the
+//   sphere/box obstacle predicate of one configuration (membership in C_free,
+//   Sec. III).
+// * Packed (value, index) keys for the min/argmin of the value iteration
+//   (Sec. IV-B): costs are non-negative floats, so their IEEE bit patterns
+//   order like unsigned integers and a 64-bit unsigned min over
+//   (bits(value) << 32 | index) is the lexicographic (value, first index)
+//   minimum, independent of the order in which candidates arrive.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gtmp {
+
+constexpr int kMaxDof = 16;
+constexpr int kMaxSpl = 8;
+constexpr uint32_t kTagUniform = 1u;
+constexpr uint32_t kTagInformed = 2u;
+constexpr uint32_t kTagCoin = 3u;
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Error bits written to the context's device error word.
+constexpr int kErrSamplerExhausted = 1;
+constexpr int kErrWaitTimeout = 2;
+
+// ----------------------------------------------------------------------------
+// Robot description passed by value (kernel parameter space, i.e. constant
+// bank): with compile-time link and sphere counts every access below is an
+// immediate constant-bank operand.
+// ----------------------------------------------------------------------------
+struct RobotDev {
+  int kind;          // 0 = point robot, 1 = DH serial arm
+  int dof;
+  int spl;           // spheres per link (arm)
+  int uniform_r;     // all robot spheres share radius r_uniform
+  float r_uniform;
+  float point_radius;
+  float d[kMaxDof], a[kMaxDof], ca[kMaxDof], sa[kMaxDof], toff[kMaxDof];
+  float4 sph[kMaxDof * kMaxSpl];  // x, y, z, r in the link frame
+};
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  constexpr uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+  constexpr uint32_t w0 = 0x9E3779B9u, w1 = 0xBB67AE85u;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k.x += w0;
+      k.y += w1;
+    }
+    const uint32_t hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+    const uint32_t hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint2 seed_key(unsigned long long seed) {
+  return make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& w, int k) {
+  switch (k & 3) {
+    case 0: return w.x;
+    case 1: return w.y;
+    case 2: return w.z;
+    default: return w.w;
+  }
+}
+
+// top 24 bits of a Philox word times 2^-24: exact float in [0, 1)
+__device__ __forceinline__ float word_to_unit(uint32_t w) {
+  return __fmul_rn(__uint2float_rn(w >> 8), 5.9604644775390625e-08f);
+}
+
+// ----------------------------------------------------------------------------
+// Packed keys
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long make_key(float value, uint32_t index) {
+  return (static_cast<unsigned long long>(__float_as_uint(value)) << 32) | index;
+}
+__device__ __forceinline__ float key_value(unsigned long long k) {
+  return k == kEmptyKey ? __int_as_float(0x7f800000) : __uint_as_float(static_cast<uint32_t>(k >> 32));
+}
+__device__ __forceinline__ int key_index(unsigned long long k) {
+  return k == kEmptyKey ? -1 : static_cast<int>(static_cast<uint32_t>(k));
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(kFull, v, off);
+    v = o < v ? o : v;
+  }
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// Obstacle predicate for a group of robot spheres.
+//
+// Sphere obstacles live in shared memory as float4 (cx, cy, cz, w):
+//   uniform robot radius r:  w = (r_obs + r)^2   (inflated squared threshold)
+//   otherwise:               w = r_obs
+// Boxes as two float4: (cx, cy, cz, hx), (hy, hz, -, -) (centre, half extents).
+// A robot sphere (c, r) collides with a sphere obstacle iff |c - o|^2 < (r+r_o)^2,
+// with a box iff the squared distance from c to the box is below r^2, or c is
+// strictly inside the box (only decisive for a zero-radius point robot).
+// ----------------------------------------------------------------------------
+template <int NS, bool UNIF, bool INSIDE_TEST>
+__device__ __forceinline__ bool spheres_hit(const float (&cx)[NS], const float (&cy)[NS], const float (&cz)[NS],
+                                            const float (&rad)[NS], int ns_active,
+                                            const float4* __restrict__ sph, int n_s,
+                                            const float4* __restrict__ box, int n_b, float r2_box_uniform) {
+  bool hit = false;
+#pragma unroll 2
+  for (int o = 0; o < n_s; ++o) {
+    const float4 ob = sph[o];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (NS > 1 && k >= ns_active) break;
+      const float dx = __fsub_rn(cx[k], ob.x);
+      const float dy = __fsub_rn(cy[k], ob.y);
+      const float dz = __fsub_rn(cz[k], ob.z);
+      const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+      float thr;
+      if (UNIF) {
+        thr = ob.w;
+      } else {
+        const float rs = __fadd_rn(rad[k], ob.w);
+        thr = __fmul_rn(rs, rs);
+      }
+      hit |= d2 < thr;
+    }
+  }
+#pragma unroll 1
+  for (int o = 0; o < n_b; ++o) {
+    const float4 b0 = box[2 * o];
+    const float4 b1 = box[2 * o + 1];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (NS > 1 && k >= ns_active) break;
+      const float ex = __fsub_rn(fabsf(__fsub_rn(cx[k], b0.x)), b0.w);
+      const float ey = __fsub_rn(fabsf(__fsub_rn(cy[k], b0.y)), b1.x);
+      const float ez = __fsub_rn(fabsf(__fsub_rn(cz[k], b0.z)), b1.y);
+      const float px = fmaxf(ex, 0.0f), py = fmaxf(ey, 0.0f), pz = fmaxf(ez, 0.0f);
+      const float d2 = __fmaf_rn(pz, pz, __fmaf_rn(py, py, __fmul_rn(px, px)));
+      const float r2 = UNIF ? r2_box_uniform : __fmul_rn(rad[k], rad[k]);
+      hit |= d2 < r2;
+      if (INSIDE_TEST) hit |= fmaxf(ex, fmaxf(ey, ez)) < 0.0f;
+    }
+  }
+  return hit;
+}
+
+// ----------------------------------------------------------------------------
+// One configuration against the scene.
+//
+// WARP_EXIT: the caller is a whole warp evaluating waypoints of the same
+// edge; after each link the warp stops as soon as any active lane has found a
+// collision (early exit).  Otherwise each thread stops at its own first hit.
+// FULL: no early exit at all (data-independent work), result unchanged.
+// Returns, for WARP_EXIT, the warp-uniform "some active lane collides"; else
+// the lane's own label.
+// ----------------------------------------------------------------------------
+template <int DOF_T, int SPL_T, bool UNIF, bool WARP_EXIT, bool FULL>
+__device__ __forceinline__ bool arm_config_collides(const float* q, bool active, const RobotDev& rb,
+                                                    const float4* __restrict__ sph, int n_s,
+                                                    const float4* __restrict__ box, int n_b) {
+  constexpr int NS = SPL_T > 0 ? SPL_T : kMaxSpl;
+  const int dof = DOF_T > 0 ? DOF_T : rb.dof;
+  const int spl = SPL_T > 0 ? SPL_T : rb.spl;
+  const float r2u = __fmul_rn(rb.r_uniform, rb.r_uniform);
+  // running frame of link i: rotation columns X, Y, Z and origin T
+  float X0 = 1.f, X1 = 0.f, X2 = 0.f, Y0 = 0.f, Y1 = 1.f, Y2 = 0.f, Z0 = 0.f, Z1 = 0.f, Z2 = 1.f;
+  float T0 = 0.f, T1 = 0.f, T2 = 0.f;
+  bool hit = false;
+#pragma unroll
+  for (int i = 0; i < (DOF_T > 0 ? DOF_T : kMaxDof); ++i) {
+    if (DOF_T == 0 && i >= dof) break;
+    float s, c;
+    sincosf(__fadd_rn(q[i], rb.toff[i]), &s, &c);
+    // A_i = Rz(theta) Tz(d) Tx(a) Rx(alpha): new x axis u = c X + s Y,
+    // v = -s X + c Y, new y = ca v + sa Z, new z = -sa v + ca Z,
+    // new origin = T + a u + d Z.
+    const float u0 = __fmaf_rn(s, Y0, __fmul_rn(c, X0));
+    const float u1 = __fmaf_rn(s, Y1, __fmul_rn(c, X1));
+    const float u2 = __fmaf_rn(s, Y2, __fmul_rn(c, X2));
+    const float v0 = __fmaf_rn(c, Y0, __fmul_rn(-s, X0));
+    const float v1 = __fmaf_rn(c, Y1, __fmul_rn(-s, X1));
+    const float v2 = __fmaf_rn(c, Y2, __fmul_rn(-s, X2));
+    const float ca = rb.ca[i], sa = rb.sa[i];
+    T0 = __fmaf_rn(rb.d[i], Z0, __fmaf_rn(rb.a[i], u0, T0));
+    T1 = __fmaf_rn(rb.d[i], Z1, __fmaf_rn(rb.a[i], u1, T1));
+    T2 = __fmaf_rn(rb.d[i], Z2, __fmaf_rn(rb.a[i], u2, T2));
+    const float y0 = __fmaf_rn(sa, Z0, __fmul_rn(ca, v0));
+    const float y1 = __fmaf_rn(sa, Z1, __fmul_rn(ca, v1));
+    const float y2 = __fmaf_rn(sa, Z2, __fmul_rn(ca, v2));
+    const float z0 = __fmaf_rn(ca, Z0, __fmul_rn(-sa, v0));
+    const float z1 = __fmaf_rn(ca, Z1, __fmul_rn(-sa, v1));
+    const float z2 = __fmaf_rn(ca, Z2, __fmul_rn(-sa, v2));
+    X0 = u0; X1 = u1; X2 = u2;
+    Y0 = y0; Y1 = y1; Y2 = y2;
+    Z0 = z0; Z1 = z1; Z2 = z2;
+    float cx[NS], cy[NS], cz[NS], rad[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (SPL_T == 0 && k >= spl) break;
+      const float4 p = rb.sph[i * (SPL_T > 0 ? SPL_T : kMaxSpl) + k];
+      cx[k] = __fmaf_rn(p.z, Z0, __fmaf_rn(p.y, Y0, __fmaf_rn(p.x, X0, T0)));
+      cy[k] = __fmaf_rn(p.z, Z1, __fmaf_rn(p.y, Y1, __fmaf_rn(p.x, X1, T1)));
+      cz[k] = __fmaf_rn(p.z, Z2, __fmaf_rn(p.y, Y2, __fmaf_rn(p.x, X2, T2)));
+      rad[k] = p.w;
+    }
+    hit |= spheres_hit<NS, UNIF, false>(cx, cy, cz, rad, spl, sph, n_s, box, n_b, r2u);
+    if (!FULL) {
+      if (WARP_EXIT) {
+        if (__any_sync(kFull, active && hit)) return true;
+      } else if (hit) {
+        return true;
+      }
+    }
+  }
+  if (WARP_EXIT) return __any_sync(kFull, active && hit);
+  return hit;
+}
+
+template <bool WARP_EXIT>
+__device__ __forceinline__ bool point_config_collides(const float* q, bool active, const RobotDev& rb,
+                                                      const float4* __restrict__ sph, int n_s,
+                                                      const float4* __restrict__ box, int n_b) {
+  const float cx[1] = {q[0]};
+  const float cy[1] = {rb.dof > 1 ? q[1] : 0.0f};
+  const float cz[1] = {rb.dof > 2 ? q[2] : 0.0f};
+  const float rad[1] = {rb.point_radius};
+  const float r2u = __fmul_rn(rb.point_radius, rb.point_radius);
+  const bool hit = spheres_hit<1, true, true>(cx, cy, cz, rad, 1, sph, n_s, box, n_b, r2u);
+  if (WARP_EXIT) return __any_sync(kFull, active && hit);
+  return hit;
+}
+
+}  // namespace gtmp

@@ -1,0 +1,790 @@
+// Kernels of the layered-graph planner (sm_103a).
+//
+//   sample_uniform      Alg. 1 "uniformly sample Q" (Philox4x32-10 stream)
+//   vertex_labels       C_free membership of every vertex (start, samples, goal)
+//   label_configs       the same exact checker on caller-supplied configurations
+//   fused_transition    straight-line edge realisation (Sec. VI SEV planner:
+//                       H waypoints -> FK -> sphere/box tests) fused with the
+//                       min-plus step J_l(u) = min_v c(u,v) + J_{l+1}(v)
+//                       (Sec. IV-B); the cost matrix is never stored
+//   edge_costs          unfused variant: writes C_l (FP32, +inf = absent)
+//   minplus             unfused variant: J_l from a stored C_l (HBM-bound)
+//   extract_paths       follow the minimisers from q0 (Alg. 1 path extraction)
+//   expand              expand-samples of Alg. 1 (AO-GTMP, Sec. IV-D)
+#include <cfloat>
+#include <cstdio>
+
+#include "gtmp_kernels.cuh"
+
+namespace gtmp {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+#define kInf __int_as_float(0x7f800000)
+
+struct Box16 {
+  float lo[kMaxDof], hi[kMaxDof];
+};
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA) staging of the obstacle list into shared memory, completed on an
+// mbarrier.  Every wait is bounded; on timeout the error word is set and the
+// block skips its work after one more bounded wait for the copy in flight.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Returns false (on all threads) if the copy did not complete in time.
+__device__ bool stage_obstacles(float4* s_obs, const float4* g_obs, int n4, uint64_t* mbar_storage, int* err) {
+  const uint32_t bytes = static_cast<uint32_t>(n4) * 16u;
+  const uint32_t mbar = smem_addr(mbar_storage);
+  if (bytes == 0) return __syncthreads_and(1) != 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(s_obs)),
+        "l"(g_obs), "r"(bytes), "r"(mbar)
+        : "memory");
+  }
+  bool ok = mbar_wait_bounded(mbar, 0, 1 << 22);
+  if (!ok) {
+    atomicOr(err, kErrWaitTimeout);
+    mbar_wait_bounded(mbar, 0, 1 << 22);  // let a late copy land before the block exits
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Plain cooperative staging (used where a kernel also writes other shared data).
+__device__ void stage_obstacles_plain(float4* s_obs, const float4* g_obs, int n4) {
+  for (int k = threadIdx.x; k < n4; k += blockDim.x) s_obs[k] = g_obs[k];
+}
+
+template <int VAR>
+struct Var;
+template <>
+struct Var<kVarPoint> {
+  static constexpr bool kArm = false;
+  static constexpr int kDof = 0, kSpl = 1, kDp = 4;
+  static constexpr bool kUnif = true;
+};
+template <>
+struct Var<kVarArm6x4> {
+  static constexpr bool kArm = true;
+  static constexpr int kDof = 6, kSpl = 4, kDp = 8;
+  static constexpr bool kUnif = true;
+};
+template <>
+struct Var<kVarArm7x4> {
+  static constexpr bool kArm = true;
+  static constexpr int kDof = 7, kSpl = 4, kDp = 8;
+  static constexpr bool kUnif = true;
+};
+template <>
+struct Var<kVarArmGeneric> {
+  static constexpr bool kArm = true;
+  static constexpr int kDof = 0, kSpl = 0, kDp = kMaxDof;
+  static constexpr bool kUnif = false;
+};
+
+template <int VAR, bool WARP_EXIT, bool FULL>
+__device__ __forceinline__ bool config_collides(const float* q, bool active, const RobotDev& rb, const float4* s_obs,
+                                                int n_s, int n_b) {
+  using V = Var<VAR>;
+  if constexpr (V::kArm) {
+    return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL>(q, active, rb, s_obs, n_s, s_obs + n_s,
+                                                                            n_b);
+  } else {
+    return point_config_collides<WARP_EXIT>(q, active, rb, s_obs, n_s, s_obs + n_s, n_b);
+  }
+}
+
+// load a padded vertex (dp floats; dp == V::kDp for the specialised variants)
+template <int DP>
+__device__ __forceinline__ void load_vertex(float (&q)[DP], const float* p, int dp) {
+  if (DP == 4 || DP == 8) {
+#pragma unroll
+    for (int d = 0; d < DP; d += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p + d));
+      q[d] = v.x;
+      q[d + 1] = v.y;
+      q[d + 2] = v.z;
+      q[d + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < DP; ++d) q[d] = d < dp ? __ldg(p + d) : 0.0f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Uniform layer sampling: thread per (r, layer 1..L, i).  Word k & 3 of
+// Philox block (i, layer - 1, restart, TAG_UNIFORM << 24 | k >> 2).
+// ---------------------------------------------------------------------------
+__global__ void sample_uniform_kernel(GraphDev g, Box16 box, int dof, unsigned long long seed, int restart0) {
+  const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long total = static_cast<long long>(g.R) * g.L * g.M;
+  if (tid >= total) return;
+  const int i = static_cast<int>(tid % g.M);
+  const int l = static_cast<int>((tid / g.M) % g.L);
+  const int r = static_cast<int>(tid / (static_cast<long long>(g.M) * g.L));
+  float* out = g.Q + vidx(g, r, l + 1, i) * g.dp;
+  const uint2 key = seed_key(seed);
+  uint4 w = make_uint4(0, 0, 0, 0);
+  for (int k = 0; k < g.dp; ++k) {
+    if (k >= dof) {
+      out[k] = 0.0f;
+      continue;
+    }
+    if ((k & 3) == 0)
+      w = philox4x32_10(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(l),
+                                   static_cast<uint32_t>(restart0 + r), (kTagUniform << 24) | (k >> 2)),
+                        key);
+    const float u = word_to_unit(word_of(w, k));
+    out[k] = __fmaf_rn(u, __fsub_rn(box.hi[k], box.lo[k]), box.lo[k]);
+  }
+}
+
+__global__ void init_keys_kernel(GraphDev g, int* counters, int n_counters) {
+  const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long per_r = static_cast<long long>(g.L + 2) * g.M_stride;
+  if (tid < n_counters) counters[tid] = 0;
+  if (tid >= per_r * g.R) return;
+  const int layer = static_cast<int>((tid % per_r) / g.M_stride);
+  const int i = static_cast<int>(tid % g.M_stride);
+  g.keys[tid] = (layer == g.L + 1 && i == 0) ? make_key(0.0f, 0u) : kEmptyKey;
+}
+
+// ---------------------------------------------------------------------------
+// Vertex labels: thread per vertex of every layer (0..L+1).
+// ---------------------------------------------------------------------------
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) vertex_labels_kernel(GraphDev g, RobotDev rb, SceneDev sc) {
+  extern __shared__ float4 s_obs[];
+  stage_obstacles_plain(s_obs, sc.obs, sc.n_s + 2 * sc.n_b);
+  __syncthreads();
+  const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long per_r = static_cast<long long>(g.L + 2) * g.M_stride;
+  if (tid >= per_r * g.R) return;
+  const int r = static_cast<int>(tid / per_r);
+  const int layer = static_cast<int>((tid % per_r) / g.M_stride);
+  const int i = static_cast<int>(tid % g.M_stride);
+  if (i >= layer_size(g, layer)) return;
+  constexpr int DP = Var<VAR>::kDp;
+  float q[DP];
+  load_vertex<DP>(q, g.Q + vidx(g, r, layer, i) * g.dp, g.dp);
+  g.vflag[vidx(g, r, layer, i)] = config_collides<VAR, false, false>(q, true, rb, s_obs, sc.n_s, sc.n_b) ? 1 : 0;
+}
+
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) label_configs_kernel(const float* q_in, int n, int dof, RobotDev rb,
+                                                                 SceneDev sc, uint8_t* out) {
+  extern __shared__ float4 s_obs[];
+  stage_obstacles_plain(s_obs, sc.obs, sc.n_s + 2 * sc.n_b);
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  constexpr int DP = Var<VAR>::kDp;
+  float q[DP];
+#pragma unroll
+  for (int d = 0; d < DP; ++d) q[d] = d < dof ? q_in[static_cast<size_t>(t) * dof + d] : 0.0f;
+  out[t] = config_collides<VAR, false, false>(q, true, rb, s_obs, sc.n_s, sc.n_b) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Fused edge realisation + min-plus for transition layer -> layer + 1.
+//
+// grid = (persistent blocks, R).  Each warp repeatedly takes a chunk of edges
+// (one row i, up to `chunk` consecutive columns) from the restart's counter;
+// the 32 lanes evaluate the H-2 interior waypoints of one edge at a time
+// (endpoint labels come from vertex_labels), the warp leaves the edge at the
+// first colliding link unless MODE == kEvalFull, and the row's best
+// (value, column) key is merged with one 64-bit atomicMin per chunk.
+// Shared memory: obstacles (bulk copy) and the column layer's cost-to-go,
+// +inf where that vertex collides or reaches no goal.
+// ---------------------------------------------------------------------------
+template <int VAR, int MODE>
+__global__ void __launch_bounds__(kThreads) fused_transition_kernel(GraphDev g, int layer, RobotDev rb, SceneDev sc,
+                                                                    int* counters, int chunk, int* err) {
+  using V = Var<VAR>;
+  constexpr int DP = V::kDp;
+  constexpr bool FULL = MODE == kEvalFull;
+  extern __shared__ __align__(128) float4 smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  const int n4 = sc.n_s + 2 * sc.n_b;
+  float4* s_obs = smem;
+  float* s_V = reinterpret_cast<float*>(smem + n4);
+  const int r = blockIdx.y;
+  const int n_rows = layer_size(g, layer), n_cols = layer_size(g, layer + 1);
+
+  for (int j = threadIdx.x; j < n_cols; j += blockDim.x) {
+    const size_t v = vidx(g, r, layer + 1, j);
+    s_V[j] = g.vflag[v] ? kInf : key_value(g.keys[v]);
+  }
+  if (!stage_obstacles(s_obs, sc.obs, n4, &mbar, err)) return;  // also a block barrier
+
+  const int lane = threadIdx.x & 31;
+  const int cpr = (n_cols + chunk - 1) / chunk;
+  const int n_chunks = n_rows * cpr;
+  const int H = g.H;
+  const float steps = static_cast<float>(H - 1);
+  int* counter = counters + r;
+  while (true) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(counter, 1);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= n_chunks) break;
+    const int i = c / cpr;
+    const int j0 = (c - i * cpr) * chunk;
+    const int j1 = min(j0 + chunk, n_cols);
+    const size_t vi = vidx(g, r, layer, i);
+    const bool row_hit = g.vflag[vi] != 0;
+    if (!FULL && row_hit) continue;
+    float qi[DP];
+    load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
+    unsigned long long best = kEmptyKey;
+    for (int j = j0; j < j1; ++j) {
+      const float Vj = s_V[j];
+      if (!FULL && !(Vj < kInf)) continue;
+      float qj[DP];
+      load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp);
+      float dq[DP];
+      float s2 = 0.0f;
+#pragma unroll
+      for (int d = 0; d < DP; ++d) {
+        dq[d] = __fsub_rn(qj[d], qi[d]);
+        s2 = __fmaf_rn(dq[d], dq[d], s2);
+      }
+      const float len = __fsqrt_rn(s2);
+      const bool too_long = len > g.max_edge_len;
+      if (!FULL && too_long) continue;
+      bool hit = false;
+      for (int kb = 1; kb <= H - 2; kb += 32) {
+        const int k = kb + lane;
+        const bool active = k <= H - 2;
+        const float t = __fdiv_rn(static_cast<float>(k), steps);
+        float q[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
+        hit |= config_collides<VAR, true, FULL>(q, active, rb, s_obs, sc.n_s, sc.n_b);
+        if (!FULL && hit) break;
+      }
+      if (!hit && !too_long && !row_hit && Vj < kInf) {
+        const unsigned long long key = make_key(__fadd_rn(len, Vj), static_cast<uint32_t>(j));
+        best = key < best ? key : best;
+      }
+    }
+    if (lane == 0 && best != kEmptyKey) atomicMin(&g.keys[vi], best);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Unfused variant, step 1: C[i][j] (row stride cs) = ||q_j - q_i|| or +inf.
+// ---------------------------------------------------------------------------
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) edge_costs_kernel(GraphDev g, int layer, RobotDev rb, SceneDev sc,
+                                                              float* C, int cs, int* counter, int chunk, int* err) {
+  using V = Var<VAR>;
+  constexpr int DP = V::kDp;
+  extern __shared__ __align__(128) float4 smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  const int n4 = sc.n_s + 2 * sc.n_b;
+  float4* s_obs = smem;
+  if (!stage_obstacles(s_obs, sc.obs, n4, &mbar, err)) return;
+  const int r = 0;
+  const int n_rows = layer_size(g, layer), n_cols = layer_size(g, layer + 1);
+  const int lane = threadIdx.x & 31;
+  const int cpr = (n_cols + chunk - 1) / chunk;
+  const int n_chunks = n_rows * cpr;
+  const int H = g.H;
+  while (true) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(counter, 1);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= n_chunks) break;
+    const int i = c / cpr;
+    const int j0 = (c - i * cpr) * chunk;
+    const int j1 = min(j0 + chunk, n_cols);
+    const size_t vi = vidx(g, r, layer, i);
+    const bool row_hit = g.vflag[vi] != 0;
+    float qi[DP];
+    load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
+    for (int j = j0; j < j1; ++j) {
+      const size_t vj = vidx(g, r, layer + 1, j);
+      float out = kInf;
+      if (!row_hit && !g.vflag[vj]) {
+        float qj[DP];
+        load_vertex<DP>(qj, g.Q + vj * g.dp, g.dp);
+        float dq[DP];
+        float s2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+          dq[d] = __fsub_rn(qj[d], qi[d]);
+          s2 = __fmaf_rn(dq[d], dq[d], s2);
+        }
+        const float len = __fsqrt_rn(s2);
+        if (!(len > g.max_edge_len)) {
+          bool hit = false;
+          for (int kb = 1; kb <= H - 2; kb += 32) {
+            const int k = kb + lane;
+            const float t = __fdiv_rn(static_cast<float>(k), static_cast<float>(H - 1));
+            float q[DP];
+#pragma unroll
+            for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
+            hit |= config_collides<VAR, true, false>(q, k <= H - 2, rb, s_obs, sc.n_s, sc.n_b);
+            if (hit) break;
+          }
+          if (!hit) out = len;
+        }
+      }
+      if (lane == 0) C[static_cast<size_t>(i) * cs + j] = out;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Unfused variant, step 2: one warp per row, J_l(i) = min_j C[i][j] + J_{l+1}(j)
+// with first-index ties; streams the row with 16-byte loads.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) minplus_kernel(GraphDev g, int layer, const float* __restrict__ C, int cs) {
+  extern __shared__ __align__(16) float s_Vm[];
+  const int n_rows = layer_size(g, layer), n_cols = layer_size(g, layer + 1);
+  for (int j = threadIdx.x; j < cs; j += blockDim.x)
+    s_Vm[j] = j < n_cols ? key_value(g.keys[vidx(g, 0, layer + 1, j)]) : kInf;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warps_total = gridDim.x * kWarps;
+  for (int i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < n_rows; i += warps_total) {
+    const float4* row = reinterpret_cast<const float4*>(C + static_cast<size_t>(i) * cs);
+    unsigned long long best = kEmptyKey;
+    for (int q4 = lane; q4 < cs / 4; q4 += 32) {
+      const float4 c = __ldcs(row + q4);
+      const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = q4 * 4 + e;
+        const float cand = __fadd_rn(cv[e], s_Vm[j]);
+        if (cand < kInf) {
+          const unsigned long long key = make_key(cand, static_cast<uint32_t>(j));
+          best = key < best ? key : best;
+        }
+      }
+    }
+    best = warp_min_u64(best);
+    if (lane == 0) g.keys[vidx(g, 0, layer, i)] = best;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Path extraction (one thread per restart) and best-restart selection.
+// ---------------------------------------------------------------------------
+__global__ void extract_paths_kernel(GraphDev g, int32_t* path, float* cost, int32_t* best) {
+  __shared__ unsigned long long s_best;
+  if (threadIdx.x == 0) s_best = kEmptyKey;
+  __syncthreads();
+  for (int r = threadIdx.x; r < g.R; r += blockDim.x) {
+    const unsigned long long k0 = g.keys[vidx(g, r, 0, 0)];
+    int32_t* p = path + static_cast<size_t>(r) * g.L;
+    if (k0 == kEmptyKey) {
+      for (int l = 0; l < g.L; ++l) p[l] = -1;
+      cost[r] = kInf;
+      continue;
+    }
+    cost[r] = key_value(k0);
+    int i = key_index(k0);
+    for (int l = 1; l <= g.L; ++l) {
+      p[l - 1] = i;
+      if (l < g.L) i = key_index(g.keys[vidx(g, r, l, i)]);
+    }
+    atomicMin(&s_best, (static_cast<unsigned long long>(__float_as_uint(key_value(k0))) << 32) | r);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && best) *best = s_best == kEmptyKey ? -1 : static_cast<int32_t>(s_best & 0xffffffffu);
+}
+
+__global__ void get_values_kernel(GraphDev g, float* V, int32_t* sigma) {
+  const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long per_r = static_cast<long long>(g.L + 2) * g.M;
+  if (tid >= per_r * g.R) return;
+  const int r = static_cast<int>(tid / per_r);
+  const int layer = static_cast<int>((tid % per_r) / g.M);
+  const int i = static_cast<int>(tid % g.M);
+  if (i >= layer_size(g, layer)) {
+    V[tid] = kInf;
+    sigma[tid] = -1;
+    return;
+  }
+  const unsigned long long k = g.keys[vidx(g, r, layer, i)];
+  V[tid] = key_value(k);
+  sigma[tid] = layer == g.L + 1 ? -1 : key_index(k);
+}
+
+// copy between caller layout [R][L][M][dof] and internal padded layout
+__global__ void pack_layers_kernel(GraphDev g, float* user, int dof, int to_internal) {
+  const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long total = static_cast<long long>(g.R) * g.L * g.M;
+  if (tid >= total) return;
+  const int i = static_cast<int>(tid % g.M);
+  const int l = static_cast<int>((tid / g.M) % g.L);
+  const int r = static_cast<int>(tid / (static_cast<long long>(g.M) * g.L));
+  float* in = g.Q + vidx(g, r, l + 1, i) * g.dp;
+  float* u = user + static_cast<size_t>(tid) * dof;
+  for (int k = 0; k < g.dp; ++k) {
+    if (to_internal)
+      in[k] = k < dof ? u[k] : 0.0f;
+    else if (k < dof)
+      u[k] = in[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// expand-samples (Alg. 1, AO-GTMP).  Thread per new slot (layer, i), i in
+// [M_old, M_new).  The rule (FP32, fixed operation order):
+//   c_best = +inf      -> box-uniform from the plain stream (restart 0);
+//   coin heads / a neighbour layer empty -> uniform in X_f(c_best) ∩ box by
+//                        rejection from [-1,1]^d (attempt a: block
+//                        (i, l, a, TAG_INFORMED << 24 | k >> 2));
+//   otherwise          -> midpoint of u = layer l-1 sample (word 1 of the coin
+//                        block mod |layer l-1|) and its nearest layer l+1
+//                        sample (first index on ties).
+// Coin = bit 0 of word 0 of block (i, l, 0, TAG_COIN << 24).  All draws see
+// only the samples present on entry (indices < M_old).
+// ---------------------------------------------------------------------------
+struct EllipsoidDev {
+  float centre[kMaxDof], axis[kMaxDof];
+  float r1, r2;
+};
+
+__device__ void informed_params(const float* q0, const float* qg, int dof, float c, EllipsoidDev& e) {
+  float s = 0.0f;
+  for (int k = 0; k < dof; ++k) {
+    const float dq = __fsub_rn(qg[k], q0[k]);
+    s = __fmaf_rn(dq, dq, s);
+  }
+  const float cmin = __fsqrt_rn(s);
+  for (int k = 0; k < dof; ++k) {
+    e.centre[k] = __fmul_rn(0.5f, __fadd_rn(q0[k], qg[k]));
+    e.axis[k] = cmin > 0.0f ? __fdiv_rn(__fsub_rn(qg[k], q0[k]), cmin) : (k == 0 ? 1.0f : 0.0f);
+  }
+  e.r1 = __fmul_rn(0.5f, c);
+  float diff = __fsub_rn(__fmul_rn(c, c), __fmul_rn(cmin, cmin));
+  if (diff < 0.0f) diff = 0.0f;
+  e.r2 = __fmul_rn(0.5f, __fsqrt_rn(diff));
+}
+
+__global__ void expand_kernel(GraphDev g, int dof, Box16 box, unsigned long long seed, int M_old, int M_new,
+                              const float* c_best_ptr, int max_attempts, int* err) {
+  const int n_new = M_new - M_old;
+  const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (tid >= static_cast<long long>(g.L) * n_new) return;
+  const int l = static_cast<int>(tid / n_new);  // 0-based sample layer (internal layer l + 1)
+  const int i = M_old + static_cast<int>(tid % n_new);
+  const uint2 key = seed_key(seed);
+  float* x = g.Q + vidx(g, 0, l + 1, i) * g.dp;
+  for (int k = dof; k < g.dp; ++k) x[k] = 0.0f;
+  const float c_best = *c_best_ptr;
+  if (!(c_best < kInf)) {
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (int k = 0; k < dof; ++k) {
+      if ((k & 3) == 0)
+        w = philox4x32_10(make_uint4(i, l, 0u, (kTagUniform << 24) | (k >> 2)), key);
+      x[k] = __fmaf_rn(word_to_unit(word_of(w, k)), __fsub_rn(box.hi[k], box.lo[k]), box.lo[k]);
+    }
+    return;
+  }
+  const uint4 coin = philox4x32_10(make_uint4(i, l, 0u, kTagCoin << 24), key);
+  const bool heuristic = (coin.x & 1u) != 0u;
+  const int n_prev = l == 0 ? 1 : M_old;
+  const int n_next = l == g.L - 1 ? 1 : M_old;
+  const float* q0 = g.Q + vidx(g, 0, 0, 0) * g.dp;
+  const float* qg = g.Q + vidx(g, 0, g.L + 1, 0) * g.dp;
+  if (!heuristic || n_prev == 0 || n_next == 0) {
+    EllipsoidDev e;
+    informed_params(q0, qg, dof, c_best, e);
+    const float rdiff = __fsub_rn(e.r1, e.r2);
+    for (int a = 0; a < max_attempts; ++a) {
+      float z[kMaxDof];
+      uint4 w = make_uint4(0, 0, 0, 0);
+      for (int k = 0; k < dof; ++k) {
+        if ((k & 3) == 0)
+          w = philox4x32_10(make_uint4(i, l, static_cast<uint32_t>(a), (kTagInformed << 24) | (k >> 2)), key);
+        z[k] = __fsub_rn(__fmul_rn(2.0f, word_to_unit(word_of(w, k))), 1.0f);
+      }
+      float ss = 0.0f;
+      for (int k = 0; k < dof; ++k) ss = __fmaf_rn(z[k], z[k], ss);
+      if (!(ss <= 1.0f)) continue;
+      float dot = 0.0f;
+      for (int k = 0; k < dof; ++k) dot = __fmaf_rn(e.axis[k], z[k], dot);
+      const float coef = __fmul_rn(rdiff, dot);
+      bool inside = true;
+      float y[kMaxDof];
+      for (int k = 0; k < dof; ++k) {
+        y[k] = __fmaf_rn(coef, e.axis[k], __fmaf_rn(e.r2, z[k], e.centre[k]));
+        inside = inside && (y[k] >= box.lo[k] && y[k] <= box.hi[k]);
+      }
+      if (inside) {
+        for (int k = 0; k < dof; ++k) x[k] = y[k];
+        return;
+      }
+    }
+    atomicOr(err, kErrSamplerExhausted);
+    for (int k = 0; k < dof; ++k) x[k] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const uint32_t pick = coin.y % static_cast<uint32_t>(n_prev);
+  const float* u = l == 0 ? q0 : g.Q + vidx(g, 0, l, pick) * g.dp;
+  const float* v = qg;
+  if (l != g.L - 1) {
+    float best = kInf;
+    int bi = 0;
+    for (int j = 0; j < n_next; ++j) {
+      const float* c = g.Q + vidx(g, 0, l + 2, j) * g.dp;
+      float d2 = 0.0f;
+      for (int k = 0; k < dof; ++k) {
+        const float dd = __fsub_rn(c[k], u[k]);
+        d2 = __fmaf_rn(dd, dd, d2);
+      }
+      if (d2 < best) {
+        best = d2;
+        bi = j;
+      }
+    }
+    v = g.Q + vidx(g, 0, l + 2, bi) * g.dp;
+  }
+  for (int k = 0; k < dof; ++k) x[k] = __fmul_rn(0.5f, __fadd_rn(u[k], v[k]));
+}
+
+__global__ void update_best_kernel(int L, const int32_t* cand_path, const float* cand_cost, int32_t* best_path,
+                                   float* best_cost) {
+  const float c = *cand_cost;
+  const float b = *best_cost;
+  __syncthreads();
+  if (c < b) {
+    for (int l = threadIdx.x; l < L; l += blockDim.x) best_path[l] = cand_path[l];
+    __syncthreads();
+    if (threadIdx.x == 0) *best_cost = c;
+  }
+}
+
+inline int blocks_for(long long n, int threads) { return static_cast<int>((n + threads - 1) / threads); }
+
+Box16 make_box(const float* lo, const float* hi, int dof) {
+  Box16 b{};
+  for (int k = 0; k < dof; ++k) {
+    b.lo[k] = lo[k];
+    b.hi[k] = hi[k];
+  }
+  return b;
+}
+
+template <int VAR, int MODE>
+cudaError_t fused_dispatch_mode(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int* counters,
+                                int grid_x, int chunk, int* err, cudaStream_t st) {
+  const size_t smem = static_cast<size_t>(sc.n_s + 2 * sc.n_b) * 16 + static_cast<size_t>(g.M_stride) * 4;
+  fused_transition_kernel<VAR, MODE><<<dim3(grid_x, g.R), kThreads, smem, st>>>(g, layer, rb, sc, counters, chunk, err);
+  return cudaGetLastError();
+}
+
+template <int VAR>
+cudaError_t fused_dispatch(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int mode,
+                           int* counters, int grid_x, int chunk, int* err, cudaStream_t st) {
+  if (mode == kEvalFull) return fused_dispatch_mode<VAR, kEvalFull>(g, layer, rb, sc, counters, grid_x, chunk, err, st);
+  return fused_dispatch_mode<VAR, kEvalEarlyExit>(g, layer, rb, sc, counters, grid_x, chunk, err, st);
+}
+
+template <template <int> class F, typename... Args>
+cudaError_t by_variant(int variant, Args&&... args) {
+  switch (variant) {
+    case kVarPoint: return F<kVarPoint>::run(args...);
+    case kVarArm6x4: return F<kVarArm6x4>::run(args...);
+    case kVarArm7x4: return F<kVarArm7x4>::run(args...);
+    default: return F<kVarArmGeneric>::run(args...);
+  }
+}
+
+template <int VAR>
+struct VertexLabelsRun {
+  static cudaError_t run(const GraphDev& g, const RobotDev& rb, const SceneDev& sc, cudaStream_t st) {
+    const long long n = static_cast<long long>(g.R) * (g.L + 2) * g.M_stride;
+    const size_t smem = static_cast<size_t>(sc.n_s + 2 * sc.n_b) * 16;
+    vertex_labels_kernel<VAR><<<blocks_for(n, kThreads), kThreads, smem, st>>>(g, rb, sc);
+    return cudaGetLastError();
+  }
+};
+
+template <int VAR>
+struct LabelConfigsRun {
+  static cudaError_t run(const float* q, int n, int dof, const RobotDev& rb, const SceneDev& sc, uint8_t* out,
+                         cudaStream_t st) {
+    const size_t smem = static_cast<size_t>(sc.n_s + 2 * sc.n_b) * 16;
+    label_configs_kernel<VAR><<<blocks_for(n, kThreads), kThreads, smem, st>>>(q, n, dof, rb, sc, out);
+    return cudaGetLastError();
+  }
+};
+
+template <int VAR>
+struct FusedRun {
+  static cudaError_t run(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int mode,
+                         int* counters, int grid_x, int chunk, int* err, cudaStream_t st) {
+    return fused_dispatch<VAR>(g, layer, rb, sc, mode, counters, grid_x, chunk, err, st);
+  }
+};
+
+template <int VAR>
+struct EdgeCostsRun {
+  static cudaError_t run(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, float* C, int cs,
+                         int* counter, int grid_x, int chunk, int* err, cudaStream_t st) {
+    const size_t smem = static_cast<size_t>(sc.n_s + 2 * sc.n_b) * 16;
+    edge_costs_kernel<VAR><<<grid_x, kThreads, smem, st>>>(g, layer, rb, sc, C, cs, counter, chunk, err);
+    return cudaGetLastError();
+  }
+};
+
+template <int VAR>
+struct OccupancyRun {
+  static cudaError_t run(int mode, int* out) {
+    if (mode == kEvalFull)
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fused_transition_kernel<VAR, kEvalFull>, kThreads,
+                                                           16 * 1024);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fused_transition_kernel<VAR, kEvalEarlyExit>, kThreads,
+                                                         16 * 1024);
+  }
+};
+
+template <int VAR>
+struct ConfigureRun {
+  static cudaError_t run(int smem_max) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(fused_transition_kernel<VAR, kEvalFull>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(fused_transition_kernel<VAR, kEvalEarlyExit>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(edge_costs_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(vertex_labels_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_max)) != cudaSuccess)
+      return e;
+    return cudaFuncSetAttribute(label_configs_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  }
+};
+
+}  // namespace
+
+cudaError_t configure_kernels(int smem_max) {
+  cudaError_t e;
+  for (int v = 0; v < 4; ++v)
+    if ((e = by_variant<ConfigureRun>(v, smem_max)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(minplus_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+}
+
+// ------------------------------------------------------------------------------------------------
+// launch wrappers
+// ------------------------------------------------------------------------------------------------
+cudaError_t launch_sample_uniform(const GraphDev& g, const float* lo, const float* hi, int dof,
+                                  unsigned long long seed, int restart0, cudaStream_t st) {
+  const long long n = static_cast<long long>(g.R) * g.L * g.M;
+  if (n == 0) return cudaSuccess;
+  sample_uniform_kernel<<<blocks_for(n, kThreads), kThreads, 0, st>>>(g, make_box(lo, hi, dof), dof, seed, restart0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_keys(const GraphDev& g, int* counters, int n_counters, cudaStream_t st) {
+  long long n = static_cast<long long>(g.R) * (g.L + 2) * g.M_stride;
+  if (n < n_counters) n = n_counters;
+  init_keys_kernel<<<blocks_for(n, kThreads), kThreads, 0, st>>>(g, counters, n_counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vertex_labels(const GraphDev& g, const RobotDev& rb, int variant, const SceneDev& sc,
+                                 cudaStream_t st) {
+  return by_variant<VertexLabelsRun>(variant, g, rb, sc, st);
+}
+
+cudaError_t launch_label_configs(const float* q, int n, int dof, const RobotDev& rb, int variant, const SceneDev& sc,
+                                 uint8_t* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return by_variant<LabelConfigsRun>(variant, q, n, dof, rb, sc, out, st);
+}
+
+cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev& rb, int variant, const SceneDev& sc,
+                                    int mode, int* counters, int grid_x, int chunk, int* err, cudaStream_t st) {
+  return by_variant<FusedRun>(variant, g, layer, rb, sc, mode, counters, grid_x, chunk, err, st);
+}
+
+int fused_max_blocks_per_sm(int variant, int mode) {
+  int out = 1;
+  if (by_variant<OccupancyRun>(variant, mode, &out) != cudaSuccess || out < 1) out = 1;
+  return out;
+}
+
+cudaError_t launch_extract_paths(const GraphDev& g, int32_t* path, float* cost, int32_t* best, cudaStream_t st) {
+  extract_paths_kernel<<<1, 256, 0, st>>>(g, path, cost, best);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_values(const GraphDev& g, float* V, int32_t* sigma, cudaStream_t st) {
+  const long long n = static_cast<long long>(g.R) * (g.L + 2) * g.M;
+  get_values_kernel<<<blocks_for(n, kThreads), kThreads, 0, st>>>(g, V, sigma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_layers(const GraphDev& g, float* user, int dof, int to_internal, cudaStream_t st) {
+  const long long n = static_cast<long long>(g.R) * g.L * g.M;
+  if (n == 0) return cudaSuccess;
+  pack_layers_kernel<<<blocks_for(n, kThreads), kThreads, 0, st>>>(g, user, dof, to_internal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_edge_costs(const GraphDev& g, int layer, const RobotDev& rb, int variant, const SceneDev& sc,
+                              float* C, int cs, int* counter, int grid_x, int chunk, int* err, cudaStream_t st) {
+  return by_variant<EdgeCostsRun>(variant, g, layer, rb, sc, C, cs, counter, grid_x, chunk, err, st);
+}
+
+cudaError_t launch_minplus(const GraphDev& g, int layer, const float* C, int cs, int grid, cudaStream_t st) {
+  minplus_kernel<<<grid, kThreads, static_cast<size_t>(cs) * 4, st>>>(g, layer, C, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const GraphDev& g, int dof, const float* lo, const float* hi, unsigned long long seed,
+                          int M_old, int M_new, const float* c_best, int max_attempts, int* err, cudaStream_t st) {
+  const long long n = static_cast<long long>(g.L) * (M_new - M_old);
+  if (n <= 0) return cudaSuccess;
+  expand_kernel<<<blocks_for(n, 128), 128, 0, st>>>(g, dof, make_box(lo, hi, dof), seed, M_old, M_new, c_best,
+                                                    max_attempts, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_best(int L, const int32_t* cand_path, const float* cand_cost, int32_t* best_path,
+                               float* best_cost, cudaStream_t st) {
+  update_best_kernel<<<1, 32, 0, st>>>(L, cand_path, cand_cost, best_path, best_cost);
+  return cudaGetLastError();
+}
+
+}  // namespace gtmp

@@ -1,0 +1,63 @@
+// Kernel launch interface shared by the C-ABI layer and the kernel sources.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gtmp_device.cuh"
+
+namespace gtmp {
+
+// Geometry of one batch of same-shaped layered graphs (R restarts or copies).
+// Vertex (r, layer, i) lives at Q[((r * (L + 2) + layer) * M + i) * dp]; layer 0
+// holds q0 at i = 0, layers 1..L the samples, layer L+1 holds qg at i = 0.
+struct GraphDev {
+  float* Q;                      // [R][L+2][M][dp]
+  uint8_t* vflag;                // [R][L+2][M]   1 = vertex in collision
+  unsigned long long* keys;      // [R][L+2][M]   packed (V, sigma)
+  int R, L, M, dp, H;            // M = active samples per layer, M_stride = allocated
+  int M_stride;
+  float max_edge_len;
+};
+
+__host__ __device__ inline size_t vidx(const GraphDev& g, int r, int layer, int i) {
+  return (static_cast<size_t>(r) * (g.L + 2) + layer) * g.M_stride + i;
+}
+__host__ __device__ inline int layer_size(const GraphDev& g, int layer) {
+  return (layer == 0 || layer == g.L + 1) ? 1 : g.M;
+}
+
+struct SceneDev {
+  const float4* obs;   // n_s sphere float4 followed by 2 * n_b box float4
+  int n_s, n_b;
+};
+
+enum EvalMode { kEvalEarlyExit = 0, kEvalFull = 1 };
+
+// Variant selector for the robot-specialised kernels.
+enum RobotVariant { kVarPoint = 0, kVarArm6x4 = 1, kVarArm7x4 = 2, kVarArmGeneric = 3 };
+
+cudaError_t configure_kernels(int smem_max);
+cudaError_t launch_sample_uniform(const GraphDev& g, const float* lo, const float* hi, int dof,
+                                  unsigned long long seed, int restart0, cudaStream_t st);
+cudaError_t launch_init_keys(const GraphDev& g, int* counters, int n_counters, cudaStream_t st);
+cudaError_t launch_vertex_labels(const GraphDev& g, const RobotDev& rb, int variant, const SceneDev& sc,
+                                 cudaStream_t st);
+cudaError_t launch_label_configs(const float* q, int n, int dof, const RobotDev& rb, int variant,
+                                 const SceneDev& sc, uint8_t* out, cudaStream_t st);
+cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev& rb, int variant,
+                                    const SceneDev& sc, int mode, int* counters, int grid_x, int chunk, int* err,
+                                    cudaStream_t st);
+int fused_max_blocks_per_sm(int variant, int mode);
+cudaError_t launch_extract_paths(const GraphDev& g, int32_t* path, float* cost, int32_t* best, cudaStream_t st);
+cudaError_t launch_get_values(const GraphDev& g, float* V, int32_t* sigma, cudaStream_t st);
+cudaError_t launch_pack_layers(const GraphDev& g, float* user, int dof, int to_internal, cudaStream_t st);
+cudaError_t launch_edge_costs(const GraphDev& g, int layer, const RobotDev& rb, int variant, const SceneDev& sc,
+                              float* C, int cs, int* counter, int grid_x, int chunk, int* err, cudaStream_t st);
+cudaError_t launch_minplus(const GraphDev& g, int layer, const float* C, int cs, int grid, cudaStream_t st);
+cudaError_t launch_expand(const GraphDev& g, int dof, const float* lo, const float* hi, unsigned long long seed,
+                          int M_old, int M_new, const float* c_best, int max_attempts, int* err, cudaStream_t st);
+cudaError_t launch_update_best(int L, const int32_t* cand_path, const float* cand_cost, int32_t* best_path,
+                               float* best_cost, cudaStream_t st);
+
+}  // namespace gtmp

@@ -1,0 +1,228 @@
+"""Parity of the CUDA planner (through the C ABI) with the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_25830_b300 import binding, scenes
+
+from parity import REL, check_values, compare_solution, decisive, scene_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _planner(sc, M, L, H, R=1, mode=binding.EVAL_EARLY_EXIT, max_edge_len=math.inf, max_obstacles=64):
+    p = binding.Planner(sc.robot, M, L, H, R=R, max_obstacles=max_obstacles, eval_mode=mode,
+                        max_edge_len=max_edge_len)
+    p.set_scene(sc)
+    return p
+
+
+def _gpu_solution(p, unfused=False):
+    path, cost = p.solve(unfused=unfused)
+    V, S = p.values()
+    p.synchronize()
+    return V.cpu().numpy(), S.cpu().numpy(), path.cpu().numpy(), float(cost.cpu()[0])
+
+
+# ---------------------------------------------------------------------------
+# samples: bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,dof,M,L,seed", [("point2d", 2, 32, 4, 0), ("arm", 7, 100, 3, 5), ("arm", 6, 33, 2, 2**40 + 3)])
+def test_uniform_samples_bit_exact(torch_cuda, kind, dof, M, L, seed):
+    sc = scene_for(kind, 0, dof, 10)
+    p = _planner(sc, M, L, 4)
+    p.sample_layers(seed, M)
+    Q = p.get_layers().cpu().numpy()
+    ref = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    assert Q.dtype == np.float32
+    np.testing.assert_array_equal(Q.view(np.uint32), ref.view(np.uint32))
+
+
+# ---------------------------------------------------------------------------
+# exact checker: configuration labels
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,dof,n_obs", [("point2d", 2, 10), ("arm", 7, 30), ("arm", 6, 40), ("arm", 5, 12)])
+def test_config_labels_match_outside_band(torch_cuda, kind, dof, n_obs):
+    torch = torch_cuda
+    sc = scene_for(kind, 1, dof, n_obs)
+    p = _planner(sc, 8, 1, 4)
+    rng = np.random.default_rng(7)
+    q = rng.uniform(sc.robot.q_lo, sc.robot.q_hi, (20000, dof)).astype(np.float32)
+    gpu = p.label_configs(torch.from_numpy(q).cuda()).cpu().numpy()
+    lab, margin = oracle.config_labels(sc, q)
+    clear = lab != oracle.AMBIGUOUS
+    np.testing.assert_array_equal(gpu[clear], (lab[clear] == oracle.COLLIDE).astype(np.uint8))
+    assert 0.05 < gpu.mean() < 0.95  # the scene has both free and colliding configurations
+
+
+# ---------------------------------------------------------------------------
+# unfused edge costs: labels and lengths per edge
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,dof,M,L,H", [("point2d", 2, 32, 4, 16), ("arm", 7, 40, 3, 32), ("arm", 6, 29, 2, 40)])
+def test_edge_costs_match_oracle(torch_cuda, kind, dof, M, L, H):
+    sc = scene_for(kind, 2, dof, 30 if kind == "arm" else 10)
+    p = _planner(sc, M, L, H)
+    p.sample_layers(11, M)
+    p.solve(unfused=True)
+    Q = oracle.sample_uniform(11, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
+    vl, _ = oracle.config_labels(sc, np.concatenate(verts))
+    for l in range(L + 1):
+        C = p.edge_costs(l).cpu().numpy()
+        lab, cost = oracle.edge_block(sc, verts[l], verts[l + 1], H)
+        clear = lab != oracle.AMBIGUOUS
+        np.testing.assert_array_equal(np.isinf(C)[clear], (lab == oracle.COLLIDE)[clear], err_msg=f"layer {l}")
+        free = lab == oracle.FREE
+        np.testing.assert_allclose(C[free], cost[free], rtol=REL)
+
+
+# ---------------------------------------------------------------------------
+# fused solve: values, minimisers, path, cost
+# ---------------------------------------------------------------------------
+
+CASES = [
+    ("point2d", 2, 32, 4, 16, 0),     # the 2D point-robot workload itself
+    ("point2d", 2, 37, 3, 16, 5),     # ragged M
+    ("arm", 7, 48, 3, 32, 1),
+    ("arm", 6, 64, 4, 32, 2),
+    ("arm", 5, 23, 2, 12, 3),         # generic (non-specialised) arm kernel
+    ("arm", 7, 1, 1, 32, 4),          # M = 1, L = 1
+    ("arm", 7, 40, 2, 2, 6),          # H = 2: endpoints only
+    ("arm", 7, 20, 2, 67, 7),         # H - 2 > 32: two waypoint rounds per warp
+]
+
+
+@pytest.mark.parametrize("kind,dof,M,L,H,seed", CASES)
+@pytest.mark.parametrize("mode", [binding.EVAL_EARLY_EXIT, binding.EVAL_FULL])
+def test_fused_solve_matches_oracle(torch_cuda, kind, dof, M, L, H, seed, mode):
+    sc = scene_for(kind, seed, dof, 30 if kind == "arm" else 10)
+    p = _planner(sc, M, L, H, mode=mode)
+    p.sample_layers(seed, M)
+    V, S, path, cost = _gpu_solution(p)
+    Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    sol = oracle.solve(sc, Q, H)
+    compare_solution(sol, V, S, path, cost, f"{kind} M={M} L={L} H={H} mode={mode}")
+    if math.isfinite(cost):
+        total, worst = oracle.path_cost(sc, Q, path, H)
+        assert worst > -oracle.EPS_DEFAULT
+        assert cost == pytest.approx(total, rel=REL)
+        assert cost >= float(np.linalg.norm(sc.q_goal.astype(np.float64) - sc.q_start)) * (1 - REL)
+
+
+@pytest.mark.parametrize("kind,dof,M,L,H,seed", CASES[:5])
+def test_fused_unfused_and_modes_agree_exactly(torch_cuda, kind, dof, M, L, H, seed):
+    sc = scene_for(kind, seed, dof, 30 if kind == "arm" else 10)
+    outs = []
+    for mode in (binding.EVAL_EARLY_EXIT, binding.EVAL_FULL):
+        p = _planner(sc, M, L, H, mode=mode)
+        p.sample_layers(seed, M)
+        outs.append(_gpu_solution(p))
+        outs.append(_gpu_solution(p, unfused=True))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[0], outs[0][0])
+        np.testing.assert_array_equal(o[1], outs[0][1])
+        np.testing.assert_array_equal(o[2], outs[0][2])
+        assert o[3] == outs[0][3] or (math.isnan(o[3]) and math.isnan(outs[0][3]))
+
+
+def test_infeasible_and_edge_limit(torch_cuda):
+    sc = scenes.point2d_scene(0, 10)
+    wall = scenes.Scene(sc.robot, np.array([[0.0, 0.0, 0.0, 0.7]], np.float32), np.zeros((0, 6), np.float32),
+                        sc.q_start, sc.q_goal)
+    blocked = scenes.Scene(sc.robot, np.concatenate([wall.spheres, [[0.9, 0.9, 0.0, 0.05]]]).astype(np.float32),
+                           wall.boxes, sc.q_start, sc.q_goal)   # the goal itself is covered
+    p = _planner(blocked, 16, 2, 8)
+    p.sample_layers(1, 16)
+    V, S, path, cost = _gpu_solution(p)
+    assert math.isinf(cost) and list(path) == [-1, -1]
+    # an edge-length limit shorter than any possible hop
+    p2 = _planner(sc, 16, 2, 8, max_edge_len=0.05)
+    p2.sample_layers(1, 16)
+    _, _, path2, cost2 = _gpu_solution(p2)
+    assert math.isinf(cost2) and list(path2) == [-1, -1]
+
+
+def test_no_obstacles_collinear_samples(torch_cuda):
+    torch = torch_cuda
+    sc = scenes.point2d_scene(0, 0)
+    L, M = 3, 8
+    rng = np.random.default_rng(0)
+    Q = rng.uniform(-1, 1, (L, M, 2)).astype(np.float32)
+    for l, t in enumerate([0.25, 0.5, 0.75]):
+        Q[l, 5] = sc.q_start + np.float32(t) * (sc.q_goal - sc.q_start)
+    p = _planner(sc, M, L, 8)
+    p.set_layers(torch.from_numpy(Q).cuda())
+    _, _, path, cost = _gpu_solution(p)
+    assert list(path) == [5, 5, 5]
+    assert cost == pytest.approx(float(np.linalg.norm(sc.q_goal.astype(np.float64) - sc.q_start)), rel=REL)
+
+
+# ---------------------------------------------------------------------------
+# anytime-gtmp: every restart is an independent gtmp
+# ---------------------------------------------------------------------------
+
+def test_anytime_restarts_match_oracle(torch_cuda):
+    sc = scene_for("arm", 3, 6, 30)
+    R, M, L, H = 6, 24, 3, 16
+    p = _planner(sc, M, L, H, R=R)
+    paths, costs, best = p.anytime(21, R)
+    p.synchronize()
+    paths, costs, best = paths.cpu().numpy(), costs.cpu().numpy(), int(best.cpu()[0])
+    sols = oracle.anytime(sc, 21, R, L, M, H)
+    for r in range(R):
+        check_values([costs[r]], [sols[r].cost_lo], [sols[r].cost_hi], f"restart {r}")
+        V, S = p.values(r)
+        compare_solution(sols[r], V.cpu().numpy(), S.cpu().numpy(), paths[r], costs[r], f"restart {r}")
+    fin = np.isfinite(costs)
+    if fin.any():
+        assert costs[best] == costs[fin].min() and best == int(np.argmin(np.where(fin, costs, np.inf)))
+    else:
+        assert best == -1
+
+
+# ---------------------------------------------------------------------------
+# AO-GTMP: expand-samples bit-exact stage by stage, non-increasing best cost
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,dof", [("arm", 6), ("point2d", 2)])
+def test_ao_stages_match_oracle(torch_cuda, kind, dof):
+    torch = torch_cuda
+    sc = scene_for(kind, 4, dof, 30 if kind == "arm" else 12)
+    L, H = 4, 16
+    sizes = [8, 16, 32, 64]
+    p = _planner(sc, sizes[-1], L, H)
+    stage_path = torch.empty(L, dtype=torch.int32, device="cuda")
+    stage_cost = torch.empty(1, dtype=torch.float32, device="cuda")
+    best_path = torch.full((L,), -1, dtype=torch.int32, device="cuda")
+    best_cost = torch.full((1,), math.inf, dtype=torch.float32, device="cuda")
+    Q_ref = np.zeros((L, 0, dof), np.float32)
+    prev_best = math.inf
+    for M in sizes:
+        c_in = float(best_cost.cpu()[0])
+        binding.aogtmp_expand(p.ctx, 99, M, stage_path, stage_cost, best_path, best_cost)
+        p.synchronize()
+        st, Q_ref = oracle.expand_layers(99, Q_ref, M, sc.q_start, sc.q_goal, sc.robot.q_lo, sc.robot.q_hi,
+                                         np.float32(c_in))
+        assert st == 0
+        Q = p.get_layers().cpu().numpy()
+        np.testing.assert_array_equal(Q.view(np.uint32), Q_ref.view(np.uint32), err_msg=f"stage M={M}")
+        sol = oracle.solve(sc, Q_ref, H)
+        V, S = p.values()
+        compare_solution(sol, V.cpu().numpy(), S.cpu().numpy(), stage_path.cpu().numpy(),
+                         float(stage_cost.cpu()[0]), f"AO stage M={M}")
+        b = float(best_cost.cpu()[0])
+        assert b <= prev_best
+        prev_best = b
+        assert b == min(c_in, float(stage_cost.cpu()[0]))
