@@ -239,7 +239,11 @@ def run_ours(args, wl):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    with ClockSampler(gpu_id) as clk:
         for s in range(args.steps):
             flush.zero_()
             evs[s][0].record(stream)

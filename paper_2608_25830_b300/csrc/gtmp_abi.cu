@@ -239,7 +239,6 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
         const float* ls = robot->link_spheres + (static_cast<size_t>(i) * robot->spheres_per_link + s) * 4;
         if (ls[3] != r0) uniform = false;
       }
-    rb.uniform_r = uniform ? 1 : 0;
     rb.r_uniform = r0;
     if (uniform && four && robot->dof == 6)
       c->variant = kVarArm6x4;
@@ -247,6 +246,9 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
       c->variant = kVarArm7x4;
     else
       c->variant = kVarArmGeneric;
+    // the specialised kernels read inflated squared thresholds (r_obs + r)^2,
+    // the generic kernel reads plain obstacle radii
+    rb.uniform_r = (c->variant == kVarArmGeneric) ? 0 : 1;
     const int stride = (c->variant == kVarArmGeneric) ? kMaxSpl : 4;
     for (int i = 0; i < robot->dof; ++i)
       for (int s = 0; s < robot->spheres_per_link; ++s) {
