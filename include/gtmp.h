@@ -216,6 +216,39 @@ typedef struct {
 GTMP_API gtmp_status gtmp_profile_enable(gtmp_ctx* ctx, int32_t enable);
 GTMP_API gtmp_status gtmp_profile_read(gtmp_ctx* ctx, gtmp_profile* out);
 
+/* Allocation-free solve.  The paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory at solve time, such
+ * as a control loop with a fixed real-time budget (cudaMalloc/cudaFree can
+ * block and synchronise the whole device), a plugin running inside a host
+ * application that owns every device allocation, or a process whose device
+ * memory is fully reserved up front.  It plans one graph like gtmp_solve
+ * (early-exit mode, same kernels, same result) from caller-supplied inputs:
+ * robot, obstacles (host, as gtmp_set_obstacles, at most 256 in total),
+ * endpoints (host [dof] each), samples dev_Q (device [L][M][dof] float32),
+ * H and max_edge_len; it writes dev_path (device [L] int32), dev_cost (device
+ * [1] float32) and, if dev_status is not NULL, the device error word (device
+ * [1] int32; 0 = fine, else the bits gtmp_synchronize would report).
+ * It calls no cudaMalloc, cudaFree or other allocating routine: all scratch
+ * (samples in kernel layout, vertex flags, value/index keys, work counters,
+ * the obstacle table) lives in one fixed 1 MiB device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Requests that need more than 1 MiB are rejected with
+ * GTMP_ERR_INVALID_ARG and a message (scratch bytes = roughly (L+2) M
+ * (4 dp + 9) with dp = 8 for 6/7-joint arms, so M = 1024, L = 8 fits).
+ * The first call on a device resolves the array's device address and
+ * queries launch limits for that device (the device must be current); make
+ * that first call before any stream capture.  Every call on a device shares
+ * the one array and overwrites it, so calls whose GPU work overlaps (other
+ * streams, other threads) race and give wrong results; serialise them.
+ * Work is enqueued on cuda_stream; outputs are valid after it completes.
+ * On failure, err_msg (host, err_msg_len bytes, may be NULL) receives a
+ * one-line reason. */
+GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, const float* spheres, int32_t n_s,
+                                        const float* boxes, int32_t n_b, const float* q_start,
+                                        const float* q_goal, const float* dev_Q, int32_t M, int32_t L, int32_t H,
+                                        float max_edge_len, void* cuda_stream, int32_t* dev_path, float* dev_cost,
+                                        int32_t* dev_status, char* err_msg, int32_t err_msg_len);
+
 /* Active samples per layer of graph 0 (after sample/set/expand). */
 GTMP_API gtmp_status gtmp_get_M(const gtmp_ctx* ctx, int32_t* M);
 

@@ -73,6 +73,8 @@ _SIGNATURES = {
     "gtmp_get_M": [_vp, ctypes.POINTER(_i32)],
     "gtmp_profile_enable": [_vp, _i32],
     "gtmp_profile_read": [_vp, ctypes.POINTER(GtmpProfile)],
+    "gtmp_solve_noalloc": [ctypes.POINTER(GtmpRobot), _fp, _i32, _fp, _i32, _fp, _fp, _vp, _i32, _i32, _i32,
+                           ctypes.c_float, _vp, _vp, _vp, _vp, ctypes.c_char_p, _i32],
 }
 
 
@@ -237,6 +239,26 @@ def gtmp_profile_read(ctx):
     _check(ctx, lib().gtmp_profile_read(ctx, ctypes.byref(out)))
     return dict(launches=out.launches, fused_launches=out.fused_launches, fused_ms=out.fused_ms,
                 fused_edges=out.fused_edges)
+
+
+def gtmp_solve_noalloc(robot: scenes.Robot, spheres, boxes, q_start, q_goal, dev_Q, H, dev_path, dev_cost,
+                       dev_status=None, max_edge_len=math.inf, stream=None):
+    """Allocation-free solve (see include/gtmp.h): caller passes every input and output."""
+    import torch
+    rs, keep = robot_struct(robot)
+    s = _f32(spheres).reshape(-1, 4)
+    b = _f32(boxes).reshape(-1, 6)
+    a, g = _f32(q_start), _f32(q_goal)
+    L, M = int(dev_Q.shape[0]), int(dev_Q.shape[1])
+    msg = ctypes.create_string_buffer(512)
+    st = stream if stream is not None else _stream()
+    status = lib().gtmp_solve_noalloc(ctypes.byref(rs), _ptr(s), s.shape[0], _ptr(b), b.shape[0], _ptr(a), _ptr(g),
+                                      _dev(dev_Q, torch.float32), M, L, H, max_edge_len, st,
+                                      _dev(dev_path, torch.int32), _dev(dev_cost, torch.float32),
+                                      _dev(dev_status, torch.int32) if dev_status is not None else None,
+                                      msg, len(msg))
+    if status != GTMP_OK:
+        raise GtmpError(status, msg.value.decode())
 
 
 def gtmp_get_M(ctx):
