@@ -48,6 +48,22 @@ def flops_per_waypoint(dof, spl, n_s, n_b, arm=True):
     return interp + fk + spheres * (8 * n_s + 11 * n_b)
 
 
+def rank_seed_base(rank: int) -> int:
+    """First Philox seed of a rank: ranks plan disjoint seed ranges (independent problems)."""
+    return 1 + rank * 1_000_003
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of a host float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -60,21 +76,24 @@ def dist_env():
 # ---------------------------------------------------------------------------
 
 def oracle_rows(sc, wl, budget_s, seed=0, max_rows=None):
-    """Run the oracle's edge realisation on whole rows of a middle transition
-    until budget_s has passed; return (edges, seconds, rows)."""
+    """Run the oracle's edge realisation on whole rows of the layer-to-layer
+    transitions (row i of transition 1, 2, ..., L-1, then row i+1, ...) until
+    budget_s has passed; return (edges, seconds, rows)."""
     import oracle
     M, L, H = wl["M"], wl["L"], wl["H"]
     Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
     verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
-    mid = max(1, L // 2)
+    mids = list(range(1, L)) or [0]
     t0 = time.perf_counter()
     rows = 0
     while True:
-        oracle.edge_block(sc, verts[mid][rows:rows + 1], verts[mid + 1], H)
+        layer = mids[rows % len(mids)]
+        i = (rows // len(mids)) % len(verts[layer])
+        oracle.edge_block(sc, verts[layer][i:i + 1], verts[layer + 1], H)
         rows += 1
         el = time.perf_counter() - t0
-        if el >= budget_s or rows >= M or (max_rows and rows >= max_rows):
-            return rows * M, el, rows
+        if el >= budget_s or (max_rows and rows >= max_rows):
+            return rows * len(verts[layer + 1]), el, rows
 
 
 def oracle_free_fn(sc):
@@ -107,7 +126,7 @@ def run_reference(args, wl):
     nominal_edges = 2 * wl["M"] + (wl["L"] - 1) * wl["M"] ** 2
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
     value = checks / secs
-    sample = (f"{rows} rows x {wl['M']} edges of a middle transition (H={wl['H']}), "
+    sample = (f"{rows} rows x {wl['M']} edges of the layer-to-layer transitions (H={wl['H']}), "
               f"{args.steps} steps of ~{per_step:.0f} s, extrapolated per check")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": world,
@@ -226,7 +245,7 @@ def run_ours(args, wl):
         binding.gtmp_sample_layers(p.ctx, seed, M)
         binding.gtmp_solve(p.ctx, path, cost)
 
-    seed0 = 1 + rank * 1_000_003
+    seed0 = rank_seed_base(rank)
     for s in range(args.warmup):
         step(seed0 + 10_000 + s)
     p.synchronize()
@@ -256,11 +275,7 @@ def run_ours(args, wl):
     binding.gtmp_profile_enable(p.ctx, False)
     p.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, "cuda")
     solves = args.steps * world
     value = nominal_checks * solves / total_s
     clocks = clk.summary()
@@ -288,10 +303,7 @@ def run_ours(args, wl):
         t0 = time.perf_counter()
         e2e_step(seed0 + s)
         e2e_s += time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, "cuda")
     e2e_value = nominal_checks * solves / e2e_s
 
     # --- roofline of the fused kernel in full-evaluation mode (data-independent FP32 work)
@@ -322,7 +334,7 @@ def run_ours(args, wl):
             edges, secs, rows = oracle_rows(sc, wl, args.cpu_budget)
             cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
             cpu = {"value": edges * H / secs, "unit": "checks/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{rows} rows x {M} edges of transition {max(1, L // 2)} (H={H}) in {secs:.1f} s, "
+                   "sample": f"{rows} rows x {M} edges of the layer-to-layer transitions (H={H}) in {secs:.1f} s, "
                              f"extrapolated per nominal check"}
         out = {
             "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": world, "steps": args.steps,

@@ -28,7 +28,7 @@ struct gtmp_ctx {
   int* counters = nullptr;
   int n_counters = 0;
   float4* obs = nullptr;
-  int n_s = 0, n_b = 0;
+  SceneDev sc{};  // counts and layout of the obstacle table at obs
   int* err = nullptr;
   float* C = nullptr;
   std::vector<size_t> c_off;
@@ -89,7 +89,13 @@ GraphDev graph(gtmp_ctx* c, int R, int M) {
   return g;
 }
 
-SceneDev scene(gtmp_ctx* c) { return SceneDev{c->obs, c->n_s, c->n_b}; }
+SceneDev scene(gtmp_ctx* c) {
+  SceneDev s = c->sc;
+  s.obs = c->obs;
+  return s;
+}
+
+bool uses_prefilter(int variant) { return variant == kVarArm6x4 || variant == kVarArm7x4; }
 
 // layer sizes and chunking of one transition
 void transition_shape(const GraphDev& g, int layer, int* rows, int* cols) {
@@ -275,7 +281,8 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
   alloc(reinterpret_cast<void**>(&c->keys), graph_vertices * sizeof(unsigned long long));
   c->n_counters = (p.L + 1) * p.R;
   alloc(reinterpret_cast<void**>(&c->counters), static_cast<size_t>(c->n_counters) * sizeof(int));
-  alloc(reinterpret_cast<void**>(&c->obs), static_cast<size_t>(p.max_obstacles) * 2 * sizeof(float4));
+  // scalar table (<= 2 float4 per obstacle) or packed tables (<= 3 (n_s + n_b) + 8 float4)
+  alloc(reinterpret_cast<void**>(&c->obs), (static_cast<size_t>(p.max_obstacles) * 3 + 8) * sizeof(float4));
   alloc(reinterpret_cast<void**>(&c->err), sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->Q, 0, graph_vertices * c->dp * sizeof(float), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
@@ -335,31 +342,46 @@ gtmp_status gtmp_set_obstacles(gtmp_ctx* c, const float* spheres, int32_t n_s, c
   if ((n_s > 0 && !finite_all(spheres, static_cast<size_t>(n_s) * 4)) ||
       (n_b > 0 && !finite_all(boxes, static_cast<size_t>(n_b) * 6)))
     return fail(c, GTMP_ERR_INVALID_ARG, "non-finite obstacle data");
-  std::vector<float4> host(static_cast<size_t>(n_s) + 2 * static_cast<size_t>(n_b));
-  for (int o = 0; o < n_s; ++o) {
-    const float* s = spheres + 4 * o;
-    if (!(s[3] >= 0.0f)) return fail(c, GTMP_ERR_INVALID_ARG, "negative sphere radius");
-    float w = s[3];
-    if (c->rb.uniform_r) {
-      const float rr = s[3] + c->rb.r_uniform;
-      w = rr * rr;  // inflated squared threshold
+  SceneDev sc{};
+  std::vector<float4> host;
+  if (uses_prefilter(c->variant)) {
+    for (int o = 0; o < n_s; ++o)
+      if (!(spheres[4 * o + 3] >= 0.0f)) return fail(c, GTMP_ERR_INVALID_ARG, "negative sphere radius");
+    for (int o = 0; o < n_b; ++o)
+      for (int k = 0; k < 3; ++k)
+        if (!(boxes[6 * o + 3 + k] >= boxes[6 * o + k])) return fail(c, GTMP_ERR_INVALID_ARG, "box with hi < lo");
+    host.resize(3 * static_cast<size_t>(n_s + n_b) + 8);
+    const int n4 = build_packed_tables(spheres, n_s, boxes, n_b, c->rb.r_uniform, arm_reach_bound(c->rb),
+                                       host.data(), &sc);
+    host.resize(n4);
+  } else {
+    host.resize(static_cast<size_t>(n_s) + 2 * static_cast<size_t>(n_b));
+    for (int o = 0; o < n_s; ++o) {
+      const float* s = spheres + 4 * o;
+      if (!(s[3] >= 0.0f)) return fail(c, GTMP_ERR_INVALID_ARG, "negative sphere radius");
+      float w = s[3];
+      if (c->rb.uniform_r) {
+        const float rr = s[3] + c->rb.r_uniform;
+        w = rr * rr;  // inflated squared threshold
+      }
+      host[o] = make_float4(s[0], s[1], s[2], w);
     }
-    host[o] = make_float4(s[0], s[1], s[2], w);
-  }
-  for (int o = 0; o < n_b; ++o) {
-    const float* b = boxes + 6 * o;
-    for (int k = 0; k < 3; ++k)
-      if (!(b[3 + k] >= b[k])) return fail(c, GTMP_ERR_INVALID_ARG, "box with hi < lo");
-    const float cx = 0.5f * (b[0] + b[3]), cy = 0.5f * (b[1] + b[4]), cz = 0.5f * (b[2] + b[5]);
-    const float hx = 0.5f * (b[3] - b[0]), hy = 0.5f * (b[4] - b[1]), hz = 0.5f * (b[5] - b[2]);
-    host[n_s + 2 * o] = make_float4(cx, cy, cz, hx);
-    host[n_s + 2 * o + 1] = make_float4(hy, hz, 0.0f, 0.0f);
+    for (int o = 0; o < n_b; ++o) {
+      const float* b = boxes + 6 * o;
+      for (int k = 0; k < 3; ++k)
+        if (!(b[3 + k] >= b[k])) return fail(c, GTMP_ERR_INVALID_ARG, "box with hi < lo");
+      const float cx = 0.5f * (b[0] + b[3]), cy = 0.5f * (b[1] + b[4]), cz = 0.5f * (b[2] + b[5]);
+      const float hx = 0.5f * (b[3] - b[0]), hy = 0.5f * (b[4] - b[1]), hz = 0.5f * (b[5] - b[2]);
+      host[n_s + 2 * o] = make_float4(cx, cy, cz, hx);
+      host[n_s + 2 * o + 1] = make_float4(hy, hz, 0.0f, 0.0f);
+    }
+    sc.n_s = n_s;
+    sc.n_b = n_b;
   }
   if (!host.empty())
     CUDA_TRY(c, cudaMemcpyAsync(c->obs, host.data(), host.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
-  c->n_s = n_s;
-  c->n_b = n_b;
+  c->sc = sc;
   return GTMP_OK;
 }
 

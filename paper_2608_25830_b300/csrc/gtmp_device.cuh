@@ -163,6 +163,122 @@ __device__ __forceinline__ bool spheres_hit(const float (&cx)[NS], const float (
 }
 
 // ----------------------------------------------------------------------------
+// Conservative prefilter (uniform robot-sphere radius r).  Every obstacle o is
+// enclosed in a ball (centre o, radius R_o = r_obs + r for a sphere,
+// |half extents| + r for a box) and stored in pairs as float4
+//   (ax_a, ax_b, ay_a, ay_b), (az_a, az_b, k_a, k_b),  a = -2 o,
+//   k = |o|^2 - R_o^2 - margin,
+// so that t = |c|^2 + a.c + k = |c - o|^2 - R_o^2 - margin takes three
+// packed FMAs per pair of obstacles.  A robot sphere may touch o only if
+// t < 0; margin (set on the host) exceeds the float32 rounding error of this
+// expanded form by two orders of magnitude, so a pair the prefilter clears is
+// also cleared by the exact test, and the exact test is run whenever any lane
+// is not cleared.  The labels are therefore those of the exact test alone.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+template <int NS>
+__device__ __forceinline__ bool prefilter_maybe(const float (&cx)[NS], const float (&cy)[NS], const float (&cz)[NS],
+                                                const float4* __restrict__ pre, int n_pairs) {
+  float2 x2[NS], y2[NS], z2[NS];
+  float m[NS], c2[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    x2[k] = make_float2(cx[k], cx[k]);
+    y2[k] = make_float2(cy[k], cy[k]);
+    z2[k] = make_float2(cz[k], cz[k]);
+    c2[k] = __fmaf_rn(cz[k], cz[k], __fmaf_rn(cy[k], cy[k], __fmul_rn(cx[k], cx[k])));
+    m[k] = __int_as_float(0x7f800000);
+  }
+#pragma unroll 2
+  for (int p = 0; p < n_pairs; ++p) {
+    const float4 P0 = pre[2 * p];
+    const float4 P1 = pre[2 * p + 1];
+    const float2 ax = make_float2(P0.x, P0.y), ay = make_float2(P0.z, P0.w);
+    const float2 az = make_float2(P1.x, P1.y), kk = make_float2(P1.z, P1.w);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const float2 t = __ffma2_rn(z2[k], az, __ffma2_rn(y2[k], ay, __ffma2_rn(x2[k], ax, kk)));
+      m[k] = fmin3(m[k], t.x, t.y);
+    }
+  }
+  bool maybe = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) maybe |= m[k] < -c2[k];
+  return maybe;
+}
+
+// ----------------------------------------------------------------------------
+// Exact test of the uniform-radius arm kernels, two obstacles per packed
+// float32x2 instruction.  Tables (negated positions, radius r of the robot
+// spheres folded into the thresholds):
+//   sphere pair: (-ox_a, -ox_b, -oy_a, -oy_b), (-oz_a, -oz_b, -T_a, -T_b),
+//                T = (r_obs + r)^2;
+//   box pair:    (-bx_a, -bx_b, -by_a, -by_b), (-bz_a, -bz_b, -hx_a, -hx_b),
+//                (-hy_a, -hy_b, -hz_a, -hz_b)   (centre b, half extents h).
+// A sphere hits iff dx^2 + dy^2 + dz^2 - T < 0 and a box iff
+// sum_k max(|c_k - b_k| - h_k, 0)^2 - r^2 < 0, each sum taken as one fma chain
+// starting from the negated threshold.  Odd counts are padded with obstacles
+// at 1e18 that never hit.
+// ----------------------------------------------------------------------------
+template <int NS>
+__device__ __forceinline__ bool exact_packed_hit(const float (&cx)[NS], const float (&cy)[NS], const float (&cz)[NS],
+                                                 const float4* __restrict__ sphp, int n_sp,
+                                                 const float4* __restrict__ boxp, int n_bp, float neg_r2) {
+  float2 x2[NS], y2[NS], z2[NS];
+  float m[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    x2[k] = make_float2(cx[k], cx[k]);
+    y2[k] = make_float2(cy[k], cy[k]);
+    z2[k] = make_float2(cz[k], cz[k]);
+    m[k] = __int_as_float(0x7f800000);
+  }
+#pragma unroll 2
+  for (int p = 0; p < n_sp; ++p) {
+    const float4 P0 = sphp[2 * p];
+    const float4 P1 = sphp[2 * p + 1];
+    const float2 nx = make_float2(P0.x, P0.y), ny = make_float2(P0.z, P0.w);
+    const float2 nz = make_float2(P1.x, P1.y), nt = make_float2(P1.z, P1.w);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const float2 dx = __fadd2_rn(x2[k], nx);
+      const float2 dy = __fadd2_rn(y2[k], ny);
+      const float2 dz = __fadd2_rn(z2[k], nz);
+      const float2 t = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, nt)));
+      m[k] = fmin3(m[k], t.x, t.y);
+    }
+  }
+  const float2 nr2 = make_float2(neg_r2, neg_r2);
+#pragma unroll 1
+  for (int p = 0; p < n_bp; ++p) {
+    const float4 B0 = boxp[3 * p];
+    const float4 B1 = boxp[3 * p + 1];
+    const float4 B2 = boxp[3 * p + 2];
+    const float2 nbx = make_float2(B0.x, B0.y), nby = make_float2(B0.z, B0.w), nbz = make_float2(B1.x, B1.y);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const float2 ux = __fadd2_rn(x2[k], nbx);
+      const float2 uy = __fadd2_rn(y2[k], nby);
+      const float2 uz = __fadd2_rn(z2[k], nbz);
+      const float2 px = make_float2(fmaxf(__fadd_rn(fabsf(ux.x), B1.z), 0.0f), fmaxf(__fadd_rn(fabsf(ux.y), B1.w), 0.0f));
+      const float2 py = make_float2(fmaxf(__fadd_rn(fabsf(uy.x), B2.x), 0.0f), fmaxf(__fadd_rn(fabsf(uy.y), B2.y), 0.0f));
+      const float2 pz = make_float2(fmaxf(__fadd_rn(fabsf(uz.x), B2.z), 0.0f), fmaxf(__fadd_rn(fabsf(uz.y), B2.w), 0.0f));
+      const float2 t = __ffma2_rn(pz, pz, __ffma2_rn(py, py, __ffma2_rn(px, px, nr2)));
+      m[k] = fmin3(m[k], t.x, t.y);
+    }
+  }
+  bool hit = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) hit |= m[k] < 0.0f;
+  return hit;
+}
+
+// ----------------------------------------------------------------------------
 // One configuration against the scene.
 //
 // WARP_EXIT: the caller is a whole warp evaluating waypoints of the same
@@ -172,23 +288,36 @@ __device__ __forceinline__ bool spheres_hit(const float (&cx)[NS], const float (
 // Returns, for WARP_EXIT, the warp-uniform "some active lane collides"; else
 // the lane's own label.
 // ----------------------------------------------------------------------------
-template <int DOF_T, int SPL_T, bool UNIF, bool WARP_EXIT, bool FULL>
+// PACKED (uniform-radius arms): sph/box are the packed pair tables of
+// exact_packed_hit with n_s/n_b pair counts, pre the prefilter table; the
+// prefilter is used only when FULL is false.  Otherwise sph/box are the
+// scalar tables of spheres_hit.
+template <int DOF_T, int SPL_T, bool UNIF, bool WARP_EXIT, bool FULL, bool PACKED = false>
 __device__ __forceinline__ bool arm_config_collides(const float* q, bool active, const RobotDev& rb,
                                                     const float4* __restrict__ sph, int n_s,
-                                                    const float4* __restrict__ box, int n_b) {
+                                                    const float4* __restrict__ box, int n_b,
+                                                    const float4* __restrict__ pre = nullptr, int n_pairs = 0) {
   constexpr int NS = SPL_T > 0 ? SPL_T : kMaxSpl;
+  constexpr int NQ = DOF_T > 0 ? DOF_T : kMaxDof;
   const int dof = DOF_T > 0 ? DOF_T : rb.dof;
   const int spl = SPL_T > 0 ? SPL_T : rb.spl;
   const float r2u = __fmul_rn(rb.r_uniform, rb.r_uniform);
+  // joint angles rotate through a register array so that the link loop stays
+  // rolled (one copy of the link body: small code, no instruction-cache misses)
+  float ang[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) ang[k] = (DOF_T > 0 || k < dof) ? q[k] : 0.0f;
   // running frame of link i: rotation columns X, Y, Z and origin T
   float X0 = 1.f, X1 = 0.f, X2 = 0.f, Y0 = 0.f, Y1 = 1.f, Y2 = 0.f, Z0 = 0.f, Z1 = 0.f, Z2 = 1.f;
   float T0 = 0.f, T1 = 0.f, T2 = 0.f;
   bool hit = false;
+#pragma unroll 1
+  for (int i = 0; i < dof; ++i) {
+    const float qi = ang[0];
 #pragma unroll
-  for (int i = 0; i < (DOF_T > 0 ? DOF_T : kMaxDof); ++i) {
-    if (DOF_T == 0 && i >= dof) break;
+    for (int k = 0; k + 1 < NQ; ++k) ang[k] = ang[k + 1];
     float s, c;
-    sincosf(__fadd_rn(q[i], rb.toff[i]), &s, &c);
+    sincosf(__fadd_rn(qi, rb.toff[i]), &s, &c);
     // A_i = Rz(theta) Tz(d) Tx(a) Rx(alpha): new x axis u = c X + s Y,
     // v = -s X + c Y, new y = ca v + sa Z, new z = -sa v + ca Z,
     // new origin = T + a u + d Z.
@@ -221,7 +350,20 @@ __device__ __forceinline__ bool arm_config_collides(const float* q, bool active,
       cz[k] = __fmaf_rn(p.z, Z2, __fmaf_rn(p.y, Y2, __fmaf_rn(p.x, X2, T2)));
       rad[k] = p.w;
     }
-    hit |= spheres_hit<NS, UNIF, false>(cx, cy, cz, rad, spl, sph, n_s, box, n_b, r2u);
+    if constexpr (PACKED && FULL) {
+      hit |= exact_packed_hit<NS>(cx, cy, cz, sph, n_s, box, n_b, -r2u);
+    } else if constexpr (PACKED) {
+      // exact tests only where the prefilter could not clear the link
+      const bool maybe = prefilter_maybe<NS>(cx, cy, cz, pre, n_pairs);
+      bool run_exact;
+      if constexpr (WARP_EXIT)
+        run_exact = __any_sync(kFull, active && maybe);
+      else
+        run_exact = maybe;
+      if (run_exact) hit |= exact_packed_hit<NS>(cx, cy, cz, sph, n_s, box, n_b, -r2u);
+    } else {
+      hit |= spheres_hit<NS, UNIF, false>(cx, cy, cz, rad, spl, sph, n_s, box, n_b, r2u);
+    }
     if (!FULL) {
       if (WARP_EXIT) {
         if (__any_sync(kFull, active && hit)) return true;

@@ -12,7 +12,9 @@
 //   extract_paths       follow the minimisers from q0 (Alg. 1 path extraction)
 //   expand              expand-samples of Alg. 1 (AO-GTMP, Sec. IV-D)
 #include <cfloat>
+#include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "gtmp_kernels.cuh"
 
@@ -22,6 +24,11 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// resident blocks per SM the edge kernels are compiled for (2 -> register budget 128)
+#ifndef GTMP_FUSED_MIN_BLOCKS
+#define GTMP_FUSED_MIN_BLOCKS 2
+#endif
+constexpr int kFusedMinBlocks = GTMP_FUSED_MIN_BLOCKS;
 #define kInf __int_as_float(0x7f800000)
 
 struct Box16 {
@@ -113,13 +120,19 @@ struct Var<kVarArmGeneric> {
 
 template <int VAR, bool WARP_EXIT, bool FULL>
 __device__ __forceinline__ bool config_collides(const float* q, bool active, const RobotDev& rb, const float4* s_obs,
-                                                int n_s, int n_b) {
+                                                const SceneDev& sc) {
   using V = Var<VAR>;
-  if constexpr (V::kArm) {
-    return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL>(q, active, rb, s_obs, n_s, s_obs + n_s,
-                                                                            n_b);
+  if constexpr (V::kArm && V::kUnif) {
+    // uniform-radius arms: packed pair tables, then the prefilter table
+    const float4* boxp = s_obs + 2 * sc.n_sp;
+    const float4* pre = boxp + 3 * sc.n_bp;
+    return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL, true>(q, active, rb, s_obs, sc.n_sp,
+                                                                                  boxp, sc.n_bp, pre, sc.n_pairs);
+  } else if constexpr (V::kArm) {
+    return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL>(q, active, rb, s_obs, sc.n_s,
+                                                                            s_obs + sc.n_s, sc.n_b);
   } else {
-    return point_config_collides<WARP_EXIT>(q, active, rb, s_obs, n_s, s_obs + n_s, n_b);
+    return point_config_collides<WARP_EXIT>(q, active, rb, s_obs, sc.n_s, s_obs + sc.n_s, sc.n_b);
   }
 }
 
@@ -185,7 +198,7 @@ __global__ void init_keys_kernel(GraphDev g, int* counters, int n_counters) {
 template <int VAR>
 __global__ void __launch_bounds__(kThreads) vertex_labels_kernel(GraphDev g, RobotDev rb, SceneDev sc) {
   extern __shared__ float4 s_obs[];
-  stage_obstacles_plain(s_obs, sc.obs, sc.n_s + 2 * sc.n_b);
+  stage_obstacles_plain(s_obs, sc.obs, scene_float4s(sc));
   __syncthreads();
   const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long per_r = static_cast<long long>(g.L + 2) * g.M_stride;
@@ -197,14 +210,14 @@ __global__ void __launch_bounds__(kThreads) vertex_labels_kernel(GraphDev g, Rob
   constexpr int DP = Var<VAR>::kDp;
   float q[DP];
   load_vertex<DP>(q, g.Q + vidx(g, r, layer, i) * g.dp, g.dp);
-  g.vflag[vidx(g, r, layer, i)] = config_collides<VAR, false, false>(q, true, rb, s_obs, sc.n_s, sc.n_b) ? 1 : 0;
+  g.vflag[vidx(g, r, layer, i)] = config_collides<VAR, false, false>(q, true, rb, s_obs, sc) ? 1 : 0;
 }
 
 template <int VAR>
 __global__ void __launch_bounds__(kThreads) label_configs_kernel(const float* q_in, int n, int dof, RobotDev rb,
                                                                  SceneDev sc, uint8_t* out) {
   extern __shared__ float4 s_obs[];
-  stage_obstacles_plain(s_obs, sc.obs, sc.n_s + 2 * sc.n_b);
+  stage_obstacles_plain(s_obs, sc.obs, scene_float4s(sc));
   __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -212,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) label_configs_kernel(const float* q_
   float q[DP];
 #pragma unroll
   for (int d = 0; d < DP; ++d) q[d] = d < dof ? q_in[static_cast<size_t>(t) * dof + d] : 0.0f;
-  out[t] = config_collides<VAR, false, false>(q, true, rb, s_obs, sc.n_s, sc.n_b) ? 1 : 0;
+  out[t] = config_collides<VAR, false, false>(q, true, rb, s_obs, sc) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -228,14 +241,14 @@ __global__ void __launch_bounds__(kThreads) label_configs_kernel(const float* q_
 // +inf where that vertex collides or reaches no goal.
 // ---------------------------------------------------------------------------
 template <int VAR, int MODE>
-__global__ void __launch_bounds__(kThreads) fused_transition_kernel(GraphDev g, int layer, RobotDev rb, SceneDev sc,
+__global__ void __launch_bounds__(kThreads, kFusedMinBlocks) fused_transition_kernel(GraphDev g, int layer, RobotDev rb, SceneDev sc,
                                                                     int* counters, int chunk, int* err) {
   using V = Var<VAR>;
   constexpr int DP = V::kDp;
   constexpr bool FULL = MODE == kEvalFull;
   extern __shared__ __align__(128) float4 smem[];
   __shared__ __align__(8) uint64_t mbar;
-  const int n4 = sc.n_s + 2 * sc.n_b;
+  const int n4 = scene_float4s(sc);
   float4* s_obs = smem;
   float* s_V = reinterpret_cast<float*>(smem + n4);
   const int r = blockIdx.y;
@@ -290,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) fused_transition_kernel(GraphDev g, 
         float q[DP];
 #pragma unroll
         for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
-        hit |= config_collides<VAR, true, FULL>(q, active, rb, s_obs, sc.n_s, sc.n_b);
+        hit |= config_collides<VAR, true, FULL>(q, active, rb, s_obs, sc);
         if (!FULL && hit) break;
       }
       if (!hit && !too_long && !row_hit && Vj < kInf) {
@@ -306,13 +319,13 @@ __global__ void __launch_bounds__(kThreads) fused_transition_kernel(GraphDev g, 
 // Unfused variant, step 1: C[i][j] (row stride cs) = ||q_j - q_i|| or +inf.
 // ---------------------------------------------------------------------------
 template <int VAR>
-__global__ void __launch_bounds__(kThreads) edge_costs_kernel(GraphDev g, int layer, RobotDev rb, SceneDev sc,
+__global__ void __launch_bounds__(kThreads, kFusedMinBlocks) edge_costs_kernel(GraphDev g, int layer, RobotDev rb, SceneDev sc,
                                                               float* C, int cs, int* counter, int chunk, int* err) {
   using V = Var<VAR>;
   constexpr int DP = V::kDp;
   extern __shared__ __align__(128) float4 smem[];
   __shared__ __align__(8) uint64_t mbar;
-  const int n4 = sc.n_s + 2 * sc.n_b;
+  const int n4 = scene_float4s(sc);
   float4* s_obs = smem;
   if (!stage_obstacles(s_obs, sc.obs, n4, &mbar, err)) return;
   const int r = 0;
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(kThreads) edge_costs_kernel(GraphDev g, int la
             float q[DP];
 #pragma unroll
             for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
-            hit |= config_collides<VAR, true, false>(q, k <= H - 2, rb, s_obs, sc.n_s, sc.n_b);
+            hit |= config_collides<VAR, true, false>(q, k <= H - 2, rb, s_obs, sc);
             if (hit) break;
           }
           if (!hit) out = len;
@@ -604,7 +617,7 @@ Box16 make_box(const float* lo, const float* hi, int dof) {
 template <int VAR, int MODE>
 cudaError_t fused_dispatch_mode(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int* counters,
                                 int grid_x, int chunk, int* err, cudaStream_t st) {
-  const size_t smem = static_cast<size_t>(sc.n_s + 2 * sc.n_b) * 16 + static_cast<size_t>(g.M_stride) * 4;
+  const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16 + static_cast<size_t>(g.M_stride) * 4;
   fused_transition_kernel<VAR, MODE><<<dim3(grid_x, g.R), kThreads, smem, st>>>(g, layer, rb, sc, counters, chunk, err);
   return cudaGetLastError();
 }
@@ -630,7 +643,7 @@ template <int VAR>
 struct VertexLabelsRun {
   static cudaError_t run(const GraphDev& g, const RobotDev& rb, const SceneDev& sc, cudaStream_t st) {
     const long long n = static_cast<long long>(g.R) * (g.L + 2) * g.M_stride;
-    const size_t smem = static_cast<size_t>(sc.n_s + 2 * sc.n_b) * 16;
+    const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16;
     vertex_labels_kernel<VAR><<<blocks_for(n, kThreads), kThreads, smem, st>>>(g, rb, sc);
     return cudaGetLastError();
   }
@@ -640,7 +653,7 @@ template <int VAR>
 struct LabelConfigsRun {
   static cudaError_t run(const float* q, int n, int dof, const RobotDev& rb, const SceneDev& sc, uint8_t* out,
                          cudaStream_t st) {
-    const size_t smem = static_cast<size_t>(sc.n_s + 2 * sc.n_b) * 16;
+    const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16;
     label_configs_kernel<VAR><<<blocks_for(n, kThreads), kThreads, smem, st>>>(q, n, dof, rb, sc, out);
     return cudaGetLastError();
   }
@@ -658,7 +671,7 @@ template <int VAR>
 struct EdgeCostsRun {
   static cudaError_t run(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, float* C, int cs,
                          int* counter, int grid_x, int chunk, int* err, cudaStream_t st) {
-    const size_t smem = static_cast<size_t>(sc.n_s + 2 * sc.n_b) * 16;
+    const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16;
     edge_costs_kernel<VAR><<<grid_x, kThreads, smem, st>>>(g, layer, rb, sc, C, cs, counter, chunk, err);
     return cudaGetLastError();
   }
@@ -696,6 +709,126 @@ struct ConfigureRun {
 };
 
 }  // namespace
+
+double arm_reach_bound(const RobotDev& rb) {
+  double reach = 0.0, offset = 0.0;
+  for (int i = 0; i < rb.dof; ++i) {
+    reach += std::fabs(static_cast<double>(rb.a[i])) + std::fabs(static_cast<double>(rb.d[i]));
+    const int stride = rb.spl > 4 || rb.uniform_r == 0 ? kMaxSpl : 4;
+    for (int k = 0; k < rb.spl; ++k) {
+      const float4 p = rb.sph[i * stride + k];
+      offset = std::fmax(offset, std::sqrt(double(p.x) * p.x + double(p.y) * p.y + double(p.z) * p.z));
+    }
+  }
+  return reach + offset;
+}
+
+int build_prefilter_table(const float* spheres, int n_s, const float* boxes, int n_b, float r, double reach,
+                          float4* out) {
+  const int n = n_s + n_b;
+  if (n == 0) return 0;
+  // bound of the obstacle centres and radii, for the rounding-error margin
+  double bo = 0.0, rmax = 0.0;
+  std::vector<double> cx(n), cy(n), cz(n), R(n);
+  for (int o = 0; o < n_s; ++o) {
+    const float* s = spheres + 4 * o;
+    cx[o] = s[0];
+    cy[o] = s[1];
+    cz[o] = s[2];
+    R[o] = double(s[3]) + double(r);
+  }
+  for (int o = 0; o < n_b; ++o) {
+    const float* b = boxes + 6 * o;
+    const float c0 = 0.5f * (b[0] + b[3]), c1 = 0.5f * (b[1] + b[4]), c2 = 0.5f * (b[2] + b[5]);
+    const float h0 = 0.5f * (b[3] - b[0]), h1 = 0.5f * (b[4] - b[1]), h2 = 0.5f * (b[5] - b[2]);
+    cx[n_s + o] = c0;
+    cy[n_s + o] = c1;
+    cz[n_s + o] = c2;
+    // enclosing ball of the box as the kernel sees it (float centre and half extents), enlarged by a hair
+    R[n_s + o] = std::sqrt(double(h0) * h0 + double(h1) * h1 + double(h2) * h2) * (1.0 + 1e-6) + 1e-7 + double(r);
+  }
+  for (int o = 0; o < n; ++o) {
+    bo = std::fmax(bo, std::sqrt(cx[o] * cx[o] + cy[o] * cy[o] + cz[o] * cz[o]));
+    rmax = std::fmax(rmax, R[o]);
+  }
+  // float32 error of |c|^2 + a.c + k is below 8 * 2^-24 * ((|c| + |o|)^2 + R^2); keep 100x of it
+  const double err = 8.0 * std::ldexp(1.0, -24) * ((reach + bo) * (reach + bo) + rmax * rmax + reach * reach);
+  const double margin = std::fmax(1e-3, 100.0 * err);
+  const int pairs = (n + 1) / 2;
+  for (int p = 0; p < pairs; ++p) {
+    float ax[2], ay[2], az[2], kk[2];
+    for (int h = 0; h < 2; ++h) {
+      const int o = 2 * p + h;
+      if (o < n) {
+        ax[h] = static_cast<float>(-2.0 * cx[o]);
+        ay[h] = static_cast<float>(-2.0 * cy[o]);
+        az[h] = static_cast<float>(-2.0 * cz[o]);
+        kk[h] = static_cast<float>(cx[o] * cx[o] + cy[o] * cy[o] + cz[o] * cz[o] - R[o] * R[o] - margin);
+      } else {  // padding: never flags
+        ax[h] = ay[h] = az[h] = 0.0f;
+        kk[h] = 1e30f;
+      }
+    }
+    out[2 * p] = make_float4(ax[0], ax[1], ay[0], ay[1]);
+    out[2 * p + 1] = make_float4(az[0], az[1], kk[0], kk[1]);
+  }
+  return pairs;
+}
+
+int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n_b, float r, double reach,
+                        float4* out, SceneDev* sc) {
+  const int n_sp = (n_s + 1) / 2, n_bp = (n_b + 1) / 2;
+  const float far = 1e18f;
+  for (int p = 0; p < n_sp; ++p) {
+    float v[2][4];
+    for (int h = 0; h < 2; ++h) {
+      const int o = 2 * p + h;
+      if (o < n_s) {
+        const float* q = spheres + 4 * o;
+        const float rr = q[3] + r;
+        v[h][0] = -q[0];
+        v[h][1] = -q[1];
+        v[h][2] = -q[2];
+        v[h][3] = -(rr * rr);
+      } else {
+        v[h][0] = v[h][1] = v[h][2] = -far;
+        v[h][3] = 0.0f;
+      }
+    }
+    out[2 * p] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+    out[2 * p + 1] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+  }
+  float4* bo = out + 2 * n_sp;
+  for (int p = 0; p < n_bp; ++p) {
+    float v[2][6];
+    for (int h = 0; h < 2; ++h) {
+      const int o = 2 * p + h;
+      if (o < n_b) {
+        const float* b = boxes + 6 * o;
+        v[h][0] = -(0.5f * (b[0] + b[3]));
+        v[h][1] = -(0.5f * (b[1] + b[4]));
+        v[h][2] = -(0.5f * (b[2] + b[5]));
+        v[h][3] = -(0.5f * (b[3] - b[0]));
+        v[h][4] = -(0.5f * (b[4] - b[1]));
+        v[h][5] = -(0.5f * (b[5] - b[2]));
+      } else {
+        v[h][0] = v[h][1] = v[h][2] = -far;
+        v[h][3] = v[h][4] = v[h][5] = 0.0f;
+      }
+    }
+    bo[3 * p] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+    bo[3 * p + 1] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+    bo[3 * p + 2] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
+  }
+  const int n_pp = build_prefilter_table(spheres, n_s, boxes, n_b, r, reach, bo + 3 * n_bp);
+  sc->n_s = n_s;
+  sc->n_b = n_b;
+  sc->packed = 1;
+  sc->n_sp = n_sp;
+  sc->n_bp = n_bp;
+  sc->n_pairs = n_pp;
+  return 2 * n_sp + 3 * n_bp + 2 * n_pp;
+}
 
 cudaError_t configure_kernels(int smem_max) {
   cudaError_t e;

@@ -27,15 +27,38 @@ __host__ __device__ inline int layer_size(const GraphDev& g, int layer) {
   return (layer == 0 || layer == g.L + 1) ? 1 : g.M;
 }
 
+// Obstacle table in device memory (staged whole into shared memory).
+//  scalar layout (point robot, generic arm): n_s sphere float4, then 2 n_b box float4;
+//  packed layout (uniform-radius 6/7-joint arms): 2 n_sp sphere-pair float4,
+//  3 n_bp box-pair float4, 2 n_pairs prefilter float4 (see gtmp_device.cuh).
 struct SceneDev {
-  const float4* obs;   // n_s sphere float4 followed by 2 * n_b box float4
-  int n_s, n_b;
+  const float4* obs;
+  int n_s, n_b;        // obstacle counts
+  int packed;          // 1 = packed layout
+  int n_sp, n_bp;      // packed: sphere pairs, box pairs
+  int n_pairs;         // packed: prefilter pairs
 };
+
+__host__ __device__ inline int scene_float4s(const SceneDev& s) {
+  return s.packed ? 2 * s.n_sp + 3 * s.n_bp + 2 * s.n_pairs : s.n_s + 2 * s.n_b;
+}
 
 enum EvalMode { kEvalEarlyExit = 0, kEvalFull = 1 };
 
 // Variant selector for the robot-specialised kernels.
 enum RobotVariant { kVarPoint = 0, kVarArm6x4 = 1, kVarArm7x4 = 2, kVarArmGeneric = 3 };
+
+// Host: tables of the uniform-radius arm kernels (see gtmp_device.cuh).
+// Prefilter: out receives 2 * pairs float4 (pairs = ceil((n_s + n_b) / 2));
+// `reach` bounds |c| for every robot-sphere centre.  Returns the pair count.
+int build_prefilter_table(const float* spheres, int n_s, const float* boxes, int n_b, float r, double reach,
+                          float4* out);
+// Packed exact + prefilter tables; fills sc's counts (not sc.obs) and returns
+// the float4 count written to out (capacity 3 * (n_s + n_b) + 8 float4).
+int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n_b, float r, double reach,
+                        float4* out, SceneDev* sc);
+// Host: a bound on |c| over all robot-sphere centres of a DH arm.
+double arm_reach_bound(const RobotDev& rb);
 
 cudaError_t configure_kernels(int smem_max);
 cudaError_t launch_sample_uniform(const GraphDev& g, const float* lo, const float* hi, int dof,

@@ -149,7 +149,9 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
 
   // ---- scratch layout and the size limit
   const size_t verts = static_cast<size_t>(L + 2) * M;
-  const int n4 = n_s + 2 * n_b;
+  const bool packed = variant == kVarArm6x4 || variant == kVarArm7x4;
+  // float4 count of the obstacle table: packed pair tables + prefilter, or the scalar table
+  const int n4 = packed ? 2 * ((n_s + 1) / 2) + 3 * ((n_b + 1) / 2) + 2 * ((n_s + n_b + 1) / 2) : n_s + 2 * n_b;
   size_t off = 0;
   const size_t off_err = off;
   off = align256(off + sizeof(int));
@@ -169,24 +171,33 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
                   M, L, dof, off, kNoallocScratchBytes);
 
   // ---- host-side tables on the stack (no heap, no device allocation)
-  float4 obs[2 * kNoallocMaxObstacles];
-  for (int o = 0; o < n_s; ++o) {
-    const float* s = spheres + 4 * o;
-    if (!(s[3] >= 0.0f)) return report(err_msg, err_msg_len, bad, "negative sphere radius");
-    float w = s[3];
-    if (rb.uniform_r) {
-      const float rr = s[3] + rb.r_uniform;
-      w = rr * rr;
-    }
-    obs[o] = make_float4(s[0], s[1], s[2], w);
-  }
-  for (int o = 0; o < n_b; ++o) {
-    const float* b = boxes + 6 * o;
+  float4 obs[3 * kNoallocMaxObstacles + 8];
+  SceneDev sc{};
+  for (int o = 0; o < n_s; ++o)
+    if (!(spheres[4 * o + 3] >= 0.0f)) return report(err_msg, err_msg_len, bad, "negative sphere radius");
+  for (int o = 0; o < n_b; ++o)
     for (int k = 0; k < 3; ++k)
-      if (!(b[3 + k] >= b[k])) return report(err_msg, err_msg_len, bad, "box with hi < lo");
-    obs[n_s + 2 * o] = make_float4(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]),
-                                   0.5f * (b[3] - b[0]));
-    obs[n_s + 2 * o + 1] = make_float4(0.5f * (b[4] - b[1]), 0.5f * (b[5] - b[2]), 0.0f, 0.0f);
+      if (!(boxes[6 * o + 3 + k] >= boxes[6 * o + k])) return report(err_msg, err_msg_len, bad, "box with hi < lo");
+  if (packed) {
+    build_packed_tables(spheres, n_s, boxes, n_b, rb.r_uniform, arm_reach_bound(rb), obs, &sc);
+  } else {
+    for (int o = 0; o < n_s; ++o) {
+      const float* s = spheres + 4 * o;
+      float w = s[3];
+      if (rb.uniform_r) {
+        const float rr = s[3] + rb.r_uniform;
+        w = rr * rr;
+      }
+      obs[o] = make_float4(s[0], s[1], s[2], w);
+    }
+    for (int o = 0; o < n_b; ++o) {
+      const float* b = boxes + 6 * o;
+      obs[n_s + 2 * o] = make_float4(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]),
+                                     0.5f * (b[3] - b[0]));
+      obs[n_s + 2 * o + 1] = make_float4(0.5f * (b[4] - b[1]), 0.5f * (b[5] - b[2]), 0.0f, 0.0f);
+    }
+    sc.n_s = n_s;
+    sc.n_b = n_b;
   }
   float ends[2][kMaxDof] = {};
   for (int k = 0; k < dof; ++k) {
@@ -218,7 +229,7 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
   g.dp = dp;
   g.H = H;
   g.max_edge_len = max_edge_len;
-  const SceneDev sc{d_obs, n_s, n_b};
+  sc.obs = d_obs;
 
 #define NA_TRY(expr)                                                                                     \
   do {                                                                                                   \
