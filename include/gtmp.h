@@ -249,6 +249,60 @@ GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, const float* sp
                                         float max_edge_len, void* cuda_stream, int32_t* dev_path, float* dev_cost,
                                         int32_t* dev_status, char* err_msg, int32_t err_msg_len);
 
+/* ---------------------------------------------------------------------------
+ * Batched planning (serving pattern; the paper plans one query at a time):
+ * n independent problems, each gtmp of Alg. 1 with its own robot, obstacles,
+ * endpoints, M, L and Philox seed, solved by one persistent launch.  Problem
+ * p's samples are those gtmp_sample_layers(seed_p) draws, and its result is
+ * the one gtmp_solve gives for that problem (same kernels and tie rule).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  gtmp_robot robot;          /* host pointers, copied at create */
+  const float* spheres;      /* host [n_s][4] */
+  int32_t n_s;
+  const float* boxes;        /* host [n_b][6] */
+  int32_t n_b;
+  const float* q_start;      /* host [dof] */
+  const float* q_goal;       /* host [dof] */
+  int32_t M;                 /* samples per layer, 1..16384 */
+  int32_t L;                 /* sample layers, 1..64 */
+  uint64_t seed;             /* Philox seed of this problem's samples */
+} gtmp_problem;
+
+typedef struct gtmp_batch gtmp_batch;
+
+/* Copy n problems (H waypoints per edge for all) to the device and build the
+ * work list (items of rows ordered by distance from the goal layer). */
+GTMP_API gtmp_status gtmp_batch_create(const gtmp_problem* problems, int32_t n, int32_t H, void* cuda_stream,
+                                       gtmp_batch** out);
+GTMP_API gtmp_status gtmp_batch_destroy(gtmp_batch* b);
+GTMP_API const char* gtmp_batch_last_error(const gtmp_batch* b);
+GTMP_API gtmp_status gtmp_batch_set_stream(gtmp_batch* b, void* cuda_stream);
+
+/* L_max = max L over problems; nominal_checks = sum over problems of
+ * H (2M + (L-1) M^2); work_items = items in the current work list. */
+GTMP_API gtmp_status gtmp_batch_info(const gtmp_batch* b, int32_t* L_max, double* nominal_checks,
+                                     int32_t* work_items);
+
+/* Sample, label and solve all problems: dev_paths device [n][L_max] int32
+ * (problem p's layer indices in columns 0..L_p-1, -1 elsewhere or when
+ * infeasible), dev_costs device [n] float32 (+inf when infeasible).  Enqueues
+ * five kernels (one persistent) and a memset on the batch stream; no host
+ * synchronisation, so the call can be captured in a CUDA graph.  Every
+ * device-side dependency wait is bounded (about 2 s); a wait that gives up
+ * sets the error word that gtmp_batch_synchronize reports. */
+GTMP_API gtmp_status gtmp_batch_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs);
+GTMP_API gtmp_status gtmp_batch_synchronize(gtmp_batch* b);
+
+/* Tiling of the work list: about target_edges candidate edges per item, and
+ * chunk columns per warp claim.  gtmp_batch_autotune times every pair of a
+ * small grid of tilings (repeats solves each, into the given buffers), keeps
+ * the fastest and returns its time per solve in *best_ms (host, optional). */
+GTMP_API gtmp_status gtmp_batch_set_tiling(gtmp_batch* b, int32_t target_edges, int32_t chunk);
+GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t* target_edges, int32_t* chunk);
+GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t* dev_paths, float* dev_costs,
+                                         float* best_ms);
+
 /* Active samples per layer of graph 0 (after sample/set/expand). */
 GTMP_API gtmp_status gtmp_get_M(const gtmp_ctx* ctx, int32_t* M);
 

@@ -53,6 +53,12 @@ _lib = None
 _vp, _i32, _u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
 _fp = ctypes.POINTER(ctypes.c_float)
 
+
+class GtmpProblem(ctypes.Structure):
+    _fields_ = [("robot", GtmpRobot), ("spheres", _fp), ("n_s", ctypes.c_int32), ("boxes", _fp),
+                ("n_b", ctypes.c_int32), ("q_start", _fp), ("q_goal", _fp), ("M", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
 _SIGNATURES = {
     "gtmp_create": [ctypes.POINTER(GtmpRobot), ctypes.POINTER(GtmpParams), _vp, ctypes.POINTER(_vp)],
     "gtmp_destroy": [_vp],
@@ -73,6 +79,15 @@ _SIGNATURES = {
     "gtmp_get_M": [_vp, ctypes.POINTER(_i32)],
     "gtmp_profile_enable": [_vp, _i32],
     "gtmp_profile_read": [_vp, ctypes.POINTER(GtmpProfile)],
+    "gtmp_batch_create": [ctypes.POINTER(GtmpProblem), _i32, _i32, _vp, ctypes.POINTER(_vp)],
+    "gtmp_batch_destroy": [_vp],
+    "gtmp_batch_set_stream": [_vp, _vp],
+    "gtmp_batch_info": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32)],
+    "gtmp_batch_solve": [_vp, _vp, _vp],
+    "gtmp_batch_synchronize": [_vp],
+    "gtmp_batch_set_tiling": [_vp, _i32, _i32],
+    "gtmp_batch_get_tiling": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
+    "gtmp_batch_autotune": [_vp, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_float)],
     "gtmp_solve_noalloc": [ctypes.POINTER(GtmpRobot), _fp, _i32, _fp, _i32, _fp, _fp, _vp, _i32, _i32, _i32,
                            ctypes.c_float, _vp, _vp, _vp, _vp, ctypes.c_char_p, _i32],
 }
@@ -92,6 +107,8 @@ def lib() -> ctypes.CDLL:
             f.restype = ctypes.c_int
         L.gtmp_last_error.argtypes = [_vp]
         L.gtmp_last_error.restype = ctypes.c_char_p
+        L.gtmp_batch_last_error.argtypes = [_vp]
+        L.gtmp_batch_last_error.restype = ctypes.c_char_p
         L.gtmp_status_string.argtypes = [ctypes.c_int]
         L.gtmp_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -347,3 +364,106 @@ class Planner:
 
     def synchronize(self):
         gtmp_synchronize(self.ctx)
+
+
+# ---------------------------------------------------------------------------
+# batched planning
+# ---------------------------------------------------------------------------
+
+def _bcheck(b, status):
+    if status != GTMP_OK:
+        msg = lib().gtmp_batch_last_error(b).decode() if b else ""
+        raise GtmpError(status, msg)
+
+
+def gtmp_batch_create(problems, H, stream=None):
+    """problems: sequence of (scenes.Scene, M, L, seed)."""
+    arr = (GtmpProblem * len(problems))()
+    keep = []
+    for k, (sc, M, L, seed) in enumerate(problems):
+        rs, kr = robot_struct(sc.robot)
+        sph = _f32(sc.spheres).reshape(-1, 4)
+        box = _f32(sc.boxes).reshape(-1, 6)
+        a, g = _f32(sc.q_start), _f32(sc.q_goal)
+        keep.append((kr, sph, box, a, g))
+        arr[k] = GtmpProblem(rs, _ptr(sph), sph.shape[0], _ptr(box), box.shape[0], _ptr(a), _ptr(g), M, L, seed)
+    out = _vp()
+    st = stream if stream is not None else _stream()
+    status = lib().gtmp_batch_create(arr, len(problems), H, st, ctypes.byref(out))
+    if status != GTMP_OK:
+        raise GtmpError(status, "gtmp_batch_create rejected its arguments or the device")
+    return out
+
+
+def gtmp_batch_destroy(b):
+    _bcheck(None, lib().gtmp_batch_destroy(b))
+
+
+def gtmp_batch_set_stream(b, stream=None):
+    _bcheck(b, lib().gtmp_batch_set_stream(b, stream if stream is not None else _stream()))
+
+
+def gtmp_batch_info(b):
+    L_max, checks, items = _i32(), ctypes.c_double(), _i32()
+    _bcheck(b, lib().gtmp_batch_info(b, ctypes.byref(L_max), ctypes.byref(checks), ctypes.byref(items)))
+    return L_max.value, checks.value, items.value
+
+
+def gtmp_batch_solve(b, dev_paths, dev_costs):
+    import torch
+    _bcheck(b, lib().gtmp_batch_solve(b, _dev(dev_paths, torch.int32), _dev(dev_costs, torch.float32)))
+
+
+def gtmp_batch_synchronize(b):
+    _bcheck(b, lib().gtmp_batch_synchronize(b))
+
+
+def gtmp_batch_set_tiling(b, target_edges, chunk):
+    _bcheck(b, lib().gtmp_batch_set_tiling(b, target_edges, chunk))
+
+
+def gtmp_batch_get_tiling(b):
+    t, c = _i32(), _i32()
+    _bcheck(b, lib().gtmp_batch_get_tiling(b, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+def gtmp_batch_autotune(b, repeats, dev_paths, dev_costs):
+    import torch
+    ms = ctypes.c_float()
+    _bcheck(b, lib().gtmp_batch_autotune(b, repeats, _dev(dev_paths, torch.int32), _dev(dev_costs, torch.float32),
+                                         ctypes.byref(ms)))
+    return ms.value
+
+
+class Batch:
+    """Many independent problems solved by one persistent launch."""
+
+    def __init__(self, problems, H):
+        import torch
+        self.n = len(problems)
+        self.handle = gtmp_batch_create(problems, H)
+        self.L_max, self.nominal_checks, self.work_items = gtmp_batch_info(self.handle)
+        self.paths = torch.empty((self.n, self.L_max), dtype=torch.int32, device="cuda")
+        self.costs = torch.empty(self.n, dtype=torch.float32, device="cuda")
+
+    def solve(self):
+        gtmp_batch_solve(self.handle, self.paths, self.costs)
+        return self.paths, self.costs
+
+    def autotune(self, repeats=2):
+        return gtmp_batch_autotune(self.handle, repeats, self.paths, self.costs)
+
+    def synchronize(self):
+        gtmp_batch_synchronize(self.handle)
+
+    def close(self):
+        if self.handle:
+            gtmp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

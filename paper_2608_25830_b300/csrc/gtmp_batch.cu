@@ -1,0 +1,679 @@
+// Batched planning: many independent layered graphs (different robots, M, L,
+// obstacle sets) solved by one persistent launch.
+//
+// Each problem is Alg. 1 gtmp with the straight-line planner, exactly as
+// gtmp_solve runs it (same samples for the same seed, same per-edge device
+// code, same tie rule), so every problem's result equals its single-problem
+// solve.  The persistent kernel serves a work list of (problem, depth,
+// block of rows) items ordered by depth (depth 0 = the transition into the
+// goal, depth L_p = the start row); a CTA takes the next item from a global
+// counter, waits until every item of the previous depth of the same problem
+// has finished, and realises its rows with the warp-per-edge fused step.
+// Because items are handed out in depth order, an item only ever waits for
+// items that were handed out before it to CTAs that are already running, so
+// the queue cannot deadlock; every wait is nevertheless bounded in time and
+// sets the error word when it gives up.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/gtmp.h"
+#include "gtmp_edge.cuh"
+
+using namespace gtmp;
+
+namespace gtmp_batch_impl {
+
+struct ProblemDev {
+  GraphDev g;          // R = 1, M_stride = M
+  SceneDev sc;         // obs points into the batch obstacle buffer
+  int variant;
+  int robot;           // index into the robot array
+  int dof;
+  int need_base;       // offset of this problem's per-depth item counts / done counters
+  unsigned long long seed;
+  float lo[kMaxDof], hi[kMaxDof];
+};
+
+struct WorkItem {
+  int p, depth, row0, rows;
+};
+
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// per-problem set-up kernels: grid.y = problem
+// ---------------------------------------------------------------------------
+__global__ void batch_init_kernel(const ProblemDev* probs) {
+  const ProblemDev& P = probs[blockIdx.y];
+  const GraphDev& g = P.g;
+  const long long n = static_cast<long long>(g.L + 2) * g.M_stride;
+  for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int layer = static_cast<int>(t / g.M_stride);
+    const int i = static_cast<int>(t % g.M_stride);
+    g.keys[t] = (layer == g.L + 1 && i == 0) ? make_key(0.0f, 0u) : kEmptyKey;
+  }
+}
+
+// Alg. 1 uniform sampling, the rule of gtmp_sample_layers (restart 0)
+__global__ void batch_sample_kernel(const ProblemDev* probs) {
+  const ProblemDev& P = probs[blockIdx.y];
+  const GraphDev& g = P.g;
+  const long long n = static_cast<long long>(g.L) * g.M;
+  const uint2 key = seed_key(P.seed);
+  for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(t % g.M);
+    const int l = static_cast<int>(t / g.M);
+    float* out = g.Q + vidx(g, 0, l + 1, i) * g.dp;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (int k = 0; k < g.dp; ++k) {
+      if (k >= P.dof) {
+        out[k] = 0.0f;
+        continue;
+      }
+      if ((k & 3) == 0)
+        w = philox4x32_10(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(l), 0u,
+                                     (kTagUniform << 24) | (k >> 2)),
+                          key);
+      out[k] = __fmaf_rn(word_to_unit(word_of(w, k)), __fsub_rn(P.hi[k], P.lo[k]), P.lo[k]);
+    }
+  }
+}
+
+template <int VAR>
+__device__ __forceinline__ bool vertex_collides(const float* p, int dp, const RobotDev& rb, const float4* s_obs,
+                                                const SceneDev& sc) {
+  constexpr int DP = Var<VAR>::kDp;
+  float q[DP];
+  load_vertex<DP>(q, p, dp);
+  return config_collides<VAR, false, false>(q, true, rb, s_obs, sc);
+}
+
+__global__ void __launch_bounds__(kThreads) batch_labels_kernel(const ProblemDev* probs, const RobotDev* robots) {
+  __shared__ RobotDev s_rb;
+  extern __shared__ __align__(16) float4 s_obs[];
+  const ProblemDev& P = probs[blockIdx.y];
+  const GraphDev& g = P.g;
+  {
+    const int* src = reinterpret_cast<const int*>(robots + P.robot);
+    int* dst = reinterpret_cast<int*>(&s_rb);
+    for (int k = threadIdx.x; k < static_cast<int>(sizeof(RobotDev) / 4); k += blockDim.x) dst[k] = src[k];
+  }
+  stage_obstacles_plain(s_obs, P.sc.obs, scene_float4s(P.sc));
+  __syncthreads();
+  const long long n = static_cast<long long>(g.L + 2) * g.M_stride;
+  for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int layer = static_cast<int>(t / g.M_stride);
+    const int i = static_cast<int>(t % g.M_stride);
+    if (i >= layer_size(g, layer)) continue;
+    const float* q = g.Q + vidx(g, 0, layer, i) * g.dp;
+    bool hit;
+    switch (P.variant) {
+      case kVarPoint: hit = vertex_collides<kVarPoint>(q, g.dp, s_rb, s_obs, P.sc); break;
+      case kVarArm6x4: hit = vertex_collides<kVarArm6x4>(q, g.dp, s_rb, s_obs, P.sc); break;
+      case kVarArm7x4: hit = vertex_collides<kVarArm7x4>(q, g.dp, s_rb, s_obs, P.sc); break;
+      default: hit = vertex_collides<kVarArmGeneric>(q, g.dp, s_rb, s_obs, P.sc); break;
+    }
+    g.vflag[vidx(g, 0, layer, i)] = hit ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the persistent kernel
+// ---------------------------------------------------------------------------
+template <int VAR>
+__device__ __forceinline__ void item_rows(const GraphDev g, const SceneDev sc, int layer, int row0, int rows,
+                                          int chunk, const float* s_V, const RobotDev& rb, const float4* s_obs,
+                                          int* s_next) {
+  const int n_cols = layer_size(g, layer + 1);
+  const int cpr = (n_cols + chunk - 1) / chunk;
+  const int n_chunks = rows * cpr;
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(s_next, 1);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= n_chunks) break;
+    const int i = row0 + c / cpr;
+    const int j0 = (c % cpr) * chunk;
+    const int j1 = min(j0 + chunk, n_cols);
+    const unsigned long long best = row_chunk_best<VAR, false>(g, 0, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
+    if (lane == 0 && best != kEmptyKey) atomicMin(&g.keys[vidx(g, 0, layer, i)], best);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
+    batch_persistent_kernel(const ProblemDev* __restrict__ probs, const RobotDev* __restrict__ robots,
+                            const WorkItem* __restrict__ items, int n_items, const int* __restrict__ need,
+                            int* done, int* next_item, int chunk, int* err) {
+  __shared__ RobotDev s_rb;
+  __shared__ int s_item, s_next, s_ok;
+  extern __shared__ __align__(16) float4 smem[];
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(next_item, 1);
+      s_next = 0;
+    }
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const WorkItem w = items[it];
+    const ProblemDev& P = probs[w.p];
+    const int layer = P.g.L - w.depth;
+    // dependency: every item of depth - 1 of this problem has finished
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      if (w.depth > 0) {
+        const int* cnt = done + P.need_base + w.depth - 1;
+        const int want = need[P.need_base + w.depth - 1];
+        const long long t0 = clock64();
+        while (ld_acquire(cnt) < want) {
+          if (*reinterpret_cast<volatile int*>(err) != 0 || clock64() - t0 > kWaitCycles) {
+            atomicOr(err, kErrWaitTimeout);
+            ok = 0;
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) continue;  // the item is abandoned; the error word reports it
+    // stage the robot, the obstacles and the column layer's cost-to-go
+    {
+      const int* src = reinterpret_cast<const int*>(robots + P.robot);
+      int* dst = reinterpret_cast<int*>(&s_rb);
+      for (int k = threadIdx.x; k < static_cast<int>(sizeof(RobotDev) / 4); k += blockDim.x) dst[k] = src[k];
+    }
+    const int n4 = scene_float4s(P.sc);
+    stage_obstacles_plain(smem, P.sc.obs, n4);
+    float* s_V = reinterpret_cast<float*>(smem + n4);
+    const int n_cols = layer_size(P.g, layer + 1);
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) {
+      const size_t v = vidx(P.g, 0, layer + 1, j);
+      s_V[j] = P.g.vflag[v] ? kInf : key_value(__ldcg(P.g.keys + v));
+    }
+    __syncthreads();
+    const GraphDev g = P.g;
+    const SceneDev sc = P.sc;
+    switch (P.variant) {
+      case kVarPoint: item_rows<kVarPoint>(g, sc, layer, w.row0, w.rows, chunk, s_V, s_rb, smem, &s_next); break;
+      case kVarArm6x4: item_rows<kVarArm6x4>(g, sc, layer, w.row0, w.rows, chunk, s_V, s_rb, smem, &s_next); break;
+      case kVarArm7x4: item_rows<kVarArm7x4>(g, sc, layer, w.row0, w.rows, chunk, s_V, s_rb, smem, &s_next); break;
+      default: item_rows<kVarArmGeneric>(g, sc, layer, w.row0, w.rows, chunk, s_V, s_rb, smem, &s_next); break;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(done + P.need_base + w.depth, 1);
+  }
+}
+
+__global__ void batch_paths_kernel(const ProblemDev* probs, int n, int L_max, int32_t* paths, float* costs) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const GraphDev& g = probs[p].g;
+  int32_t* out = paths + static_cast<size_t>(p) * L_max;
+  for (int l = 0; l < L_max; ++l) out[l] = -1;
+  const unsigned long long k0 = g.keys[vidx(g, 0, 0, 0)];
+  if (k0 == kEmptyKey) {
+    costs[p] = kInf;
+    return;
+  }
+  costs[p] = key_value(k0);
+  int i = key_index(k0);
+  for (int l = 1; l <= g.L; ++l) {
+    out[l - 1] = i;
+    if (l < g.L) i = key_index(g.keys[vidx(g, 0, l, i)]);
+  }
+}
+
+bool finite_all(const float* v, size_t n) {
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(v[k])) return false;
+  return true;
+}
+
+}  // namespace gtmp_batch_impl
+
+using namespace gtmp_batch_impl;
+
+struct gtmp_batch {
+  int n = 0, H = 0, L_max = 0, M_max = 0, obs4_max = 0;
+  int num_sms = 148, bps = 1;
+  cudaStream_t stream = nullptr;
+  // host copies
+  std::vector<ProblemDev> probs;
+  std::vector<RobotDev> robots;
+  std::vector<int> need;  // items per (problem, depth)
+  double nominal_checks = 0.0;
+  // tiling (autotuned)
+  int target_edges = 8192;
+  int chunk = 16;
+  int n_items = 0;
+  // device memory
+  ProblemDev* d_probs = nullptr;
+  RobotDev* d_robots = nullptr;
+  WorkItem* d_items = nullptr;
+  int* d_need = nullptr;
+  int* d_done = nullptr;  // [need.size()] done counters followed by the item counter
+  int* d_err = nullptr;
+  float4* d_obs = nullptr;
+  float* d_Q = nullptr;
+  uint8_t* d_vflag = nullptr;
+  unsigned long long* d_keys = nullptr;
+  std::string last_error;
+};
+
+namespace gtmp_batch_impl {
+
+gtmp_status bfail(gtmp_batch* b, gtmp_status s, const char* fmt, ...) {
+  if (b) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    b->last_error = buf;
+  }
+  return s;
+}
+
+#define BATCH_TRY(b, expr)                                                                               \
+  do {                                                                                                   \
+    cudaError_t e_ = (expr);                                                                             \
+    if (e_ != cudaSuccess)                                                                               \
+      return bfail((b), e_ == cudaErrorMemoryAllocation ? GTMP_ERR_OOM : GTMP_ERR_CUDA, "%s: %s", #expr, \
+                   cudaGetErrorString(e_));                                                              \
+  } while (0)
+
+// robot constants and kernel variant, as gtmp_create chooses them
+bool make_robot(const gtmp_robot& r, RobotDev* rb, int* variant, int* dp) {
+  *rb = RobotDev{};
+  rb->kind = r.kind;
+  rb->dof = r.dof;
+  rb->point_radius = r.point_radius;
+  if (r.kind == GTMP_ROBOT_POINT) {
+    if (r.dof < 1 || r.dof > 3 || !(r.point_radius >= 0.0f) || !std::isfinite(r.point_radius)) return false;
+    rb->spl = 1;
+    rb->uniform_r = 1;
+    rb->r_uniform = r.point_radius;
+    *variant = kVarPoint;
+    *dp = 4;
+    return true;
+  }
+  if (r.kind != GTMP_ROBOT_DH_ARM || r.dof < 1 || r.dof > kMaxDof || !r.dh || !r.link_spheres ||
+      r.spheres_per_link < 1 || r.spheres_per_link > kMaxSpl)
+    return false;
+  const int spl = r.spheres_per_link;
+  if (!finite_all(r.dh, static_cast<size_t>(r.dof) * 4) ||
+      !finite_all(r.link_spheres, static_cast<size_t>(r.dof) * spl * 4))
+    return false;
+  bool uniform = true;
+  const float r0 = r.link_spheres[3];
+  for (int s = 0; s < r.dof * spl; ++s) {
+    if (!(r.link_spheres[s * 4 + 3] > 0.0f)) return false;
+    if (r.link_spheres[s * 4 + 3] != r0) uniform = false;
+  }
+  *variant = (uniform && spl == 4 && r.dof == 6) ? kVarArm6x4
+             : (uniform && spl == 4 && r.dof == 7) ? kVarArm7x4
+                                                   : kVarArmGeneric;
+  const int stride = *variant == kVarArmGeneric ? kMaxSpl : 4;
+  *dp = *variant == kVarArmGeneric ? kMaxDof : 8;
+  rb->spl = spl;
+  rb->uniform_r = *variant == kVarArmGeneric ? 0 : 1;
+  rb->r_uniform = r0;
+  for (int i = 0; i < r.dof; ++i) {
+    rb->d[i] = r.dh[i * 4 + 0];
+    rb->a[i] = r.dh[i * 4 + 1];
+    rb->ca[i] = cosf(r.dh[i * 4 + 2]);
+    rb->sa[i] = sinf(r.dh[i * 4 + 2]);
+    rb->toff[i] = r.dh[i * 4 + 3];
+    for (int s = 0; s < spl; ++s) {
+      const float* ls = r.link_spheres + (static_cast<size_t>(i) * spl + s) * 4;
+      rb->sph[i * stride + s] = make_float4(ls[0], ls[1], ls[2], ls[3]);
+    }
+  }
+  return true;
+}
+
+// scalar or packed obstacle table of one problem (the layout gtmp_set_obstacles writes)
+int obstacle_table(const gtmp_problem& q, const RobotDev& rb, int variant, std::vector<float4>& out, SceneDev* sc) {
+  *sc = SceneDev{};
+  if (variant == kVarArm6x4 || variant == kVarArm7x4) {
+    out.resize(3 * static_cast<size_t>(q.n_s + q.n_b) + 8);
+    const int n4 = build_packed_tables(q.spheres, q.n_s, q.boxes, q.n_b, rb.r_uniform, arm_reach_bound(rb),
+                                       out.data(), sc);
+    out.resize(n4);
+    return n4;
+  }
+  out.resize(static_cast<size_t>(q.n_s) + 2 * static_cast<size_t>(q.n_b));
+  for (int o = 0; o < q.n_s; ++o) {
+    const float* s = q.spheres + 4 * o;
+    float w = s[3];
+    if (rb.uniform_r) {
+      const float rr = s[3] + rb.r_uniform;
+      w = rr * rr;
+    }
+    out[o] = make_float4(s[0], s[1], s[2], w);
+  }
+  for (int o = 0; o < q.n_b; ++o) {
+    const float* bx = q.boxes + 6 * o;
+    out[q.n_s + 2 * o] = make_float4(0.5f * (bx[0] + bx[3]), 0.5f * (bx[1] + bx[4]), 0.5f * (bx[2] + bx[5]),
+                                     0.5f * (bx[3] - bx[0]));
+    out[q.n_s + 2 * o + 1] = make_float4(0.5f * (bx[4] - bx[1]), 0.5f * (bx[5] - bx[2]), 0.0f, 0.0f);
+  }
+  sc->n_s = q.n_s;
+  sc->n_b = q.n_b;
+  return static_cast<int>(out.size());
+}
+
+// work list for the current tiling: items sorted by depth, then problem
+gtmp_status build_items(gtmp_batch* b) {
+  std::vector<WorkItem> items;
+  std::fill(b->need.begin(), b->need.end(), 0);
+  for (int d = 0; d <= b->L_max; ++d)
+    for (int p = 0; p < b->n; ++p) {
+      const ProblemDev& P = b->probs[p];
+      if (d > P.g.L) continue;
+      const int layer = P.g.L - d;
+      const int rows = layer_size(P.g, layer), cols = layer_size(P.g, layer + 1);
+      int per = b->target_edges / std::max(cols, 1);
+      per = std::max(1, std::min(per, rows));
+      for (int r0 = 0; r0 < rows; r0 += per) {
+        items.push_back(WorkItem{p, d, r0, std::min(per, rows - r0)});
+        b->need[P.need_base + d] += 1;
+      }
+    }
+  b->n_items = static_cast<int>(items.size());
+  cudaFree(b->d_items);
+  b->d_items = nullptr;
+  BATCH_TRY(b, cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)));
+  BATCH_TRY(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+  BATCH_TRY(b, cudaMemcpy(b->d_need, b->need.data(), b->need.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return GTMP_OK;
+}
+
+gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
+  cudaStream_t st = b->stream;
+  const size_t n_done = b->need.size() + 1;
+  BATCH_TRY(b, cudaMemsetAsync(b->d_done, 0, n_done * sizeof(int), st));
+  const int per_problem_blocks = std::max(1, std::min(64, ((b->L_max + 2) * b->M_max + kThreads - 1) / kThreads));
+  batch_init_kernel<<<dim3(per_problem_blocks, b->n), kThreads, 0, st>>>(b->d_probs);
+  BATCH_TRY(b, cudaGetLastError());
+  batch_sample_kernel<<<dim3(per_problem_blocks, b->n), kThreads, 0, st>>>(b->d_probs);
+  BATCH_TRY(b, cudaGetLastError());
+  batch_labels_kernel<<<dim3(per_problem_blocks, b->n), kThreads, b->obs4_max * sizeof(float4), st>>>(b->d_probs,
+                                                                                                    b->d_robots);
+  BATCH_TRY(b, cudaGetLastError());
+  const size_t smem = b->obs4_max * sizeof(float4) + static_cast<size_t>(b->M_max) * sizeof(float);
+  batch_persistent_kernel<<<b->num_sms * b->bps, kThreads, smem, st>>>(
+      b->d_probs, b->d_robots, b->d_items, b->n_items, b->d_need, b->d_done, b->d_done + b->need.size(), b->chunk,
+      b->d_err);
+  BATCH_TRY(b, cudaGetLastError());
+  batch_paths_kernel<<<(b->n + 127) / 128, 128, 0, st>>>(b->d_probs, b->n, b->L_max, dev_paths, dev_costs);
+  BATCH_TRY(b, cudaGetLastError());
+  return GTMP_OK;
+}
+
+}  // namespace gtmp_batch_impl
+
+extern "C" {
+
+GTMP_API gtmp_status gtmp_batch_create(const gtmp_problem* problems, int32_t n, int32_t H, void* cuda_stream,
+                                       gtmp_batch** out) {
+  if (!out || !problems || n < 1 || n > (1 << 20) || H < 2 || H > 1024) return GTMP_ERR_INVALID_ARG;
+  *out = nullptr;
+  gtmp_batch* b = new gtmp_batch();
+  b->n = n;
+  b->H = H;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->probs.resize(n);
+  b->robots.resize(n);
+  std::vector<std::vector<float4>> tables(n);
+  size_t q_floats = 0, verts = 0, obs4 = 0;
+  int need_total = 0;
+  for (int p = 0; p < n; ++p) {
+    const gtmp_problem& q = problems[p];
+    RobotDev rb;
+    int variant = 0, dp = 0;
+    if (!make_robot(q.robot, &rb, &variant, &dp) || q.M < 1 || q.M > 16384 || q.L < 1 || q.L > 64 || q.n_s < 0 ||
+        q.n_b < 0 || q.n_s + q.n_b > 4096 || (q.n_s > 0 && !q.spheres) || (q.n_b > 0 && !q.boxes) ||
+        !q.q_start || !q.q_goal || !q.robot.q_lo || !q.robot.q_hi) {
+      delete b;
+      return GTMP_ERR_INVALID_ARG;
+    }
+    const int dof = q.robot.dof;
+    bool ok = finite_all(q.robot.q_lo, dof) && finite_all(q.robot.q_hi, dof) &&
+              (q.n_s == 0 || finite_all(q.spheres, static_cast<size_t>(q.n_s) * 4)) &&
+              (q.n_b == 0 || finite_all(q.boxes, static_cast<size_t>(q.n_b) * 6));
+    for (int k = 0; ok && k < dof; ++k)
+      ok = q.robot.q_hi[k] > q.robot.q_lo[k] && std::isfinite(q.q_start[k]) && std::isfinite(q.q_goal[k]) &&
+           q.q_start[k] >= q.robot.q_lo[k] && q.q_start[k] <= q.robot.q_hi[k] && q.q_goal[k] >= q.robot.q_lo[k] &&
+           q.q_goal[k] <= q.robot.q_hi[k];
+    for (int o = 0; ok && o < q.n_s; ++o) ok = q.spheres[4 * o + 3] >= 0.0f;
+    for (int o = 0; ok && o < q.n_b; ++o)
+      for (int k = 0; k < 3; ++k) ok = ok && q.boxes[6 * o + 3 + k] >= q.boxes[6 * o + k];
+    if (!ok) {
+      delete b;
+      return GTMP_ERR_INVALID_ARG;
+    }
+    b->robots[p] = rb;
+    ProblemDev& P = b->probs[p];
+    P = ProblemDev{};
+    P.variant = variant;
+    P.robot = p;
+    P.dof = dof;
+    P.seed = q.seed;
+    for (int k = 0; k < dof; ++k) {
+      P.lo[k] = q.robot.q_lo[k];
+      P.hi[k] = q.robot.q_hi[k];
+    }
+    P.g.R = 1;
+    P.g.L = q.L;
+    P.g.M = q.M;
+    P.g.M_stride = q.M;
+    P.g.dp = dp;
+    P.g.H = H;
+    P.g.max_edge_len = INFINITY;
+    const int n4 = obstacle_table(q, rb, variant, tables[p], &P.sc);
+    // offsets (converted to pointers once the buffers exist)
+    P.g.Q = reinterpret_cast<float*>(q_floats);
+    P.g.vflag = reinterpret_cast<uint8_t*>(verts);
+    P.g.keys = reinterpret_cast<unsigned long long*>(verts);
+    P.sc.obs = reinterpret_cast<const float4*>(obs4);
+    const size_t v = static_cast<size_t>(q.L + 2) * q.M;
+    q_floats += v * dp;
+    verts += v;
+    obs4 += n4;
+    P.need_base = need_total;
+    need_total += q.L + 1;
+    b->L_max = std::max(b->L_max, q.L);
+    b->M_max = std::max(b->M_max, q.M);
+    b->obs4_max = std::max(b->obs4_max, n4);
+    b->nominal_checks += static_cast<double>(H) * (2.0 * q.M + (q.L - 1.0) * q.M * q.M);
+  }
+  b->need.assign(need_total, 0);
+  auto fail_create = [&](cudaError_t e) {
+    gtmp_batch_destroy(b);
+    return e == cudaErrorMemoryAllocation ? GTMP_ERR_OOM : GTMP_ERR_CUDA;
+  };
+  cudaError_t e = cudaSuccess;
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return fail_create(e);
+  if ((e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return fail_create(e);
+  if ((e = cudaFuncSetAttribute(batch_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024)) != cudaSuccess)
+    return fail_create(e);
+  if ((e = cudaFuncSetAttribute(batch_labels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) !=
+      cudaSuccess)
+    return fail_create(e);
+  const size_t smem = b->obs4_max * sizeof(float4) + static_cast<size_t>(b->M_max) * sizeof(float);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->bps, batch_persistent_kernel, kThreads, smem)) !=
+      cudaSuccess)
+    return fail_create(e);
+  if (b->bps < 1) b->bps = 1;
+  if ((e = cudaMalloc(&b->d_Q, std::max<size_t>(q_floats, 1) * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_vflag, std::max<size_t>(verts, 1))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_keys, std::max<size_t>(verts, 1) * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_obs, std::max<size_t>(obs4, 1) * sizeof(float4))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_probs, n * sizeof(ProblemDev))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_robots, n * sizeof(RobotDev))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_need, (need_total + 1) * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_done, (need_total + 1) * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess)
+    return fail_create(e);
+  // rebase offsets to device pointers; write endpoints and obstacle tables
+  std::vector<float4> all_obs(obs4);
+  std::vector<float> ends;
+  for (int p = 0; p < n; ++p) {
+    ProblemDev& P = b->probs[p];
+    const size_t qo = reinterpret_cast<size_t>(P.g.Q), vo = reinterpret_cast<size_t>(P.g.vflag);
+    const size_t oo = reinterpret_cast<size_t>(P.sc.obs);
+    std::copy(tables[p].begin(), tables[p].end(), all_obs.begin() + oo);
+    P.g.Q = b->d_Q + qo;
+    P.g.vflag = b->d_vflag + vo;
+    P.g.keys = b->d_keys + vo;
+    P.sc.obs = b->d_obs + oo;
+    ends.assign(P.g.dp, 0.0f);
+    for (int k = 0; k < P.dof; ++k) ends[k] = problems[p].q_start[k];
+    if ((e = cudaMemcpy(P.g.Q, ends.data(), P.g.dp * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail_create(e);
+    for (int k = 0; k < P.dof; ++k) ends[k] = problems[p].q_goal[k];
+    if ((e = cudaMemcpy(P.g.Q + static_cast<size_t>(P.g.L + 1) * P.g.M * P.g.dp, ends.data(), P.g.dp * sizeof(float),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail_create(e);
+  }
+  if ((obs4 > 0 && (e = cudaMemcpy(b->d_obs, all_obs.data(), obs4 * sizeof(float4), cudaMemcpyHostToDevice)) !=
+                       cudaSuccess) ||
+      (e = cudaMemcpy(b->d_probs, b->probs.data(), n * sizeof(ProblemDev), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_robots, b->robots.data(), n * sizeof(RobotDev), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(b->d_err, 0, sizeof(int))) != cudaSuccess)
+    return fail_create(e);
+  gtmp_status s = build_items(b);
+  if (s != GTMP_OK) {
+    gtmp_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return GTMP_OK;
+}
+
+GTMP_API gtmp_status gtmp_batch_destroy(gtmp_batch* b) {
+  if (!b) return GTMP_OK;
+  cudaStreamSynchronize(b->stream);
+  cudaFree(b->d_probs);
+  cudaFree(b->d_robots);
+  cudaFree(b->d_items);
+  cudaFree(b->d_need);
+  cudaFree(b->d_done);
+  cudaFree(b->d_err);
+  cudaFree(b->d_obs);
+  cudaFree(b->d_Q);
+  cudaFree(b->d_vflag);
+  cudaFree(b->d_keys);
+  delete b;
+  return GTMP_OK;
+}
+
+GTMP_API const char* gtmp_batch_last_error(const gtmp_batch* b) { return b ? b->last_error.c_str() : "null batch"; }
+
+GTMP_API gtmp_status gtmp_batch_set_stream(gtmp_batch* b, void* cuda_stream) {
+  if (!b) return GTMP_ERR_INVALID_ARG;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  return GTMP_OK;
+}
+
+GTMP_API gtmp_status gtmp_batch_info(const gtmp_batch* b, int32_t* L_max, double* nominal_checks,
+                                     int32_t* work_items) {
+  if (!b) return GTMP_ERR_INVALID_ARG;
+  if (L_max) *L_max = b->L_max;
+  if (nominal_checks) *nominal_checks = b->nominal_checks;
+  if (work_items) *work_items = b->n_items;
+  return GTMP_OK;
+}
+
+GTMP_API gtmp_status gtmp_batch_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
+  if (!b || !dev_paths || !dev_costs) return bfail(b, GTMP_ERR_INVALID_ARG, "NULL output");
+  return enqueue_solve(b, dev_paths, dev_costs);
+}
+
+GTMP_API gtmp_status gtmp_batch_synchronize(gtmp_batch* b) {
+  if (!b) return GTMP_ERR_INVALID_ARG;
+  BATCH_TRY(b, cudaStreamSynchronize(b->stream));
+  int err = 0;
+  BATCH_TRY(b, cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    BATCH_TRY(b, cudaMemset(b->d_err, 0, sizeof(int)));
+    return bfail(b, GTMP_ERR_TIMEOUT, "device error flags 0x%x (2 = a dependency wait timed out)", err);
+  }
+  return GTMP_OK;
+}
+
+GTMP_API gtmp_status gtmp_batch_set_tiling(gtmp_batch* b, int32_t target_edges, int32_t chunk) {
+  if (!b || target_edges < 1 || chunk < 1 || chunk > 4096) return bfail(b, GTMP_ERR_INVALID_ARG, "bad tiling");
+  BATCH_TRY(b, cudaStreamSynchronize(b->stream));
+  b->target_edges = target_edges;
+  b->chunk = chunk;
+  return build_items(b);
+}
+
+GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t* dev_paths, float* dev_costs,
+                                         float* best_ms) {
+  if (!b || repeats < 1 || !dev_paths || !dev_costs) return bfail(b, GTMP_ERR_INVALID_ARG, "bad autotune request");
+  static const int kTargets[] = {2048, 8192, 32768, 131072};
+  static const int kChunks[] = {4, 16, 64};
+  cudaEvent_t e0, e1;
+  BATCH_TRY(b, cudaEventCreate(&e0));
+  BATCH_TRY(b, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_t = b->target_edges, best_c = b->chunk;
+  gtmp_status s = GTMP_OK;
+  for (int t : kTargets) {
+    for (int c : kChunks) {
+      if ((s = gtmp_batch_set_tiling(b, t, c)) != GTMP_OK) break;
+      if ((s = enqueue_solve(b, dev_paths, dev_costs)) != GTMP_OK) break;  // warm-up
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < repeats && s == GTMP_OK; ++r) s = enqueue_solve(b, dev_paths, dev_costs);
+      cudaEventRecord(e1, b->stream);
+      if (s != GTMP_OK) break;
+      if ((s = gtmp_batch_synchronize(b)) != GTMP_OK) break;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= repeats;
+      if (ms < best) {
+        best = ms;
+        best_t = t;
+        best_c = c;
+      }
+    }
+    if (s != GTMP_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != GTMP_OK) return s;
+  if (best_ms) *best_ms = best;
+  return gtmp_batch_set_tiling(b, best_t, best_c);
+}
+
+GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t* target_edges, int32_t* chunk) {
+  if (!b) return GTMP_ERR_INVALID_ARG;
+  if (target_edges) *target_edges = b->target_edges;
+  if (chunk) *chunk = b->chunk;
+  return GTMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Device-side pieces shared by the single-problem kernels (gtmp_kernels.cu)
+// and the batched persistent solver (gtmp_batch.cu): launch constants, the
+// bounded TMA staging of obstacle tables, robot-variant traits, the per-
+// configuration collision test and the per-row chunk of the fused edge +
+// min-plus step.  Everything here has internal linkage.
+#pragma once
+
+#include "gtmp_kernels.cuh"
+
+namespace gtmp {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+// resident blocks per SM the edge kernels are compiled for (2 -> register budget 128)
+#ifndef GTMP_FUSED_MIN_BLOCKS
+#define GTMP_FUSED_MIN_BLOCKS 2
+#endif
+constexpr int kFusedMinBlocks = GTMP_FUSED_MIN_BLOCKS;
+#define kInf __int_as_float(0x7f800000)
+
+struct Box16 {
+  float lo[kMaxDof], hi[kMaxDof];
+};
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA) staging of the obstacle list into shared memory, completed on an
+// mbarrier.  Every wait is bounded; on timeout the error word is set and the
+// block skips its work after one more bounded wait for the copy in flight.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Returns false (on all threads) if the copy did not complete in time.
+__device__ bool stage_obstacles(float4* s_obs, const float4* g_obs, int n4, uint64_t* mbar_storage, int* err) {
+  const uint32_t bytes = static_cast<uint32_t>(n4) * 16u;
+  const uint32_t mbar = smem_addr(mbar_storage);
+  if (bytes == 0) return __syncthreads_and(1) != 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(s_obs)),
+        "l"(g_obs), "r"(bytes), "r"(mbar)
+        : "memory");
+  }
+  bool ok = mbar_wait_bounded(mbar, 0, 1 << 22);
+  if (!ok) {
+    atomicOr(err, kErrWaitTimeout);
+    mbar_wait_bounded(mbar, 0, 1 << 22);  // let a late copy land before the block exits
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Plain cooperative staging (used where a kernel also writes other shared data).
+__device__ void stage_obstacles_plain(float4* s_obs, const float4* g_obs, int n4) {
+  for (int k = threadIdx.x; k < n4; k += blockDim.x) s_obs[k] = g_obs[k];
+}
+
+template <int VAR>
+struct Var;
+template <>
+struct Var<kVarPoint> {
+  static constexpr bool kArm = false;
+  static constexpr int kDof = 0, kSpl = 1, kDp = 4;
+  static constexpr bool kUnif = true;
+};
+template <>
+struct Var<kVarArm6x4> {
+  static constexpr bool kArm = true;
+  static constexpr int kDof = 6, kSpl = 4, kDp = 8;
+  static constexpr bool kUnif = true;
+};
+template <>
+struct Var<kVarArm7x4> {
+  static constexpr bool kArm = true;
+  static constexpr int kDof = 7, kSpl = 4, kDp = 8;
+  static constexpr bool kUnif = true;
+};
+template <>
+struct Var<kVarArmGeneric> {
+  static constexpr bool kArm = true;
+  static constexpr int kDof = 0, kSpl = 0, kDp = kMaxDof;
+  static constexpr bool kUnif = false;
+};
+
+template <int VAR, bool WARP_EXIT, bool FULL>
+__device__ __forceinline__ bool config_collides(const float* q, bool active, const RobotDev& rb, const float4* s_obs,
+                                                const SceneDev& sc) {
+  using V = Var<VAR>;
+  if constexpr (V::kArm && V::kUnif) {
+    // uniform-radius arms: packed pair tables, then the prefilter table
+    const float4* boxp = s_obs + 2 * sc.n_sp;
+    const float4* pre = boxp + 3 * sc.n_bp;
+    return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL, true>(q, active, rb, s_obs, sc.n_sp,
+                                                                                  boxp, sc.n_bp, pre, sc.n_pairs);
+  } else if constexpr (V::kArm) {
+    return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL>(q, active, rb, s_obs, sc.n_s,
+                                                                            s_obs + sc.n_s, sc.n_b);
+  } else {
+    return point_config_collides<WARP_EXIT>(q, active, rb, s_obs, sc.n_s, s_obs + sc.n_s, sc.n_b);
+  }
+}
+
+// load a padded vertex (dp floats; dp == V::kDp for the specialised variants)
+template <int DP>
+__device__ __forceinline__ void load_vertex(float (&q)[DP], const float* p, int dp) {
+  if (DP == 4 || DP == 8) {
+#pragma unroll
+    for (int d = 0; d < DP; d += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p + d));
+      q[d] = v.x;
+      q[d + 1] = v.y;
+      q[d + 2] = v.z;
+      q[d + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < DP; ++d) q[d] = d < dp ? __ldg(p + d) : 0.0f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One warp, one row i of the transition layer -> layer + 1 of graph r, columns
+// [j0, j1): the 32 lanes carry the H-2 interior waypoints of one edge at a
+// time (endpoint labels are the vertex flags), the warp leaves an edge at its
+// first colliding link unless FULL, and the best (value, column) key of the
+// chunk is returned on every lane (kEmptyKey if no edge is realised).
+// s_V holds the column layer's cost-to-go, +inf where the vertex collides or
+// reaches no goal.
+// ---------------------------------------------------------------------------
+template <int VAR, bool FULL>
+__device__ __forceinline__ unsigned long long row_chunk_best(const GraphDev& g, int r, int layer, int i, int j0,
+                                                             int j1, const float* s_V, const RobotDev& rb,
+                                                             const float4* s_obs, const SceneDev& sc, int lane) {
+  using V = Var<VAR>;
+  constexpr int DP = V::kDp;
+  const size_t vi = vidx(g, r, layer, i);
+  const bool row_hit = g.vflag[vi] != 0;
+  unsigned long long best = kEmptyKey;
+  if (!FULL && row_hit) return best;
+  const int H = g.H;
+  const float steps = static_cast<float>(H - 1);
+  float qi[DP];
+  load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
+  for (int j = j0; j < j1; ++j) {
+    const float Vj = s_V[j];
+    if (!FULL && !(Vj < kInf)) continue;
+    float qj[DP];
+    load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp);
+    float dq[DP];
+    float s2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DP; ++d) {
+      dq[d] = __fsub_rn(qj[d], qi[d]);
+      s2 = __fmaf_rn(dq[d], dq[d], s2);
+    }
+    const float len = __fsqrt_rn(s2);
+    const bool too_long = len > g.max_edge_len;
+    if (!FULL && too_long) continue;
+    bool hit = false;
+    for (int kb = 1; kb <= H - 2; kb += 32) {
+      const int k = kb + lane;
+      const bool active = k <= H - 2;
+      const float t = __fdiv_rn(static_cast<float>(k), steps);
+      float q[DP];
+#pragma unroll
+      for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
+      hit |= config_collides<VAR, true, FULL>(q, active, rb, s_obs, sc);
+      if (!FULL && hit) break;
+    }
+    if (!hit && !too_long && !row_hit && Vj < kInf) {
+      const unsigned long long key = make_key(__fadd_rn(len, Vj), static_cast<uint32_t>(j));
+      best = key < best ? key : best;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+}  // namespace gtmp

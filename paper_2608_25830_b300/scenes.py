@@ -180,6 +180,7 @@ WORKLOADS = {
     "arm6_anytime_r64_m256_l6_h32": dict(kind="arm", dof=6, seed=0, n_obs=30, M=256, L=6, H=32, R=64),
     "arm6_ao_m64to4096_l6_h32": dict(kind="arm", dof=6, seed=0, n_obs=30, M0=64, M1=4096, L=6, H=32),
     "arm7_m4096_l8_h32_n40": dict(kind="arm", dof=7, seed=0, n_obs=40, M=4096, L=8, H=32),
+    "batched512_h32": dict(kind="batched", seed=0, n=512, H=32),
 }
 
 

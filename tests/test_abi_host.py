@@ -26,7 +26,7 @@ def test_library_builds_and_exports_every_declared_symbol():
     L = binding.lib()
     for n in names:
         assert hasattr(L, n), n
-        assert n in binding._SIGNATURES or n in ("gtmp_last_error", "gtmp_status_string"), n
+        assert n in binding._SIGNATURES or n in ("gtmp_last_error", "gtmp_status_string", "gtmp_batch_last_error"), n
 
 
 def test_status_strings():

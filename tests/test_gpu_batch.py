@@ -1,0 +1,129 @@
+"""Batched persistent solver: every problem equals its single-problem solve
+(and the oracle on small cases), under every tiling, eagerly and replayed from
+a captured CUDA graph."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_25830_b300 import binding, scenes
+
+from parity import REL, check_values, scene_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_problems():
+    probs = []
+    for k in range(4):
+        probs.append((scenes.point2d_scene(10 + k, 5 + 9 * k), [32, 97, 64, 200][k], [3, 5, 4, 2][k], 100 + k))
+    for k, (dof, M, L) in enumerate([(7, 64, 3), (7, 150, 4), (6, 96, 5), (5, 40, 3), (7, 33, 6), (6, 1, 1)]):
+        probs.append((scene_for("arm", 20 + k, dof, 12 + 5 * k), M, L, 200 + k))
+    return probs
+
+
+def _single(sc, M, L, H, seed):
+    p = binding.Planner(sc.robot, M, L, H, max_obstacles=64)
+    p.set_scene(sc)
+    p.sample_layers(seed, M)
+    path, cost = p.solve()
+    p.synchronize()
+    out = path.cpu().numpy(), float(cost.cpu()[0])
+    p.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    import torch
+    probs = _mixed_problems()
+    H = 32
+    singles = [_single(sc, M, L, H, seed) for sc, M, L, seed in probs]
+    return probs, H, singles
+
+
+def _check_against_singles(b, probs, singles):
+    paths = b.paths.cpu().numpy()
+    costs = b.costs.cpu().numpy()
+    for k, ((sc, M, L, seed), (p1, c1)) in enumerate(zip(probs, singles)):
+        assert (costs[k] == c1) or (math.isinf(costs[k]) and math.isinf(c1)), (k, costs[k], c1)
+        np.testing.assert_array_equal(paths[k, :L], p1, err_msg=f"problem {k}")
+        assert np.all(paths[k, L:] == -1)
+
+
+def test_batch_equals_single_solves(mixed):
+    probs, H, singles = mixed
+    b = binding.Batch(probs, H)
+    b.solve()
+    b.synchronize()
+    _check_against_singles(b, probs, singles)
+    assert b.L_max == max(L for _, _, L, _ in probs)
+    assert b.nominal_checks == sum(H * (2 * M + (L - 1) * M * M) for _, M, L, _ in probs)
+    b.close()
+
+
+@pytest.mark.parametrize("target,chunk", [(1, 1), (64, 3), (4096, 16), (1 << 20, 64)])
+def test_every_tiling_gives_the_same_plans(mixed, target, chunk):
+    probs, H, singles = mixed
+    b = binding.Batch(probs, H)
+    binding.gtmp_batch_set_tiling(b.handle, target, chunk)
+    b.solve()
+    b.synchronize()
+    _check_against_singles(b, probs, singles)
+    b.close()
+
+
+def test_autotune_keeps_results(mixed):
+    probs, H, singles = mixed
+    b = binding.Batch(probs, H)
+    ms = b.autotune(repeats=1)
+    assert ms > 0
+    t, c = binding.gtmp_batch_get_tiling(b.handle)
+    assert t in (2048, 8192, 32768, 131072) and c in (4, 16, 64)
+    b.solve()
+    b.synchronize()
+    _check_against_singles(b, probs, singles)
+    b.close()
+
+
+def test_graph_capture_and_replay(mixed):
+    import torch
+    probs, H, singles = mixed
+    b = binding.Batch(probs, H)
+    s = torch.cuda.Stream()
+    binding.gtmp_batch_set_stream(b.handle, ctypes.c_void_p(s.cuda_stream))
+    with torch.cuda.stream(s):
+        b.solve()                       # warm-up outside capture
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        binding.gtmp_batch_solve(b.handle, b.paths, b.costs)
+    for _ in range(2):
+        b.paths.fill_(-5)
+        b.costs.fill_(-1.0)
+        graph.replay()
+        torch.cuda.synchronize()
+        b.synchronize()
+        _check_against_singles(b, probs, singles)
+    b.close()
+
+
+def test_small_batch_matches_oracle():
+    probs = [(scenes.point2d_scene(3, 8), 24, 3, 5), (scene_for("arm", 8, 7, 20), 24, 2, 6),
+             (scene_for("arm", 9, 6, 25), 16, 3, 7)]
+    H = 16
+    b = binding.Batch(probs, H)
+    b.solve()
+    b.synchronize()
+    paths, costs = b.paths.cpu().numpy(), b.costs.cpu().numpy()
+    for k, (sc, M, L, seed) in enumerate(probs):
+        Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+        sol = oracle.solve(sc, Q, H)
+        check_values([costs[k]], [sol.cost_lo], [sol.cost_hi], f"problem {k}")
+        if math.isfinite(costs[k]):
+            total, worst = oracle.path_cost(sc, Q, paths[k, :L], H)
+            assert worst > -oracle.EPS_DEFAULT
+            assert costs[k] == pytest.approx(total, rel=REL)
+    b.close()
