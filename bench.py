@@ -383,8 +383,8 @@ def run_batched(args, wl):
                 torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
             probe.close()
         problems.append((sc, bp.M, bp.L, bp.seed))
-    # tile autotuning on the first 64 problems (untimed), applied to the whole batch
-    tune = binding.Batch(problems[:64], H)
+    # tile autotuning on a fixed subset of 96 problems (untimed), applied to the whole batch
+    tune = binding.Batch(problems[::max(1, len(problems) // 96)][:96], H)
     tune.autotune(repeats=1)
     tiling = binding.gtmp_batch_get_tiling(tune.handle)
     tune.close()
@@ -412,6 +412,67 @@ def run_batched(args, wl):
     step_ms = [a.elapsed_time(e) for a, e in evs]
     total_s = max_over_ranks(sum(step_ms) / 1e3, world, "cuda")
     costs = b.costs.cpu().numpy()
+    # the same problems through the plain single-problem solver, one after another
+    planners = []
+    for sc, M, L, seed in problems:
+        pl = binding.Planner(sc.robot, M, L, H, max_obstacles=64)
+        pl.set_scene(sc)
+        planners.append((pl, M, L, seed))
+    outs = [(torch.empty(L, dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.float32, device="cuda"))
+            for _, _, L, _ in planners]
+
+    def plain_pass():
+        for (pl, M, L, seed), (pa, co) in zip(planners, outs):
+            binding.gtmp_sample_layers(pl.ctx, seed, M)
+            binding.gtmp_solve(pl.ctx, pa, co)
+
+    plain_pass()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    e0.record(stream)
+    plain_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    plain_same = all(float(co.cpu()[0]) == float(costs[k]) or (math.isinf(costs[k]) and math.isinf(float(co.cpu()[0])))
+                     for k, (_, co) in enumerate(outs))
+    for pl, _, _, _ in planners:
+        pl.close()
+    breakdown = None
+    if args.breakdown:
+        breakdown = {}
+        for name, keep in (("arm", lambda sc: sc.robot.dof > 3), ("point2d", lambda sc: sc.robot.dof <= 3)):
+            sub = [p for p in problems if keep(p[0])]
+            sb = binding.Batch(sub, H)
+            binding.gtmp_batch_set_tiling(sb.handle, *tiling)
+            sb.solve()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sb.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_batched = e0.elapsed_time(e1) / 1e3
+            sb.close()
+            pls = []
+            for sc, M, L, seed in sub:
+                pl = binding.Planner(sc.robot, M, L, H, max_obstacles=64)
+                pl.set_scene(sc)
+                pls.append((pl, M, L, seed, torch.empty(L, dtype=torch.int32, device="cuda"),
+                            torch.empty(1, dtype=torch.float32, device="cuda")))
+            for pl, M, L, seed, pa, co in pls:
+                binding.gtmp_sample_layers(pl.ctx, seed, M)
+                binding.gtmp_solve(pl.ctx, pa, co)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for pl, M, L, seed, pa, co in pls:
+                binding.gtmp_sample_layers(pl.ctx, seed, M)
+                binding.gtmp_solve(pl.ctx, pa, co)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            breakdown[name] = {"problems": len(sub), "batched_s": t_batched, "plain_s": e0.elapsed_time(e1) / 1e3}
+            for pl, *_ in pls:
+                pl.close()
     if rank == 0:
         out = {
             "metric": METRIC, "value": b.nominal_checks * args.steps * world / total_s, "unit": "checks/s",
@@ -424,9 +485,121 @@ def run_batched(args, wl):
                        "feasible": int(np.isfinite(costs).sum()), "l2": "flushed between steps"},
             "gpu_launches": 5 * args.steps,
             "clocks": clk.summary(),
+            "plain_sequential": {"solves_per_s": wl["n"] / plain_s, "s_per_batch": plain_s,
+                                 "same_costs_as_batched": bool(plain_same)},
+            "breakdown": breakdown,
         }
         print(json.dumps(out), flush=True)
     b.close()
+
+
+def run_anytime(args, wl):
+    """Anytime-GTMP: R restarts of one problem, all in one batch of launches."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25830_b300 import binding, scenes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    M, L, H, R = wl["M"], wl["L"], wl["H"], wl["R"]
+    base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
+    probe = binding.Planner(base.robot, 8, 1, 2, max_obstacles=64)
+    binding.gtmp_set_obstacles(probe.ctx, base.spheres, base.boxes)
+    sc = scenes.pick_endpoints(base, lambda q: probe.label_configs(
+        torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
+    probe.close()
+    p = binding.Planner(sc.robot, M, L, H, R=R, max_obstacles=64)
+    p.set_scene(sc)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    paths = torch.empty((R, L), dtype=torch.int32, device="cuda")
+    costs = torch.empty(R, dtype=torch.float32, device="cuda")
+    best = torch.empty(1, dtype=torch.int32, device="cuda")
+    seed0 = rank_seed_base(rank)
+    for s in range(args.warmup):
+        binding.gtmp_anytime(p.ctx, seed0 + 10_000 + s, R, paths, costs, best)
+    p.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s in range(args.steps):
+        flush.zero_()
+        evs[s][0].record(stream)
+        binding.gtmp_anytime(p.ctx, seed0 + s, R, paths, costs, best)
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    p.synchronize()
+    total_s = max_over_ranks(sum(a.elapsed_time(e) for a, e in evs) / 1e3, world, "cuda")
+    checks = R * H * (2 * M + (L - 1) * M * M)
+    c = costs.cpu().numpy()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": checks * args.steps * world / total_s, "unit": "checks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "solves_per_s": R * args.steps * world / total_s,
+            "config": {"workload": args.workload, "restarts": R, "M": M, "L": L, "H": H, "dof": wl["dof"],
+                       "checks_per_launch_batch": checks, "feasible_restarts": int(np.isfinite(c).sum()),
+                       "best_cost": float(c[int(best.cpu()[0])]) if int(best.cpu()[0]) >= 0 else None,
+                       "l2": "flushed between steps"}}), flush=True)
+    p.close()
+
+
+def run_ao(args, wl):
+    """AO-GTMP: M doubles from M0 to M1 (L fixed), best cost against device time."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25830_b300 import binding, scenes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    L, H = wl["L"], wl["H"]
+    sizes = []
+    m = wl["M0"]
+    while m <= wl["M1"]:
+        sizes.append(m)
+        m *= 2
+    base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
+    probe = binding.Planner(base.robot, 8, 1, 2, max_obstacles=64)
+    binding.gtmp_set_obstacles(probe.ctx, base.spheres, base.boxes)
+    sc = scenes.pick_endpoints(base, lambda q: probe.label_configs(
+        torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
+    probe.close()
+    stream = torch.cuda.current_stream()
+
+    def run_schedule(seed):
+        p = binding.Planner(sc.robot, sizes[-1], L, H, max_obstacles=64)
+        p.set_scene(sc)
+        sp = torch.empty(L, dtype=torch.int32, device="cuda")
+        scost = torch.empty(1, dtype=torch.float32, device="cuda")
+        bp = torch.full((L,), -1, dtype=torch.int32, device="cuda")
+        bc = torch.full((1,), math.inf, dtype=torch.float32, device="cuda")
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(sizes) + 1)]
+        best = []
+        evs[0].record(stream)
+        for k, M in enumerate(sizes):
+            binding.aogtmp_expand(p.ctx, seed, M, sp, scost, bp, bc)
+            evs[k + 1].record(stream)
+            best.append(bc.clone())
+        torch.cuda.synchronize()
+        p.synchronize()
+        curve = [(evs[0].elapsed_time(evs[k + 1]), float(best[k].cpu()[0])) for k in range(len(sizes))]
+        p.close()
+        return curve
+
+    for s in range(args.warmup):
+        run_schedule(rank_seed_base(rank) + 50_000 + s)
+    curves = [run_schedule(rank_seed_base(rank) + s) for s in range(args.steps)]
+    total_s = max_over_ranks(sum(c[-1][0] for c in curves) / 1e3, world, "cuda")
+    checks = sum(H * (2 * M + (L - 1) * M * M) for M in sizes)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": checks * args.steps * world / total_s, "unit": "checks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "M_stages": sizes, "L": L, "H": H, "dof": wl["dof"],
+                       "checks_per_schedule": checks, "l2": "not flushed inside a schedule (stages are sequential)"},
+            "best_cost_vs_time_ms": [[round(t, 3), c] for t, c in curves[0]]}), flush=True)
 
 
 def main():
@@ -440,12 +613,13 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=10.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--breakdown", action="store_true", help="batched workload: time arm and 2D subsets separately")
     args = ap.parse_args()
     wl = dict(scenes.WORKLOADS[args.workload])
-    if wl["kind"] == "batched":
+    if wl["kind"] == "batched" or "R" in wl or "M0" in wl:
         if args.impl == "reference":
-            raise SystemExit("the reference arm times single solves only")
-        run_batched(args, wl)
+            raise SystemExit("the reference arm times the single-solve workload")
+        {"batched": run_batched}.get(wl["kind"], run_anytime if "R" in wl else run_ao)(args, wl)
         return
     if "M" not in wl:
         raise SystemExit(f"{args.workload} is not a single-solve workload")

@@ -289,8 +289,9 @@ GTMP_API gtmp_status gtmp_batch_info(const gtmp_batch* b, int32_t* L_max, double
  * infeasible), dev_costs device [n] float32 (+inf when infeasible).  Enqueues
  * five kernels (one persistent) and a memset on the batch stream; no host
  * synchronisation, so the call can be captured in a CUDA graph.  Every
- * device-side dependency wait is bounded (about 2 s); a wait that gives up
- * sets the error word that gtmp_batch_synchronize reports. */
+ * device-side dependency wait is bounded (about 2 s without progress of the
+ * awaited items); a wait that gives up abandons its item and sets the error
+ * word that gtmp_batch_synchronize reports. */
 GTMP_API gtmp_status gtmp_batch_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs);
 GTMP_API gtmp_status gtmp_batch_synchronize(gtmp_batch* b);
 

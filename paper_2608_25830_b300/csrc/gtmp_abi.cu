@@ -133,6 +133,7 @@ gtmp_status run_fused(gtmp_ctx* c, const GraphDev& g, int mode) {
     long long chunk = edges / (warps * 8);
     if (chunk < 1) chunk = 1;
     if (chunk > 32) chunk = 32;
+    if (c->variant == kVarPoint) chunk = 32;  // one edge per lane
     if (chunk > cols) chunk = cols;
     const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
     const long long useful_blocks = (n_chunks + 7) / 8;

@@ -39,10 +39,11 @@ struct ProblemDev {
 };
 
 struct WorkItem {
-  int p, depth, row0, rows;
+  int p, depth, row0, rows, col0, cols;
 };
 
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int kBoundaryItemEdges = 256;          // item size cap for the start row and the goal column
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz without progress
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -135,10 +136,10 @@ __global__ void __launch_bounds__(kThreads) batch_labels_kernel(const ProblemDev
 // ---------------------------------------------------------------------------
 template <int VAR>
 __device__ __forceinline__ void item_rows(const GraphDev g, const SceneDev sc, int layer, int row0, int rows,
-                                          int chunk, const float* s_V, const RobotDev& rb, const float4* s_obs,
-                                          int* s_next) {
-  const int n_cols = layer_size(g, layer + 1);
-  const int cpr = (n_cols + chunk - 1) / chunk;
+                                          int col0, int cols, int chunk, const float* s_V, const RobotDev& rb,
+                                          const float4* s_obs, int* s_next) {
+  if (VAR == kVarPoint) chunk = chunk < 32 ? 32 : chunk;  // one edge per lane
+  const int cpr = (cols + chunk - 1) / chunk;
   const int n_chunks = rows * cpr;
   const int lane = threadIdx.x & 31;
   while (true) {
@@ -147,11 +148,21 @@ __device__ __forceinline__ void item_rows(const GraphDev g, const SceneDev sc, i
     c = __shfl_sync(kFull, c, 0);
     if (c >= n_chunks) break;
     const int i = row0 + c / cpr;
-    const int j0 = (c % cpr) * chunk;
-    const int j1 = min(j0 + chunk, n_cols);
+    const int j0 = col0 + (c % cpr) * chunk;
+    const int j1 = min(j0 + chunk, col0 + cols);
     const unsigned long long best = row_chunk_best<VAR, false>(g, 0, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
     if (lane == 0 && best != kEmptyKey) atomicMin(&g.keys[vidx(g, 0, layer, i)], best);
   }
+}
+
+// one out-of-line body per robot variant: the persistent loop's own state
+// stays out of the register budget of the edge code (measured faster than
+// inlining the variants into one switch, which spills)
+template <int VAR>
+__device__ __noinline__ void item_rows_call(const GraphDev g, const SceneDev sc, int layer, int row0, int rows,
+                                            int col0, int cols, int chunk, const float* s_V, const RobotDev& rb,
+                                            const float4* s_obs, int* s_next) {
+  item_rows<VAR>(g, sc, layer, row0, rows, col0, cols, chunk, s_V, rb, s_obs, s_next);
 }
 
 __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
@@ -178,8 +189,15 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
       if (w.depth > 0) {
         const int* cnt = done + P.need_base + w.depth - 1;
         const int want = need[P.need_base + w.depth - 1];
-        const long long t0 = clock64();
-        while (ld_acquire(cnt) < want) {
+        // the limit applies to time without progress: it restarts whenever
+        // another item of the awaited depth finishes
+        long long t0 = clock64();
+        int seen = -1;
+        for (int v = ld_acquire(cnt); v < want; v = ld_acquire(cnt)) {
+          if (v != seen) {
+            seen = v;
+            t0 = clock64();
+          }
           if (*reinterpret_cast<volatile int*>(err) != 0 || clock64() - t0 > kWaitCycles) {
             atomicOr(err, kErrWaitTimeout);
             ok = 0;
@@ -201,8 +219,7 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
     const int n4 = scene_float4s(P.sc);
     stage_obstacles_plain(smem, P.sc.obs, n4);
     float* s_V = reinterpret_cast<float*>(smem + n4);
-    const int n_cols = layer_size(P.g, layer + 1);
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) {
+    for (int j = w.col0 + threadIdx.x; j < w.col0 + w.cols; j += blockDim.x) {
       const size_t v = vidx(P.g, 0, layer + 1, j);
       s_V[j] = P.g.vflag[v] ? kInf : key_value(__ldcg(P.g.keys + v));
     }
@@ -210,10 +227,19 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
     const GraphDev g = P.g;
     const SceneDev sc = P.sc;
     switch (P.variant) {
-      case kVarPoint: item_rows<kVarPoint>(g, sc, layer, w.row0, w.rows, chunk, s_V, s_rb, smem, &s_next); break;
-      case kVarArm6x4: item_rows<kVarArm6x4>(g, sc, layer, w.row0, w.rows, chunk, s_V, s_rb, smem, &s_next); break;
-      case kVarArm7x4: item_rows<kVarArm7x4>(g, sc, layer, w.row0, w.rows, chunk, s_V, s_rb, smem, &s_next); break;
-      default: item_rows<kVarArmGeneric>(g, sc, layer, w.row0, w.rows, chunk, s_V, s_rb, smem, &s_next); break;
+      case kVarPoint:
+        item_rows_call<kVarPoint>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem, &s_next);
+        break;
+      case kVarArm6x4:
+        item_rows_call<kVarArm6x4>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem, &s_next);
+        break;
+      case kVarArm7x4:
+        item_rows_call<kVarArm7x4>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem, &s_next);
+        break;
+      default:
+        item_rows_call<kVarArmGeneric>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem,
+                                       &s_next);
+        break;
     }
     __threadfence();
     __syncthreads();
@@ -390,10 +416,21 @@ gtmp_status build_items(gtmp_batch* b) {
       if (d > P.g.L) continue;
       const int layer = P.g.L - d;
       const int rows = layer_size(P.g, layer), cols = layer_size(P.g, layer + 1);
-      int per = b->target_edges / std::max(cols, 1);
+      // boundary transitions (start row, goal column) sit at the two ends of
+      // every problem's dependency chain: cut them into small items
+      const int edges_per_item = (rows == 1 || cols == 1) ? std::min(b->target_edges, kBoundaryItemEdges)
+                                                           : b->target_edges;
+      if (rows == 1) {
+        for (int c0 = 0; c0 < cols; c0 += edges_per_item) {
+          items.push_back(WorkItem{p, d, 0, 1, c0, std::min(edges_per_item, cols - c0)});
+          b->need[P.need_base + d] += 1;
+        }
+        continue;
+      }
+      int per = edges_per_item / std::max(cols, 1);
       per = std::max(1, std::min(per, rows));
       for (int r0 = 0; r0 < rows; r0 += per) {
-        items.push_back(WorkItem{p, d, r0, std::min(per, rows - r0)});
+        items.push_back(WorkItem{p, d, r0, std::min(per, rows - r0), 0, cols});
         b->need[P.need_base + d] += 1;
       }
     }
@@ -635,7 +672,7 @@ GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t
                                          float* best_ms) {
   if (!b || repeats < 1 || !dev_paths || !dev_costs) return bfail(b, GTMP_ERR_INVALID_ARG, "bad autotune request");
   static const int kTargets[] = {2048, 8192, 32768, 131072};
-  static const int kChunks[] = {4, 16, 64};
+  static const int kChunks[] = {8, 16, 32, 64};
   cudaEvent_t e0, e1;
   BATCH_TRY(b, cudaEventCreate(&e0));
   BATCH_TRY(b, cudaEventCreate(&e1));

@@ -152,10 +152,64 @@ __device__ __forceinline__ void load_vertex(float (&q)[DP], const float* p, int 
 // s_V holds the column layer's cost-to-go, +inf where the vertex collides or
 // reaches no goal.
 // ---------------------------------------------------------------------------
+// Point robots: one waypoint test is a handful of flops, so the 32 lanes take
+// 32 columns (edges) at a time and each lane walks its own edge's waypoints.
+template <bool FULL>
+__device__ __forceinline__ unsigned long long point_row_chunk_best(const GraphDev& g, int r, int layer, int i,
+                                                                   int j0, int j1, const float* s_V,
+                                                                   const RobotDev& rb, const float4* s_obs,
+                                                                   const SceneDev& sc, int lane) {
+  constexpr int DP = Var<kVarPoint>::kDp;
+  const size_t vi = vidx(g, r, layer, i);
+  const bool row_hit = g.vflag[vi] != 0;
+  unsigned long long best = kEmptyKey;
+  if (!FULL && row_hit) return best;
+  const int H = g.H;
+  const float steps = static_cast<float>(H - 1);
+  float qi[DP];
+  load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
+  for (int jb = j0; jb < j1; jb += 32) {
+    const int j = jb + lane;
+    unsigned long long key = kEmptyKey;
+    if (j < j1) {
+      const float Vj = s_V[j];
+      float qj[DP];
+      load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp);
+      float dq[DP];
+      float s2 = 0.0f;
+#pragma unroll
+      for (int d = 0; d < DP; ++d) {
+        dq[d] = __fsub_rn(qj[d], qi[d]);
+        s2 = __fmaf_rn(dq[d], dq[d], s2);
+      }
+      const float len = __fsqrt_rn(s2);
+      const bool skip = !(Vj < kInf) || len > g.max_edge_len || row_hit;
+      bool hit = false;
+      if (FULL || !skip) {
+        for (int k = 1; k <= H - 2; ++k) {
+          const float t = __fdiv_rn(static_cast<float>(k), steps);
+          float q[DP];
+#pragma unroll
+          for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
+          hit |= point_config_collides<false>(q, true, rb, s_obs, sc.n_s, s_obs + sc.n_s, sc.n_b);
+          if (!FULL && hit) break;
+        }
+      }
+      if (!hit && !skip) key = make_key(__fadd_rn(len, Vj), static_cast<uint32_t>(j));
+    }
+    key = warp_min_u64(key);
+    best = key < best ? key : best;
+  }
+  return best;
+}
+
 template <int VAR, bool FULL>
 __device__ __forceinline__ unsigned long long row_chunk_best(const GraphDev& g, int r, int layer, int i, int j0,
                                                              int j1, const float* s_V, const RobotDev& rb,
                                                              const float4* s_obs, const SceneDev& sc, int lane) {
+  if constexpr (VAR == kVarPoint) {
+    return point_row_chunk_best<FULL>(g, r, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
+  }
   using V = Var<VAR>;
   constexpr int DP = V::kDp;
   const size_t vi = vidx(g, r, layer, i);

@@ -255,6 +255,7 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
     long long chunk = edges / (static_cast<long long>(grid_x) * 8 * 8);
     if (chunk < 1) chunk = 1;
     if (chunk > 32) chunk = 32;
+    if (variant == kVarPoint) chunk = 32;  // one edge per lane
     if (chunk > cols) chunk = cols;
     const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
     if (grid_x > (n_chunks + 7) / 8) grid_x = static_cast<int>((n_chunks + 7) / 8);

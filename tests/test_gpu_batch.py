@@ -81,7 +81,7 @@ def test_autotune_keeps_results(mixed):
     ms = b.autotune(repeats=1)
     assert ms > 0
     t, c = binding.gtmp_batch_get_tiling(b.handle)
-    assert t in (2048, 8192, 32768, 131072) and c in (4, 16, 64)
+    assert t in (2048, 8192, 32768, 131072) and c in (8, 16, 32, 64)
     b.solve()
     b.synchronize()
     _check_against_singles(b, probs, singles)
