@@ -304,6 +304,85 @@ GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t* target_
 GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t* dev_paths, float* dev_costs,
                                          float* best_ms);
 
+/* ---------------------------------------------------------------------------
+ * Learned collision surrogate and surrogate-pruned solve (serving pattern; the
+ * paper has no surrogate and names lazy edge realisation as future work,
+ * Sec. VII).  Model: Fourier features [sin(Bq), cos(Bq)] (B: 64 x dof, drawn
+ * N(0, sigma^2) per rad), three ReLU layers of 256 units, one logit; BF16 weights and
+ * activations, FP32 accumulation on the tcgen05 tensor cores.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t n_train;    /* training configurations, a multiple of 64 (uniform in the joint box, labelled by
+                         the exact checker) */
+  int32_t n_holdout;  /* held-out configurations for the reported rates */
+  int32_t epochs;
+  int32_t batch;      /* multiple of 64, <= n_train */
+  float lr;           /* Adam step size */
+  uint64_t seed;      /* Philox seed of the configurations and of the initial weights */
+  float fourier_sigma;/* standard deviation of the Fourier frequencies per rad (<= 0: 1) */
+} gtmp_surrogate_config;
+
+typedef struct {
+  float final_loss;       /* mean binary cross-entropy over the last epoch */
+  float holdout_accuracy; /* at p = 1/2 */
+  float holdout_fn_rate;  /* colliding held-out configurations predicted free */
+  float holdout_fp_rate;  /* free held-out configurations predicted colliding */
+  float train_ms;         /* device time of data generation, labelling and training */
+} gtmp_surrogate_stats;
+
+typedef struct {
+  double edges;     /* candidate edges of the graph */
+  double pruned;    /* edges dropped before exact checking */
+  float score_ms;   /* device time of the surrogate scoring */
+  float solve_ms;   /* device time of the exact fused transitions */
+} gtmp_prune_stats;
+
+/* Train the context's surrogate for its robot and current obstacles
+ * (synchronous; allocates its buffers on first use). */
+GTMP_API gtmp_status gtmp_surrogate_train(gtmp_ctx* ctx, const gtmp_surrogate_config* cfg,
+                                          gtmp_surrogate_stats* stats);
+
+/* Logits of configurations dev_q device [n][dof] -> dev_logits device [n]. */
+GTMP_API gtmp_status gtmp_surrogate_predict(gtmp_ctx* ctx, const float* dev_q, int32_t n, float* dev_logits);
+
+/* FP32 master parameters (host [gtmp_surrogate_param_count()]: W1[256][128],
+ * b1[256], W2[256][256], b2, W3[256][256], b3, w4[256], b4) and the Fourier
+ * matrix (host [64][dof]). */
+GTMP_API int64_t gtmp_surrogate_param_count(void);
+GTMP_API gtmp_status gtmp_surrogate_get_params(gtmp_ctx* ctx, float* host_params, int64_t n, float* host_fourier,
+                                               int64_t n_fourier);
+
+/* Load FP32 parameters (layout of gtmp_surrogate_get_params) instead of
+ * training, and the mean binary cross-entropy and its gradient (host
+ * [gtmp_surrogate_param_count()]) at the current parameters for n labelled
+ * configurations (dev_q device [n][dof], dev_labels device [n] uint8, n a
+ * multiple of 64 up to 65536): one forward and backward pass of training,
+ * without the update.  Synchronous. */
+GTMP_API gtmp_status gtmp_surrogate_set_params(gtmp_ctx* ctx, const float* host_params, int64_t n,
+                                               const float* host_fourier, int64_t n_fourier);
+GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* ctx, const float* dev_q, const uint8_t* dev_labels, int32_t n,
+                                              double* host_loss, float* host_grad, int64_t n_grad);
+
+/* gtmp_solve on graph 0 in which an edge is dropped before exact checking when
+ * the surrogate's collision probability at any of its scored waypoints
+ * (score_waypoints = 1: t = 1/2; 3: t = 1/4, 1/2, 3/4) exceeds threshold;
+ * scoring runs in one fused tensor-core kernel per transition.  Every
+ * surviving edge is realised by the exact checker, so a returned path is
+ * collision free at its H waypoints; the cost can exceed gtmp_solve's when a
+ * free edge is dropped.  Synchronous (returns the stats); allocates an M x M
+ * mask on first use. */
+GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* ctx, float threshold, int32_t score_waypoints, int32_t* dev_path,
+                                       float* dev_cost, gtmp_prune_stats* stats);
+
+/* The surrogate's tensor-core GEMM on its own: C[m][n] = sum_k A[m][k] B[n][k]
+ * with A device [M][lda] and B device [N][ldb] bf16 (K contiguous; lda, ldb
+ * multiples of 8, 16-byte aligned bases), C device [M][ldc] float32; N a
+ * multiple of 16, K a multiple of 8.  Enqueued on cuda_stream; a timed-out
+ * wait sets *dev_err (device int32). */
+GTMP_API gtmp_status gtmp_umma_gemm_f32(const void* dev_A, int32_t lda, const void* dev_B, int32_t ldb, int32_t M,
+                                        int32_t N, int32_t K, float* dev_C, int32_t ldc, void* cuda_stream,
+                                        int32_t* dev_err);
+
 /* Active samples per layer of graph 0 (after sample/set/expand). */
 GTMP_API gtmp_status gtmp_get_M(const gtmp_ctx* ctx, int32_t* M);
 

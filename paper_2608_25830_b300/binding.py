@@ -54,6 +54,23 @@ _vp, _i32, _u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
 _fp = ctypes.POINTER(ctypes.c_float)
 
 
+class GtmpSurrogateConfig(ctypes.Structure):
+    _fields_ = [("n_train", ctypes.c_int32), ("n_holdout", ctypes.c_int32), ("epochs", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("fourier_sigma", ctypes.c_float)]
+
+
+class GtmpSurrogateStats(ctypes.Structure):
+    _fields_ = [("final_loss", ctypes.c_float), ("holdout_accuracy", ctypes.c_float),
+                ("holdout_fn_rate", ctypes.c_float), ("holdout_fp_rate", ctypes.c_float),
+                ("train_ms", ctypes.c_float)]
+
+
+class GtmpPruneStats(ctypes.Structure):
+    _fields_ = [("edges", ctypes.c_double), ("pruned", ctypes.c_double), ("score_ms", ctypes.c_float),
+                ("solve_ms", ctypes.c_float)]
+
+
 class GtmpProblem(ctypes.Structure):
     _fields_ = [("robot", GtmpRobot), ("spheres", _fp), ("n_s", ctypes.c_int32), ("boxes", _fp),
                 ("n_b", ctypes.c_int32), ("q_start", _fp), ("q_goal", _fp), ("M", ctypes.c_int32),
@@ -88,6 +105,13 @@ _SIGNATURES = {
     "gtmp_batch_set_tiling": [_vp, _i32, _i32],
     "gtmp_batch_get_tiling": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "gtmp_batch_autotune": [_vp, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_float)],
+    "gtmp_surrogate_train": [_vp, ctypes.POINTER(GtmpSurrogateConfig), ctypes.POINTER(GtmpSurrogateStats)],
+    "gtmp_surrogate_predict": [_vp, _vp, _i32, _vp],
+    "gtmp_surrogate_get_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
+    "gtmp_solve_pruned": [_vp, ctypes.c_float, _i32, _vp, _vp, ctypes.POINTER(GtmpPruneStats)],
+    "gtmp_surrogate_set_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
+    "gtmp_surrogate_loss_grad": [_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _fp, ctypes.c_int64],
+    "gtmp_umma_gemm_f32": [_vp, _i32, _vp, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp],
     "gtmp_solve_noalloc": [ctypes.POINTER(GtmpRobot), _fp, _i32, _fp, _i32, _fp, _fp, _vp, _i32, _i32, _i32,
                            ctypes.c_float, _vp, _vp, _vp, _vp, ctypes.c_char_p, _i32],
 }
@@ -107,6 +131,8 @@ def lib() -> ctypes.CDLL:
             f.restype = ctypes.c_int
         L.gtmp_last_error.argtypes = [_vp]
         L.gtmp_last_error.restype = ctypes.c_char_p
+        L.gtmp_surrogate_param_count.argtypes = []
+        L.gtmp_surrogate_param_count.restype = ctypes.c_int64
         L.gtmp_batch_last_error.argtypes = [_vp]
         L.gtmp_batch_last_error.restype = ctypes.c_char_p
         L.gtmp_status_string.argtypes = [ctypes.c_int]
@@ -467,3 +493,93 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# learned collision surrogate
+# ---------------------------------------------------------------------------
+
+def gtmp_surrogate_train(ctx, n_train=1 << 20, n_holdout=1 << 16, epochs=2, batch=8192, lr=1e-3, seed=1,
+                         fourier_sigma=1.0):
+    cfg = GtmpSurrogateConfig(n_train, n_holdout, epochs, batch, lr, seed, fourier_sigma)
+    st = GtmpSurrogateStats()
+    _check(ctx, lib().gtmp_surrogate_train(ctx, ctypes.byref(cfg), ctypes.byref(st)))
+    return dict(final_loss=st.final_loss, holdout_accuracy=st.holdout_accuracy, holdout_fn_rate=st.holdout_fn_rate,
+                holdout_fp_rate=st.holdout_fp_rate, train_ms=st.train_ms)
+
+
+def gtmp_surrogate_predict(ctx, dev_q, dev_logits):
+    import torch
+    _check(ctx, lib().gtmp_surrogate_predict(ctx, _dev(dev_q, torch.float32), dev_q.shape[0],
+                                             _dev(dev_logits, torch.float32)))
+
+
+def gtmp_surrogate_param_count():
+    return int(lib().gtmp_surrogate_param_count())
+
+
+def gtmp_surrogate_get_params(ctx, dof):
+    n = gtmp_surrogate_param_count()
+    P = np.zeros(n, np.float32)
+    B = np.zeros(64 * dof, np.float32)
+    _check(ctx, lib().gtmp_surrogate_get_params(ctx, _ptr(P), n, _ptr(B), B.size))
+    o = 0
+    out = {}
+    for name, shape in (("W1", (256, 128)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)),
+                        ("W3", (256, 256)), ("b3", (256,)), ("w4", (256,)), ("b4", (1,))):
+        size = int(np.prod(shape))
+        out[name] = P[o:o + size].reshape(shape)
+        o += size
+    out["B"] = B.reshape(64, dof)
+    return out
+
+
+def gtmp_solve_pruned(ctx, threshold, dev_path, dev_cost, score_waypoints=1):
+    import torch
+    st = GtmpPruneStats()
+    _check(ctx, lib().gtmp_solve_pruned(ctx, threshold, score_waypoints, _dev(dev_path, torch.int32),
+                                        _dev(dev_cost, torch.float32), ctypes.byref(st)))
+    return dict(edges=st.edges, pruned=st.pruned, score_ms=st.score_ms, solve_ms=st.solve_ms)
+
+
+def gtmp_umma_gemm_f32(A, B, C, err, stream=None):
+    """C = A @ B.T on the tcgen05 tensor cores (A [M][K], B [N][K] bf16, C [M][N] float32)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    st = stream if stream is not None else _stream()
+    _check(None, lib().gtmp_umma_gemm_f32(_dev(A, torch.bfloat16), A.stride(0), _dev(B, torch.bfloat16), B.stride(0),
+                                          M, N, K, _dev(C, torch.float32), C.stride(0), st, _dev(err, torch.int32)))
+
+
+_PARAM_LAYOUT = (("W1", (256, 128)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
+                 ("b3", (256,)), ("w4", (256,)), ("b4", (1,)))
+
+
+def flatten_params(P):
+    return np.concatenate([np.asarray(P[k], np.float32).reshape(-1) for k, _ in _PARAM_LAYOUT])
+
+
+def unflatten_params(v):
+    out, o = {}, 0
+    for name, shape in _PARAM_LAYOUT:
+        size = int(np.prod(shape))
+        out[name] = v[o:o + size].reshape(shape)
+        o += size
+    return out
+
+
+def gtmp_surrogate_set_params(ctx, P):
+    flat = flatten_params(P)
+    B = _f32(P["B"]).reshape(-1)
+    _check(ctx, lib().gtmp_surrogate_set_params(ctx, _ptr(flat), flat.size, _ptr(B), B.size))
+
+
+def gtmp_surrogate_loss_grad(ctx, dev_q, dev_labels):
+    import torch
+    n = gtmp_surrogate_param_count()
+    g = np.zeros(n, np.float32)
+    loss = ctypes.c_double()
+    _check(ctx, lib().gtmp_surrogate_loss_grad(ctx, _dev(dev_q, torch.float32), _dev(dev_labels, torch.uint8),
+                                               dev_q.shape[0], ctypes.byref(loss), _ptr(g), n))
+    return loss.value, unflatten_params(g)

@@ -7,44 +7,10 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gtmp.h"
-#include "gtmp_kernels.cuh"
+#include "gtmp_ctx.h"
 
 using namespace gtmp;
 
-struct gtmp_ctx {
-  int device = 0;
-  int num_sms = 148;
-  cudaStream_t stream = nullptr;
-  gtmp_params p{};
-  RobotDev rb{};
-  int variant = kVarArmGeneric;
-  int dof = 0, dp = 0;
-  float q_lo[kMaxDof] = {}, q_hi[kMaxDof] = {};
-  // device memory
-  float* Q = nullptr;
-  uint8_t* vflag = nullptr;
-  unsigned long long* keys = nullptr;
-  int* counters = nullptr;
-  int n_counters = 0;
-  float4* obs = nullptr;
-  SceneDev sc{};  // counts and layout of the obstacle table at obs
-  int* err = nullptr;
-  float* C = nullptr;
-  std::vector<size_t> c_off;
-  std::vector<int> c_cs;
-  // state
-  bool have_endpoints = false;
-  int M_active = 0;
-  int fused_bps[2] = {1, 1};
-  std::string last_error;
-  // instrumentation
-  long long launches = 0;
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, int>> ev_used;  // (start, end) indices into ev_pool
-  double timed_edges = 0.0;
-};
 
 namespace {
 
@@ -312,6 +278,8 @@ gtmp_status gtmp_destroy(gtmp_ctx* c) {
   cudaFree(c->obs);
   cudaFree(c->err);
   cudaFree(c->C);
+  cudaFree(c->prune);
+  surrogate_free(c->sur);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
   return GTMP_OK;

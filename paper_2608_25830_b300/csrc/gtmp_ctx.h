@@ -1,0 +1,56 @@
+// Context of the C ABI (private to the library's host code).
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/gtmp.h"
+#include "gtmp_kernels.cuh"
+
+namespace gtmp {
+struct SurrogateState;  // gtmp_surrogate.cu
+void surrogate_free(SurrogateState* s);
+}  // namespace gtmp
+
+using gtmp::RobotDev;
+using gtmp::SceneDev;
+using gtmp::kMaxDof;
+using gtmp::kVarArmGeneric;
+
+struct gtmp_ctx {
+  int device = 0;
+  int num_sms = 148;
+  cudaStream_t stream = nullptr;
+  gtmp_params p{};
+  RobotDev rb{};
+  int variant = kVarArmGeneric;
+  int dof = 0, dp = 0;
+  float q_lo[kMaxDof] = {}, q_hi[kMaxDof] = {};
+  // device memory
+  float* Q = nullptr;
+  uint8_t* vflag = nullptr;
+  unsigned long long* keys = nullptr;
+  int* counters = nullptr;
+  int n_counters = 0;
+  float4* obs = nullptr;
+  SceneDev sc{};  // counts and layout of the obstacle table at obs
+  int* err = nullptr;
+  float* C = nullptr;
+  std::vector<size_t> c_off;
+  std::vector<int> c_cs;
+  // state
+  bool have_endpoints = false;
+  int M_active = 0;
+  int fused_bps[2] = {1, 1};
+  std::string last_error;
+  // instrumentation
+  long long launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;  // (start, end) indices into ev_pool
+  double timed_edges = 0.0;
+  // learned collision surrogate (allocated by gtmp_surrogate_train)
+  gtmp::SurrogateState* sur = nullptr;
+  uint8_t* prune = nullptr;  // per-transition prune mask, M x M
+};

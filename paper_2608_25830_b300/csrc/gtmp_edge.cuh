@@ -183,7 +183,8 @@ __device__ __forceinline__ unsigned long long point_row_chunk_best(const GraphDe
         s2 = __fmaf_rn(dq[d], dq[d], s2);
       }
       const float len = __fsqrt_rn(s2);
-      const bool skip = !(Vj < kInf) || len > g.max_edge_len || row_hit;
+      const bool skip = !(Vj < kInf) || len > g.max_edge_len || row_hit ||
+                        (g.prune && g.prune[static_cast<size_t>(i) * layer_size(g, layer + 1) + j]);
       bool hit = false;
       if (FULL || !skip) {
         for (int k = 1; k <= H - 2; ++k) {
@@ -220,9 +221,11 @@ __device__ __forceinline__ unsigned long long row_chunk_best(const GraphDev& g, 
   const float steps = static_cast<float>(H - 1);
   float qi[DP];
   load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
+  const int n_cols = layer_size(g, layer + 1);
   for (int j = j0; j < j1; ++j) {
     const float Vj = s_V[j];
     if (!FULL && !(Vj < kInf)) continue;
+    if (g.prune && g.prune[static_cast<size_t>(i) * n_cols + j]) continue;  // dropped by the surrogate
     float qj[DP];
     load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp);
     float dq[DP];

@@ -18,6 +18,7 @@ struct GraphDev {
   int R, L, M, dp, H;            // M = active samples per layer, M_stride = allocated
   int M_stride;
   float max_edge_len;
+  const uint8_t* prune = nullptr;  // [rows][cols] of the transition being run; 1 = edge dropped before checking
 };
 
 __host__ __device__ inline size_t vidx(const GraphDev& g, int r, int layer, int i) {

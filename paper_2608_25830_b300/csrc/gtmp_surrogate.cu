@@ -1,0 +1,1194 @@
+// Learned collision surrogate on the tcgen05 tensor cores, and the
+// surrogate-pruned solve.  The paper has no surrogate; it names lazy edge
+// realisation as future work (Sec. VII).  Model (BF16 weights, FP32
+// accumulation):
+//   phi(q) = [sin(B q), cos(B q)]      B: 64 x d Fourier frequencies (fixed)
+//   h1 = relu(W1 phi + b1)   h2 = relu(W2 h1 + b2)   h3 = relu(W3 h2 + b3)
+//   logit = w4 . h3 + b4                (256 hidden units per layer)
+// Hidden activations are rounded to BF16 between layers; the head reads the
+// FP32 h3.  Training: binary cross-entropy against the exact checker's labels,
+// Adam, FP32 master weights.  Pruning: an edge is dropped before exact
+// checking when the surrogate calls any of its waypoints t = 1/4, 1/2, 3/4 a
+// collision with probability above the threshold; every edge that survives
+// is still realised by the exact checker, which therefore judges every
+// returned path.
+#include <cmath>
+#include <cstdio>
+#include <random>
+#include <vector>
+
+#include "../../include/gtmp.h"
+#include "gtmp_edge.cuh"
+#include "gtmp_umma.cuh"
+
+namespace gtmp {
+namespace umma_impl {
+
+constexpr int kMbarLimit = 1 << 24;
+
+__device__ __forceinline__ uint32_t s_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// UMMA shared-memory descriptor: start, leading (K-direction) and stride
+// (8-row-group) byte offsets >> 4, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFF) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t mbar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kUmmaThreads, 1) umma_gemm_kernel(UmmaArgs a) {
+  constexpr int kA = kUmmaBM * kUmmaBK * 2;
+  constexpr int kB = BN * kUmmaBK * 2;
+  constexpr int kStage = kA + kB;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kUmmaBM, n0 = blockIdx.x * BN;
+  const int nk = (a.K + kUmmaBK - 1) / kUmmaBK;
+  const uint32_t mb = s_u32(&mbar);
+
+  auto load_stage = [&](int kt, int s) {
+    const int k0 = kt * kUmmaBK;
+    const uint32_t sA = s_u32(smem + s * kStage), sB = sA + kA;
+    for (int c = tid; c < kUmmaBM * 8; c += kUmmaThreads) {
+      const int r = c >> 3, kc = c & 7;
+      const int gm = m0 + r, gk = k0 + kc * 8;
+      const bool ok = gm < a.M && gk < a.K;
+      const __nv_bfloat16* src = ok ? a.A + static_cast<size_t>(gm) * a.lda + gk : a.A;
+      cp_async16(sA + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16, src, ok ? 16u : 0u);
+    }
+    for (int c = tid; c < BN * 8; c += kUmmaThreads) {
+      const int r = c >> 3, kc = c & 7;
+      const int gn = n0 + r, gk = k0 + kc * 8;
+      const bool ok = gn < a.N && gk < a.K;
+      const __nv_bfloat16* src = ok ? a.B + static_cast<size_t>(gn) * a.ldb + gk : a.B;
+      cp_async16(sB + ((r >> 3) * 8 + kc) * 128 + (r & 7) * 16, src, ok ? 16u : 0u);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  load_stage(0, 0);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  // kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, N >> 3, M >> 4
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
+                         (static_cast<uint32_t>(kUmmaBM >> 4) << 24);
+  bool ok = true;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int s = kt & 1;
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (kt + 1 < nk) load_stage(kt + 1, s ^ 1);  // that buffer's MMAs completed in the previous iteration
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sA = s_u32(smem + s * kStage), sB = sA + kA;
+#pragma unroll
+      for (int kk = 0; kk < kUmmaBK / 16; ++kk) {
+        const uint64_t da = smem_desc(sA + kk * 256, 128, 1024);
+        const uint64_t db = smem_desc(sB + kk * 256, 128, 1024);
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                   : "memory");
+    }
+    const bool done = mbar_wait_parity(mb, static_cast<uint32_t>(kt & 1), kMbarLimit);
+    ok = __syncthreads_and(done) != 0;
+    if (!ok) {
+      if (tid == 0) atomicOr(a.err, kErrWaitTimeout);
+      mbar_wait_parity(mb, static_cast<uint32_t>(kt & 1), kMbarLimit);  // let the MMAs drain
+      break;
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    const bool row_ok = row < a.M;
+    float dot = 0.0f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!row_ok) continue;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = n0 + c0 + j;
+        if (n >= a.N) break;
+        float x = __uint_as_float(v[j]);
+        if constexpr (EPI == kEpiF32) {
+          a.outf[static_cast<size_t>(row) * a.ldf + n] = x;
+          continue;
+        } else if constexpr (EPI == kEpiMaskBf16) {
+          x = __bfloat162float(a.mask[static_cast<size_t>(row) * a.ldm + n]) > 0.0f ? x : 0.0f;
+        } else {
+          x = fmaxf(x + a.bias[n], 0.0f);
+          if constexpr (EPI == kEpiHead) dot = __fmaf_rn(x, a.w4[n], dot);
+        }
+        const __nv_bfloat16 hx = __float2bfloat16_rn(x);
+        if (a.out) a.out[static_cast<size_t>(row) * a.ldo + n] = hx;
+        if (a.outT) a.outT[static_cast<size_t>(n) * a.ldoT + row] = hx;
+      }
+    }
+    if constexpr (EPI == kEpiHead) {
+      if (row_ok) a.logits[row] = dot + *a.b4;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Fourier features of configurations, and of edge waypoints for scoring
+// ---------------------------------------------------------------------------
+struct FourierDev {
+  float B[64 * kMaxDof];  // [64][dof]
+  int dof;
+};
+
+__device__ __forceinline__ void fourier_row(const float* q, const FourierDev& f, __nv_bfloat16* out) {
+  for (int k = 0; k < 64; ++k) {
+    float z = 0.0f;
+    for (int d = 0; d < f.dof; ++d) z = __fmaf_rn(f.B[k * f.dof + d], q[d], z);
+    float s, c;
+    sincosf(z, &s, &c);
+    out[k] = __float2bfloat16_rn(s);
+    out[64 + k] = __float2bfloat16_rn(c);
+  }
+}
+
+// q [n][dof] -> X [n][128] and XT [128][ldT] (column offset 0)
+__global__ void features_kernel(const float* q, int n, FourierDev f, __nv_bfloat16* X, __nv_bfloat16* XT, int ldT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  __nv_bfloat16 row[128];
+  fourier_row(q + static_cast<size_t>(i) * f.dof, f, row);
+  for (int k = 0; k < 128; ++k) {
+    X[static_cast<size_t>(i) * 128 + k] = row[k];
+    if (XT) XT[static_cast<size_t>(k) * ldT + i] = row[k];
+  }
+}
+
+// edges e in [e0, e0 + ne) of the transition (row-major over rows x cols),
+// waypoints t = 1/4, 1/2, 3/4 -> X rows 3 (e - e0) + w
+__global__ void edge_features_kernel(GraphDev g, int layer, long long e0, long long ne, FourierDev f,
+                                     __nv_bfloat16* X) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= 3 * ne) return;
+  const long long e = e0 + t / 3;
+  const int w = static_cast<int>(t % 3);
+  const int cols = layer_size(g, layer + 1);
+  const int i = static_cast<int>(e / cols), j = static_cast<int>(e % cols);
+  const float* u = g.Q + vidx(g, 0, layer, i) * g.dp;
+  const float* v = g.Q + vidx(g, 0, layer + 1, j) * g.dp;
+  const float tw = 0.25f * static_cast<float>(w + 1);
+  float q[kMaxDof];
+  for (int d = 0; d < f.dof; ++d) q[d] = __fmaf_rn(tw, __fsub_rn(v[d], u[d]), u[d]);
+  __nv_bfloat16 row[128];
+  fourier_row(q, f, row);
+  uint4* dst = reinterpret_cast<uint4*>(X + static_cast<size_t>(t) * 128);
+  const uint4* src = reinterpret_cast<const uint4*>(row);
+  for (int k = 0; k < 16; ++k) dst[k] = src[k];
+}
+
+// prune[e] = max over the edge's 3 waypoint logits > cut
+__global__ void prune_mask_kernel(const float* logits, long long e0, long long ne, float cut, uint8_t* prune,
+                                  unsigned long long* n_pruned) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  bool p = false;
+  if (t < ne) {
+    const float z = fmaxf(logits[3 * t], fmaxf(logits[3 * t + 1], logits[3 * t + 2]));
+    p = z > cut;
+    prune[e0 + t] = p ? 1 : 0;
+  }
+  const unsigned b = __ballot_sync(kFull, p);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_pruned, static_cast<unsigned long long>(__popc(b)));
+}
+
+// ---------------------------------------------------------------------------
+// training pieces
+// ---------------------------------------------------------------------------
+// training configurations: uniform in the joint box, Philox block (i, 0, 0, 4<<24 | k>>2)
+__global__ void train_configs_kernel(int n, int dof, FourierDev f, unsigned long long seed, const float* lo,
+                                     const float* hi, float* q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint2 key = seed_key(seed);
+  uint4 w = make_uint4(0, 0, 0, 0);
+  for (int k = 0; k < dof; ++k) {
+    if ((k & 3) == 0) w = philox4x32_10(make_uint4(static_cast<uint32_t>(i), 0u, 0u, (4u << 24) | (k >> 2)), key);
+    q[static_cast<size_t>(i) * dof + k] = __fmaf_rn(word_to_unit(word_of(w, k)), __fsub_rn(hi[k], lo[k]), lo[k]);
+  }
+}
+
+// dz = (sigmoid(z) - y) / B; loss += BCE; dA3 = dz * w4 * (h3 > 0) (+ transposed)
+__global__ void head_backward_kernel(const float* logits, const uint8_t* labels, int b0, int B, const float* w4,
+                                     const __nv_bfloat16* H3, __nv_bfloat16* dA3, __nv_bfloat16* dA3T, int ldT,
+                                     float* dz, double* loss) {
+  const int i = blockIdx.x;  // row of the batch
+  const float z = logits[i];
+  const float y = labels[b0 + i] ? 1.0f : 0.0f;
+  const float p = 1.0f / (1.0f + __expf(-z));
+  const float g = (p - y) / static_cast<float>(B);
+  if (threadIdx.x == 0) {
+    dz[i] = g;
+    // numerically stable BCE with logits
+    const float l = fmaxf(z, 0.0f) - z * y + log1pf(__expf(-fabsf(z)));
+    atomicAdd(loss, static_cast<double>(l));
+  }
+  for (int n = threadIdx.x; n < 256; n += blockDim.x) {
+    const float h = __bfloat162float(H3[static_cast<size_t>(i) * 256 + n]);
+    const __nv_bfloat16 d = __float2bfloat16_rn(h > 0.0f ? g * w4[n] : 0.0f);
+    dA3[static_cast<size_t>(i) * 256 + n] = d;
+    dA3T[static_cast<size_t>(n) * ldT + i] = d;
+  }
+}
+
+// gw4[n] = sum_i dz[i] h3[i][n] (h3T rows), gb4 = sum dz; bias grads = row sums of dAT
+__global__ void colsum_kernel(const __nv_bfloat16* T, int ld, int B, const float* weights, float* out) {
+  const int n = blockIdx.x;
+  float s = 0.0f;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    const float x = __bfloat162float(T[static_cast<size_t>(n) * ld + i]);
+    s += weights ? x * weights[i] : x;
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) t += part[w];
+    out[n] = t;
+  }
+}
+
+__global__ void sum_kernel(const float* x, int n, float* out) {
+  float s = 0.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < (blockDim.x + 31) / 32; ++w) t += part[w];
+    *out = t;
+  }
+}
+
+// Adam on a flat fp32 parameter vector; also writes bf16 copies (row-major and transposed) of weight matrices
+__global__ void adam_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2, __nv_bfloat16* wb, __nv_bfloat16* wbT, int rows, int cols) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  if (wb) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(wi);
+    wb[i] = h;
+    const int r = i / cols, c = i % cols;
+    wbT[static_cast<size_t>(c) * rows + r] = h;
+  }
+}
+
+__global__ void f32_to_bf16_kernel(const float* w, int rows, int cols, __nv_bfloat16* wb, __nv_bfloat16* wbT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const __nv_bfloat16 h = __float2bfloat16_rn(w[i]);
+  wb[i] = h;
+  if (wbT) wbT[static_cast<size_t>(i % cols) * rows + i / cols] = h;
+}
+
+inline int nblk(long long n, int t) { return static_cast<int>((n + t - 1) / t); }
+
+}  // namespace umma_impl
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+using namespace umma_impl;
+
+cudaError_t umma_gemm(const UmmaArgs& a, int epi, cudaStream_t st) {
+  const int bn = a.N > 128 ? 256 : 128;
+  const dim3 grid((a.N + bn - 1) / bn, (a.M + kUmmaBM - 1) / kUmmaBM);
+  const size_t smem = 2 * static_cast<size_t>(kUmmaBM * kUmmaBK * 2 + bn * kUmmaBK * 2);
+  if (epi == kEpiHead && a.N > 256) return cudaErrorInvalidValue;
+#define UMMA_LAUNCH(BN, EPI)                                                                                    \
+  do {                                                                                                          \
+    cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         static_cast<int>(smem));                                               \
+    if (e != cudaSuccess) return e;                                                                             \
+    umma_gemm_kernel<BN, EPI><<<grid, kUmmaThreads, smem, st>>>(a);                                             \
+    return cudaGetLastError();                                                                                  \
+  } while (0)
+  if (bn == 256) {
+    switch (epi) {
+      case kEpiBiasReluBf16: UMMA_LAUNCH(256, kEpiBiasReluBf16);
+      case kEpiF32: UMMA_LAUNCH(256, kEpiF32);
+      case kEpiMaskBf16: UMMA_LAUNCH(256, kEpiMaskBf16);
+      default: UMMA_LAUNCH(256, kEpiHead);
+    }
+  } else {
+    switch (epi) {
+      case kEpiBiasReluBf16: UMMA_LAUNCH(128, kEpiBiasReluBf16);
+      case kEpiF32: UMMA_LAUNCH(128, kEpiF32);
+      case kEpiMaskBf16: UMMA_LAUNCH(128, kEpiMaskBf16);
+      default: UMMA_LAUNCH(128, kEpiHead);
+    }
+  }
+#undef UMMA_LAUNCH
+}
+
+}  // namespace gtmp
+
+// ===========================================================================
+// C ABI: training, prediction and the pruned solve
+// ===========================================================================
+#include "gtmp_ctx.h"
+
+namespace gtmp {
+
+// Parameter tensors, in the order of gtmp_surrogate_get_params.
+constexpr int kHid = 256, kFeat = 128;
+constexpr int kNW1 = kHid * kFeat, kNW2 = kHid * kHid, kNW3 = kHid * kHid;
+constexpr int kParamCount = kNW1 + kHid + kNW2 + kHid + kNW3 + kHid + kHid + 1;
+
+
+// ---------------------------------------------------------------------------
+// Fused surrogate scoring of edges: features -> 3 layers -> head -> prune mask
+// in one persistent kernel (one CTA per SM, 8 warps).  Shared memory (bytes,
+// canonical K-major no-swizzle layouts): W1 [256 x 128] resident (64 K), the
+// tile's features X [128 x 128] (32 K), hidden activations H [128 x 256] (64 K,
+// reused by every layer), two 32 K stream buffers for 256 x 64 K-chunks of W2
+// and W3 fetched from L2 with cp.async.  TMEM: one 128 x 256 fp32 accumulator.
+// A tile is 128 queries: Q = 128 / kw edges with kw waypoints each (t = 1/2
+// for kw = 1; 1/4, 1/2, 3/4 for kw = 3); an edge is pruned when its largest
+// logit exceeds `cut`.
+// ---------------------------------------------------------------------------
+constexpr int kScoreThreads = 256;
+constexpr int kSmemW1 = 256 * 128 * 2, kSmemX = 128 * 128 * 2, kSmemH = 128 * 256 * 2, kSmemS = 256 * 64 * 2;
+constexpr int kScoreSmem = kSmemW1 + kSmemX + kSmemH + 2 * kSmemS;
+
+struct ScoreArgs {
+  GraphDev g;
+  int layer;
+  long long n_edges;       // edges of the transition
+  int kw;                  // waypoints per edge (1 or 3)
+  float cut;               // logit threshold
+  const __nv_bfloat16* W1b;
+  const __nv_bfloat16* W2b;
+  const __nv_bfloat16* W3b;
+  const float* P;          // fp32 parameters (biases, w4, b4)
+  uint8_t* prune;
+  unsigned long long* n_pruned;
+  int* err;
+};
+
+// byte offset of element (r, k) in a canonical K-major tile whose rows hold kdim elements
+__device__ __forceinline__ uint32_t canon(int r, int k, int kdim) {
+  return static_cast<uint32_t>(((r >> 3) * (kdim >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void issue_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs a, FourierDev f) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float s_part[2][128];
+  __shared__ float s_logit[128];
+  uint8_t* sW1 = smem;
+  uint8_t* sX = sW1 + kSmemW1;
+  uint8_t* sH = sX + kSmemX;
+  uint8_t* sS = sH + kSmemH;  // two stream buffers
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t mb = s_u32(&mbar);
+  const float* b1 = a.P + kNW1;
+  const float* b2 = b1 + kHid + kNW2;
+  const float* b3 = b2 + kHid + kNW3;
+  const float* w4 = b3 + kHid;
+  const float b4 = w4[kHid];
+
+  // weight chunk c: 0..3 = W2 columns [64c, 64c+64), 4..7 = W3 columns [64(c-4), ...)
+  auto load_chunk = [&](int c, int buf) {
+    const __nv_bfloat16* W = c < 4 ? a.W2b : a.W3b;
+    const int k0 = (c & 3) * 64;
+    const uint32_t dst = s_u32(sS + buf * kSmemS);
+    for (int t = tid; t < 256 * 8; t += kScoreThreads) {
+      const int n = t >> 3, kc = t & 7;
+      cp_async16(dst + canon(n, kc * 8, 64), W + static_cast<size_t>(n) * kHid + k0 + kc * 8, 16u);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto wait_mma = [&](uint32_t& phase) -> bool {
+    const bool ok = mbar_wait_parity(mb, phase, kMbarLimit);
+    if (!ok) mbar_wait_parity(mb, phase, kMbarLimit);  // let late MMAs drain before TMEM is freed
+    phase ^= 1u;
+    return __syncthreads_and(ok) != 0;
+  };
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // resident W1
+  for (int t = tid; t < 256 * 16; t += kScoreThreads) {
+    const int n = t >> 4, kc = t & 15;
+    cp_async16(s_u32(sW1) + canon(n, kc * 8, 128), a.W1b + static_cast<size_t>(n) * kFeat + kc * 8, 16u);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (256u >> 3 << 17) | (128u >> 4 << 24);
+  const int q_per_tile = 128 / a.kw * a.kw, e_per_tile = 128 / a.kw;
+  const long long n_tiles = (a.n_edges + e_per_tile - 1) / e_per_tile;
+  const int cols = layer_size(a.g, a.layer + 1);
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = quarter * 32 + lane;  // TMEM lane = tile row this thread reads
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const long long e_first = tile * e_per_tile;
+    load_chunk(0, 0);
+    // features of the tile's queries -> X (threads 0..127 one query each)
+    if (tid < 128) {
+      __nv_bfloat16 feat[128];
+      const int qidx = tid;
+      const long long e = e_first + qidx / a.kw;
+      if (qidx < q_per_tile && e < a.n_edges) {
+        const int i = static_cast<int>(e / cols), j = static_cast<int>(e % cols);
+        const float* u = a.g.Q + vidx(a.g, 0, a.layer, i) * a.g.dp;
+        const float* v = a.g.Q + vidx(a.g, 0, a.layer + 1, j) * a.g.dp;
+        const float t = a.kw == 1 ? 0.5f : 0.25f * static_cast<float>(qidx % a.kw + 1);
+        float q[kMaxDof];
+        for (int d = 0; d < f.dof; ++d) q[d] = __fmaf_rn(t, __fsub_rn(v[d], u[d]), u[d]);
+        fourier_row(q, f, feat);
+      } else {
+        for (int k = 0; k < 128; ++k) feat[k] = __float2bfloat16_rn(0.0f);
+      }
+      for (int kc = 0; kc < 16; ++kc)
+        *reinterpret_cast<uint4*>(sX + canon(qidx, kc * 8, 128)) = *reinterpret_cast<const uint4*>(feat + kc * 8);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // W1 (first tile) and chunk 0
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // layer 1: D = X W1^T
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kk = 0; kk < 8; ++kk)
+        issue_mma(tmem, smem_desc(s_u32(sX) + kk * 256, 128, 2048), smem_desc(s_u32(sW1) + kk * 256, 128, 2048), idesc,
+                  kk > 0);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+    }
+    if (!(ok = wait_mma(phase))) break;
+    for (int c = 0; c <= 8 && ok; ++c) {
+      // epilogue of the previous layer: TMEM -> relu(acc + b) -> bf16 -> H (after layer 1 and layer 2)
+      if (c == 0 || c == 4) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float* bias = c == 0 ? b1 : b2;
+        for (int cc = 0; cc < 4; ++cc) {
+          const int n0 = half * 128 + cc * 32;
+          uint32_t v[32];
+          tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + n0, v);
+          for (int g8 = 0; g8 < 4; ++g8) {
+            __align__(16) __nv_bfloat16 h[8];
+            for (int j = 0; j < 8; ++j)
+              h[j] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[g8 * 8 + j]) + bias[n0 + g8 * 8 + j], 0.0f));
+            *reinterpret_cast<uint4*>(sH + canon(row, n0 + g8 * 8, 256)) = *reinterpret_cast<const uint4*>(h);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      }
+      if (c == 8) break;
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (c + 1 < 8) load_chunk(c + 1, (c + 1) & 1);  // that buffer's MMAs finished last iteration
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sb = s_u32(sS + (c & 1) * kSmemS);
+        const int kc = c & 3;
+        for (int kk = 0; kk < 4; ++kk)
+          issue_mma(tmem, smem_desc(s_u32(sH) + kc * 1024 + kk * 256, 128, 4096), smem_desc(sb + kk * 256, 128, 1024),
+                    idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                     : "memory");
+      }
+      ok = wait_mma(phase);
+    }
+    if (!ok) break;
+    // head: relu(acc + b3) . w4 + b4, per query; then the edge's max against the cut
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float dot = 0.0f;
+    for (int cc = 0; cc < 4; ++cc) {
+      const int n0 = half * 128 + cc * 32;
+      uint32_t v[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + n0, v);
+      for (int j = 0; j < 32; ++j) dot = __fmaf_rn(fmaxf(__uint_as_float(v[j]) + b3[n0 + j], 0.0f), w4[n0 + j], dot);
+    }
+    s_part[half][row] = dot;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid < 128) s_logit[tid] = s_part[0][tid] + s_part[1][tid] + b4;
+    __syncthreads();
+    if (tid < 128) {  // warps 0..3, full warps for the ballot
+      bool pr = false;
+      const long long e = e_first + tid;
+      if (tid < e_per_tile && e < a.n_edges) {
+        float z = s_logit[tid * a.kw];
+        for (int w = 1; w < a.kw; ++w) z = fmaxf(z, s_logit[tid * a.kw + w]);
+        pr = z > a.cut;
+        a.prune[e] = pr ? 1 : 0;
+      }
+      const unsigned b = __ballot_sync(kFull, pr);
+      if (lane == 0 && b) atomicAdd(a.n_pruned, static_cast<unsigned long long>(__popc(b)));
+    }
+    __syncthreads();
+  }
+  if (!ok && tid == 0) atomicOr(a.err, kErrWaitTimeout);
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+}
+
+struct SurrogateState {
+  int dof = 0;
+  FourierDev four{};
+  float* P = nullptr;  // fp32 master parameters [kParamCount]: W1 b1 W2 b2 W3 b3 w4 b4
+  float* G = nullptr;  // gradients, same layout
+  float* Mm = nullptr;
+  float* Vv = nullptr;
+  __nv_bfloat16 *W1b = nullptr, *W1bT = nullptr, *W2b = nullptr, *W2bT = nullptr, *W3b = nullptr, *W3bT = nullptr;
+  int cap = 0;  // rows of the activation buffers
+  __nv_bfloat16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *H2T = nullptr,
+                *H3 = nullptr, *H3T = nullptr, *dA = nullptr, *dAT = nullptr, *dB = nullptr, *dBT = nullptr;
+  float *logits = nullptr, *dz = nullptr;
+  double* loss = nullptr;
+  unsigned long long* counter = nullptr;
+  bool trained = false;
+  long long steps = 0;
+};
+
+void surrogate_free(SurrogateState* s) {
+  if (!s) return;
+  void* bufs[] = {s->P,   s->G,   s->Mm,  s->Vv,  s->W1b, s->W1bT,   s->W2b,     s->W2bT, s->W3b,
+                  s->W3bT, s->X,  s->XT,  s->H1,  s->H1T, s->H2,     s->H2T,     s->H3,   s->H3T,
+                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter};
+  for (void* b : bufs) cudaFree(b);
+  delete s;
+}
+
+namespace {
+
+float* pW1(SurrogateState* s, float* base) { return base; }
+float* pb1(SurrogateState* s, float* base) { return base + kNW1; }
+float* pW2(SurrogateState* s, float* base) { return base + kNW1 + kHid; }
+float* pb2(SurrogateState* s, float* base) { return pW2(s, base) + kNW2; }
+float* pW3(SurrogateState* s, float* base) { return pb2(s, base) + kHid; }
+float* pb3(SurrogateState* s, float* base) { return pW3(s, base) + kNW3; }
+float* pw4(SurrogateState* s, float* base) { return pb3(s, base) + kHid; }
+float* pb4(SurrogateState* s, float* base) { return pw4(s, base) + kHid; }
+
+cudaError_t ensure_buffers(SurrogateState* s, int cap) {
+  if (s->cap >= cap) return cudaSuccess;
+  __nv_bfloat16** bufs[] = {&s->X, &s->XT, &s->H1, &s->H1T, &s->H2, &s->H2T, &s->H3, &s->H3T,
+                            &s->dA, &s->dAT, &s->dB, &s->dBT};
+  for (auto b : bufs) {
+    cudaFree(*b);
+    *b = nullptr;
+  }
+  cudaFree(s->logits);
+  cudaFree(s->dz);
+  s->logits = s->dz = nullptr;
+  s->cap = 0;
+  cudaError_t e = cudaSuccess;
+  for (auto b : bufs)
+    if (e == cudaSuccess) e = cudaMalloc(b, static_cast<size_t>(cap) * kHid * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&s->logits, static_cast<size_t>(cap) * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s->dz, static_cast<size_t>(cap) * sizeof(float));
+  if (e == cudaSuccess) s->cap = cap;
+  return e;
+}
+
+UmmaArgs gemm_args(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K, int* err) {
+  UmmaArgs a{};
+  a.A = A;
+  a.lda = lda;
+  a.B = B;
+  a.ldb = ldb;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.err = err;
+  return a;
+}
+
+// forward of rows [X] (bf16 [n][128]) -> logits; training also keeps H and H^T
+cudaError_t forward(SurrogateState* s, const __nv_bfloat16* X, int n, bool keep, int ldT, int* err,
+                    cudaStream_t st) {
+  cudaError_t e;
+  UmmaArgs a = gemm_args(X, kFeat, s->W1b, kFeat, n, kHid, kFeat, err);
+  a.bias = pb1(s, s->P);
+  a.out = s->H1;
+  a.ldo = kHid;
+  a.outT = keep ? s->H1T : nullptr;
+  a.ldoT = ldT;
+  if ((e = umma_gemm(a, kEpiBiasReluBf16, st)) != cudaSuccess) return e;
+  a = gemm_args(s->H1, kHid, s->W2b, kHid, n, kHid, kHid, err);
+  a.bias = pb2(s, s->P);
+  a.out = s->H2;
+  a.ldo = kHid;
+  a.outT = keep ? s->H2T : nullptr;
+  a.ldoT = ldT;
+  if ((e = umma_gemm(a, kEpiBiasReluBf16, st)) != cudaSuccess) return e;
+  a = gemm_args(s->H2, kHid, s->W3b, kHid, n, kHid, kHid, err);
+  a.bias = pb3(s, s->P);
+  a.w4 = pw4(s, s->P);
+  a.b4 = pb4(s, s->P);
+  a.out = keep ? s->H3 : nullptr;
+  a.ldo = kHid;
+  a.outT = keep ? s->H3T : nullptr;
+  a.ldoT = ldT;
+  a.logits = s->logits;
+  return umma_gemm(a, kEpiHead, st);
+}
+
+// Forward and backward of one batch: gradients of the mean binary
+// cross-entropy into s->G, summed loss added to *s->loss.  X: bf16 [batch][128]
+// features; XT: the same features transposed, rows of stride ldXT.
+cudaError_t batch_gradients(SurrogateState* s, const __nv_bfloat16* X, const __nv_bfloat16* XT, int ldXT,
+                            const uint8_t* labels, int batch, int* err, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = forward(s, X, batch, true, batch, err, st)) != cudaSuccess) return e;
+  head_backward_kernel<<<batch, 256, 0, st>>>(s->logits, labels, 0, batch, pw4(s, s->P), s->H3, s->dA, s->dAT,
+                                              batch, s->dz, s->loss);
+  colsum_kernel<<<kHid, 256, 0, st>>>(s->H3T, batch, batch, s->dz, pw4(s, s->G));
+  sum_kernel<<<1, 256, 0, st>>>(s->dz, batch, pb4(s, s->G));
+  // layer 3: dW3 = dA3^T H2, db3, dA2 = (dA3 W3) * (H2 > 0)
+  UmmaArgs a = gemm_args(s->dAT, batch, s->H2T, batch, kHid, kHid, batch, err);
+  a.outf = pW3(s, s->G);
+  a.ldf = kHid;
+  if ((e = umma_gemm(a, kEpiF32, st)) != cudaSuccess) return e;
+  colsum_kernel<<<kHid, 256, 0, st>>>(s->dAT, batch, batch, nullptr, pb3(s, s->G));
+  a = gemm_args(s->dA, kHid, s->W3bT, kHid, batch, kHid, kHid, err);
+  a.mask = s->H2;
+  a.ldm = kHid;
+  a.out = s->dB;
+  a.ldo = kHid;
+  a.outT = s->dBT;
+  a.ldoT = batch;
+  if ((e = umma_gemm(a, kEpiMaskBf16, st)) != cudaSuccess) return e;
+  // layer 2
+  a = gemm_args(s->dBT, batch, s->H1T, batch, kHid, kHid, batch, err);
+  a.outf = pW2(s, s->G);
+  a.ldf = kHid;
+  if ((e = umma_gemm(a, kEpiF32, st)) != cudaSuccess) return e;
+  colsum_kernel<<<kHid, 256, 0, st>>>(s->dBT, batch, batch, nullptr, pb2(s, s->G));
+  a = gemm_args(s->dB, kHid, s->W2bT, kHid, batch, kHid, kHid, err);
+  a.mask = s->H1;
+  a.ldm = kHid;
+  a.out = s->dA;
+  a.ldo = kHid;
+  a.outT = s->dAT;
+  a.ldoT = batch;
+  if ((e = umma_gemm(a, kEpiMaskBf16, st)) != cudaSuccess) return e;
+  // layer 1: dW1 = dA1^T X
+  a = gemm_args(s->dAT, batch, XT, ldXT, kHid, kFeat, batch, err);
+  a.outf = pW1(s, s->G);
+  a.ldf = kFeat;
+  if ((e = umma_gemm(a, kEpiF32, st)) != cudaSuccess) return e;
+  colsum_kernel<<<kHid, 256, 0, st>>>(s->dAT, batch, batch, nullptr, pb1(s, s->G));
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace gtmp
+
+using namespace gtmp;
+
+namespace {
+
+gtmp_status sfail(gtmp_ctx* c, gtmp_status s, const char* msg, cudaError_t e = cudaSuccess) {
+  if (c) {
+    c->last_error = msg;
+    if (e != cudaSuccess) c->last_error += std::string(": ") + cudaGetErrorString(e);
+  }
+  return s;
+}
+
+#define SUR_TRY(ctx, expr)                                                                                  \
+  do {                                                                                                      \
+    cudaError_t e_ = (expr);                                                                                \
+    if (e_ != cudaSuccess)                                                                                  \
+      return sfail((ctx), e_ == cudaErrorMemoryAllocation ? GTMP_ERR_OOM : GTMP_ERR_CUDA, #expr, e_);       \
+  } while (0)
+
+SceneDev ctx_scene(gtmp_ctx* c) {
+  SceneDev s = c->sc;
+  s.obs = c->obs;
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+GTMP_API gtmp_status gtmp_surrogate_train(gtmp_ctx* c, const gtmp_surrogate_config* cfg, gtmp_surrogate_stats* out) {
+  if (!c || !cfg) return GTMP_ERR_INVALID_ARG;
+  const int n_train = cfg->n_train, n_hold = cfg->n_holdout, batch = cfg->batch, epochs = cfg->epochs;
+  if (n_train < 64 || n_train % 64 != 0 || n_hold < 0 || batch < 64 || batch % 64 != 0 || batch > n_train ||
+      epochs < 1 ||
+      !(cfg->lr > 0.0f) || n_train > (1 << 26) || n_hold > (1 << 26) || c->dof > kMaxDof)
+    return sfail(c, GTMP_ERR_INVALID_ARG,
+                 "bad surrogate configuration (n_train and batch multiples of 64, batch <= n_train)");
+  cudaStream_t st = c->stream;
+  if (!c->sur) c->sur = new SurrogateState();
+  SurrogateState* s = c->sur;
+  s->dof = c->dof;
+  // ---- parameters: Fourier frequencies B ~ N(0, 1) per rad, Kaiming-uniform weights, zero biases
+  std::mt19937_64 rng(cfg->seed ^ 0x5eed5u);
+  std::normal_distribution<float> nd(0.0f, cfg->fourier_sigma > 0.0f ? cfg->fourier_sigma : 1.0f);
+  s->four.dof = c->dof;
+  for (int k = 0; k < 64 * c->dof; ++k) s->four.B[k] = nd(rng);
+  std::vector<float> host(kParamCount, 0.0f);
+  auto init = [&](float* w, int n, int fan_in) {
+    std::uniform_real_distribution<float> ud(-1.0f / std::sqrt(float(fan_in)), 1.0f / std::sqrt(float(fan_in)));
+    for (int i = 0; i < n; ++i) w[i] = ud(rng);
+  };
+  init(pW1(s, host.data()), kNW1, kFeat);
+  init(pW2(s, host.data()), kNW2, kHid);
+  init(pW3(s, host.data()), kNW3, kHid);
+  init(pw4(s, host.data()), kHid, kHid);
+  if (!s->P) {
+    SUR_TRY(c, cudaMalloc(&s->P, kParamCount * sizeof(float)));
+    SUR_TRY(c, cudaMalloc(&s->G, kParamCount * sizeof(float)));
+    SUR_TRY(c, cudaMalloc(&s->Mm, kParamCount * sizeof(float)));
+    SUR_TRY(c, cudaMalloc(&s->Vv, kParamCount * sizeof(float)));
+    SUR_TRY(c, cudaMalloc(&s->W1b, kNW1 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W1bT, kNW1 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W2b, kNW2 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W2bT, kNW2 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W3b, kNW3 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W3bT, kNW3 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->loss, sizeof(double)));
+    SUR_TRY(c, cudaMalloc(&s->counter, sizeof(unsigned long long)));
+  }
+  SUR_TRY(c, cudaMemcpyAsync(s->P, host.data(), kParamCount * sizeof(float), cudaMemcpyHostToDevice, st));
+  SUR_TRY(c, cudaMemsetAsync(s->Mm, 0, kParamCount * sizeof(float), st));
+  SUR_TRY(c, cudaMemsetAsync(s->Vv, 0, kParamCount * sizeof(float), st));
+  f32_to_bf16_kernel<<<nblk(kNW1, 256), 256, 0, st>>>(pW1(s, s->P), kHid, kFeat, s->W1b, s->W1bT);
+  f32_to_bf16_kernel<<<nblk(kNW2, 256), 256, 0, st>>>(pW2(s, s->P), kHid, kHid, s->W2b, s->W2bT);
+  f32_to_bf16_kernel<<<nblk(kNW3, 256), 256, 0, st>>>(pW3(s, s->P), kHid, kHid, s->W3b, s->W3bT);
+  SUR_TRY(c, cudaGetLastError());
+  SUR_TRY(c, ensure_buffers(s, batch));
+  // ---- data: configurations uniform in the joint box, labelled by the exact checker
+  const int n_all = n_train + n_hold;
+  float *q = nullptr, *lo = nullptr, *hi = nullptr;
+  uint8_t* y = nullptr;
+  __nv_bfloat16 *F = nullptr, *FT = nullptr;
+  auto release = [&]() {
+    cudaFree(q);
+    cudaFree(lo);
+    cudaFree(hi);
+    cudaFree(y);
+    cudaFree(F);
+    cudaFree(FT);
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&q, static_cast<size_t>(n_all) * c->dof * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&lo, kMaxDof * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&hi, kMaxDof * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&y, n_all);
+  if (e == cudaSuccess) e = cudaMalloc(&F, static_cast<size_t>(n_all) * kFeat * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&FT, static_cast<size_t>(n_train) * kFeat * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lo, c->q_lo, kMaxDof * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hi, c->q_hi, kMaxDof * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    release();
+    return sfail(c, e == cudaErrorMemoryAllocation ? GTMP_ERR_OOM : GTMP_ERR_CUDA, "surrogate data buffers", e);
+  }
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, st);
+  train_configs_kernel<<<nblk(n_all, 256), 256, 0, st>>>(n_all, c->dof, s->four, cfg->seed, lo, hi, q);
+  e = launch_label_configs(q, n_all, c->dof, c->rb, c->variant, ctx_scene(c), y, st);
+  if (e == cudaSuccess) {
+    features_kernel<<<nblk(n_train, 128), 128, 0, st>>>(q, n_train, s->four, F, FT, n_train);
+    features_kernel<<<nblk(n_hold, 128), 128, 0, st>>>(q + static_cast<size_t>(n_train) * c->dof, n_hold, s->four,
+                                                         F + static_cast<size_t>(n_train) * kFeat, nullptr, 0);
+    e = cudaGetLastError();
+  }
+  // ---- epochs of mini-batch Adam on binary cross-entropy
+  const int steps_per_epoch = n_train / batch;
+  double last_loss = 0.0;
+  for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+    cudaMemsetAsync(s->loss, 0, sizeof(double), st);
+    for (int b = 0; b < steps_per_epoch && e == cudaSuccess; ++b) {
+      const int b0 = b * batch;
+      const __nv_bfloat16* X = F + static_cast<size_t>(b0) * kFeat;
+      const __nv_bfloat16* XT = FT + b0;  // rows of FT have stride n_train
+      if ((e = batch_gradients(s, X, XT, n_train, y + b0, batch, c->err, st)) != cudaSuccess) break;
+      // Adam
+      s->steps += 1;
+      const float b1 = 0.9f, b2 = 0.999f;
+      const float c1 = 1.0f - std::pow(b1, float(s->steps)), c2 = 1.0f - std::pow(b2, float(s->steps));
+      struct T {
+        float* (*at)(SurrogateState*, float*);
+        int n, rows, cols;
+        __nv_bfloat16 *wb, *wbT;
+      } tensors[] = {{pW1, kNW1, kHid, kFeat, s->W1b, s->W1bT}, {pb1, kHid, 1, kHid, nullptr, nullptr},
+                     {pW2, kNW2, kHid, kHid, s->W2b, s->W2bT},  {pb2, kHid, 1, kHid, nullptr, nullptr},
+                     {pW3, kNW3, kHid, kHid, s->W3b, s->W3bT},  {pb3, kHid, 1, kHid, nullptr, nullptr},
+                     {pw4, kHid, 1, kHid, nullptr, nullptr},    {pb4, 1, 1, 1, nullptr, nullptr}};
+      for (const T& t : tensors)
+        adam_kernel<<<nblk(t.n, 256), 256, 0, st>>>(t.at(s, s->P), t.at(s, s->G), t.at(s, s->Mm), t.at(s, s->Vv),
+                                                    t.n, cfg->lr, b1, b2, 1e-8f, c1, c2, t.wb, t.wbT, t.rows, t.cols);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      double l = 0.0;
+      e = cudaMemcpyAsync(&l, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      last_loss = l / (static_cast<double>(steps_per_epoch) * batch);
+    }
+  }
+  cudaEventRecord(t1, st);
+  // ---- held-out statistics
+  float acc = 0.0f, fn = 0.0f, fp = 0.0f;
+  if (e == cudaSuccess && n_hold > 0) {
+    std::vector<float> z(n_hold);
+    std::vector<uint8_t> yl(n_hold);
+    for (int r0 = 0; r0 < n_hold && e == cudaSuccess; r0 += batch) {
+      const int nr = std::min(batch, n_hold - r0);
+      e = forward(s, F + static_cast<size_t>(n_train + r0) * kFeat, nr, false, 0, c->err, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(z.data() + r0, s->logits, nr * sizeof(float), cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(yl.data(), y + n_train, n_hold, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    long long n_pos = 0, n_neg = 0, ok = 0, miss = 0, false_alarm = 0;
+    for (int i = 0; i < n_hold; ++i) {
+      const bool pred = z[i] > 0.0f;  // p > 1/2
+      const bool lab = yl[i] != 0;
+      ok += pred == lab;
+      if (lab) {
+        ++n_pos;
+        miss += !pred;
+      } else {
+        ++n_neg;
+        false_alarm += pred;
+      }
+    }
+    acc = float(ok) / n_hold;
+    fn = n_pos ? float(miss) / n_pos : 0.0f;
+    fp = n_neg ? float(false_alarm) / n_neg : 0.0f;
+  }
+  float ms = 0.0f;
+  if (e == cudaSuccess) {
+    cudaEventSynchronize(t1);
+    cudaEventElapsedTime(&ms, t0, t1);
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  release();
+  if (e != cudaSuccess) return sfail(c, GTMP_ERR_CUDA, "surrogate training", e);
+  s->trained = true;
+  if (out) {
+    out->final_loss = static_cast<float>(last_loss);
+    out->holdout_accuracy = acc;
+    out->holdout_fn_rate = fn;
+    out->holdout_fp_rate = fp;
+    out->train_ms = ms;
+  }
+  return GTMP_OK;
+}
+
+GTMP_API gtmp_status gtmp_surrogate_predict(gtmp_ctx* c, const float* dev_q, int32_t n, float* dev_logits) {
+  if (!c || n < 0 || (n > 0 && (!dev_q || !dev_logits))) return GTMP_ERR_INVALID_ARG;
+  if (!c->sur || !c->sur->trained) return sfail(c, GTMP_ERR_NOT_READY, "surrogate not trained");
+  SurrogateState* s = c->sur;
+  cudaStream_t st = c->stream;
+  const int chunk = 1 << 16;
+  SUR_TRY(c, ensure_buffers(s, std::min(std::max(n, 128), chunk)));
+  for (int r0 = 0; r0 < n; r0 += s->cap) {
+    const int nr = std::min(s->cap, n - r0);
+    features_kernel<<<nblk(nr, 128), 128, 0, st>>>(dev_q + static_cast<size_t>(r0) * c->dof, nr, s->four, s->X,
+                                                   nullptr, 0);
+    SUR_TRY(c, cudaGetLastError());
+    SUR_TRY(c, forward(s, s->X, nr, false, 0, c->err, st));
+    SUR_TRY(c, cudaMemcpyAsync(dev_logits + r0, s->logits, nr * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  }
+  return GTMP_OK;
+}
+
+GTMP_API gtmp_status gtmp_surrogate_get_params(gtmp_ctx* c, float* host_params, int64_t n, float* host_fourier,
+                                               int64_t n_fourier) {
+  if (!c || !host_params || n != kParamCount || !host_fourier || n_fourier != 64 * c->dof)
+    return sfail(c, GTMP_ERR_INVALID_ARG, "parameter buffer sizes must match gtmp_surrogate_param_count");
+  if (!c->sur || !c->sur->trained) return sfail(c, GTMP_ERR_NOT_READY, "surrogate not trained");
+  SUR_TRY(c, cudaMemcpyAsync(host_params, c->sur->P, kParamCount * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  SUR_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 64 * c->dof; ++k) host_fourier[k] = c->sur->four.B[k];
+  return GTMP_OK;
+}
+
+GTMP_API int64_t gtmp_surrogate_param_count(void) { return kParamCount; }
+
+GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t score_waypoints, int32_t* dev_path,
+                                       float* dev_cost, gtmp_prune_stats* stats) {
+  if (!c || !dev_path || !dev_cost || !(threshold > 0.0f && threshold < 1.0f) ||
+      (score_waypoints != 1 && score_waypoints != 3))
+    return sfail(c, GTMP_ERR_INVALID_ARG, "bad pruned-solve request (threshold in (0, 1), 1 or 3 waypoints)");
+  if (!c->sur || !c->sur->trained) return sfail(c, GTMP_ERR_NOT_READY, "surrogate not trained");
+  if (!c->have_endpoints || c->M_active < 1) return sfail(c, GTMP_ERR_NOT_READY, "endpoints or samples missing");
+  SurrogateState* s = c->sur;
+  cudaStream_t st = c->stream;
+  const int M = c->M_active, L = c->p.L;
+  if (!c->prune) SUR_TRY(c, cudaMalloc(&c->prune, static_cast<size_t>(c->p.M) * c->p.M));
+  SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
+  const float cut = std::log(threshold / (1.0f - threshold));  // logit of the threshold
+  GraphDev g;
+  g.Q = c->Q;
+  g.vflag = c->vflag;
+  g.keys = c->keys;
+  g.R = 1;
+  g.L = L;
+  g.M = M;
+  g.dp = c->dp;
+  g.H = c->p.H;
+  g.M_stride = c->p.M;
+  g.max_edge_len = c->p.max_edge_len;
+  cudaEvent_t e0, e1, e2;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventCreate(&e2);
+  float score_ms = 0.0f, solve_ms = 0.0f;
+  SUR_TRY(c, cudaMemsetAsync(s->counter, 0, sizeof(unsigned long long), st));
+  SUR_TRY(c, launch_init_keys(g, c->counters, L + 1, st));
+  SUR_TRY(c, launch_vertex_labels(g, c->rb, c->variant, ctx_scene(c), st));
+  const int resident = c->num_sms * c->fused_bps[0];
+  double edges_total = 0.0;
+  for (int layer = L; layer >= 0; --layer) {
+    const int rows = layer_size(g, layer), cols = layer_size(g, layer + 1);
+    const long long ne = static_cast<long long>(rows) * cols;
+    edges_total += static_cast<double>(ne);
+    cudaEventRecord(e0, st);
+    // score every edge of the transition with the fused tensor-core kernel
+    ScoreArgs sa{};
+    sa.g = g;
+    sa.layer = layer;
+    sa.n_edges = ne;
+    sa.kw = score_waypoints;
+    sa.cut = cut;
+    sa.W1b = s->W1b;
+    sa.W2b = s->W2b;
+    sa.W3b = s->W3b;
+    sa.P = s->P;
+    sa.prune = c->prune;
+    sa.n_pruned = s->counter;
+    sa.err = c->err;
+    const long long tiles = (ne + 128 / score_waypoints - 1) / (128 / score_waypoints);
+    const int score_grid = static_cast<int>(std::min<long long>(tiles, c->num_sms));
+    score_edges_kernel<<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
+    SUR_TRY(c, cudaGetLastError());
+    cudaEventRecord(e1, st);
+    // exact realisation of the surviving edges, fused with the min-plus step
+    GraphDev gp = g;
+    gp.prune = c->prune;
+    long long chunk = ne / (static_cast<long long>(resident) * 64);
+    if (chunk < 1) chunk = 1;
+    if (chunk > 32) chunk = 32;
+    if (c->variant == kVarPoint) chunk = 32;
+    if (chunk > cols) chunk = cols;
+    const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
+    int grid = resident;
+    if (grid > (n_chunks + 7) / 8) grid = static_cast<int>((n_chunks + 7) / 8);
+    SUR_TRY(c, launch_fused_transition(gp, layer, c->rb, c->variant, ctx_scene(c), GTMP_EVAL_EARLY_EXIT,
+                                       c->counters + layer, grid, static_cast<int>(chunk), c->err, st));
+    cudaEventRecord(e2, st);
+    SUR_TRY(c, cudaEventSynchronize(e2));
+    float a = 0.0f, b = 0.0f;
+    cudaEventElapsedTime(&a, e0, e1);
+    cudaEventElapsedTime(&b, e1, e2);
+    score_ms += a;
+    solve_ms += b;
+  }
+  SUR_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, st));
+  unsigned long long pruned = 0;
+  SUR_TRY(c, cudaMemcpyAsync(&pruned, s->counter, sizeof(pruned), cudaMemcpyDeviceToHost, st));
+  SUR_TRY(c, cudaStreamSynchronize(st));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  if (stats) {
+    stats->edges = edges_total;
+    stats->pruned = static_cast<double>(pruned);
+    stats->score_ms = score_ms;
+    stats->solve_ms = solve_ms;
+  }
+  return GTMP_OK;
+}
+
+}  // extern "C"
+
+extern "C" GTMP_API gtmp_status gtmp_umma_gemm_f32(const void* dev_A, int32_t lda, const void* dev_B, int32_t ldb,
+                                                   int32_t M, int32_t N, int32_t K, float* dev_C, int32_t ldc,
+                                                   void* cuda_stream, int32_t* dev_err) {
+  if (!dev_A || !dev_B || !dev_C || !dev_err || M < 1 || N < 16 || N % 16 != 0 || K < 8 || K % 8 != 0 || lda < K ||
+      ldb < K || lda % 8 != 0 || ldb % 8 != 0 || ldc < N)
+    return GTMP_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(dev_A) | reinterpret_cast<uintptr_t>(dev_B)) & 15) return GTMP_ERR_INVALID_ARG;
+  UmmaArgs a{};
+  a.A = static_cast<const __nv_bfloat16*>(dev_A);
+  a.lda = lda;
+  a.B = static_cast<const __nv_bfloat16*>(dev_B);
+  a.ldb = ldb;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.outf = dev_C;
+  a.ldf = ldc;
+  a.err = dev_err;
+  return gtmp::umma_gemm(a, gtmp::kEpiF32, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? GTMP_OK
+                                                                                                 : GTMP_ERR_CUDA;
+}
+
+
+// ---------------------------------------------------------------------------
+// parameter injection and one-batch gradients (training diagnostics)
+// ---------------------------------------------------------------------------
+extern "C" GTMP_API gtmp_status gtmp_surrogate_set_params(gtmp_ctx* c, const float* host_params, int64_t n,
+                                                          const float* host_fourier, int64_t n_fourier) {
+  if (!c || !host_params || n != kParamCount || !host_fourier || n_fourier != 64 * c->dof || c->dof > kMaxDof)
+    return sfail(c, GTMP_ERR_INVALID_ARG, "parameter buffer sizes must match gtmp_surrogate_param_count");
+  if (!c->sur) c->sur = new SurrogateState();
+  SurrogateState* s = c->sur;
+  cudaStream_t st = c->stream;
+  if (!s->P) {
+    SUR_TRY(c, cudaMalloc(&s->P, kParamCount * sizeof(float)));
+    SUR_TRY(c, cudaMalloc(&s->G, kParamCount * sizeof(float)));
+    SUR_TRY(c, cudaMalloc(&s->Mm, kParamCount * sizeof(float)));
+    SUR_TRY(c, cudaMalloc(&s->Vv, kParamCount * sizeof(float)));
+    SUR_TRY(c, cudaMalloc(&s->W1b, kNW1 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W1bT, kNW1 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W2b, kNW2 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W2bT, kNW2 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W3b, kNW3 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->W3bT, kNW3 * sizeof(__nv_bfloat16)));
+    SUR_TRY(c, cudaMalloc(&s->loss, sizeof(double)));
+    SUR_TRY(c, cudaMalloc(&s->counter, sizeof(unsigned long long)));
+  }
+  s->dof = c->dof;
+  s->four.dof = c->dof;
+  for (int k = 0; k < 64 * c->dof; ++k) s->four.B[k] = host_fourier[k];
+  SUR_TRY(c, cudaMemcpyAsync(s->P, host_params, kParamCount * sizeof(float), cudaMemcpyHostToDevice, st));
+  f32_to_bf16_kernel<<<nblk(kNW1, 256), 256, 0, st>>>(pW1(s, s->P), kHid, kFeat, s->W1b, s->W1bT);
+  f32_to_bf16_kernel<<<nblk(kNW2, 256), 256, 0, st>>>(pW2(s, s->P), kHid, kHid, s->W2b, s->W2bT);
+  f32_to_bf16_kernel<<<nblk(kNW3, 256), 256, 0, st>>>(pW3(s, s->P), kHid, kHid, s->W3b, s->W3bT);
+  SUR_TRY(c, cudaGetLastError());
+  SUR_TRY(c, cudaStreamSynchronize(st));
+  s->trained = true;
+  return GTMP_OK;
+}
+
+extern "C" GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* c, const float* dev_q, const uint8_t* dev_labels,
+                                                         int32_t n, double* host_loss, float* host_grad,
+                                                         int64_t n_grad) {
+  if (!c || !dev_q || !dev_labels || n < 64 || n % 64 != 0 || n > (1 << 16) || !host_loss || !host_grad ||
+      n_grad != kParamCount)
+    return sfail(c, GTMP_ERR_INVALID_ARG, "bad gradient request (n a multiple of 64, at most 65536)");
+  if (!c->sur || !c->sur->trained) return sfail(c, GTMP_ERR_NOT_READY, "surrogate has no parameters");
+  SurrogateState* s = c->sur;
+  cudaStream_t st = c->stream;
+  SUR_TRY(c, ensure_buffers(s, n));
+  SUR_TRY(c, cudaMemsetAsync(s->loss, 0, sizeof(double), st));
+  features_kernel<<<nblk(n, 128), 128, 0, st>>>(dev_q, n, s->four, s->X, s->XT, n);
+  SUR_TRY(c, cudaGetLastError());
+  SUR_TRY(c, batch_gradients(s, s->X, s->XT, n, dev_labels, n, c->err, st));
+  SUR_TRY(c, cudaMemcpyAsync(host_grad, s->G, kParamCount * sizeof(float), cudaMemcpyDeviceToHost, st));
+  SUR_TRY(c, cudaMemcpyAsync(host_loss, s->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SUR_TRY(c, cudaStreamSynchronize(st));
+  *host_loss /= n;
+  return GTMP_OK;
+}

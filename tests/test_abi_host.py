@@ -26,7 +26,8 @@ def test_library_builds_and_exports_every_declared_symbol():
     L = binding.lib()
     for n in names:
         assert hasattr(L, n), n
-        assert n in binding._SIGNATURES or n in ("gtmp_last_error", "gtmp_status_string", "gtmp_batch_last_error"), n
+        assert n in binding._SIGNATURES or n in ("gtmp_last_error", "gtmp_status_string", "gtmp_batch_last_error",
+                                                 "gtmp_surrogate_param_count"), n
 
 
 def test_status_strings():
