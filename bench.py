@@ -306,6 +306,35 @@ def run_ours(args, wl):
     e2e_s = max_over_ranks(e2e_s, world, "cuda")
     e2e_value = nominal_checks * solves / e2e_s
 
+    # --- the same plans in lazy mode (exact: identical values and paths, most edges never realised)
+    plz = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_LAZY)
+    plz.set_scene(sc)
+    lz_path = torch.empty(L, dtype=torch.int32, device="cuda")
+    lz_cost = torch.empty(1, dtype=torch.float32, device="cuda")
+    ref_path = torch.empty(L, dtype=torch.int32, device="cuda")
+    ref_cost = torch.empty(1, dtype=torch.float32, device="cuda")
+    for s in range(args.warmup):
+        binding.gtmp_sample_layers(plz.ctx, seed0 + 10_000 + s, M)
+        binding.gtmp_solve(plz.ctx, lz_path, lz_cost)
+    plz.synchronize()
+    lz_ms = []
+    lz_same = True
+    for s in range(args.steps):
+        flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        binding.gtmp_sample_layers(plz.ctx, seed0 + s, M)
+        binding.gtmp_solve(plz.ctx, lz_path, lz_cost)
+        a1.record(stream)
+        binding.gtmp_sample_layers(p.ctx, seed0 + s, M)
+        binding.gtmp_solve(p.ctx, ref_path, ref_cost)
+        torch.cuda.synchronize()
+        lz_ms.append(a0.elapsed_time(a1))
+        lz_same = lz_same and bool(torch.equal(lz_path, ref_path)) and (
+            float(lz_cost.cpu()[0]) == float(ref_cost.cpu()[0]) or math.isinf(float(ref_cost.cpu()[0])))
+    plz.close()
+    lazy_s = max_over_ranks(sum(lz_ms) / 1e3, world, "cuda")
+
     # --- roofline of the fused kernel in full-evaluation mode (data-independent FP32 work)
     pf = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_FULL)
     pf.set_scene(sc)
@@ -352,6 +381,10 @@ def run_ours(args, wl):
                          "flops_per_waypoint": fpw,
                          "fused_ms_per_solve": fprof["fused_ms"] / full_steps},
             "fused_ms_per_solve_early_exit": prof["fused_ms"] / args.steps,
+            "lazy": {"solves_per_s": solves / lazy_s, "ms_per_step": sum(lz_ms) / len(lz_ms),
+                     "same_paths_and_costs_as_early_exit": lz_same,
+                     "note": "exact mode GTMP_EVAL_LAZY: an edge is realised only if c(u,v)+J(v) beats its row's "
+                             "best so far; value above counts the nominal checks of the early-exit mode"},
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

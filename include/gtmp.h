@@ -66,11 +66,15 @@ typedef enum {
 
 enum { GTMP_ROBOT_POINT = 0, GTMP_ROBOT_DH_ARM = 1 };
 
-/* Edge evaluation mode of the fused solver.  Both give the same result.
+/* Edge evaluation mode of the fused solver.  All give the same values,
+ * minimisers and paths, bit for bit.
  * EARLY_EXIT leaves an edge at its first colliding link and skips edges that
  * cannot lie on a finite chain; FULL evaluates every interior waypoint of
- * every candidate edge (data-independent work, used to measure the kernel). */
-enum { GTMP_EVAL_EARLY_EXIT = 0, GTMP_EVAL_FULL = 1 };
+ * every candidate edge (data-independent work, used to measure the kernel);
+ * LAZY checks an edge only if its cost c(u,v) + J_{l+1}(v) is below the best
+ * realised edge of its row found so far, visiting each block of 32 columns in
+ * ascending order of that bound (most edges are never realised). */
+enum { GTMP_EVAL_EARLY_EXIT = 0, GTMP_EVAL_FULL = 1, GTMP_EVAL_LAZY = 2 };
 
 /* Robot model (Sec. III: the map from a configuration to the robot's occupied
  * space that defines C_free).
@@ -98,7 +102,7 @@ typedef struct {
   int32_t H;            /* waypoints per edge including both endpoints (2..1024) */
   int32_t R;            /* capacity: graphs solved together by gtmp_anytime (1..4096) */
   int32_t max_obstacles;/* capacity: spheres + boxes accepted by gtmp_set_obstacles (0..4096) */
-  int32_t eval_mode;    /* GTMP_EVAL_EARLY_EXIT or GTMP_EVAL_FULL */
+  int32_t eval_mode;    /* GTMP_EVAL_EARLY_EXIT, GTMP_EVAL_FULL or GTMP_EVAL_LAZY */
   float max_edge_len;   /* edge-length limit l of Sec. III-B/IV-A; +INFINITY = none */
 } gtmp_params;
 

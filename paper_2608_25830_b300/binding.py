@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libgtmp.so")
 GTMP_OK = 0
 STATUS = {0: "GTMP_OK", 1: "GTMP_ERR_INVALID_ARG", 2: "GTMP_ERR_CUDA", 3: "GTMP_ERR_OOM", 4: "GTMP_ERR_TIMEOUT",
           5: "GTMP_ERR_UNSUPPORTED", 6: "GTMP_ERR_NOT_READY"}
-EVAL_EARLY_EXIT, EVAL_FULL = 0, 1
+EVAL_EARLY_EXIT, EVAL_FULL, EVAL_LAZY = 0, 1, 2
 ROBOT_POINT, ROBOT_DH_ARM = 0, 1
 
 

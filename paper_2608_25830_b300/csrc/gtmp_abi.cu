@@ -1,5 +1,6 @@
 // C ABI of the layered-graph planner: argument checking, context memory, and
 // the launch sequences of gtmp / anytime-gtmp / ao-gtmp (Alg. 1).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -85,6 +86,34 @@ cudaError_t event_at(gtmp_ctx* c, size_t slot, cudaEvent_t* out) {
 
 gtmp_status run_fused(gtmp_ctx* c, const GraphDev& g, int mode) {
   const int bps = c->fused_bps[mode == GTMP_EVAL_FULL ? 1 : 0];
+  if (mode == GTMP_EVAL_LAZY) {
+    // a warp per (32-column block, row) unit: grid = enough blocks for every unit, at most the resident count
+    CUDA_TRY(c, launch_init_keys(g, c->counters, (g.L + 1) * g.R, c->stream));
+    CUDA_TRY(c, launch_vertex_labels(g, c->rb, c->variant, scene(c), c->stream));
+    LAUNCHED(c, 2);
+    for (int layer = g.L; layer >= 0; --layer) {
+      const int rows = layer_size(g, layer);
+      const long long units = static_cast<long long>(rows) * ((layer_size(g, layer + 1) + 31) / 32);
+      int grid_x = static_cast<int>(std::max(1LL, std::min<long long>(c->num_sms * bps / g.R, (units + 7) / 8)));
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (c->timing) {
+        const size_t slot = c->ev_used.size() * 2;
+        CUDA_TRY(c, event_at(c, slot, &e0));
+        CUDA_TRY(c, event_at(c, slot + 1, &e1));
+        CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+      }
+      CUDA_TRY(c, launch_fused_transition(g, layer, c->rb, c->variant, scene(c), mode, c->counters + layer * g.R,
+                                          grid_x, 32, c->err, c->stream));
+      LAUNCHED(c, 1);
+      if (c->timing) {
+        CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+        const size_t slot = c->ev_used.size() * 2;
+        c->ev_used.emplace_back(static_cast<int>(slot), static_cast<int>(slot + 1));
+        c->timed_edges += static_cast<double>(rows) * layer_size(g, layer + 1) * g.R;
+      }
+    }
+    return GTMP_OK;
+  }
   const int resident = c->num_sms * bps;
   CUDA_TRY(c, launch_init_keys(g, c->counters, (g.L + 1) * g.R, c->stream));
   CUDA_TRY(c, launch_vertex_labels(g, c->rb, c->variant, scene(c), c->stream));
@@ -174,7 +203,8 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
   }
   if (p.M < 1 || p.M > 16384 || p.L < 1 || p.L > 64 || p.H < 2 || p.H > 1024 || p.R < 1 || p.R > 4096 ||
       p.max_obstacles < 0 || p.max_obstacles > 4096 ||
-      (p.eval_mode != GTMP_EVAL_EARLY_EXIT && p.eval_mode != GTMP_EVAL_FULL) || std::isnan(p.max_edge_len) ||
+      (p.eval_mode != GTMP_EVAL_EARLY_EXIT && p.eval_mode != GTMP_EVAL_FULL && p.eval_mode != GTMP_EVAL_LAZY) ||
+      std::isnan(p.max_edge_len) ||
       !(p.max_edge_len > 0.0f))
     return GTMP_ERR_INVALID_ARG;
   const size_t graph_vertices = static_cast<size_t>(p.R) * (p.L + 2) * p.M;

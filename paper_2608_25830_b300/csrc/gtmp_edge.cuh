@@ -257,5 +257,117 @@ __device__ __forceinline__ unsigned long long row_chunk_best(const GraphDev& g, 
   return best;
 }
 
+// ---------------------------------------------------------------------------
+// Lazy realisation (exact).  The best key of row i is the smallest
+// (c(i,j) + J_{l+1}(j), j) over realised edges; an edge whose key is not below
+// a key already found for the row cannot change the row's minimum, so it is
+// never checked.  The unit of work is one block of 32 columns of one row:
+// the warp scores the block's candidates (lane = column), drops those at or
+// above the row's current best (the row's key word in global memory, which
+// every unit of the row lowers with atomicMin), sorts the rest (bitonic,
+// 64-bit keys, one per lane) and checks them in ascending order, re-reading
+// the row's best before each check, until the first free edge (published at
+// once) or the first key at or above the best.  Units are handed out block-
+// major (block 0 of every row, then block 1, ...), so later blocks of a row
+// usually start with a bound from its earlier ones.  The final key word is
+// the one the exhaustive modes compute, bit for bit: the row's minimal free
+// edge is skipped only if its own key has already been published.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long warp_sort32_u64(unsigned long long key, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(kFull, key, j);
+      const bool up = (lane & k) == 0;
+      const bool low = (lane & j) == 0;
+      key = (low == up) ? (other < key ? other : key) : (other > key ? other : key);
+    }
+  }
+  return key;
+}
+
+template <int VAR>
+__device__ __forceinline__ void lazy_block(const GraphDev& g, int r, int layer, int i, int j0, const float* s_V,
+                                           const RobotDev& rb, const float4* s_obs, const SceneDev& sc, int lane) {
+  using V = Var<VAR>;
+  constexpr int DP = V::kDp;
+  const size_t vi = vidx(g, r, layer, i);
+  if (g.vflag[vi] != 0) return;
+  unsigned long long* row_key = g.keys + vi;
+  unsigned long long bound = __ldcg(row_key);
+  const int H = g.H;
+  const float steps = static_cast<float>(H - 1);
+  const int n_cols = layer_size(g, layer + 1);
+  float qi[DP];
+  load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
+  const int jl = j0 + lane;
+  unsigned long long key = kEmptyKey;
+  if (jl < n_cols) {
+    const float Vj = s_V[jl];
+    if (Vj < kInf && !(g.prune && g.prune[static_cast<size_t>(i) * n_cols + jl])) {
+      float qj[DP];
+      load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, jl) * g.dp, g.dp);
+      float s2 = 0.0f;
+#pragma unroll
+      for (int d = 0; d < DP; ++d) {
+        const float e = __fsub_rn(qj[d], qi[d]);
+        s2 = __fmaf_rn(e, e, s2);
+      }
+      const float len = __fsqrt_rn(s2);
+      if (!(len > g.max_edge_len)) key = make_key(__fadd_rn(len, Vj), static_cast<uint32_t>(jl));
+    }
+  }
+  if (key >= bound) key = kEmptyKey;
+  const unsigned live = __ballot_sync(kFull, key != kEmptyKey);
+  if (live == 0) return;
+  if (live & (live - 1)) key = warp_sort32_u64(key, lane);
+  else key = __shfl_sync(kFull, key, __ffs(live) - 1);  // a single candidate: move it to slot 0
+  const int n_live = __popc(live);
+  for (int t = 0; t < n_live; ++t) {
+    const unsigned long long kt = __shfl_sync(kFull, key, t);
+    if (t > 0) {
+      unsigned long long b = 0;
+      if (lane == 0) b = __ldcg(row_key);
+      b = __shfl_sync(kFull, b, 0);
+      bound = b < bound ? b : bound;
+    }
+    if (kt >= bound) break;
+    const int j = static_cast<int>(static_cast<uint32_t>(kt));
+    float qj[DP];
+    load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp);
+    float dq[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) dq[d] = __fsub_rn(qj[d], qi[d]);
+    bool hit = false;
+    if constexpr (VAR == kVarPoint) {
+      // lanes take waypoints here as well
+      for (int kb = 1; kb <= H - 2 && !hit; kb += 32) {
+        const int k = kb + lane;
+        const float tt = __fdiv_rn(static_cast<float>(k), steps);
+        float q[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(tt, dq[d], qi[d]);
+        hit = point_config_collides<true>(q, k <= H - 2, rb, s_obs, sc.n_s, s_obs + sc.n_s, sc.n_b);
+      }
+    } else {
+      for (int kb = 1; kb <= H - 2; kb += 32) {
+        const int k = kb + lane;
+        const float tt = __fdiv_rn(static_cast<float>(k), steps);
+        float q[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(tt, dq[d], qi[d]);
+        hit |= config_collides<VAR, true, false>(q, k <= H - 2, rb, s_obs, sc);
+        if (hit) break;
+      }
+    }
+    if (!hit) {
+      // the smallest remaining key of the block is free: nothing later in it can win
+      if (lane == 0) atomicMin(row_key, kt);
+      return;
+    }
+  }
+}
+
 }  // namespace
 }  // namespace gtmp

@@ -130,17 +130,31 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) fused_transition_ke
   const int cpr = (n_cols + chunk - 1) / chunk;
   const int n_chunks = n_rows * cpr;
   int* counter = counters + r;
-  while (true) {
-    int c = 0;
-    if (lane == 0) c = atomicAdd(counter, 1);
-    c = __shfl_sync(kFull, c, 0);
-    if (c >= n_chunks) break;
-    const int i = c / cpr;
-    const int j0 = (c - i * cpr) * chunk;
-    const int j1 = min(j0 + chunk, n_cols);
-    const size_t vi = vidx(g, r, layer, i);
-    const unsigned long long best = row_chunk_best<VAR, FULL>(g, r, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
-    if (lane == 0 && best != kEmptyKey) atomicMin(&g.keys[vi], best);
+  if constexpr (MODE == kEvalLazy) {
+    // units = (32-column block, row), block-major, so a row's later blocks see its earlier results
+    const int n_blk = (n_cols + 31) / 32;
+    const int n_units = n_rows * n_blk;
+    while (true) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(counter, 1);
+      c = __shfl_sync(kFull, c, 0);
+      if (c >= n_units) break;
+      const int b = c / n_rows;
+      lazy_block<VAR>(g, r, layer, c - b * n_rows, b * 32, s_V, rb, s_obs, sc, lane);
+    }
+  } else {
+    while (true) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(counter, 1);
+      c = __shfl_sync(kFull, c, 0);
+      if (c >= n_chunks) break;
+      const int i = c / cpr;
+      const int j0 = (c - i * cpr) * chunk;
+      const int j1 = min(j0 + chunk, n_cols);
+      const size_t vi = vidx(g, r, layer, i);
+      const unsigned long long best = row_chunk_best<VAR, FULL>(g, r, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
+      if (lane == 0 && best != kEmptyKey) atomicMin(&g.keys[vi], best);
+    }
   }
 }
 
@@ -455,6 +469,7 @@ template <int VAR>
 cudaError_t fused_dispatch(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int mode,
                            int* counters, int grid_x, int chunk, int* err, cudaStream_t st) {
   if (mode == kEvalFull) return fused_dispatch_mode<VAR, kEvalFull>(g, layer, rb, sc, counters, grid_x, chunk, err, st);
+  if (mode == kEvalLazy) return fused_dispatch_mode<VAR, kEvalLazy>(g, layer, rb, sc, counters, grid_x, chunk, err, st);
   return fused_dispatch_mode<VAR, kEvalEarlyExit>(g, layer, rb, sc, counters, grid_x, chunk, err, st);
 }
 
@@ -525,6 +540,9 @@ struct ConfigureRun {
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess)
       return e;
     if ((e = cudaFuncSetAttribute(fused_transition_kernel<VAR, kEvalEarlyExit>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(fused_transition_kernel<VAR, kEvalLazy>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess)
       return e;
     if ((e = cudaFuncSetAttribute(edge_costs_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) !=

@@ -44,7 +44,7 @@ __host__ __device__ inline int scene_float4s(const SceneDev& s) {
   return s.packed ? 2 * s.n_sp + 3 * s.n_bp + 2 * s.n_pairs : s.n_s + 2 * s.n_b;
 }
 
-enum EvalMode { kEvalEarlyExit = 0, kEvalFull = 1 };
+enum EvalMode { kEvalEarlyExit = 0, kEvalFull = 1, kEvalLazy = 2 };
 
 // Variant selector for the robot-specialised kernels.
 enum RobotVariant { kVarPoint = 0, kVarArm6x4 = 1, kVarArm7x4 = 2, kVarArmGeneric = 3 };

@@ -30,7 +30,7 @@ def fullsize():
     import torch
     sc = scene_for("arm", 0, 7, 30)
     out = {}
-    for mode in (binding.EVAL_EARLY_EXIT, binding.EVAL_FULL):
+    for mode in (binding.EVAL_EARLY_EXIT, binding.EVAL_FULL, binding.EVAL_LAZY):
         p = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=mode)
         p.set_scene(sc)
         p.sample_layers(7, M)
@@ -56,9 +56,10 @@ def test_samples_bit_exact(fullsize):
     np.testing.assert_array_equal(out[binding.EVAL_EARLY_EXIT]["Q"].view(np.uint32), ref.view(np.uint32))
 
 
-def test_full_evaluation_mode_is_identical(fullsize):
+@pytest.mark.parametrize("mode", [binding.EVAL_FULL, binding.EVAL_LAZY])
+def test_other_modes_are_identical(fullsize, mode):
     _, out = fullsize
-    a, b = out[binding.EVAL_EARLY_EXIT], out[binding.EVAL_FULL]
+    a, b = out[binding.EVAL_EARLY_EXIT], out[mode]
     np.testing.assert_array_equal(a["V"], b["V"])
     np.testing.assert_array_equal(a["S"], b["S"])
     np.testing.assert_array_equal(a["path"], b["path"])

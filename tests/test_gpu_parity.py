@@ -105,7 +105,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("kind,dof,M,L,H,seed", CASES)
-@pytest.mark.parametrize("mode", [binding.EVAL_EARLY_EXIT, binding.EVAL_FULL])
+@pytest.mark.parametrize("mode", [binding.EVAL_EARLY_EXIT, binding.EVAL_FULL, binding.EVAL_LAZY])
 def test_fused_solve_matches_oracle(torch_cuda, kind, dof, M, L, H, seed, mode):
     sc = scene_for(kind, seed, dof, 30 if kind == "arm" else 10)
     p = _planner(sc, M, L, H, mode=mode)
@@ -125,7 +125,7 @@ def test_fused_solve_matches_oracle(torch_cuda, kind, dof, M, L, H, seed, mode):
 def test_fused_unfused_and_modes_agree_exactly(torch_cuda, kind, dof, M, L, H, seed):
     sc = scene_for(kind, seed, dof, 30 if kind == "arm" else 10)
     outs = []
-    for mode in (binding.EVAL_EARLY_EXIT, binding.EVAL_FULL):
+    for mode in (binding.EVAL_EARLY_EXIT, binding.EVAL_FULL, binding.EVAL_LAZY):
         p = _planner(sc, M, L, H, mode=mode)
         p.sample_layers(seed, M)
         outs.append(_gpu_solution(p))
@@ -173,10 +173,11 @@ def test_no_obstacles_collinear_samples(torch_cuda):
 # anytime-gtmp: every restart is an independent gtmp
 # ---------------------------------------------------------------------------
 
-def test_anytime_restarts_match_oracle(torch_cuda):
+@pytest.mark.parametrize("mode", [binding.EVAL_EARLY_EXIT, binding.EVAL_LAZY])
+def test_anytime_restarts_match_oracle(torch_cuda, mode):
     sc = scene_for("arm", 3, 6, 30)
     R, M, L, H = 6, 24, 3, 16
-    p = _planner(sc, M, L, H, R=R)
+    p = _planner(sc, M, L, H, R=R, mode=mode)
     paths, costs, best = p.anytime(21, R)
     p.synchronize()
     paths, costs, best = paths.cpu().numpy(), costs.cpu().numpy(), int(best.cpu()[0])
