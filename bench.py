@@ -472,6 +472,55 @@ def run_batched(args, wl):
                      for k, (_, co) in enumerate(outs))
     for pl, _, _, _ in planners:
         pl.close()
+    # lazy mode, both forms: one persistent launch vs the plain solver one problem after another
+    lazy = None
+    if args.lazy:
+        tune = binding.Batch(problems[::max(1, len(problems) // 96)][:96], H, eval_mode=binding.EVAL_LAZY)
+        tune.autotune(repeats=1)
+        lz_tiling = binding.gtmp_batch_get_tiling(tune.handle)
+        tune.close()
+        bl = binding.Batch(problems, H, eval_mode=binding.EVAL_LAZY)
+        binding.gtmp_batch_set_tiling(bl.handle, *lz_tiling)
+        for _ in range(args.warmup):
+            bl.solve()
+        bl.synchronize()
+        lz_ms = []
+        for s in range(args.steps):
+            flush.zero_()
+            e0.record(stream)
+            bl.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lz_ms.append(e0.elapsed_time(e1))
+        bl.synchronize()
+        lz_costs = bl.costs.cpu().numpy()
+        bl.close()
+        lz_batched_s = max_over_ranks(sum(lz_ms) / 1e3, world, "cuda")
+        planners = []
+        for sc, M, L, seed in problems:
+            pl = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_LAZY)
+            pl.set_scene(sc)
+            planners.append((pl, M, L, seed))
+        plain_pass()
+        torch.cuda.synchronize()
+        plz_ms = []
+        for s in range(args.steps):
+            flush.zero_()
+            e0.record(stream)
+            plain_pass()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plz_ms.append(e0.elapsed_time(e1))
+        lz_same = all(float(co.cpu()[0]) == float(costs[k]) or (math.isinf(costs[k]) and math.isinf(float(co.cpu()[0])))
+                      for k, (_, co) in enumerate(outs))
+        lz_same = lz_same and bool(np.array_equal(lz_costs, costs))
+        for pl, _, _, _ in planners:
+            pl.close()
+        plz_s = max_over_ranks(sum(plz_ms) / 1e3, world, "cuda")
+        lazy = {"batched_solves_per_s": wl["n"] * args.steps * world / lz_batched_s,
+                "plain_sequential_solves_per_s": wl["n"] * args.steps * world / plz_s,
+                "batched_ms_per_batch": sum(lz_ms) / len(lz_ms), "plain_ms_per_batch": sum(plz_ms) / len(plz_ms),
+                "tiling": list(lz_tiling), "same_costs_as_early_exit": lz_same}
     breakdown = None
     if args.breakdown:
         breakdown = {}
@@ -520,10 +569,114 @@ def run_batched(args, wl):
             "clocks": clk.summary(),
             "plain_sequential": {"solves_per_s": wl["n"] / plain_s, "s_per_batch": plain_s,
                                  "same_costs_as_batched": bool(plain_same)},
+            "lazy": lazy,
             "breakdown": breakdown,
         }
         print(json.dumps(out), flush=True)
     b.close()
+
+
+def run_surrogate(args, wl):
+    """Surrogate-pruned solves against plain solves of the same samples, early-exit and lazy."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25830_b300 import binding, scenes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    M, L, H = wl["M"], wl["L"], wl["H"]
+    base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
+    probe = binding.Planner(base.robot, 8, 1, 2, max_obstacles=64)
+    binding.gtmp_set_obstacles(probe.ctx, base.spheres, base.boxes)
+    sc = scenes.pick_endpoints(base, lambda q: probe.label_configs(
+        torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
+    probe.close()
+    planners = {}
+    for name, mode in (("early_exit", binding.EVAL_EARLY_EXIT), ("lazy", binding.EVAL_LAZY)):
+        planners[name] = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=mode)
+        planners[name].set_scene(sc)
+    train = binding.gtmp_surrogate_train(planners["early_exit"].ctx, n_train=wl["n_train"], n_holdout=1 << 16,
+                                         epochs=wl["epochs"], batch=1024, lr=1e-3, seed=1,
+                                         fourier_sigma=wl["sigma"])
+    binding.gtmp_surrogate_set_params(planners["lazy"].ctx,
+                                      binding.gtmp_surrogate_get_params(planners["early_exit"].ctx, sc.robot.dof))
+    thr, kw = wl["threshold"], wl["score_waypoints"]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    path = torch.empty(L, dtype=torch.int32, device="cuda")
+    cost = torch.empty(1, dtype=torch.float32, device="cuda")
+    seed0 = rank_seed_base(rank)
+    steps = {k: [] for k in ("early_exit", "early_exit_pruned", "lazy", "lazy_pruned")}
+    ratios, pruned_frac, colliding_waypoints, checked = [], [], 0, 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def recheck(pl, pa):
+        """Every waypoint of a returned chain through the exact checker (GPU)."""
+        Q = pl.get_layers().double().cpu().numpy()
+        verts = [sc.q_start.astype(np.float64)] + [Q[l, pa[l]] for l in range(L)] + [sc.q_goal.astype(np.float64)]
+        t = np.arange(H, dtype=np.float64)[:, None] / (H - 1)
+        wps = np.concatenate([u + t * (v - u) for u, v in zip(verts[:-1], verts[1:])]).astype(np.float32)
+        return int(pl.label_configs(torch.from_numpy(wps).cuda()).sum()), len(wps)
+
+    for s in range(-args.warmup, args.steps):
+        seed = seed0 + (10_000 + s if s < 0 else s)
+        row = {}
+        for name, pl in planners.items():
+            pl.sample_layers(seed, M)
+            ms, _ = timed(lambda: binding.gtmp_solve(pl.ctx, path, cost))
+            c_plain = float(cost.cpu()[0])
+            msp, st = timed(lambda: binding.gtmp_solve_pruned(pl.ctx, thr, path, cost, score_waypoints=kw))
+            c_pruned = float(cost.cpu()[0])
+            row[name] = (ms, msp, c_plain, c_pruned, st)
+            if s >= 0 and math.isfinite(c_pruned):
+                bad, n = recheck(pl, path.cpu().numpy())
+                colliding_waypoints += bad
+                checked += n
+        if s < 0:
+            continue
+        for name in planners:
+            ms, msp, c_plain, c_pruned, st = row[name]
+            steps[name].append(ms)
+            steps[name + "_pruned"].append(msp)
+        ms, msp, c_plain, c_pruned, st = row["early_exit"]
+        assert row["lazy"][2] == c_plain or (math.isinf(c_plain) and math.isinf(row["lazy"][2]))
+        pruned_frac.append(st["pruned"] / st["edges"])
+        if math.isfinite(c_plain):
+            ratios.append(c_pruned / c_plain if math.isfinite(c_pruned) else math.inf)
+    tot = {k: max_over_ranks(sum(v) / 1e3, world, "cuda") for k, v in steps.items()}
+    sps = {k: args.steps * world / v for k, v in tot.items()}
+    if rank == 0:
+        fin = [r for r in ratios if math.isfinite(r)]
+        print(json.dumps({
+            "metric": "solves/s, surrogate-pruned vs plain (7-DoF, M=4096, L=8, H=32, 40 obstacles)",
+            "value": sps["early_exit_pruned"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(steps["early_exit_pruned"]) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 surrogate, f32 checker",
+            "data": "synthetic (seeded scene and samples)",
+            "config": {"workload": args.workload, "M": M, "L": L, "H": H, "dof": wl["dof"], "obstacles": wl["n_obs"],
+                       "threshold": thr, "score_waypoints": kw, "l2": "flushed between solves"},
+            "solves_per_s": sps,
+            "surrogate_over_plain": {"early_exit": sps["early_exit_pruned"] / sps["early_exit"],
+                                     "lazy": sps["lazy_pruned"] / sps["lazy"]},
+            "cost_ratio_pruned_over_plain": {"mean": float(np.mean(fin)) if fin else None,
+                                             "max": float(np.max(fin)) if fin else None,
+                                             "lost_feasibility": len(ratios) - len(fin), "solves": len(ratios)},
+            "pruned_edge_fraction": float(np.mean(pruned_frac)),
+            "returned_paths_recheck": {"waypoints": checked, "colliding": colliding_waypoints},
+            "training": train,
+        }), flush=True)
+    for pl in planners.values():
+        pl.close()
 
 
 def run_anytime(args, wl):
@@ -646,6 +799,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=10.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lazy", action="store_true", help="batched workload: also time the lazy mode, both forms")
     ap.add_argument("--breakdown", action="store_true", help="batched workload: time arm and 2D subsets separately")
     args = ap.parse_args()
     wl = dict(scenes.WORKLOADS[args.workload])
@@ -653,6 +807,11 @@ def main():
         if args.impl == "reference":
             raise SystemExit("the reference arm times the single-solve workload")
         {"batched": run_batched}.get(wl["kind"], run_anytime if "R" in wl else run_ao)(args, wl)
+        return
+    if "n_train" in wl:
+        if args.impl == "reference":
+            raise SystemExit("the reference arm times the single-solve workload")
+        run_surrogate(args, wl)
         return
     if "M" not in wl:
         raise SystemExit(f"{args.workload} is not a single-solve workload")

@@ -308,6 +308,12 @@ GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t* target_
 GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t* dev_paths, float* dev_costs,
                                          float* best_ms);
 
+/* Edge realisation of the batched solve: GTMP_EVAL_EARLY_EXIT (default) or
+ * GTMP_EVAL_LAZY (the bound-ordered exact mode of gtmp_params.eval_mode; each
+ * problem's result is unchanged bit for bit).  Takes effect at the next
+ * gtmp_batch_solve; GTMP_ERR_INVALID_ARG for any other mode. */
+GTMP_API gtmp_status gtmp_batch_set_eval_mode(gtmp_batch* b, int32_t eval_mode);
+
 /* ---------------------------------------------------------------------------
  * Learned collision surrogate and surrogate-pruned solve (serving pattern; the
  * paper has no surrogate and names lazy edge realisation as future work,
@@ -371,7 +377,8 @@ GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* ctx, const float* dev_q,
  * the surrogate's collision probability at any of its scored waypoints
  * (score_waypoints = 1: t = 1/2; 3: t = 1/4, 1/2, 3/4) exceeds threshold;
  * scoring runs in one fused tensor-core kernel per transition.  Every
- * surviving edge is realised by the exact checker, so a returned path is
+ * surviving edge is realised by the exact checker (lazily when the context's
+ * eval_mode is GTMP_EVAL_LAZY, else with early exit), so a returned path is
  * collision free at its H waypoints; the cost can exceed gtmp_solve's when a
  * free edge is dropped.  Synchronous (returns the stats); allocates an M x M
  * mask on first use. */

@@ -105,6 +105,7 @@ _SIGNATURES = {
     "gtmp_batch_set_tiling": [_vp, _i32, _i32],
     "gtmp_batch_get_tiling": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "gtmp_batch_autotune": [_vp, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_float)],
+    "gtmp_batch_set_eval_mode": [_vp, _i32],
     "gtmp_surrogate_train": [_vp, ctypes.POINTER(GtmpSurrogateConfig), ctypes.POINTER(GtmpSurrogateStats)],
     "gtmp_surrogate_predict": [_vp, _vp, _i32, _vp],
     "gtmp_surrogate_get_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
@@ -454,6 +455,10 @@ def gtmp_batch_get_tiling(b):
     return t.value, c.value
 
 
+def gtmp_batch_set_eval_mode(b, eval_mode):
+    _bcheck(b, lib().gtmp_batch_set_eval_mode(b, eval_mode))
+
+
 def gtmp_batch_autotune(b, repeats, dev_paths, dev_costs):
     import torch
     ms = ctypes.c_float()
@@ -465,10 +470,12 @@ def gtmp_batch_autotune(b, repeats, dev_paths, dev_costs):
 class Batch:
     """Many independent problems solved by one persistent launch."""
 
-    def __init__(self, problems, H):
+    def __init__(self, problems, H, eval_mode=None):
         import torch
         self.n = len(problems)
         self.handle = gtmp_batch_create(problems, H)
+        if eval_mode is not None:
+            gtmp_batch_set_eval_mode(self.handle, eval_mode)
         self.L_max, self.nominal_checks, self.work_items = gtmp_batch_info(self.handle)
         self.paths = torch.empty((self.n, self.L_max), dtype=torch.int32, device="cuda")
         self.costs = torch.empty(self.n, dtype=torch.float32, device="cuda")

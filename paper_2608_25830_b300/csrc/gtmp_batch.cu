@@ -136,12 +136,26 @@ __global__ void __launch_bounds__(kThreads) batch_labels_kernel(const ProblemDev
 // ---------------------------------------------------------------------------
 template <int VAR>
 __device__ __forceinline__ void item_rows(const GraphDev g, const SceneDev sc, int layer, int row0, int rows,
-                                          int col0, int cols, int chunk, const float* s_V, const RobotDev& rb,
-                                          const float4* s_obs, int* s_next) {
+                                          int col0, int cols, int chunk, bool lazy, const float* s_V,
+                                          const RobotDev& rb, const float4* s_obs, int* s_next) {
+  const int lane = threadIdx.x & 31;
+  if (lazy) {
+    // (32-column block, row) units, block-major, as the single-problem lazy kernel
+    const int n_blk = (cols + 31) / 32;
+    const int n_units = rows * n_blk;
+    while (true) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(s_next, 1);
+      c = __shfl_sync(kFull, c, 0);
+      if (c >= n_units) break;
+      const int b = c / rows;
+      lazy_block<VAR>(g, 0, layer, row0 + c - b * rows, col0 + b * 32, col0 + cols, s_V, rb, s_obs, sc, lane);
+    }
+    return;
+  }
   if (VAR == kVarPoint) chunk = chunk < 32 ? 32 : chunk;  // one edge per lane
   const int cpr = (cols + chunk - 1) / chunk;
   const int n_chunks = rows * cpr;
-  const int lane = threadIdx.x & 31;
   while (true) {
     int c = 0;
     if (lane == 0) c = atomicAdd(s_next, 1);
@@ -160,15 +174,15 @@ __device__ __forceinline__ void item_rows(const GraphDev g, const SceneDev sc, i
 // inlining the variants into one switch, which spills)
 template <int VAR>
 __device__ __noinline__ void item_rows_call(const GraphDev g, const SceneDev sc, int layer, int row0, int rows,
-                                            int col0, int cols, int chunk, const float* s_V, const RobotDev& rb,
-                                            const float4* s_obs, int* s_next) {
-  item_rows<VAR>(g, sc, layer, row0, rows, col0, cols, chunk, s_V, rb, s_obs, s_next);
+                                            int col0, int cols, int chunk, bool lazy, const float* s_V,
+                                            const RobotDev& rb, const float4* s_obs, int* s_next) {
+  item_rows<VAR>(g, sc, layer, row0, rows, col0, cols, chunk, lazy, s_V, rb, s_obs, s_next);
 }
 
 __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
     batch_persistent_kernel(const ProblemDev* __restrict__ probs, const RobotDev* __restrict__ robots,
                             const WorkItem* __restrict__ items, int n_items, const int* __restrict__ need,
-                            int* done, int* next_item, int chunk, int* err) {
+                            int* done, int* next_item, int chunk, int lazy, int* err) {
   __shared__ RobotDev s_rb;
   __shared__ int s_item, s_next, s_ok;
   extern __shared__ __align__(16) float4 smem[];
@@ -228,17 +242,20 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
     const SceneDev sc = P.sc;
     switch (P.variant) {
       case kVarPoint:
-        item_rows_call<kVarPoint>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem, &s_next);
+        item_rows_call<kVarPoint>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, lazy != 0, s_V, s_rb,
+                                  smem, &s_next);
         break;
       case kVarArm6x4:
-        item_rows_call<kVarArm6x4>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem, &s_next);
+        item_rows_call<kVarArm6x4>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, lazy != 0, s_V, s_rb,
+                                   smem, &s_next);
         break;
       case kVarArm7x4:
-        item_rows_call<kVarArm7x4>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem, &s_next);
+        item_rows_call<kVarArm7x4>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, lazy != 0, s_V, s_rb,
+                                   smem, &s_next);
         break;
       default:
-        item_rows_call<kVarArmGeneric>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem,
-                                       &s_next);
+        item_rows_call<kVarArmGeneric>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, lazy != 0, s_V, s_rb,
+                                       smem, &s_next);
         break;
     }
     __threadfence();
@@ -288,6 +305,7 @@ struct gtmp_batch {
   // tiling (autotuned)
   int target_edges = 8192;
   int chunk = 16;
+  int eval_mode = GTMP_EVAL_EARLY_EXIT;
   int n_items = 0;
   // device memory
   ProblemDev* d_probs = nullptr;
@@ -458,7 +476,7 @@ gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
   const size_t smem = b->obs4_max * sizeof(float4) + static_cast<size_t>(b->M_max) * sizeof(float);
   batch_persistent_kernel<<<b->num_sms * b->bps, kThreads, smem, st>>>(
       b->d_probs, b->d_robots, b->d_items, b->n_items, b->d_need, b->d_done, b->d_done + b->need.size(), b->chunk,
-      b->d_err);
+      b->eval_mode == GTMP_EVAL_LAZY ? 1 : 0, b->d_err);
   BATCH_TRY(b, cudaGetLastError());
   batch_paths_kernel<<<(b->n + 127) / 128, 128, 0, st>>>(b->d_probs, b->n, b->L_max, dev_paths, dev_costs);
   BATCH_TRY(b, cudaGetLastError());
@@ -704,6 +722,13 @@ GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t
   if (s != GTMP_OK) return s;
   if (best_ms) *best_ms = best;
   return gtmp_batch_set_tiling(b, best_t, best_c);
+}
+
+GTMP_API gtmp_status gtmp_batch_set_eval_mode(gtmp_batch* b, int32_t eval_mode) {
+  if (!b || (eval_mode != GTMP_EVAL_EARLY_EXIT && eval_mode != GTMP_EVAL_LAZY))
+    return bfail(b, GTMP_ERR_INVALID_ARG, "batch eval mode must be GTMP_EVAL_EARLY_EXIT or GTMP_EVAL_LAZY");
+  b->eval_mode = eval_mode;
+  return GTMP_OK;
 }
 
 GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t* target_edges, int32_t* chunk) {

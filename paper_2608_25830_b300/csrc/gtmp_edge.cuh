@@ -261,7 +261,8 @@ __device__ __forceinline__ unsigned long long row_chunk_best(const GraphDev& g, 
 // Lazy realisation (exact).  The best key of row i is the smallest
 // (c(i,j) + J_{l+1}(j), j) over realised edges; an edge whose key is not below
 // a key already found for the row cannot change the row's minimum, so it is
-// never checked.  The unit of work is one block of 32 columns of one row:
+// never checked.  The unit of work is one block of (up to) 32 columns
+// [j0, min(j0 + 32, j_end)) of one row:
 // the warp scores the block's candidates (lane = column), drops those at or
 // above the row's current best (the row's key word in global memory, which
 // every unit of the row lowers with atomicMin), sorts the rest (bitonic,
@@ -288,8 +289,9 @@ __device__ __forceinline__ unsigned long long warp_sort32_u64(unsigned long long
 }
 
 template <int VAR>
-__device__ __forceinline__ void lazy_block(const GraphDev& g, int r, int layer, int i, int j0, const float* s_V,
-                                           const RobotDev& rb, const float4* s_obs, const SceneDev& sc, int lane) {
+__device__ __forceinline__ void lazy_block(const GraphDev& g, int r, int layer, int i, int j0, int j_end,
+                                           const float* s_V, const RobotDev& rb, const float4* s_obs,
+                                           const SceneDev& sc, int lane) {
   using V = Var<VAR>;
   constexpr int DP = V::kDp;
   const size_t vi = vidx(g, r, layer, i);
@@ -303,7 +305,7 @@ __device__ __forceinline__ void lazy_block(const GraphDev& g, int r, int layer, 
   load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
   const int jl = j0 + lane;
   unsigned long long key = kEmptyKey;
-  if (jl < n_cols) {
+  if (jl < j_end) {
     const float Vj = s_V[jl];
     if (Vj < kInf && !(g.prune && g.prune[static_cast<size_t>(i) * n_cols + jl])) {
       float qj[DP];

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) fused_transition_ke
       c = __shfl_sync(kFull, c, 0);
       if (c >= n_units) break;
       const int b = c / n_rows;
-      lazy_block<VAR>(g, r, layer, c - b * n_rows, b * 32, s_V, rb, s_obs, sc, lane);
+      lazy_block<VAR>(g, r, layer, c - b * n_rows, b * 32, n_cols, s_V, rb, s_obs, sc, lane);
     }
   } else {
     while (true) {

@@ -12,6 +12,7 @@
 // collision with probability above the threshold; every edge that survives
 // is still realised by the exact checker, which therefore judges every
 // returned path.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <random>
@@ -1076,16 +1077,24 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     // exact realisation of the surviving edges, fused with the min-plus step
     GraphDev gp = g;
     gp.prune = c->prune;
-    long long chunk = ne / (static_cast<long long>(resident) * 64);
-    if (chunk < 1) chunk = 1;
-    if (chunk > 32) chunk = 32;
-    if (c->variant == kVarPoint) chunk = 32;
-    if (chunk > cols) chunk = cols;
-    const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
-    int grid = resident;
-    if (grid > (n_chunks + 7) / 8) grid = static_cast<int>((n_chunks + 7) / 8);
-    SUR_TRY(c, launch_fused_transition(gp, layer, c->rb, c->variant, ctx_scene(c), GTMP_EVAL_EARLY_EXIT,
-                                       c->counters + layer, grid, static_cast<int>(chunk), c->err, st));
+    if (c->p.eval_mode == GTMP_EVAL_LAZY) {
+      // bound-ordered realisation of the surviving edges (one warp per 32-column block of a row)
+      const long long units = static_cast<long long>(rows) * ((cols + 31) / 32);
+      const int lgrid = static_cast<int>(std::max(1LL, std::min<long long>(resident, (units + 7) / 8)));
+      SUR_TRY(c, launch_fused_transition(gp, layer, c->rb, c->variant, ctx_scene(c), GTMP_EVAL_LAZY,
+                                         c->counters + layer, lgrid, 32, c->err, st));
+    } else {
+      long long chunk = ne / (static_cast<long long>(resident) * 64);
+      if (chunk < 1) chunk = 1;
+      if (chunk > 32) chunk = 32;
+      if (c->variant == kVarPoint) chunk = 32;
+      if (chunk > cols) chunk = cols;
+      const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
+      int grid = resident;
+      if (grid > (n_chunks + 7) / 8) grid = static_cast<int>((n_chunks + 7) / 8);
+      SUR_TRY(c, launch_fused_transition(gp, layer, c->rb, c->variant, ctx_scene(c), GTMP_EVAL_EARLY_EXIT,
+                                         c->counters + layer, grid, static_cast<int>(chunk), c->err, st));
+    }
     cudaEventRecord(e2, st);
     SUR_TRY(c, cudaEventSynchronize(e2));
     float a = 0.0f, b = 0.0f;

@@ -179,7 +179,8 @@ WORKLOADS = {
     "arm7_m1024_l8_h32": dict(kind="arm", dof=7, seed=0, n_obs=30, M=1024, L=8, H=32),
     "arm6_anytime_r64_m256_l6_h32": dict(kind="arm", dof=6, seed=0, n_obs=30, M=256, L=6, H=32, R=64),
     "arm6_ao_m64to4096_l6_h32": dict(kind="arm", dof=6, seed=0, n_obs=30, M0=64, M1=4096, L=6, H=32),
-    "arm7_m4096_l8_h32_n40": dict(kind="arm", dof=7, seed=0, n_obs=40, M=4096, L=8, H=32),
+    "arm7_m4096_l8_h32_n40": dict(kind="arm", dof=7, seed=0, n_obs=40, M=4096, L=8, H=32,
+                                  n_train=1 << 21, epochs=3, sigma=0.25, threshold=0.5, score_waypoints=1),
     "batched512_h32": dict(kind="batched", seed=0, n=512, H=32),
 }
 

@@ -75,6 +75,30 @@ def test_every_tiling_gives_the_same_plans(mixed, target, chunk):
     b.close()
 
 
+@pytest.mark.parametrize("target", [1, 4096, 1 << 20])
+def test_lazy_batch_gives_the_same_plans(mixed, target):
+    probs, H, singles = mixed
+    b = binding.Batch(probs, H, eval_mode=binding.EVAL_LAZY)
+    binding.gtmp_batch_set_tiling(b.handle, target, 16)
+    for _ in range(2):
+        b.solve()
+        b.synchronize()
+        _check_against_singles(b, probs, singles)
+    binding.gtmp_batch_set_eval_mode(b.handle, binding.EVAL_EARLY_EXIT)
+    b.solve()
+    b.synchronize()
+    _check_against_singles(b, probs, singles)
+    b.close()
+
+
+def test_batch_rejects_full_mode(mixed):
+    probs, H, _ = mixed
+    b = binding.Batch(probs[:2], H)
+    assert binding.lib().gtmp_batch_set_eval_mode(b.handle, binding.EVAL_FULL) == 1
+    assert binding.lib().gtmp_batch_set_eval_mode(b.handle, 9) == 1
+    b.close()
+
+
 def test_autotune_keeps_results(mixed):
     probs, H, singles = mixed
     b = binding.Batch(probs, H)
