@@ -215,6 +215,10 @@ typedef struct {
   int64_t fused_launches;  /* fused edge + min-plus launches timed */
   double fused_ms;         /* their summed device time (ms) */
   double fused_edges;      /* candidate edges those launches processed */
+  int64_t minplus_launches;  /* min-plus launches of gtmp_solve_unfused timed */
+  double minplus_ms;         /* their summed device time (ms) */
+  double minplus_bytes;      /* their algorithmic HBM bytes: 4 per stored edge cost read, 8 per
+                                cost-to-go read and 8 per cost-to-go written */
 } gtmp_profile;
 
 GTMP_API gtmp_status gtmp_profile_enable(gtmp_ctx* ctx, int32_t enable);
@@ -299,8 +303,9 @@ GTMP_API gtmp_status gtmp_batch_info(const gtmp_batch* b, int32_t* L_max, double
 GTMP_API gtmp_status gtmp_batch_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs);
 GTMP_API gtmp_status gtmp_batch_synchronize(gtmp_batch* b);
 
-/* Tiling of the work list: about target_edges candidate edges per item, and
- * chunk columns per warp claim.  gtmp_batch_autotune times every pair of a
+/* Tiling of the work list: about target_edges candidate edges per item (arm
+ * edges; point-robot items hold 16 times as many; an item smaller than a row
+ * is a column piece of one row), and chunk columns per warp claim.  gtmp_batch_autotune times every pair of a
  * small grid of tilings (repeats solves each, into the given buffers), keeps
  * the fastest and returns its time per solve in *best_ms (host, optional). */
 GTMP_API gtmp_status gtmp_batch_set_tiling(gtmp_batch* b, int32_t target_edges, int32_t chunk);

@@ -46,7 +46,8 @@ class GtmpParams(ctypes.Structure):
 
 class GtmpProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("fused_launches", ctypes.c_int64), ("fused_ms", ctypes.c_double),
-                ("fused_edges", ctypes.c_double)]
+                ("fused_edges", ctypes.c_double), ("minplus_launches", ctypes.c_int64), ("minplus_ms", ctypes.c_double),
+                ("minplus_bytes", ctypes.c_double)]
 
 
 _lib = None
@@ -282,7 +283,8 @@ def gtmp_profile_read(ctx):
     out = GtmpProfile()
     _check(ctx, lib().gtmp_profile_read(ctx, ctypes.byref(out)))
     return dict(launches=out.launches, fused_launches=out.fused_launches, fused_ms=out.fused_ms,
-                fused_edges=out.fused_edges)
+                fused_edges=out.fused_edges, minplus_launches=out.minplus_launches, minplus_ms=out.minplus_ms,
+                minplus_bytes=out.minplus_bytes)
 
 
 def gtmp_solve_noalloc(robot: scenes.Robot, spheres, boxes, q_start, q_goal, dev_Q, H, dev_path, dev_cost,

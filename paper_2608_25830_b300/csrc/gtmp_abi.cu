@@ -97,7 +97,7 @@ gtmp_status run_fused(gtmp_ctx* c, const GraphDev& g, int mode) {
       int grid_x = static_cast<int>(std::max(1LL, std::min<long long>(c->num_sms * bps / g.R, (units + 7) / 8)));
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (c->timing) {
-        const size_t slot = c->ev_used.size() * 2;
+        const size_t slot = (c->ev_used.size() + c->ev_minplus.size()) * 2;
         CUDA_TRY(c, event_at(c, slot, &e0));
         CUDA_TRY(c, event_at(c, slot + 1, &e1));
         CUDA_TRY(c, cudaEventRecord(e0, c->stream));
@@ -107,7 +107,7 @@ gtmp_status run_fused(gtmp_ctx* c, const GraphDev& g, int mode) {
       LAUNCHED(c, 1);
       if (c->timing) {
         CUDA_TRY(c, cudaEventRecord(e1, c->stream));
-        const size_t slot = c->ev_used.size() * 2;
+        const size_t slot = (c->ev_used.size() + c->ev_minplus.size()) * 2;
         c->ev_used.emplace_back(static_cast<int>(slot), static_cast<int>(slot + 1));
         c->timed_edges += static_cast<double>(rows) * layer_size(g, layer + 1) * g.R;
       }
@@ -135,7 +135,7 @@ gtmp_status run_fused(gtmp_ctx* c, const GraphDev& g, int mode) {
     if (grid_x > useful_blocks) grid_x = static_cast<int>(useful_blocks);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->timing) {
-      const size_t slot = c->ev_used.size() * 2;
+      const size_t slot = (c->ev_used.size() + c->ev_minplus.size()) * 2;
       CUDA_TRY(c, event_at(c, slot, &e0));
       CUDA_TRY(c, event_at(c, slot + 1, &e1));
       CUDA_TRY(c, cudaEventRecord(e0, c->stream));
@@ -145,7 +145,7 @@ gtmp_status run_fused(gtmp_ctx* c, const GraphDev& g, int mode) {
     LAUNCHED(c, 1);
     if (c->timing) {
       CUDA_TRY(c, cudaEventRecord(e1, c->stream));
-      const size_t slot = c->ev_used.size() * 2;
+      const size_t slot = (c->ev_used.size() + c->ev_minplus.size()) * 2;
       c->ev_used.emplace_back(static_cast<int>(slot), static_cast<int>(slot + 1));
       c->timed_edges += static_cast<double>(edges) * g.R;
     }
@@ -459,9 +459,20 @@ gtmp_status gtmp_profile_read(gtmp_ctx* c, gtmp_profile* out) {
   out->fused_launches = static_cast<int64_t>(c->ev_used.size());
   out->fused_ms = ms;
   out->fused_edges = c->timed_edges;
+  double mp = 0.0;
+  for (const auto& pr : c->ev_minplus) {
+    float t = 0.0f;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev_pool[pr.first], c->ev_pool[pr.second]));
+    mp += t;
+  }
+  out->minplus_launches = static_cast<int64_t>(c->ev_minplus.size());
+  out->minplus_ms = mp;
+  out->minplus_bytes = c->minplus_bytes;
   c->launches = 0;
   c->ev_used.clear();
   c->timed_edges = 0.0;
+  c->ev_minplus.clear();
+  c->minplus_bytes = 0.0;
   return GTMP_OK;
 }
 
@@ -552,8 +563,22 @@ gtmp_status gtmp_solve_unfused(gtmp_ctx* c, int32_t* dev_path, float* dev_cost) 
     transition_shape(g, layer, &rows, &cols);
     int grid = (rows + 7) / 8;
     if (grid > c->num_sms * 8) grid = c->num_sms * 8;
+    size_t slot = 0;
+    if (c->timing) {
+      slot = (c->ev_used.size() + c->ev_minplus.size()) * 2;
+      cudaEvent_t e0 = nullptr;
+      CUDA_TRY(c, event_at(c, slot, &e0));
+      CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+    }
     CUDA_TRY(c, launch_minplus(g, layer, c->C + c->c_off[layer], c->c_cs[layer], grid, c->stream));
     LAUNCHED(c, 1);
+    if (c->timing) {
+      cudaEvent_t e1 = nullptr;
+      CUDA_TRY(c, event_at(c, slot + 1, &e1));
+      CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+      c->ev_minplus.emplace_back(static_cast<int>(slot), static_cast<int>(slot + 1));
+      c->minplus_bytes += 4.0 * rows * cols + 8.0 * cols + 8.0 * rows;
+    }
   }
   CUDA_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, c->stream));
   LAUNCHED(c, 1);

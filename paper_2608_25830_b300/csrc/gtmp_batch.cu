@@ -43,6 +43,7 @@ struct WorkItem {
 };
 
 constexpr int kBoundaryItemEdges = 256;          // item size cap for the start row and the goal column
+constexpr int kPointItemScale = 16;              // point-robot items hold this many times more edges
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz without progress
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -134,12 +135,12 @@ __global__ void __launch_bounds__(kThreads) batch_labels_kernel(const ProblemDev
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <int VAR>
-__device__ __forceinline__ void item_rows(const GraphDev g, const SceneDev sc, int layer, int row0, int rows,
-                                          int col0, int cols, int chunk, bool lazy, const float* s_V,
-                                          const RobotDev& rb, const float4* s_obs, int* s_next) {
+template <int VAR, bool LAZY>
+__device__ __forceinline__ void item_rows(const GraphDev& g, const SceneDev& sc, int layer, int row0, int rows,
+                                          int col0, int cols, int chunk, const float* s_V, const RobotDev& rb,
+                                          const float4* s_obs, int* s_next) {
   const int lane = threadIdx.x & 31;
-  if (lazy) {
+  if constexpr (LAZY) {
     // (32-column block, row) units, block-major, as the single-problem lazy kernel
     const int n_blk = (cols + 31) / 32;
     const int n_units = rows * n_blk;
@@ -151,32 +152,55 @@ __device__ __forceinline__ void item_rows(const GraphDev g, const SceneDev sc, i
       const int b = c / rows;
       lazy_block<VAR>(g, 0, layer, row0 + c - b * rows, col0 + b * 32, col0 + cols, s_V, rb, s_obs, sc, lane);
     }
-    return;
-  }
-  if (VAR == kVarPoint) chunk = chunk < 32 ? 32 : chunk;  // one edge per lane
-  const int cpr = (cols + chunk - 1) / chunk;
-  const int n_chunks = rows * cpr;
-  while (true) {
-    int c = 0;
-    if (lane == 0) c = atomicAdd(s_next, 1);
-    c = __shfl_sync(kFull, c, 0);
-    if (c >= n_chunks) break;
-    const int i = row0 + c / cpr;
-    const int j0 = col0 + (c % cpr) * chunk;
-    const int j1 = min(j0 + chunk, col0 + cols);
-    const unsigned long long best = row_chunk_best<VAR, false>(g, 0, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
-    if (lane == 0 && best != kEmptyKey) atomicMin(&g.keys[vidx(g, 0, layer, i)], best);
+  } else {
+    if (VAR == kVarPoint) chunk = chunk < 32 ? 32 : chunk;  // one edge per lane
+    const int cpr = (cols + chunk - 1) / chunk;
+    const int n_chunks = rows * cpr;
+    while (true) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(s_next, 1);
+      c = __shfl_sync(kFull, c, 0);
+      if (c >= n_chunks) break;
+      const int i = row0 + c / cpr;
+      const int j0 = col0 + (c % cpr) * chunk;
+      const int j1 = min(j0 + chunk, col0 + cols);
+      const unsigned long long best = row_chunk_best<VAR, false>(g, 0, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
+      if (lane == 0 && best != kEmptyKey) atomicMin(&g.keys[vidx(g, 0, layer, i)], best);
+    }
   }
 }
 
-// one out-of-line body per robot variant: the persistent loop's own state
-// stays out of the register budget of the edge code (measured faster than
-// inlining the variants into one switch, which spills)
-template <int VAR>
-__device__ __noinline__ void item_rows_call(const GraphDev g, const SceneDev sc, int layer, int row0, int rows,
-                                            int col0, int cols, int chunk, bool lazy, const float* s_V,
-                                            const RobotDev& rb, const float4* s_obs, int* s_next) {
-  item_rows<VAR>(g, sc, layer, row0, rows, col0, cols, chunk, lazy, s_V, rb, s_obs, s_next);
+// one out-of-line body per robot variant and mode: the persistent loop's own
+// state stays out of the register budget of the edge code (measured faster
+// than inlining the variants into one switch, which spills); the problem's
+// graph and scene descriptors are read from shared memory, not held in
+// registers (the single-problem kernel has them in its parameter bank)
+template <int VAR, bool LAZY>
+__device__ __noinline__ void item_rows_call(const GraphDev& g, const SceneDev& sc, int layer, int row0, int rows,
+                                            int col0, int cols, int chunk, const float* s_V, const RobotDev& rb,
+                                            const float4* s_obs, int* s_next) {
+  item_rows<VAR, LAZY>(g, sc, layer, row0, rows, col0, cols, chunk, s_V, rb, s_obs, s_next);
+}
+
+template <bool LAZY>
+__device__ __forceinline__ void item_dispatch(int variant, const GraphDev& g, const SceneDev& sc, int layer,
+                                              const WorkItem& w, int chunk, const float* s_V, const RobotDev& rb,
+                                              const float4* s_obs, int* s_next) {
+  switch (variant) {
+    case kVarPoint:
+      item_rows_call<kVarPoint, LAZY>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, rb, s_obs, s_next);
+      break;
+    case kVarArm6x4:
+      item_rows_call<kVarArm6x4, LAZY>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, rb, s_obs, s_next);
+      break;
+    case kVarArm7x4:
+      item_rows_call<kVarArm7x4, LAZY>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, rb, s_obs, s_next);
+      break;
+    default:
+      item_rows_call<kVarArmGeneric, LAZY>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, rb, s_obs,
+                                           s_next);
+      break;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
@@ -184,6 +208,11 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
                             const WorkItem* __restrict__ items, int n_items, const int* __restrict__ need,
                             int* done, int* next_item, int chunk, int lazy, int* err) {
   __shared__ RobotDev s_rb;
+  // raw storage: the descriptor types have default member initialisers
+  __shared__ __align__(16) unsigned char s_g_raw[sizeof(GraphDev)];
+  __shared__ __align__(16) unsigned char s_sc_raw[sizeof(SceneDev)];
+  GraphDev& s_g = *reinterpret_cast<GraphDev*>(s_g_raw);
+  SceneDev& s_sc = *reinterpret_cast<SceneDev*>(s_sc_raw);
   __shared__ int s_item, s_next, s_ok;
   extern __shared__ __align__(16) float4 smem[];
   while (true) {
@@ -224,11 +253,15 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
     }
     __syncthreads();
     if (!s_ok) continue;  // the item is abandoned; the error word reports it
-    // stage the robot, the obstacles and the column layer's cost-to-go
+    // stage the robot, the problem's descriptors, the obstacles and the column layer's cost-to-go
     {
       const int* src = reinterpret_cast<const int*>(robots + P.robot);
       int* dst = reinterpret_cast<int*>(&s_rb);
       for (int k = threadIdx.x; k < static_cast<int>(sizeof(RobotDev) / 4); k += blockDim.x) dst[k] = src[k];
+      if (threadIdx.x == 0) {
+        s_g = P.g;
+        s_sc = P.sc;
+      }
     }
     const int n4 = scene_float4s(P.sc);
     stage_obstacles_plain(smem, P.sc.obs, n4);
@@ -238,26 +271,10 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
       s_V[j] = P.g.vflag[v] ? kInf : key_value(__ldcg(P.g.keys + v));
     }
     __syncthreads();
-    const GraphDev g = P.g;
-    const SceneDev sc = P.sc;
-    switch (P.variant) {
-      case kVarPoint:
-        item_rows_call<kVarPoint>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, lazy != 0, s_V, s_rb,
-                                  smem, &s_next);
-        break;
-      case kVarArm6x4:
-        item_rows_call<kVarArm6x4>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, lazy != 0, s_V, s_rb,
-                                   smem, &s_next);
-        break;
-      case kVarArm7x4:
-        item_rows_call<kVarArm7x4>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, lazy != 0, s_V, s_rb,
-                                   smem, &s_next);
-        break;
-      default:
-        item_rows_call<kVarArmGeneric>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, lazy != 0, s_V, s_rb,
-                                       smem, &s_next);
-        break;
-    }
+    if (lazy)
+      item_dispatch<true>(P.variant, s_g, s_sc, layer, w, chunk, s_V, s_rb, smem, &s_next);
+    else
+      item_dispatch<false>(P.variant, s_g, s_sc, layer, w, chunk, s_V, s_rb, smem, &s_next);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(done + P.need_base + w.depth, 1);
@@ -436,13 +453,25 @@ gtmp_status build_items(gtmp_batch* b) {
       const int rows = layer_size(P.g, layer), cols = layer_size(P.g, layer + 1);
       // boundary transitions (start row, goal column) sit at the two ends of
       // every problem's dependency chain: cut them into small items
-      const int edges_per_item = (rows == 1 || cols == 1) ? std::min(b->target_edges, kBoundaryItemEdges)
-                                                           : b->target_edges;
+      // a point-robot edge costs about 1/20 of an arm edge: its items hold more edges
+      const long long target = static_cast<long long>(b->target_edges) * (P.variant == kVarPoint ? kPointItemScale : 1);
+      const int edges_per_item = static_cast<int>(
+          (rows == 1 || cols == 1) ? std::min<long long>(target, kBoundaryItemEdges) : std::min<long long>(target, 1 << 30));
       if (rows == 1) {
         for (int c0 = 0; c0 < cols; c0 += edges_per_item) {
           items.push_back(WorkItem{p, d, 0, 1, c0, std::min(edges_per_item, cols - c0)});
           b->need[P.need_base + d] += 1;
         }
+        continue;
+      }
+      if (edges_per_item < cols) {
+        // items smaller than a row: column pieces of one row (keeps a depth's
+        // items many and short, so its last wave leaves few CTAs idle)
+        for (int r0 = 0; r0 < rows; ++r0)
+          for (int c0 = 0; c0 < cols; c0 += edges_per_item) {
+            items.push_back(WorkItem{p, d, r0, 1, c0, std::min(edges_per_item, cols - c0)});
+            b->need[P.need_base + d] += 1;
+          }
         continue;
       }
       int per = edges_per_item / std::max(cols, 1);
@@ -689,7 +718,7 @@ GTMP_API gtmp_status gtmp_batch_set_tiling(gtmp_batch* b, int32_t target_edges, 
 GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t* dev_paths, float* dev_costs,
                                          float* best_ms) {
   if (!b || repeats < 1 || !dev_paths || !dev_costs) return bfail(b, GTMP_ERR_INVALID_ARG, "bad autotune request");
-  static const int kTargets[] = {2048, 8192, 32768, 131072};
+  static const int kTargets[] = {256, 1024, 4096, 16384};
   static const int kChunks[] = {8, 16, 32, 64};
   cudaEvent_t e0, e1;
   BATCH_TRY(b, cudaEventCreate(&e0));

@@ -50,6 +50,8 @@ struct gtmp_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_used;  // (start, end) indices into ev_pool
   double timed_edges = 0.0;
+  std::vector<std::pair<int, int>> ev_minplus;  // (start, end) indices into ev_pool
+  double minplus_bytes = 0.0;
   // learned collision surrogate (allocated by gtmp_surrogate_train)
   gtmp::SurrogateState* sur = nullptr;
   uint8_t* prune = nullptr;  // per-transition prune mask, M x M

@@ -224,34 +224,78 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) edge_costs_kernel(G
 
 // ---------------------------------------------------------------------------
 // Unfused variant, step 2: one warp per row, J_l(i) = min_j C[i][j] + J_{l+1}(j)
-// with first-index ties; streams the row with 16-byte loads.
+// with first-index ties.  HBM-bound: the row streams through 16-byte
+// streaming loads in batches of kMpBatch per lane, and the first batch of the
+// warp's first row is issued before J_{l+1} is staged in shared memory, so the
+// prologue overlaps the first DRAM round trip.  J_{l+1} is read from shared
+// memory as float4 (conflict-free).  Each lane keeps a float minimum and the
+// first column reaching it (its columns are visited in increasing order, so a
+// strict comparison keeps the first); the warp then reduces (value, index)
+// keys, which keeps the smallest index among equal values.
 // ---------------------------------------------------------------------------
+constexpr int kMpBatch = 8;
+
+__device__ __forceinline__ void minplus_take(const float4 c, const float4 v, int j, float& bv, int& bj) {
+  const float x0 = __fadd_rn(c.x, v.x), x1 = __fadd_rn(c.y, v.y), x2 = __fadd_rn(c.z, v.z), x3 = __fadd_rn(c.w, v.w);
+  if (x0 < bv) { bv = x0; bj = j; }
+  if (x1 < bv) { bv = x1; bj = j + 1; }
+  if (x2 < bv) { bv = x2; bj = j + 2; }
+  if (x3 < bv) { bv = x3; bj = j + 3; }
+}
+
+__device__ __forceinline__ void minplus_load(float4 (&c)[kMpBatch], const float4* row, int q0, int n4) {
+#pragma unroll
+  for (int k = 0; k < kMpBatch; ++k) {
+    const int q = q0 + 32 * k;
+    if (q < n4) c[k] = __ldcs(row + q);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) minplus_kernel(GraphDev g, int layer, const float* __restrict__ C, int cs) {
   extern __shared__ __align__(16) float s_Vm[];
   const int n_rows = layer_size(g, layer), n_cols = layer_size(g, layer + 1);
-  for (int j = threadIdx.x; j < cs; j += blockDim.x)
-    s_Vm[j] = j < n_cols ? key_value(g.keys[vidx(g, 0, layer + 1, j)]) : kInf;
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * kWarps;
-  for (int i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < n_rows; i += warps_total) {
-    const float4* row = reinterpret_cast<const float4*>(C + static_cast<size_t>(i) * cs);
-    unsigned long long best = kEmptyKey;
-    for (int q4 = lane; q4 < cs / 4; q4 += 32) {
-      const float4 c = __ldcs(row + q4);
-      const float cv[4] = {c.x, c.y, c.z, c.w};
+  const int n4 = cs / 4;
+  int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  float4 c[kMpBatch];
+  if (i < n_rows) minplus_load(c, reinterpret_cast<const float4*>(C + static_cast<size_t>(i) * cs), lane, n4);
+  // stage J_{l+1}: all of a thread's key loads are issued before the first is used
+  constexpr int kFill = 8;
+  const unsigned long long* knext = g.keys + vidx(g, 0, layer + 1, 0);
+  for (int j0 = threadIdx.x; j0 < cs; j0 += kThreads * kFill) {
+    float v[kFill];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int j = q4 * 4 + e;
-        const float cand = __fadd_rn(cv[e], s_Vm[j]);
-        if (cand < kInf) {
-          const unsigned long long key = make_key(cand, static_cast<uint32_t>(j));
-          best = key < best ? key : best;
-        }
+    for (int u = 0; u < kFill; ++u) {
+      const int j = j0 + u * kThreads;
+      v[u] = j < n_cols ? key_value(__ldcg(knext + j)) : kInf;
+    }
+#pragma unroll
+    for (int u = 0; u < kFill; ++u) {
+      const int j = j0 + u * kThreads;
+      if (j < cs) s_Vm[j] = v[u];
+    }
+  }
+  __syncthreads();
+  const float4* s_V4 = reinterpret_cast<const float4*>(s_Vm);
+  for (; i < n_rows; i += warps_total) {
+    const float4* row = reinterpret_cast<const float4*>(C + static_cast<size_t>(i) * cs);
+    float bv = kInf;
+    int bj = 0;
+    for (int q0 = lane; q0 < n4; q0 += 32 * kMpBatch) {
+      if (q0 != lane) minplus_load(c, row, q0, n4);
+#pragma unroll
+      for (int k = 0; k < kMpBatch; ++k) {
+        const int q = q0 + 32 * k;
+        if (q < n4) minplus_take(c[k], s_V4[q], 4 * q, bv, bj);
       }
     }
+    unsigned long long best = bv < kInf ? make_key(bv, static_cast<uint32_t>(bj)) : kEmptyKey;
     best = warp_min_u64(best);
     if (lane == 0) g.keys[vidx(g, 0, layer, i)] = best;
+    // first batch of the next row
+    if (i + warps_total < n_rows)
+      minplus_load(c, reinterpret_cast<const float4*>(C + static_cast<size_t>(i + warps_total) * cs), lane, n4);
   }
 }
 
