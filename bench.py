@@ -199,6 +199,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one full-evaluation launch of the fused kernel on a 1024 x 1024
+# transition of this workload, from an ncu capture of this kernel (set back to None whenever the
+# kernel changes); the algorithmic bytes per launch are the two sample layers, the cost-to-go and
+# the obstacle table, about 0.1 MB, so HBM is not the bound
+FULL_MODE_DRAM_BYTES_PER_LAUNCH = 426752
+
+
 def measured_peaks():
     """HBM copy bandwidth and bf16 GEMM rate measured on this GPU model (file beside this script), else the
     fallback figures of an earlier B300 measurement."""
@@ -420,7 +427,10 @@ def run_ours(args, wl):
             "gpu_launches": int(prof["launches"]),
             "roofline": {"bound": "alu", "kernel": "fused_transition_kernel (full-evaluation mode)",
                          "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                         "traffic": None, "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock)",
+                         "traffic": FULL_MODE_DRAM_BYTES_PER_LAUNCH,
+                         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one 1024 x 1024 transition "
+                                         "launch (ncu), unchanged kernel",
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock)",
                          "flops_per_waypoint": fpw,
                          "fused_ms_per_solve": fprof["fused_ms"] / full_steps},
             "fused_ms_per_solve_early_exit": prof["fused_ms"] / args.steps,
@@ -739,7 +749,8 @@ def run_anytime(args, wl):
     sc = scenes.pick_endpoints(base, lambda q: probe.label_configs(
         torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
     probe.close()
-    p = binding.Planner(sc.robot, M, L, H, R=R, max_obstacles=64)
+    p = binding.Planner(sc.robot, M, L, H, R=R, max_obstacles=64,
+                        eval_mode=binding.EVAL_LAZY if args.lazy else binding.EVAL_EARLY_EXIT)
     p.set_scene(sc)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     paths = torch.empty((R, L), dtype=torch.int32, device="cuda")
@@ -768,6 +779,7 @@ def run_anytime(args, wl):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "solves_per_s": R * args.steps * world / total_s,
             "config": {"workload": args.workload, "restarts": R, "M": M, "L": L, "H": H, "dof": wl["dof"],
+                       "eval_mode": "lazy" if args.lazy else "early_exit",
                        "checks_per_launch_batch": checks, "feasible_restarts": int(np.isfinite(c).sum()),
                        "best_cost": float(c[int(best.cpu()[0])]) if int(best.cpu()[0]) >= 0 else None,
                        "l2": "flushed between steps"}}), flush=True)
@@ -798,7 +810,8 @@ def run_ao(args, wl):
     stream = torch.cuda.current_stream()
 
     def run_schedule(seed):
-        p = binding.Planner(sc.robot, sizes[-1], L, H, max_obstacles=64)
+        p = binding.Planner(sc.robot, sizes[-1], L, H, max_obstacles=64,
+                            eval_mode=binding.EVAL_LAZY if args.lazy else binding.EVAL_EARLY_EXIT)
         p.set_scene(sc)
         sp = torch.empty(L, dtype=torch.int32, device="cuda")
         scost = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -828,6 +841,7 @@ def run_ao(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "M_stages": sizes, "L": L, "H": H, "dof": wl["dof"],
+                       "eval_mode": "lazy" if args.lazy else "early_exit",
                        "checks_per_schedule": checks, "l2": "not flushed inside a schedule (stages are sequential)"},
             "best_cost_vs_time_ms": [[round(t, 3), c] for t, c in curves[0]]}), flush=True)
 
@@ -844,7 +858,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=10.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused min-plus roofline (M=4096)")
-    ap.add_argument("--lazy", action="store_true", help="batched workload: also time the lazy mode, both forms")
+    ap.add_argument("--lazy", action="store_true",
+                    help="batched workload: also time the lazy mode, both forms; anytime / AO workloads: lazy mode")
     ap.add_argument("--breakdown", action="store_true", help="batched workload: time arm and 2D subsets separately")
     args = ap.parse_args()
     wl = dict(scenes.WORKLOADS[args.workload])
