@@ -347,7 +347,7 @@ typedef struct {
 
 typedef struct {
   double edges;     /* candidate edges of the graph */
-  double pruned;    /* edges dropped before exact checking */
+  double pruned;    /* live edges dropped before exact checking */
   float score_ms;   /* device time of the surrogate scoring */
   float solve_ms;   /* device time of the exact fused transitions */
 } gtmp_prune_stats;
@@ -381,7 +381,9 @@ GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* ctx, const float* dev_q,
 /* gtmp_solve on graph 0 in which an edge is dropped before exact checking when
  * the surrogate's collision probability at any of its scored waypoints
  * (score_waypoints = 1: t = 1/2; 3: t = 1/4, 1/2, 3/4) exceeds threshold;
- * scoring runs in one fused tensor-core kernel per transition.  Every
+ * scoring runs in one fused tensor-core kernel per transition and covers the
+ * live edges only (row vertex free, column vertex free with a finite
+ * cost-to-go: the exact solve skips every other edge anyway).  Every
  * surviving edge is realised by the exact checker (lazily when the context's
  * eval_mode is GTMP_EVAL_LAZY, else with early exit), so a returned path is
  * collision free at its H waypoints; the cost can exceed gtmp_solve's when a

@@ -418,6 +418,44 @@ constexpr int kParamCount = kNW1 + kHid + kNW2 + kHid + kNW3 + kHid + kHid + 1;
 // for kw = 1; 1/4, 1/2, 3/4 for kw = 3); an edge is pruned when its largest
 // logit exceeds `cut`.
 // ---------------------------------------------------------------------------
+// Live rows (vertex free) and live columns (vertex free, finite cost-to-go)
+// of a transition, in increasing order: one block, ballot + prefix per warp.
+__global__ void __launch_bounds__(1024) live_lists_kernel(GraphDev g, int layer, int cap, int* live) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int side = 0; side < 2; ++side) {
+    const int lay = layer + side;
+    const int n = layer_size(g, lay);
+    int* out = live + 2 + side * cap;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+      const int i = i0 + threadIdx.x;
+      bool on = false;
+      if (i < n) {
+        const size_t v = vidx(g, 0, lay, i);
+        on = g.vflag[v] == 0 && (side == 0 || g.keys[v] != kEmptyKey);
+      }
+      const unsigned b = __ballot_sync(kFull, on);
+      if (lane == 0) s_warp[warp] = __popc(b);
+      __syncthreads();
+      int before = 0;
+      for (int w = 0; w < warp; ++w) before += s_warp[w];
+      if (on) out[s_base + before + __popc(b & ((1u << lane) - 1u))] = i;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) tot += s_warp[w];
+        s_base += tot;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) live[side] = s_base;
+    __syncthreads();
+  }
+}
+
 constexpr int kScoreThreads = 256;
 constexpr int kSmemW1 = 256 * 128 * 2, kSmemX = 128 * 128 * 2, kSmemH = 128 * 256 * 2, kSmemS = 256 * 64 * 2;
 constexpr int kScoreSmem = kSmemW1 + kSmemX + kSmemH + 2 * kSmemS;
@@ -425,7 +463,8 @@ constexpr int kScoreSmem = kSmemW1 + kSmemX + kSmemH + 2 * kSmemS;
 struct ScoreArgs {
   GraphDev g;
   int layer;
-  long long n_edges;       // edges of the transition
+  const int* live;         // [0]: live rows nr, [1]: live columns nc, then nr row and nc column indices
+  int cap;                 // capacity of each index list (>= rows, cols)
   int kw;                  // waypoints per edge (1 or 3)
   float cut;               // logit threshold
   const __nv_bfloat16* W1b;
@@ -462,6 +501,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// the features of one query half: frequencies [32 HF, 32 HF + 32); DOF > 0
+// gives compile-time indices (B from the parameter bank, q in registers)
+template <int DOF, int HF>
+__device__ __forceinline__ void score_features(const float* u, const float* v, float t, const FourierDev& f,
+                                               __nv_bfloat16 (&sv)[32], __nv_bfloat16 (&cv)[32]) {
+  constexpr int ND = DOF > 0 ? DOF : kMaxDof;
+  const int dof = DOF > 0 ? DOF : f.dof;
+  float q[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) q[d] = d < dof ? __fmaf_rn(t, __fsub_rn(v[d], u[d]), u[d]) : 0.0f;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    float z = 0.0f;
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+      if (d < dof) z = __fmaf_rn(f.B[(HF * 32 + k) * dof + d], q[d], z);
+    float sn, cs;
+    __sincosf(z, &sn, &cs);
+    sv[k] = __float2bfloat16_rn(sn);
+    cv[k] = __float2bfloat16_rn(cs);
+  }
+}
+
+template <int DOF>
 __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs a, FourierDev f) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar;
@@ -520,7 +583,13 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (256u >> 3 << 17) | (128u >> 4 << 24);
   const int q_per_tile = 128 / a.kw * a.kw, e_per_tile = 128 / a.kw;
-  const long long n_tiles = (a.n_edges + e_per_tile - 1) / e_per_tile;
+  // only live edges are scored: a row whose vertex collides, or a column with
+  // no path to the goal, is skipped by the exact solve whatever its mask says
+  const int nr = a.live[0], nc = a.live[1];
+  const int* rows_live = a.live + 2;
+  const int* cols_live = a.live + 2 + a.cap;
+  const long long n_live = static_cast<long long>(nr) * nc;
+  const long long n_tiles = (n_live + e_per_tile - 1) / e_per_tile;
   const int cols = layer_size(a.g, a.layer + 1);
   const int quarter = warp & 3, half = warp >> 2;
   const int row = quarter * 32 + lane;  // TMEM lane = tile row this thread reads
@@ -530,24 +599,31 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const long long e_first = tile * e_per_tile;
     load_chunk(0, 0);
-    // features of the tile's queries -> X (threads 0..127 one query each)
-    if (tid < 128) {
-      __nv_bfloat16 feat[128];
-      const int qidx = tid;
+    // features of the tile's queries -> X: two threads per query, 32 frequencies
+    // each; the fast __sincosf is ample here (|Bq| < 10, absolute error ~1e-6,
+    // the features are rounded to bf16 right after)
+    {
+      const int qidx = tid & 127, hf = tid >> 7;
+      __align__(16) __nv_bfloat16 sv[32];
+      __align__(16) __nv_bfloat16 cv[32];
       const long long e = e_first + qidx / a.kw;
-      if (qidx < q_per_tile && e < a.n_edges) {
-        const int i = static_cast<int>(e / cols), j = static_cast<int>(e % cols);
+      if (qidx < q_per_tile && e < n_live) {
+        const int i = rows_live[e / nc], j = cols_live[e % nc];
         const float* u = a.g.Q + vidx(a.g, 0, a.layer, i) * a.g.dp;
         const float* v = a.g.Q + vidx(a.g, 0, a.layer + 1, j) * a.g.dp;
         const float t = a.kw == 1 ? 0.5f : 0.25f * static_cast<float>(qidx % a.kw + 1);
-        float q[kMaxDof];
-        for (int d = 0; d < f.dof; ++d) q[d] = __fmaf_rn(t, __fsub_rn(v[d], u[d]), u[d]);
-        fourier_row(q, f, feat);
+        if (hf == 0)
+          score_features<DOF, 0>(u, v, t, f, sv, cv);
+        else
+          score_features<DOF, 1>(u, v, t, f, sv, cv);
       } else {
-        for (int k = 0; k < 128; ++k) feat[k] = __float2bfloat16_rn(0.0f);
+        for (int k = 0; k < 32; ++k) sv[k] = cv[k] = __float2bfloat16_rn(0.0f);
       }
-      for (int kc = 0; kc < 16; ++kc)
-        *reinterpret_cast<uint4*>(sX + canon(qidx, kc * 8, 128)) = *reinterpret_cast<const uint4*>(feat + kc * 8);
+      for (int g8 = 0; g8 < 4; ++g8) {
+        *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + g8 * 8, 128)) = *reinterpret_cast<const uint4*>(sv + g8 * 8);
+        *reinterpret_cast<uint4*>(sX + canon(qidx, 64 + hf * 32 + g8 * 8, 128)) =
+            *reinterpret_cast<const uint4*>(cv + g8 * 8);
+      }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // W1 (first tile) and chunk 0
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -614,11 +690,11 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     if (tid < 128) {  // warps 0..3, full warps for the ballot
       bool pr = false;
       const long long e = e_first + tid;
-      if (tid < e_per_tile && e < a.n_edges) {
+      if (tid < e_per_tile && e < n_live) {
         float z = s_logit[tid * a.kw];
         for (int w = 1; w < a.kw; ++w) z = fmaxf(z, s_logit[tid * a.kw + w]);
         pr = z > a.cut;
-        a.prune[e] = pr ? 1 : 0;
+        a.prune[static_cast<size_t>(rows_live[e / nc]) * cols + cols_live[e % nc]] = pr ? 1 : 0;
       }
       const unsigned b = __ballot_sync(kFull, pr);
       if (lane == 0 && b) atomicAdd(a.n_pruned, static_cast<unsigned long long>(__popc(b)));
@@ -646,6 +722,8 @@ struct SurrogateState {
   float *logits = nullptr, *dz = nullptr;
   double* loss = nullptr;
   unsigned long long* counter = nullptr;
+  int* live = nullptr;  // live rows / columns of the transition being scored: [2 + 2 * live_cap]
+  int live_cap = 0;
   bool trained = false;
   long long steps = 0;
 };
@@ -654,7 +732,7 @@ void surrogate_free(SurrogateState* s) {
   if (!s) return;
   void* bufs[] = {s->P,   s->G,   s->Mm,  s->Vv,  s->W1b, s->W1bT,   s->W2b,     s->W2bT, s->W3b,
                   s->W3bT, s->X,  s->XT,  s->H1,  s->H1T, s->H2,     s->H2T,     s->H3,   s->H3T,
-                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter};
+                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter, s->live};
   for (void* b : bufs) cudaFree(b);
   delete s;
 }
@@ -1027,7 +1105,16 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
   cudaStream_t st = c->stream;
   const int M = c->M_active, L = c->p.L;
   if (!c->prune) SUR_TRY(c, cudaMalloc(&c->prune, static_cast<size_t>(c->p.M) * c->p.M));
-  SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
+  if (s->live_cap < c->p.M) {
+    cudaFree(s->live);
+    s->live = nullptr;
+    s->live_cap = 0;
+    SUR_TRY(c, cudaMalloc(&s->live, (2 + 2 * static_cast<size_t>(c->p.M)) * sizeof(int)));
+    s->live_cap = c->p.M;
+  }
+  SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
+  SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
+  SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
   const float cut = std::log(threshold / (1.0f - threshold));  // logit of the threshold
   GraphDev g;
   g.Q = c->Q;
@@ -1059,7 +1146,8 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     ScoreArgs sa{};
     sa.g = g;
     sa.layer = layer;
-    sa.n_edges = ne;
+    sa.live = s->live;
+    sa.cap = s->live_cap;
     sa.kw = score_waypoints;
     sa.cut = cut;
     sa.W1b = s->W1b;
@@ -1069,9 +1157,17 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     sa.prune = c->prune;
     sa.n_pruned = s->counter;
     sa.err = c->err;
+    // the live count stays on the device: a persistent grid reads it
+    live_lists_kernel<<<1, 1024, 0, st>>>(g, layer, s->live_cap, s->live);
+    SUR_TRY(c, cudaGetLastError());
     const long long tiles = (ne + 128 / score_waypoints - 1) / (128 / score_waypoints);
     const int score_grid = static_cast<int>(std::min<long long>(tiles, c->num_sms));
-    score_edges_kernel<<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
+    if (s->four.dof == 7)
+      score_edges_kernel<7><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
+    else if (s->four.dof == 6)
+      score_edges_kernel<6><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
+    else
+      score_edges_kernel<0><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
     SUR_TRY(c, cudaGetLastError());
     cudaEventRecord(e1, st);
     // exact realisation of the surviving edges, fused with the min-plus step
