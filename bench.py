@@ -650,8 +650,9 @@ def run_surrogate(args, wl):
     for name, mode in (("early_exit", binding.EVAL_EARLY_EXIT), ("lazy", binding.EVAL_LAZY)):
         planners[name] = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=mode)
         planners[name].set_scene(sc)
-    train = binding.gtmp_surrogate_train(planners["early_exit"].ctx, n_train=wl["n_train"], n_holdout=1 << 16,
-                                         epochs=wl["epochs"], batch=1024, lr=1e-3, seed=1,
+    n_train = args.sur_train or wl["n_train"]
+    train = binding.gtmp_surrogate_train(planners["early_exit"].ctx, n_train=n_train, n_holdout=1 << 16,
+                                         epochs=wl["epochs"] if not args.sur_train else 1, batch=1024, lr=1e-3, seed=1,
                                          fourier_sigma=wl["sigma"])
     binding.gtmp_surrogate_set_params(planners["lazy"].ctx,
                                       binding.gtmp_surrogate_get_params(planners["early_exit"].ctx, sc.robot.dof))
@@ -663,6 +664,7 @@ def run_surrogate(args, wl):
     seed0 = rank_seed_base(rank)
     steps = {k: [] for k in ("early_exit", "early_exit_pruned", "lazy", "lazy_pruned")}
     ratios, pruned_frac, colliding_waypoints, checked = [], [], 0, 0
+    score_ms, live_edges = [], []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn):
@@ -705,8 +707,22 @@ def run_surrogate(args, wl):
         ms, msp, c_plain, c_pruned, st = row["early_exit"]
         assert row["lazy"][2] == c_plain or (math.isinf(c_plain) and math.isinf(row["lazy"][2]))
         pruned_frac.append(st["pruned"] / st["edges"])
+        score_ms.append(st["score_ms"])
+        live_edges.append(st["scored"])
         if math.isfinite(c_plain):
             ratios.append(c_pruned / c_plain if math.isfinite(c_pruned) else math.inf)
+    # tensor-core roofline of the fused scoring kernel: 164 096 MAC per scored waypoint (128x256 + 2x256x256
+    # + 256), one scored waypoint per live edge; the live-edge count is measured from the same solves
+    score_roofline = None
+    if score_ms and live_edges:
+        peaks = measured_peaks()
+        tfl = 2.0 * 164096 * kw * (sum(live_edges) / len(live_edges)) / (sum(score_ms) / len(score_ms) / 1e3) / 1e12
+        pk = peaks.get("bf16_tflops")
+        score_roofline = {"bound": "tensor", "kernel": "score_edges_kernel (BF16 MLP, tcgen05)", "achieved": tfl,
+                          "peak": pk, "unit": "TFLOP/s", "frac": tfl / pk if pk else None, "traffic": None,
+                          "peak_basis": f"cuBLAS bf16 GEMM burst (bf16_tflops, {peaks['source']})",
+                          "score_ms_per_solve": sum(score_ms) / len(score_ms),
+                          "live_edges_per_solve": sum(live_edges) / len(live_edges)}
     tot = {k: max_over_ranks(sum(v) / 1e3, world, "cuda") for k, v in steps.items()}
     sps = {k: args.steps * world / v for k, v in tot.items()}
     if rank == 0:
@@ -718,13 +734,15 @@ def run_surrogate(args, wl):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 surrogate, f32 checker",
             "data": "synthetic (seeded scene and samples)",
             "config": {"workload": args.workload, "M": M, "L": L, "H": H, "dof": wl["dof"], "obstacles": wl["n_obs"],
-                       "threshold": thr, "score_waypoints": kw, "l2": "flushed between solves"},
+                       "threshold": thr, "score_waypoints": kw, "train_configs": n_train,
+                       "l2": "flushed between solves"},
             "solves_per_s": sps,
             "surrogate_over_plain": {"early_exit": sps["early_exit_pruned"] / sps["early_exit"],
                                      "lazy": sps["lazy_pruned"] / sps["lazy"]},
             "cost_ratio_pruned_over_plain": {"mean": float(np.mean(fin)) if fin else None,
                                              "max": float(np.max(fin)) if fin else None,
                                              "lost_feasibility": len(ratios) - len(fin), "solves": len(ratios)},
+            "roofline": score_roofline,
             "pruned_edge_fraction": float(np.mean(pruned_frac)),
             "returned_paths_recheck": {"waypoints": checked, "colliding": colliding_waypoints},
             "training": train,
@@ -860,6 +878,8 @@ def main():
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused min-plus roofline (M=4096)")
     ap.add_argument("--lazy", action="store_true",
                     help="batched workload: also time the lazy mode, both forms; anytime / AO workloads: lazy mode")
+    ap.add_argument("--sur-train", type=int, default=0,
+                    help="surrogate workload: train on this many configurations for one epoch (short runs for profiling)")
     ap.add_argument("--breakdown", action="store_true", help="batched workload: time arm and 2D subsets separately")
     args = ap.parse_args()
     wl = dict(scenes.WORKLOADS[args.workload])

@@ -350,6 +350,7 @@ typedef struct {
   double pruned;    /* live edges dropped before exact checking */
   float score_ms;   /* device time of the surrogate scoring */
   float solve_ms;   /* device time of the exact fused transitions */
+  double scored;    /* live edges scored by the surrogate (row and column live) */
 } gtmp_prune_stats;
 
 /* Train the context's surrogate for its robot and current obstacles

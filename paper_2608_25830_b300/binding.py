@@ -69,7 +69,7 @@ class GtmpSurrogateStats(ctypes.Structure):
 
 class GtmpPruneStats(ctypes.Structure):
     _fields_ = [("edges", ctypes.c_double), ("pruned", ctypes.c_double), ("score_ms", ctypes.c_float),
-                ("solve_ms", ctypes.c_float)]
+                ("solve_ms", ctypes.c_float), ("scored", ctypes.c_double)]
 
 
 class GtmpProblem(ctypes.Structure):
@@ -548,7 +548,7 @@ def gtmp_solve_pruned(ctx, threshold, dev_path, dev_cost, score_waypoints=1):
     st = GtmpPruneStats()
     _check(ctx, lib().gtmp_solve_pruned(ctx, threshold, score_waypoints, _dev(dev_path, torch.int32),
                                         _dev(dev_cost, torch.float32), ctypes.byref(st)))
-    return dict(edges=st.edges, pruned=st.pruned, score_ms=st.score_ms, solve_ms=st.solve_ms)
+    return dict(edges=st.edges, pruned=st.pruned, score_ms=st.score_ms, solve_ms=st.solve_ms, scored=st.scored)
 
 
 def gtmp_umma_gemm_f32(A, B, C, err, stream=None):

@@ -1136,7 +1136,7 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
   SUR_TRY(c, launch_init_keys(g, c->counters, L + 1, st));
   SUR_TRY(c, launch_vertex_labels(g, c->rb, c->variant, ctx_scene(c), st));
   const int resident = c->num_sms * c->fused_bps[0];
-  double edges_total = 0.0;
+  double edges_total = 0.0, scored_total = 0.0;
   for (int layer = L; layer >= 0; --layer) {
     const int rows = layer_size(g, layer), cols = layer_size(g, layer + 1);
     const long long ne = static_cast<long long>(rows) * cols;
@@ -1191,8 +1191,11 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
       SUR_TRY(c, launch_fused_transition(gp, layer, c->rb, c->variant, ctx_scene(c), GTMP_EVAL_EARLY_EXIT,
                                          c->counters + layer, grid, static_cast<int>(chunk), c->err, st));
     }
+    int live_n[2] = {0, 0};
+    SUR_TRY(c, cudaMemcpyAsync(live_n, s->live, sizeof(live_n), cudaMemcpyDeviceToHost, st));
     cudaEventRecord(e2, st);
     SUR_TRY(c, cudaEventSynchronize(e2));
+    scored_total += static_cast<double>(live_n[0]) * live_n[1];
     float a = 0.0f, b = 0.0f;
     cudaEventElapsedTime(&a, e0, e1);
     cudaEventElapsedTime(&b, e1, e2);
@@ -1211,6 +1214,7 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     stats->pruned = static_cast<double>(pruned);
     stats->score_ms = score_ms;
     stats->solve_ms = solve_ms;
+    stats->scored = scored_total;
   }
   return GTMP_OK;
 }

@@ -197,13 +197,14 @@ def test_anytime_restarts_match_oracle(torch_cuda, mode):
 # AO-GTMP: expand-samples bit-exact stage by stage, non-increasing best cost
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kind,dof", [("arm", 6), ("point2d", 2)])
-def test_ao_stages_match_oracle(torch_cuda, kind, dof):
+@pytest.mark.parametrize("kind,dof,mode", [("arm", 6, binding.EVAL_EARLY_EXIT), ("point2d", 2, binding.EVAL_EARLY_EXIT),
+                                           ("arm", 6, binding.EVAL_LAZY)])
+def test_ao_stages_match_oracle(torch_cuda, kind, dof, mode):
     torch = torch_cuda
     sc = scene_for(kind, 4, dof, 30 if kind == "arm" else 12)
     L, H = 4, 16
     sizes = [8, 16, 32, 64]
-    p = _planner(sc, sizes[-1], L, H)
+    p = _planner(sc, sizes[-1], L, H, mode=mode)
     stage_path = torch.empty(L, dtype=torch.int32, device="cuda")
     stage_cost = torch.empty(1, dtype=torch.float32, device="cuda")
     best_path = torch.full((L,), -1, dtype=torch.int32, device="cuda")

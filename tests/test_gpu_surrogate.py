@@ -110,6 +110,30 @@ def test_pruned_solve_is_exactly_checked(trained):
             assert c1 == pytest.approx(total, rel=REL)
 
 
+def test_lazy_pruned_solve_equals_early_exit_pruned_solve(trained):
+    """Same scene, samples and surrogate: the lazy exact pass over the surviving edges returns the early-exit
+    pass's path and cost bit for bit (it skips only edges that cannot lower a row's minimum)."""
+    import torch
+    sc, p, _ = trained
+    L, H, M = 4, 32, 128
+    lz = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_LAZY)
+    lz.set_scene(sc)
+    binding.gtmp_surrogate_set_params(lz.ctx, binding.gtmp_surrogate_get_params(p.ctx, sc.robot.dof))
+    for seed, kw, thr in ((5, 1, 0.5), (8, 3, 0.3)):
+        out = []
+        for pl in (p, lz):
+            pl.sample_layers(seed, M)
+            path = torch.empty(L, dtype=torch.int32, device="cuda")
+            cost = torch.empty(1, dtype=torch.float32, device="cuda")
+            st = binding.gtmp_solve_pruned(pl.ctx, thr, path, cost, score_waypoints=kw)
+            pl.synchronize()
+            out.append((path.cpu().numpy(), float(cost.cpu()[0]), st["pruned"]))
+        np.testing.assert_array_equal(out[0][0], out[1][0])
+        assert out[0][1] == out[1][1] or (math.isinf(out[0][1]) and math.isinf(out[1][1]))
+        assert out[0][2] == out[1][2]
+    lz.close()
+
+
 def reference_gradients(P, q, y):
     """FP64 backward pass of the mean binary cross-entropy, with the kernel's BF16 rounding points."""
     z = q.astype(np.float64) @ P["B"].astype(np.float64).T
