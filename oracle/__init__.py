@@ -323,3 +323,101 @@ def anytime(scene, seed, R, L, M, H, eps=EPS_DEFAULT):
     """anytime-gtmp of Alg. 1 with R restarts (single class): per-restart solutions."""
     return [solve(scene, sample_uniform(seed, r, L, M, scene.robot.q_lo, scene.robot.q_hi), H, eps)
             for r in range(R)]
+
+
+# ---------------------------------------------------------------------------
+# Class-augmented value iteration (Prop. 1; Alg. 1 with a class-indexed archive)
+# for planar scenes.  Label of a start-to-goal chain: the winding numbers of
+# the closed loop (chain, then the straight segment qg -> q0) about every
+# obstacle's centre, a homology invariant like the h-signature.  It splits
+# over the chain's edges: edge (u, v) contributes the winding numbers of the
+# triangle u -> v -> qg -> u (0 or +-1 per obstacle), because the triangles'
+# extra sides cancel in pairs.  Labels compose by addition.
+# ---------------------------------------------------------------------------
+
+def obstacle_centres_2d(scene):
+    """Representative point of every obstacle in the plane: disk centres, then box centres (float64)."""
+    pts = [(float(s[0]), float(s[1])) for s in np.asarray(scene.spheres, np.float64)]
+    pts += [(0.5 * (float(b[0]) + float(b[3])), 0.5 * (float(b[1]) + float(b[4])))
+            for b in np.asarray(scene.boxes, np.float64)]
+    return pts
+
+
+def orient2d(a, b, c) -> float:
+    """(b - a) x (c - a) in float64.  For float32 coordinates the differences and products are exact and the
+    final subtraction is correctly rounded, so the sign is the exact sign."""
+    return (float(b[0]) - float(a[0])) * (float(c[1]) - float(a[1])) - \
+           (float(b[1]) - float(a[1])) * (float(c[0]) - float(a[0]))
+
+
+def triangle_winding(a, b, c, p) -> int:
+    """Winding number of the closed triangle a -> b -> c -> a about p: the sign of its orientation when p lies
+    strictly inside, else 0 (p on the boundary counts as outside)."""
+    o = orient2d(a, b, c)
+    if o == 0.0:
+        return 0
+    d1, d2, d3 = orient2d(a, b, p), orient2d(b, c, p), orient2d(c, a, p)
+    if o > 0 and d1 > 0 and d2 > 0 and d3 > 0:
+        return 1
+    if o < 0 and d1 < 0 and d2 < 0 and d3 < 0:
+        return -1
+    return 0
+
+
+def edge_class_label(u, v, g, centres) -> tuple:
+    """Label of edge (u, v) toward goal g: per obstacle, the winding number of triangle u -> v -> g."""
+    return tuple(triangle_winding(u, v, g, p) for p in centres)
+
+
+def class_value_iteration(edges, verts, centres, ambiguous_free=False):
+    """Prop. 1: J_l(u, chi) = min over (v, chi') with kappa(u, v) + chi' = chi of c(u, v) + J_{l+1}(v, chi'),
+    from J_{L+1}(qg, 0) = 0.  Returns tables[l][u] = {chi: (cost, v, chi')}; among equal costs the first v
+    (lowest index) is kept.  Plain Python loops: small graphs only."""
+    g = verts[-1][0]
+    zero = (0,) * len(centres)
+    n_layers = len(verts)
+    tables = [None] * n_layers
+    tables[-1] = [{zero: (0.0, -1, None)}]
+    for l in range(n_layers - 2, -1, -1):
+        labels_e, costs = edges[l]
+        ok = (labels_e == FREE) | ((labels_e == AMBIGUOUS) if ambiguous_free else False)
+        rows = []
+        for i, u in enumerate(verts[l]):
+            tab = {}
+            for j, v in enumerate(verts[l + 1]):
+                if not ok[i, j] or not tables[l + 1][j]:
+                    continue
+                k = edge_class_label(u, v, g, centres)
+                for chi2, (c2, _, _) in tables[l + 1][j].items():
+                    chi = tuple(a + b for a, b in zip(k, chi2))
+                    c = float(costs[i, j]) + c2
+                    if chi not in tab or c < tab[chi][0]:
+                        tab[chi] = (c, j, chi2)
+            rows.append(tab)
+        tables[l] = rows
+    return tables
+
+
+def class_paths(tables):
+    """For every label of the start vertex: (cost, chain of sample indices, one per layer 1..L)."""
+    out = {}
+    L = len(tables) - 2
+    for chi, (c, j, chi2) in tables[0][0].items():
+        path = []
+        for l in range(1, L + 1):
+            path.append(j)
+            c_l, j, chi2 = tables[l][j][chi2]
+        out[chi] = (c, path)
+    return out
+
+
+def polygon_winding(points, p) -> int:
+    """Winding number of the closed polygon points[0] -> ... -> points[-1] -> points[0] about p, from the sum
+    of the signed angles the edges subtend at p (an independent definition used to pin the labels)."""
+    total = 0.0
+    n = len(points)
+    for k in range(n):
+        a = (float(points[k][0]) - p[0], float(points[k][1]) - p[1])
+        b = (float(points[(k + 1) % n][0]) - p[0], float(points[(k + 1) % n][1]) - p[1])
+        total += math.atan2(a[0] * b[1] - a[1] * b[0], a[0] * b[0] + a[1] * b[1])
+    return int(round(total / (2 * math.pi)))

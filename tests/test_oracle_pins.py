@@ -451,3 +451,101 @@ def test_expand_keeps_old_samples_and_mixes_heuristic_midpoints():
                 assert s <= c * (1 + 1e-6)
     # fair coin: about half of the new samples are heuristic midpoints
     assert abs(n_mid / n_new - 0.5) < 0.08, n_mid / n_new
+
+
+# ---------------------------------------------------------------------------
+# class-augmented value iteration (Prop. 1) on planar scenes
+# ---------------------------------------------------------------------------
+
+def test_edge_labels_sum_to_the_winding_of_the_closed_chain():
+    """Summing the triangle labels u -> v -> g over a chain gives the winding numbers of the loop (chain,
+    then g -> start) computed independently from subtended angles."""
+    rng = np.random.default_rng(11)
+    for trial in range(200):
+        centres = [tuple(c) for c in rng.uniform(-1, 1, (4, 2))]
+        pts = rng.uniform(-1, 1, (rng.integers(3, 8), 2)).astype(np.float32)
+        # keep points away from the centres (the winding number is undefined on the loop)
+        if min(np.hypot(*(pts - np.array(c, np.float32)).T).min() for c in centres) < 1e-3:
+            continue
+        g = pts[-1]
+        lab = np.zeros(len(centres), int)
+        for a, b in zip(pts[:-1], pts[1:]):
+            lab += np.array(oracle.edge_class_label(a, b, g, centres))
+        want = [oracle.polygon_winding(list(pts), c) for c in centres]
+        assert list(lab) == want, (trial, lab, want)
+
+
+def test_triangle_winding_hand_cases():
+    a, b, c = (0.0, 0.0), (1.0, 0.0), (0.0, 1.0)
+    assert oracle.triangle_winding(a, b, c, (0.25, 0.25)) == 1          # counter-clockwise, inside
+    assert oracle.triangle_winding(a, c, b, (0.25, 0.25)) == -1         # clockwise, inside
+    assert oracle.triangle_winding(a, b, c, (1.0, 1.0)) == 0            # outside
+    assert oracle.triangle_winding(a, b, c, (0.5, 0.0)) == 0            # on an edge: outside by convention
+    assert oracle.triangle_winding(a, b, (2.0, 0.0), (0.5, 0.0)) == 0   # degenerate triangle
+
+
+def _chain_labels_brute_force(sc, Q, H, centres):
+    """Every chain q0 -> Q[0][i1] -> ... -> qg with all edges free: label from subtended angles, cost."""
+    verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
+    edges = oracle.realize_edges(sc, verts, H)
+    L, M = Q.shape[0], Q.shape[1]
+    best = {}
+    for chain in itertools.product(range(M), repeat=L):
+        idx = [0] + list(chain) + [0]
+        ok, cost = True, 0.0
+        for l in range(L + 1):
+            lab, c = edges[l][0][idx[l], idx[l + 1]], edges[l][1][idx[l], idx[l + 1]]
+            assert lab != oracle.AMBIGUOUS
+            if lab != oracle.FREE:
+                ok = False
+                break
+            cost += float(c)
+        if not ok:
+            continue
+        pts = [verts[l][idx[l]] for l in range(L + 2)]
+        chi = tuple(oracle.polygon_winding(pts, p) for p in centres)
+        if chi not in best or cost < best[chi]:
+            best[chi] = cost
+    return best, verts, edges
+
+
+@pytest.mark.parametrize("seed,n_obs,M,L", [(3, 4, 5, 3), (7, 6, 4, 3), (12, 3, 6, 2)])
+def test_class_value_iteration_equals_brute_force(seed, n_obs, M, L):
+    sc = scenes.point2d_scene(seed, n_obs)
+    H = 16
+    Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    centres = oracle.obstacle_centres_2d(sc)
+    best, verts, edges = _chain_labels_brute_force(sc, Q, H, centres)
+    tables = oracle.class_value_iteration(edges, verts, centres)
+    got = {chi: c for chi, (c, _, _) in tables[0][0].items()}
+    assert set(got) == set(best)
+    for chi in best:
+        assert got[chi] == pytest.approx(best[chi], rel=1e-12)
+    # the best over classes is the plain value iteration's optimum
+    V, _, _ = oracle.value_iteration(edges, ambiguous_free=False)
+    if best:
+        assert min(best.values()) == pytest.approx(V[0][0], rel=1e-12)
+    else:
+        assert math.isinf(V[0][0])
+    # every extracted chain carries its label and its cost
+    for chi, (c, path) in oracle.class_paths(tables).items():
+        pts = [verts[0][0]] + [verts[l + 1][path[l]] for l in range(L)] + [verts[-1][0]]
+        assert tuple(oracle.polygon_winding(pts, p) for p in centres) == chi
+        total, worst = oracle.path_cost(sc, Q, np.array(path), H)
+        assert total == pytest.approx(c, rel=1e-12) and worst > oracle.EPS_DEFAULT
+
+
+def test_class_value_iteration_single_disk_has_two_sides():
+    """One disk on the straight line between the endpoints: chains pass it on either side, two labels
+    (winding 0 and +-1 about its centre, depending on the side relative to the closing segment)."""
+    base = scenes.point2d_scene(0, 0)
+    disk = np.array([[0.05, -0.03, 0.0, 0.3]], np.float32)   # off the segment q0 -> qg
+    sc = scenes.Scene(base.robot, disk, np.zeros((0, 6), np.float32), base.q_start, base.q_goal)
+    L, M, H = 2, 24, 16
+    Q = oracle.sample_uniform(5, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
+    edges = oracle.realize_edges(sc, verts, H)
+    tables = oracle.class_value_iteration(edges, verts, oracle.obstacle_centres_2d(sc))
+    labels = set(tables[0][0])
+    # passing on the closing segment's side of the centre winds 0 times, the other side once
+    assert labels in ({(0,), (1,)}, {(0,), (-1,)})
