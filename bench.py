@@ -751,6 +751,79 @@ def run_surrogate(args, wl):
         pl.close()
 
 
+def run_classes(args, wl):
+    """Class-augmented value iteration (Prop. 1) on a planar scene: each step samples one layered graph and
+    returns a minimum-cost chain in every realised class; then Alg. 1's anytime-gtmp class archive over R
+    restarts.  The oracle's class sweep of the same graphs is the CPU baseline."""
+    import numpy as np
+    import torch
+
+    from paper_2608_25830_b300 import binding, scenes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    M, L, H, K, R = wl["M"], wl["L"], wl["H"], wl["K"], wl["R"]
+    sc = scenes.point2d_scene(wl["seed"], wl["n_obs"])
+    p = binding.Planner(sc.robot, M, L, H, max_obstacles=64)
+    p.set_scene(sc)
+    paths = torch.empty((K, L), dtype=torch.int32, device="cuda")
+    costs = torch.empty(K, dtype=torch.float32, device="cuda")
+    labels = torch.empty((K, 16), dtype=torch.int8, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    seed0 = rank_seed_base(rank)
+    for s in range(args.warmup):
+        binding.gtmp_sample_layers(p.ctx, seed0 + 10_000 + s, M)
+        binding.gtmp_solve_classes(p.ctx, K, K, paths, costs, labels)
+    torch.cuda.synchronize()
+    binding.gtmp_profile_read(p.ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, n_cls = [], []
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        binding.gtmp_sample_layers(p.ctx, seed0 + s, M)
+        n_cls.append(binding.gtmp_solve_classes(p.ctx, K, K, paths, costs, labels))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = binding.gtmp_profile_read(p.ctx)["launches"]
+    total_s = max_over_ranks(sum(ms) / 1e3, world, "cuda")
+    t0 = time.perf_counter()
+    archive = p.anytime_classes(seed0 + 20_000, R, K, K)
+    torch.cuda.synchronize()
+    archive_ms = (time.perf_counter() - t0) * 1e3
+    p.close()
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            done, t0 = 0, time.perf_counter()
+            while time.perf_counter() - t0 < args.cpu_budget:
+                Q = oracle.sample_uniform(seed0 + done, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+                verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
+                oracle.class_value_iteration(oracle.realize_edges(sc, verts, H), verts, oracle.obstacle_centres_2d(sc))
+                done += 1
+            secs = time.perf_counter() - t0
+            cpu = {"value": done / secs, "unit": "solves/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+                   "kind": "oracle", "sample": f"{done} whole graphs (edges in C with OpenMP, class sweep in Python) "
+                                               f"in {secs:.1f} s"}
+        print(json.dumps({
+            "metric": "class-augmented solves/s (every realised class of one layered graph)",
+            "value": args.steps * world / total_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 costs, exact f64 orientation labels",
+            "data": "synthetic (seeded planar scene and samples)",
+            "config": {"workload": args.workload, "M": M, "L": L, "H": H, "obstacles": wl["n_obs"], "max_labels": K,
+                       "l2": "flushed between steps"},
+            "classes_per_solve": sum(n_cls) / len(n_cls), "gpu_launches": int(launches),
+            "anytime_archive": {"restarts": R, "classes": len(archive), "ms": archive_ms,
+                                "best_cost": min(c for c, _, _ in archive.values()) if archive else None},
+            "cpu_baseline": cpu,
+        }), flush=True)
+
+
 def run_anytime(args, wl):
     """Anytime-GTMP: R restarts of one problem, all in one batch of launches."""
     import numpy as np
@@ -883,6 +956,11 @@ def main():
     ap.add_argument("--breakdown", action="store_true", help="batched workload: time arm and 2D subsets separately")
     args = ap.parse_args()
     wl = dict(scenes.WORKLOADS[args.workload])
+    if wl["kind"] == "classes":
+        if args.impl == "reference":
+            raise SystemExit("the reference arm times the single-solve workload")
+        run_classes(args, wl)
+        return
     if wl["kind"] == "batched" or "R" in wl or "M0" in wl:
         if args.impl == "reference":
             raise SystemExit("the reference arm times the single-solve workload")

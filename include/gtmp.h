@@ -177,6 +177,25 @@ GTMP_API gtmp_status gtmp_solve_unfused(gtmp_ctx* ctx, int32_t* dev_path, float*
  * Requires a previous gtmp_solve_unfused. */
 GTMP_API gtmp_status gtmp_get_edge_costs(gtmp_ctx* ctx, int32_t l, float* dev_C);
 
+/* Class-augmented value iteration (Prop. 1; the class-indexed archive of
+ * Alg. 1 anytime-gtmp) on graph 0 of a planar point robot (GTMP_ROBOT_POINT,
+ * dof 2, at most 16 obstacles): a minimum-cost chain in every realised class.
+ * Class label of a start-to-goal chain: the winding numbers of the loop
+ * (chain, then the straight segment qg -> q0) about each obstacle's centre
+ * (sphere centres in input order, then box centres), one signed byte per
+ * obstacle; edge (u, v) adds the winding numbers of the triangle u -> v -> qg,
+ * decided by exact orientation tests.  Uses the unfused step-1 cost matrices
+ * (allocated like gtmp_solve_unfused) and (L+2) M max_labels 24-byte table
+ * entries.  max_labels (a power of two in [32, 4096]) bounds the labels of
+ * one vertex: more gives GTMP_ERR_OOM.  Writes up to max_classes classes,
+ * in no particular order: dev_paths device [max_classes][L] int32 (sample
+ * indices of layers 1..L), dev_costs device [max_classes] float32, dev_labels
+ * device [max_classes][16] int8 (entries past the obstacle count are 0);
+ * *n_classes (host) = the number of classes found (may exceed max_classes).
+ * Synchronous.  GTMP_ERR_UNSUPPORTED for other robots or more obstacles. */
+GTMP_API gtmp_status gtmp_solve_classes(gtmp_ctx* ctx, int32_t max_labels, int32_t max_classes, int32_t* dev_paths,
+                                        float* dev_costs, int8_t* dev_labels, int32_t* n_classes);
+
 /* anytime-gtmp of Alg. 1 (single class): `restarts` independent graphs
  * (restart r uses Philox restart word r of gtmp_sample_layers' rule) solved
  * in one batch of launches.  dev_paths device [restarts][L], dev_costs device

@@ -107,6 +107,7 @@ _SIGNATURES = {
     "gtmp_batch_get_tiling": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "gtmp_batch_autotune": [_vp, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_float)],
     "gtmp_batch_set_eval_mode": [_vp, _i32],
+    "gtmp_solve_classes": [_vp, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32)],
     "gtmp_surrogate_train": [_vp, ctypes.POINTER(GtmpSurrogateConfig), ctypes.POINTER(GtmpSurrogateStats)],
     "gtmp_surrogate_predict": [_vp, _vp, _i32, _vp],
     "gtmp_surrogate_get_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
@@ -340,6 +341,7 @@ class Planner:
 
     def set_scene(self, scene: scenes.Scene):
         gtmp_set_obstacles(self.ctx, scene.spheres, scene.boxes)
+        self.n_obstacles = int(np.asarray(scene.spheres).shape[0] + np.asarray(scene.boxes).shape[0])
         gtmp_set_endpoints(self.ctx, scene.q_start, scene.q_goal)
 
     def sample_layers(self, seed, M=None):
@@ -353,6 +355,31 @@ class Planner:
         Q = torch.empty((self.L, gtmp_get_M(self.ctx), self.robot.dof), dtype=torch.float32, device=self.dev)
         gtmp_get_layers(self.ctx, Q)
         return Q
+
+    def solve_classes(self, max_labels=256, max_classes=256):
+        """Minimum-cost chain per class of graph 0 (planar point robots): {label tuple: (cost, path)}."""
+        import torch
+        paths = torch.empty((max_classes, self.L), dtype=torch.int32, device=self.dev)
+        costs = torch.empty(max_classes, dtype=torch.float32, device=self.dev)
+        labels = torch.empty((max_classes, 16), dtype=torch.int8, device=self.dev)
+        n = gtmp_solve_classes(self.ctx, max_labels, max_classes, paths, costs, labels)
+        k = min(n, max_classes)
+        n_obs = self.n_obstacles
+        P, C, Lb = paths[:k].cpu().numpy(), costs[:k].cpu().numpy(), labels[:k].cpu().numpy()
+        return {tuple(int(x) for x in Lb[i, :n_obs]): (float(C[i]), P[i].copy()) for i in range(k)}, n
+
+    def anytime_classes(self, seed, restarts, max_labels=256, max_classes=256):
+        """anytime-gtmp of Alg. 1 with its class-indexed archive: `restarts` fresh graphs (sample seeds
+        seed, seed + 1, ...), each swept class by class on the device; the archive keeps, per label, the
+        cheapest chain found so far.  Returns {label: (cost, restart, path)}."""
+        archive = {}
+        for r in range(restarts):
+            self.sample_layers(seed + r, self.M)
+            classes, _ = self.solve_classes(max_labels, max_classes)
+            for chi, (c, path) in classes.items():
+                if chi not in archive or c < archive[chi][0]:
+                    archive[chi] = (c, r, path)
+        return archive
 
     def label_configs(self, q):
         import torch
@@ -455,6 +482,16 @@ def gtmp_batch_get_tiling(b):
     t, c = _i32(), _i32()
     _bcheck(b, lib().gtmp_batch_get_tiling(b, ctypes.byref(t), ctypes.byref(c)))
     return t.value, c.value
+
+
+def gtmp_solve_classes(ctx, max_labels, max_classes, dev_paths, dev_costs, dev_labels):
+    """Class-augmented sweep (Prop. 1): returns the number of classes found."""
+    import torch
+    n = _i32()
+    _check(ctx, lib().gtmp_solve_classes(ctx, max_labels, max_classes, _dev(dev_paths, torch.int32),
+                                         _dev(dev_costs, torch.float32), _dev(dev_labels, torch.int8),
+                                         ctypes.byref(n)))
+    return n.value
 
 
 def gtmp_batch_set_eval_mode(b, eval_mode):

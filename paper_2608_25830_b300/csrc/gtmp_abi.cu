@@ -161,6 +161,52 @@ gtmp_status check_ready(gtmp_ctx* c) {
 
 }  // namespace
 
+// Step 1 of the unfused variant, shared with the class-augmented sweep: vertex
+// labels and every transition's cost matrix C_l (C_L first, so that, when the
+// matrices outgrow L2, the sweep that follows reads each from HBM).
+gtmp_status gtmp_internal_edge_costs(gtmp_ctx* c) {
+  const int L = c->p.L;
+  if (!c->C) {
+    GraphDev cap = graph(c, 1, c->p.M);
+    size_t total = 0;
+    c->c_off.assign(L + 2, 0);
+    c->c_cs.assign(L + 1, 0);
+    for (int layer = 0; layer <= L; ++layer) {
+      int rows, cols;
+      transition_shape(cap, layer, &rows, &cols);
+      c->c_cs[layer] = ((cols + 3) / 4) * 4;
+      c->c_off[layer] = total;
+      total += static_cast<size_t>(rows) * c->c_cs[layer];
+    }
+    c->c_off[L + 1] = total;
+    CUDA_TRY(c, cudaMalloc(&c->C, total * sizeof(float)));
+  }
+  GraphDev g = graph(c, 1, c->M_active);
+  CUDA_TRY(c, launch_init_keys(g, c->counters, (L + 1), c->stream));
+  CUDA_TRY(c, launch_vertex_labels(g, c->rb, c->variant, scene(c), c->stream));
+  LAUNCHED(c, 2);
+  const int resident = c->num_sms * c->fused_bps[0];
+  for (int layer = L; layer >= 0; --layer) {
+    int rows, cols;
+    transition_shape(g, layer, &rows, &cols);
+    // the unfused step recomputes its own row stride for the active M
+    const int cs = ((cols + 3) / 4) * 4;
+    c->c_cs[layer] = cs;
+    const long long edges = static_cast<long long>(rows) * cols;
+    long long chunk = edges / (static_cast<long long>(resident) * 64);
+    if (chunk < 1) chunk = 1;
+    if (chunk > 32) chunk = 32;
+    if (chunk > cols) chunk = cols;
+    const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
+    int grid = resident;
+    if (grid > (n_chunks + 7) / 8) grid = static_cast<int>((n_chunks + 7) / 8);
+    CUDA_TRY(c, launch_edge_costs(g, layer, c->rb, c->variant, scene(c), c->C + c->c_off[layer], cs,
+                                  c->counters + layer, grid, static_cast<int>(chunk), c->err, c->stream));
+    LAUNCHED(c, 1);
+  }
+  return GTMP_OK;
+}
+
 extern "C" {
 
 const char* gtmp_status_string(gtmp_status s) {
@@ -308,6 +354,7 @@ gtmp_status gtmp_destroy(gtmp_ctx* c) {
   cudaFree(c->obs);
   cudaFree(c->err);
   cudaFree(c->C);
+  cudaFree(c->cls);
   cudaFree(c->prune);
   surrogate_free(c->sur);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -381,6 +428,14 @@ gtmp_status gtmp_set_obstacles(gtmp_ctx* c, const float* spheres, int32_t n_s, c
     CUDA_TRY(c, cudaMemcpyAsync(c->obs, host.data(), host.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
   c->sc = sc;
+  // obstacle centres in the plane, kept for the class-augmented sweep (its labels
+  // wind about these points; float64 sums of float32 inputs are exact)
+  c->centres.clear();
+  for (int o = 0; o < n_s; ++o) c->centres.emplace_back(double(spheres[4 * o]), double(spheres[4 * o + 1]));
+  for (int o = 0; o < n_b; ++o) {
+    const float* b = boxes + 6 * o;
+    c->centres.emplace_back(0.5 * (double(b[0]) + double(b[3])), 0.5 * (double(b[1]) + double(b[4])));
+  }
   return GTMP_OK;
 }
 
@@ -517,46 +572,9 @@ gtmp_status gtmp_solve_unfused(gtmp_ctx* c, int32_t* dev_path, float* dev_cost) 
   if (!c || !dev_path || !dev_cost) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
   gtmp_status s = check_ready(c);
   if (s != GTMP_OK) return s;
+  if ((s = gtmp_internal_edge_costs(c)) != GTMP_OK) return s;
   const int L = c->p.L;
-  if (!c->C) {
-    GraphDev cap = graph(c, 1, c->p.M);
-    size_t total = 0;
-    c->c_off.assign(L + 2, 0);
-    c->c_cs.assign(L + 1, 0);
-    for (int layer = 0; layer <= L; ++layer) {
-      int rows, cols;
-      transition_shape(cap, layer, &rows, &cols);
-      c->c_cs[layer] = ((cols + 3) / 4) * 4;
-      c->c_off[layer] = total;
-      total += static_cast<size_t>(rows) * c->c_cs[layer];
-    }
-    c->c_off[L + 1] = total;
-    CUDA_TRY(c, cudaMalloc(&c->C, total * sizeof(float)));
-  }
   GraphDev g = graph(c, 1, c->M_active);
-  CUDA_TRY(c, launch_init_keys(g, c->counters, (L + 1), c->stream));
-  CUDA_TRY(c, launch_vertex_labels(g, c->rb, c->variant, scene(c), c->stream));
-  LAUNCHED(c, 2);
-  const int resident = c->num_sms * c->fused_bps[0];
-  // step 1: C_L first so that, when the matrices outgrow L2, step 2 reads each from HBM
-  for (int layer = L; layer >= 0; --layer) {
-    int rows, cols;
-    transition_shape(g, layer, &rows, &cols);
-    // the unfused step recomputes its own row stride for the active M
-    const int cs = ((cols + 3) / 4) * 4;
-    c->c_cs[layer] = cs;
-    const long long edges = static_cast<long long>(rows) * cols;
-    long long chunk = edges / (static_cast<long long>(resident) * 64);
-    if (chunk < 1) chunk = 1;
-    if (chunk > 32) chunk = 32;
-    if (chunk > cols) chunk = cols;
-    const long long n_chunks = rows * ((cols + chunk - 1) / chunk);
-    int grid = resident;
-    if (grid > (n_chunks + 7) / 8) grid = static_cast<int>((n_chunks + 7) / 8);
-    CUDA_TRY(c, launch_edge_costs(g, layer, c->rb, c->variant, scene(c), c->C + c->c_off[layer], cs,
-                                  c->counters + layer, grid, static_cast<int>(chunk), c->err, c->stream));
-    LAUNCHED(c, 1);
-  }
   // step 2: the min-plus sweep over the stored matrices
   for (int layer = L; layer >= 0; --layer) {
     int rows, cols;

@@ -55,4 +55,11 @@ struct gtmp_ctx {
   // learned collision surrogate (allocated by gtmp_surrogate_train)
   gtmp::SurrogateState* sur = nullptr;
   uint8_t* prune = nullptr;  // per-transition prune mask, M x M
+  // class-augmented sweep (allocated by gtmp_solve_classes)
+  void* cls = nullptr;
+  size_t cls_bytes = 0;
+  std::vector<std::pair<double, double>> centres;  // obstacle centres in the plane (host)
 };
+
+// vertex labels and every transition's stored cost matrix (step 1 of gtmp_solve_unfused)
+gtmp_status gtmp_internal_edge_costs(gtmp_ctx* c);
