@@ -132,8 +132,23 @@ GTMP_API gtmp_status gtmp_synchronize(gtmp_ctx* ctx);
  * Copied (the call returns after the copy).  n_s + n_b <= max_obstacles. */
 GTMP_API gtmp_status gtmp_set_obstacles(gtmp_ctx* ctx, const float* spheres, int32_t n_s, const float* boxes, int32_t n_b);
 
-/* Start q0 and goal qg (host [dof] each, inside the joint box).  Sec. III. */
+/* Start q0 and goal qg (host [dof] each, inside the joint box).  Sec. III.
+ * Resets the goal set to this single goal with terminal value 0. */
 GTMP_API gtmp_status gtmp_set_endpoints(gtmp_ctx* ctx, const float* q_start, const float* q_goal);
+
+/* Goal set of Alg. 1 (its G with terminal values V_g: the last layer's values
+ * are min over goals of C_l + V_g): goals host [G][dof] inside the joint box,
+ * values host [G] (finite, >= 0; NULL = all 0), 1 <= G <= M (capacity).
+ * Replaces the goal of gtmp_set_endpoints, which must have set the start.
+ * Every solve, restart and mode uses the set; informed expansion
+ * (aogtmp_expand) and class sweeps (gtmp_solve_classes) need a single goal
+ * and return GTMP_ERR_UNSUPPORTED otherwise. */
+GTMP_API gtmp_status gtmp_set_goals(gtmp_ctx* ctx, const float* goals, const float* values, int32_t G);
+
+/* The goal vertex (index into the goal set) that graph `graph`'s best chain
+ * reaches, -1 if infeasible: dev_goal device [1] int32.  Enqueued after the
+ * solve on the context's stream. */
+GTMP_API gtmp_status gtmp_get_goal_reached(gtmp_ctx* ctx, int32_t graph, int32_t* dev_goal);
 
 /* Alg. 1 "uniformly sample Q": M samples per layer (M <= capacity) for graph 0.
  * Q[l][i][k] = fma(u, hi_k - lo_k, lo_k) in float32 with u = (w >> 8) * 2^-24,

@@ -233,8 +233,10 @@ def expand_layers(seed, Q_old, M_new, q0, qg, q_lo, q_hi, c_best, max_attempts=1
 # ---------------------------------------------------------------------------
 
 def layer_vertices(Q, q0, qg):
-    """Vertex sets V_0 = {q0}, V_1..V_L = Q[0..L-1], V_{L+1} = {qg}."""
-    return [_c32(q0)[None, :]] + [_c32(Q[l]) for l in range(Q.shape[0])] + [_c32(qg)[None, :]]
+    """Vertex sets V_0 = {q0}, V_1..V_L = Q[0..L-1], V_{L+1} = {qg} (qg [dof]) or the goal set (qg [G][dof])."""
+    goals = _c32(qg)
+    goals = goals[None, :] if goals.ndim == 1 else goals
+    return [_c32(q0)[None, :]] + [_c32(Q[l]) for l in range(Q.shape[0])] + [goals]
 
 
 def realize_edges(scene, verts, H, eps=EPS_DEFAULT, max_len=math.inf):
@@ -242,9 +244,10 @@ def realize_edges(scene, verts, H, eps=EPS_DEFAULT, max_len=math.inf):
     return [edge_block(scene, verts[l], verts[l + 1], H, eps, max_len) for l in range(len(verts) - 1)]
 
 
-def value_iteration(edges, ambiguous_free: bool):
+def value_iteration(edges, ambiguous_free: bool, terminal=None):
     """Backward pass J_l(u) = min_v c(u,v) + J_{l+1}(v); returns V, sigma, second.
 
+    J_{L+1} = the goals' terminal values V_g (Alg. 1; `terminal`, default 0).
     V[l] float64 [n_l], sigma[l] int64 [n_l] (-1 if no finite candidate),
     second[l] = the second smallest candidate value (over distinct v).
     """
@@ -252,7 +255,8 @@ def value_iteration(edges, ambiguous_free: bool):
     V = [None] * n_layers
     sigma = [None] * n_layers
     second = [None] * n_layers
-    V[-1] = np.zeros(edges[-1][0].shape[1])
+    n_goals = edges[-1][0].shape[1]
+    V[-1] = np.zeros(n_goals) if terminal is None else np.asarray(terminal, np.float64).reshape(n_goals)
     sigma[-1] = np.full(V[-1].shape, -1)
     second[-1] = np.full(V[-1].shape, np.inf)
     for l in range(len(edges) - 1, -1, -1):
@@ -298,12 +302,13 @@ class Solution:
     verts: list
 
 
-def solve(scene, Q, H: int, eps=EPS_DEFAULT, max_len=math.inf) -> Solution:
-    """gtmp of Alg. 1 for given samples Q float32 [L][M][dof]."""
-    verts = layer_vertices(Q, scene.q_start, scene.q_goal)
+def solve(scene, Q, H: int, eps=EPS_DEFAULT, max_len=math.inf, goals=None, goal_values=None) -> Solution:
+    """gtmp of Alg. 1 for given samples Q float32 [L][M][dof]; the goal set G with terminal values V_g
+    (`goals` [G][dof], `goal_values` [G]) replaces the scene's goal when given."""
+    verts = layer_vertices(Q, scene.q_start, scene.q_goal if goals is None else goals)
     edges = realize_edges(scene, verts, H, eps, max_len)
-    V_lo, sig_lo, sec_lo = value_iteration(edges, ambiguous_free=True)
-    V_hi, _, _ = value_iteration(edges, ambiguous_free=False)
+    V_lo, sig_lo, sec_lo = value_iteration(edges, ambiguous_free=True, terminal=goal_values)
+    V_hi, _, _ = value_iteration(edges, ambiguous_free=False, terminal=goal_values)
     path = extract_path(sig_lo)
     return Solution(V_lo, V_hi, sig_lo, sec_lo, path, float(V_lo[0][0]), float(V_hi[0][0]), edges, verts)
 

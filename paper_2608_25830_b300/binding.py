@@ -108,6 +108,8 @@ _SIGNATURES = {
     "gtmp_batch_autotune": [_vp, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_float)],
     "gtmp_batch_set_eval_mode": [_vp, _i32],
     "gtmp_solve_classes": [_vp, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32)],
+    "gtmp_set_goals": [_vp, _fp, _fp, _i32],
+    "gtmp_get_goal_reached": [_vp, _i32, _vp],
     "gtmp_surrogate_train": [_vp, ctypes.POINTER(GtmpSurrogateConfig), ctypes.POINTER(GtmpSurrogateStats)],
     "gtmp_surrogate_predict": [_vp, _vp, _i32, _vp],
     "gtmp_surrogate_get_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
@@ -482,6 +484,17 @@ def gtmp_batch_get_tiling(b):
     t, c = _i32(), _i32()
     _bcheck(b, lib().gtmp_batch_get_tiling(b, ctypes.byref(t), ctypes.byref(c)))
     return t.value, c.value
+
+
+def gtmp_set_goals(ctx, goals, values=None):
+    g = _f32(goals)
+    v = None if values is None else _f32(values)
+    _check(ctx, lib().gtmp_set_goals(ctx, _ptr(g), None if v is None else _ptr(v), g.shape[0]))
+
+
+def gtmp_get_goal_reached(ctx, graph, dev_goal):
+    import torch
+    _check(ctx, lib().gtmp_get_goal_reached(ctx, graph, _dev(dev_goal, torch.int32)))
 
 
 def gtmp_solve_classes(ctx, max_labels, max_classes, dev_paths, dev_costs, dev_labels):

@@ -53,6 +53,8 @@ GraphDev graph(gtmp_ctx* c, int R, int M) {
   g.H = c->p.H;
   g.M_stride = c->p.M;
   g.max_edge_len = c->p.max_edge_len;
+  g.G = c->G;
+  g.gval = c->goal_values ? c->gval : nullptr;
   return g;
 }
 
@@ -355,6 +357,7 @@ gtmp_status gtmp_destroy(gtmp_ctx* c) {
   cudaFree(c->err);
   cudaFree(c->C);
   cudaFree(c->cls);
+  cudaFree(c->gval);
   cudaFree(c->prune);
   surrogate_free(c->sur);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -463,6 +466,49 @@ gtmp_status gtmp_set_endpoints(gtmp_ctx* c, const float* q_start, const float* q
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->have_endpoints = true;
+  c->G = 1;
+  c->goal_values = false;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_set_goals(gtmp_ctx* c, const float* goals, const float* values, int32_t G) {
+  if (!c || !goals) return fail(c, GTMP_ERR_INVALID_ARG, "NULL goal array");
+  if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "set the start with gtmp_set_endpoints first");
+  if (G < 1 || G > c->p.M) return fail(c, GTMP_ERR_INVALID_ARG, "goal count %d outside [1, M = %d]", G, c->p.M);
+  for (int i = 0; i < G; ++i) {
+    for (int k = 0; k < c->dof; ++k) {
+      const float q = goals[static_cast<size_t>(i) * c->dof + k];
+      if (!std::isfinite(q) || q < c->q_lo[k] || q > c->q_hi[k])
+        return fail(c, GTMP_ERR_INVALID_ARG, "goal %d non-finite or outside the joint box", i);
+    }
+    if (values && !(std::isfinite(values[i]) && values[i] >= 0.0f))
+      return fail(c, GTMP_ERR_INVALID_ARG, "goal value %d must be finite and >= 0", i);
+  }
+  std::vector<float> g(static_cast<size_t>(c->p.R) * G * c->dp, 0.0f);
+  for (int r = 0; r < c->p.R; ++r)
+    for (int i = 0; i < G; ++i)
+      for (int k = 0; k < c->dof; ++k)
+        g[(static_cast<size_t>(r) * G + i) * c->dp + k] = goals[static_cast<size_t>(i) * c->dof + k];
+  const size_t graph_stride = static_cast<size_t>(c->p.L + 2) * c->p.M * c->dp * sizeof(float);
+  const size_t width = static_cast<size_t>(G) * c->dp * sizeof(float);
+  float* dst = c->Q + static_cast<size_t>(c->p.L + 1) * c->p.M * c->dp;
+  CUDA_TRY(c, cudaMemcpy2DAsync(dst, graph_stride, g.data(), width, width, c->p.R, cudaMemcpyHostToDevice, c->stream));
+  if (values) {
+    if (!c->gval) CUDA_TRY(c, cudaMalloc(&c->gval, static_cast<size_t>(c->p.M) * sizeof(float)));
+    CUDA_TRY(c, cudaMemcpyAsync(c->gval, values, G * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->G = G;
+  c->goal_values = values != nullptr;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_get_goal_reached(gtmp_ctx* c, int32_t gi, int32_t* dev_goal) {
+  if (!c || !dev_goal || gi < 0 || gi >= c->p.R) return fail(c, GTMP_ERR_INVALID_ARG, "bad request");
+  if (c->M_active < 1) return fail(c, GTMP_ERR_NOT_READY, "no samples");
+  GraphDev g = graph(c, c->p.R, c->M_active);
+  CUDA_TRY(c, launch_goal_reached(g, gi, dev_goal, c->stream));
+  LAUNCHED(c, 1);
   return GTMP_OK;
 }
 
@@ -636,6 +682,8 @@ gtmp_status aogtmp_expand(gtmp_ctx* c, uint64_t seed, int32_t M_new, int32_t* de
   if (!c || !dev_stage_path || !dev_stage_cost || !dev_best_path || !dev_best_cost)
     return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
   if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "endpoints not set");
+  if (c->G != 1)
+    return fail(c, GTMP_ERR_UNSUPPORTED, "informed expansion is defined for a single goal (the ellipsoid's focus)");
   const int M_old = c->M_active;
   if (M_new < M_old || M_new < 1 || M_new > c->p.M)
     return fail(c, GTMP_ERR_INVALID_ARG, "M_new=%d outside %d..%d", M_new, M_old, c->p.M);

@@ -262,6 +262,7 @@ extern "C" GTMP_API gtmp_status gtmp_solve_classes(gtmp_ctx* c, int32_t max_labe
     return cfail(c, GTMP_ERR_UNSUPPORTED, "class labels support at most %d obstacles", kMaxClassObstacles);
   if (!c->have_endpoints || c->M_active < 1)
     return cfail(c, GTMP_ERR_NOT_READY, "endpoints or samples missing");
+  if (c->G != 1) return cfail(c, GTMP_ERR_UNSUPPORTED, "class labels are defined for a single goal");
   gtmp_status s = gtmp_internal_edge_costs(c);
   if (s != GTMP_OK) return s;
   const int L = c->p.L, K = max_labels;

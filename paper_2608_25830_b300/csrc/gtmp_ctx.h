@@ -39,6 +39,10 @@ struct gtmp_ctx {
   float* C = nullptr;
   std::vector<size_t> c_off;
   std::vector<int> c_cs;
+  // goal set (Alg. 1's G with terminal values V_g); gtmp_set_endpoints resets it to its single goal
+  int G = 1;
+  float* gval = nullptr;  // [p.M] device, valid when goal_values is set
+  bool goal_values = false;
   // state
   bool have_endpoints = false;
   int M_active = 0;

@@ -57,7 +57,9 @@ __global__ void init_keys_kernel(GraphDev g, int* counters, int n_counters) {
   if (tid >= per_r * g.R) return;
   const int layer = static_cast<int>((tid % per_r) / g.M_stride);
   const int i = static_cast<int>(tid % g.M_stride);
-  g.keys[tid] = (layer == g.L + 1 && i == 0) ? make_key(0.0f, 0u) : kEmptyKey;
+  // goal vertex i starts at its terminal value V_g[i] (Alg. 1: V_h[M-1] <- min(C_l + V_g))
+  g.keys[tid] = (layer == g.L + 1 && i < g.G) ? make_key(g.gval ? g.gval[i] : 0.0f, static_cast<uint32_t>(i))
+                                               : kEmptyKey;
 }
 
 // ---------------------------------------------------------------------------
@@ -793,6 +795,22 @@ cudaError_t launch_edge_costs(const GraphDev& g, int layer, const RobotDev& rb, 
 
 cudaError_t launch_minplus(const GraphDev& g, int layer, const float* C, int cs, int grid, cudaStream_t st) {
   minplus_kernel<<<grid, kThreads, static_cast<size_t>(cs) * 4, st>>>(g, layer, C, cs);
+  return cudaGetLastError();
+}
+
+// goal vertex reached by graph gi's best chain (-1 if infeasible)
+__global__ void goal_reached_kernel(GraphDev g, int gi, int32_t* goal) {
+  unsigned long long k = g.keys[vidx(g, gi, 0, 0)];
+  if (k == kEmptyKey) {
+    *goal = -1;
+    return;
+  }
+  for (int l = 1; l <= g.L; ++l) k = g.keys[vidx(g, gi, l, key_index(k))];
+  *goal = static_cast<int32_t>(key_index(k));
+}
+
+cudaError_t launch_goal_reached(const GraphDev& g, int gi, int32_t* goal, cudaStream_t st) {
+  goal_reached_kernel<<<1, 1, 0, st>>>(g, gi, goal);
   return cudaGetLastError();
 }
 

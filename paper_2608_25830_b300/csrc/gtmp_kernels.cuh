@@ -19,13 +19,15 @@ struct GraphDev {
   int M_stride;
   float max_edge_len;
   const uint8_t* prune = nullptr;  // [rows][cols] of the transition being run; 1 = edge dropped before checking
+  int G = 1;                       // goal vertices (layer L+1)
+  const float* gval = nullptr;     // [G] terminal values V_g (null: all 0)
 };
 
 __host__ __device__ inline size_t vidx(const GraphDev& g, int r, int layer, int i) {
   return (static_cast<size_t>(r) * (g.L + 2) + layer) * g.M_stride + i;
 }
 __host__ __device__ inline int layer_size(const GraphDev& g, int layer) {
-  return (layer == 0 || layer == g.L + 1) ? 1 : g.M;
+  return layer == 0 ? 1 : layer == g.L + 1 ? g.G : g.M;
 }
 
 // Obstacle table in device memory (staged whole into shared memory).
@@ -74,6 +76,7 @@ cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev
                                     cudaStream_t st);
 int fused_max_blocks_per_sm(int variant, int mode);
 cudaError_t launch_extract_paths(const GraphDev& g, int32_t* path, float* cost, int32_t* best, cudaStream_t st);
+cudaError_t launch_goal_reached(const GraphDev& g, int gi, int32_t* goal, cudaStream_t st);
 cudaError_t launch_get_values(const GraphDev& g, float* V, int32_t* sigma, cudaStream_t st);
 cudaError_t launch_pack_layers(const GraphDev& g, float* user, int dof, int to_internal, cudaStream_t st);
 cudaError_t launch_edge_costs(const GraphDev& g, int layer, const RobotDev& rb, int variant, const SceneDev& sc,

@@ -1127,6 +1127,8 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
   g.H = c->p.H;
   g.M_stride = c->p.M;
   g.max_edge_len = c->p.max_edge_len;
+  g.G = c->G;
+  g.gval = c->goal_values ? c->gval : nullptr;
   cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

@@ -228,3 +228,88 @@ def test_ao_stages_match_oracle(torch_cuda, kind, dof, mode):
         assert b <= prev_best
         prev_best = b
         assert b == min(c_in, float(stage_cost.cpu()[0]))
+
+
+# ---------------------------------------------------------------------------
+# goal sets with terminal values (Alg. 1's G and V_g)
+# ---------------------------------------------------------------------------
+
+def _goal_set(sc, seed, G=3):
+    """The scene's goal plus seeded configurations the oracle finds free."""
+    rng = np.random.default_rng(seed + 100)
+    cand = rng.uniform(sc.robot.q_lo, sc.robot.q_hi, (256, sc.robot.dof)).astype(np.float32)
+    free = oracle.config_free(sc, cand)
+    return np.array([sc.q_goal] + [c for c, f in zip(cand, free) if f][:G - 1], np.float32)
+
+
+@pytest.mark.parametrize("kind,dof,M,L,H,seed", [("point2d", 2, 32, 3, 16, 1), ("arm", 7, 40, 3, 32, 2),
+                                                 ("arm", 6, 24, 2, 16, 3)])
+@pytest.mark.parametrize("mode", [binding.EVAL_EARLY_EXIT, binding.EVAL_FULL, binding.EVAL_LAZY])
+@pytest.mark.parametrize("with_values", [False, True])
+def test_goal_set_matches_oracle(torch_cuda, kind, dof, M, L, H, seed, mode, with_values):
+    torch = torch_cuda
+    sc = scene_for(kind, seed, dof, 30 if kind == "arm" else 10)
+    goals = _goal_set(sc, seed)
+    vals = np.array([0.6, 0.0, 0.3], np.float32)[:len(goals)] if with_values else None
+    p = _planner(sc, M, L, H, mode=mode)
+    binding.gtmp_set_goals(p.ctx, goals, vals)
+    p.sample_layers(seed, M)
+    V, S, path, cost = _gpu_solution(p)
+    Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    sol = oracle.solve(sc, Q, H, goals=goals, goal_values=vals)
+    compare_solution(sol, V, S, path, cost, f"{kind} goals mode={mode} values={with_values}")
+    goal = torch.empty(1, dtype=torch.int32, device="cuda")
+    binding.gtmp_get_goal_reached(p.ctx, 0, goal)
+    p.synchronize()
+    g = int(goal.cpu()[0])
+    if not math.isfinite(cost):
+        assert g == -1
+        return
+    assert 0 <= g < len(goals)
+    last = int(path[-1])
+    if decisive(sol, L)[last] and list(path) == list(sol.path):
+        assert g == sol.sigma[L][last]
+    # the chain through the reached goal costs what the planner returned
+    verts = [sc.q_start] + [Q[l, path[l]] for l in range(L)] + [goals[g]]
+    total = sum(oracle.lib().orc_edge_length(dof, oracle._ptr(oracle._c32(a), oracle._f32p),
+                                             oracle._ptr(oracle._c32(b), oracle._f32p))
+                for a, b in zip(verts[:-1], verts[1:]))
+    total += 0.0 if vals is None else float(vals[g])
+    assert cost == pytest.approx(total, rel=REL)
+
+
+def test_single_goal_set_equals_endpoints(torch_cuda):
+    sc = scene_for("arm", 5, 7, 30)
+    M, L, H = 48, 3, 32
+    outs = []
+    for use_set in (False, True):
+        p = _planner(sc, M, L, H)
+        if use_set:
+            binding.gtmp_set_goals(p.ctx, sc.q_goal[None, :], None)
+        p.sample_layers(9, M)
+        outs.append(_gpu_solution(p))
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_goal_set_restarts_and_ao_guard(torch_cuda):
+    torch = torch_cuda
+    sc = scene_for("arm", 3, 6, 30)
+    R, M, L, H = 3, 20, 2, 16
+    goals = _goal_set(sc, 3)
+    vals = np.array([0.2, 0.0, 0.5], np.float32)
+    p = _planner(sc, M, L, H, R=R)
+    binding.gtmp_set_goals(p.ctx, goals, vals)
+    paths, costs, best = p.anytime(21, R)
+    p.synchronize()
+    costs = costs.cpu().numpy()
+    for r in range(R):
+        Q = oracle.sample_uniform(21, r, L, M, sc.robot.q_lo, sc.robot.q_hi)
+        sol = oracle.solve(sc, Q, H, goals=goals, goal_values=vals)
+        check_values([costs[r]], [sol.cost_lo], [sol.cost_hi], f"restart {r}")
+    # informed expansion is defined for one goal
+    p2 = _planner(sc, 64, L, H)
+    binding.gtmp_set_goals(p2.ctx, goals, None)
+    t = lambda *s, d=torch.int32: torch.empty(*s, dtype=d, device="cuda")
+    with pytest.raises(binding.GtmpError, match="UNSUPPORTED"):
+        binding.aogtmp_expand(p2.ctx, 1, 16, t(L), t(1, d=torch.float32), t(L), t(1, d=torch.float32))

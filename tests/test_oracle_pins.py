@@ -549,3 +549,37 @@ def test_class_value_iteration_single_disk_has_two_sides():
     labels = set(tables[0][0])
     # passing on the closing segment's side of the centre winds 0 times, the other side once
     assert labels in ({(0,), (1,)}, {(0,), (-1,)})
+
+
+@pytest.mark.parametrize("seed", [0, 4])
+def test_goal_set_value_iteration_equals_brute_force(seed):
+    """Alg. 1's goal set G with terminal values V_g: the value of q0 is the minimum over every chain and every
+    goal of the chain's cost plus that goal's value; the last layer's minimiser is that goal."""
+    sc = scenes.point2d_scene(seed, 4)
+    L, M, H = 2, 6, 16
+    Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    goals = np.array([sc.q_goal, [0.85, -0.7], [-0.75, 0.8]], np.float32)
+    vals = np.array([0.0, 0.4, 0.15])
+    verts = oracle.layer_vertices(Q, sc.q_start, goals)
+    assert verts[-1].shape == (3, 2)
+    edges = oracle.realize_edges(sc, verts, H)
+    best, best_goal = math.inf, -1
+    for chain in itertools.product(range(M), repeat=L):
+        for gi in range(3):
+            idx = [0] + list(chain) + [gi]
+            total = 0.0
+            for l in range(L + 1):
+                lab = edges[l][0][idx[l], idx[l + 1]]
+                assert lab != oracle.AMBIGUOUS
+                if lab != oracle.FREE:
+                    total = math.inf
+                    break
+                total += float(edges[l][1][idx[l], idx[l + 1]])
+            total += vals[gi]
+            if total < best:
+                best, best_goal = total, gi
+    sol = oracle.solve(sc, Q, H, goals=goals, goal_values=vals)
+    assert sol.cost_lo == pytest.approx(best, rel=1e-12)
+    if math.isfinite(best):
+        assert sol.sigma[L][sol.path[-1]] == best_goal
+        np.testing.assert_array_equal(sol.V_lo[-1], vals)
