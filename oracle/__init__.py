@@ -74,6 +74,8 @@ def _declare(L):
     L.orc_config_margin.argtypes = [_P(OrcScene), _f64p]
     L.orc_config_margin.restype = ctypes.c_double
     L.orc_config_labels.argtypes = [_P(OrcScene), ctypes.c_int, _f32p, ctypes.c_double, _i8p, _f64p]
+    L.orc_sample_free.argtypes = [_P(OrcScene), ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, _f32p,
+                                  _f32p, ctypes.c_double, ctypes.c_int, _f32p, _P(ctypes.c_int32), _i8p]
     L.orc_edge_label.argtypes = [_P(OrcScene), _f32p, _f32p, ctypes.c_int, ctypes.c_double]
     L.orc_edge_label.restype = ctypes.c_int
     L.orc_edge_length.argtypes = [ctypes.c_int, _f32p, _f32p]
@@ -142,6 +144,22 @@ class _SceneHandle:
                           int(scene.boxes.shape[0]), _ptr(self.boxes, _f64p))
         self.ref = ctypes.byref(self.s)
         self.dof = int(r.dof)
+
+
+def sample_free(scene, seed: int, restart: int, L: int, M: int, max_attempts: int = 64, eps=EPS_DEFAULT):
+    """Layer samples on C_free by rejection (Sec. III's pi_m on C_free): attempt 0 is the uniform sample,
+    attempt a >= 1 its own Philox block; returns Q float32 [L][M][dof], the accepted attempt per sample
+    (-1: none of max_attempts was free, the last is kept) and an `undecided` flag (an earlier attempt lay in
+    the +-eps band)."""
+    dof = scene.robot.dof
+    lo, hi = _c32(scene.robot.q_lo), _c32(scene.robot.q_hi)
+    Q = np.zeros((L, M, dof), np.float32)
+    used = np.zeros(L * M, np.int32)
+    und = np.zeros(L * M, np.int8)
+    h = _SceneHandle(scene)
+    lib().orc_sample_free(h.ref, seed, restart, L, M, _ptr(lo, _f32p), _ptr(hi, _f32p), eps, max_attempts,
+                          _ptr(Q, _f32p), used.ctypes.data_as(_P(ctypes.c_int32)), _ptr(und, _i8p))
+    return Q, used.reshape(L, M), und.reshape(L, M).astype(bool)
 
 
 def fk_spheres(scene, q) -> np.ndarray:

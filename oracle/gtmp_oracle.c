@@ -30,6 +30,7 @@
 #define TAG_UNIFORM 1u
 #define TAG_INFORMED 2u
 #define TAG_COIN 3u
+#define TAG_FREE 5u
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,        */
@@ -199,6 +200,44 @@ void orc_config_labels(const orc_scene* sc, int n, const float* q, double eps, i
         double m = orc_config_margin(sc, qd);
         if (margins) margins[i] = m;
         labels[i] = (int8_t)label_of_margin(m, eps);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Layer sampling on C_free (Sec. III: pi_m is a measure on C_m and C_free)  */
+/* by rejection.  Sample (r, l, i), attempt a: attempt 0 is the uniform       */
+/* sample of orc_sample_uniform; attempt a >= 1 takes word k & 3 of Philox    */
+/* block (i, l, r, TAG_FREE<<24 | a<<2 | k>>2).  The first attempt whose      */
+/* label is free is kept; if none of max_attempts is, the last one is kept    */
+/* (its edges then collide through their endpoint).  used[] = the accepted    */
+/* attempt or -1; undecided[] = 1 when an attempt before the accepted one     */
+/* lay in the +-eps band (a float32 checker may decide it either way).        */
+/* ------------------------------------------------------------------------ */
+void orc_sample_free(const orc_scene* sc, uint64_t seed, uint32_t restart, int L, int M, const float* lo,
+                     const float* hi, double eps, int max_attempts, float* Q, int32_t* used, int8_t* undecided) {
+    const int dof = sc->dof;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int t = 0; t < L * M; ++t) {
+        const int l = t / M, i = t % M;
+        float* q = Q + (size_t)t * dof;
+        double qd[64];
+        int acc = -1;
+        int8_t und = 0;
+        for (int a = 0; a < max_attempts && acc < 0; ++a) {
+            for (int k = 0; k < dof; ++k) {
+                uint32_t w[4];
+                const uint32_t word3 = a == 0 ? (TAG_UNIFORM << 24) | (uint32_t)(k >> 2)
+                                              : (TAG_FREE << 24) | ((uint32_t)a << 2) | (uint32_t)(k >> 2);
+                philox_block(seed, (uint32_t)i, (uint32_t)l, restart, word3, w);
+                q[k] = fmaf(word_to_unit(w[k & 3]), hi[k] - lo[k], lo[k]);
+                qd[k] = (double)q[k];
+            }
+            const int lab = label_of_margin(orc_config_margin(sc, qd), eps);
+            if (lab == ORC_FREE) acc = a;
+            else if (lab == ORC_AMBIGUOUS) und = 1;
+        }
+        used[t] = acc;
+        undecided[t] = und;
     }
 }
 

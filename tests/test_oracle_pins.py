@@ -583,3 +583,55 @@ def test_goal_set_value_iteration_equals_brute_force(seed):
     if math.isfinite(best):
         assert sol.sigma[L][sol.path[-1]] == best_goal
         np.testing.assert_array_equal(sol.V_lo[-1], vals)
+
+
+# ---------------------------------------------------------------------------
+# layer sampling on C_free (Sec. III: pi_m lives on C_m and C_free)
+# ---------------------------------------------------------------------------
+
+def test_free_sampler_without_obstacles_is_the_uniform_sampler():
+    sc = scenes.point2d_scene(0, 0)
+    Q, used, und = oracle.sample_free(sc, 7, 0, 3, 50)
+    np.testing.assert_array_equal(Q.view(np.uint32),
+                                  oracle.sample_uniform(7, 0, 3, 50, sc.robot.q_lo, sc.robot.q_hi).view(np.uint32))
+    assert np.all(used == 0) and not und.any()
+
+
+def _arm_scene_with_free_ends(seed):
+    sc = scenes.arm_scene(seed, 7, 30)
+    return scenes.pick_endpoints(sc, lambda q: oracle.config_free(sc, q))
+
+
+@pytest.mark.parametrize("kind", ["point2d", "arm"])
+def test_free_sampler_keeps_free_uniform_samples_and_rejects_colliding_ones(kind):
+    sc = scenes.point2d_scene(2, 14) if kind == "point2d" else _arm_scene_with_free_ends(1)
+    L, M = 3, 200
+    Q, used, und = oracle.sample_free(sc, 11, 2, L, M, max_attempts=256)
+    U = oracle.sample_uniform(11, 2, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    lab_u, _ = oracle.config_labels(sc, U.reshape(-1, sc.robot.dof))
+    lab_q, _ = oracle.config_labels(sc, Q.reshape(-1, sc.robot.dof))
+    free_u = (lab_u == oracle.FREE).reshape(L, M)
+    # a uniform sample that is free is kept as is (attempt 0)
+    np.testing.assert_array_equal(Q[free_u].view(np.uint32), U[free_u].view(np.uint32))
+    assert np.all(used[free_u] == 0)
+    # every accepted sample is free; colliding uniform samples were replaced
+    acc = used >= 0
+    assert np.all(lab_q.reshape(L, M)[acc] == oracle.FREE)
+    replaced = ~free_u & acc
+    assert replaced.any() and np.all(used[replaced] >= 1)
+    assert acc.mean() > 0.99
+
+
+def test_free_sampler_is_uniform_on_the_free_space():
+    """Accepted samples against an independent uniform batch restricted to C_free (two-sample KS per
+    coordinate), on a scene where a third of the box collides."""
+    sc = scenes.point2d_scene(4, 25)
+    Q, used, _ = oracle.sample_free(sc, 5, 0, 4, 1000, max_attempts=256)
+    X = Q.reshape(-1, 2)[used.reshape(-1) >= 0]
+    rng = np.random.default_rng(99)
+    Y = rng.uniform(sc.robot.q_lo, sc.robot.q_hi, (20000, 2)).astype(np.float32)
+    Y = Y[oracle.config_labels(sc, Y)[0] == oracle.FREE]
+    frac_coll = 1 - len(Y) / 20000
+    assert 0.1 < frac_coll < 0.7
+    for k in range(2):
+        assert stats.ks_2samp(X[:, k], Y[:, k]).pvalue > 1e-3, k
