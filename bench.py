@@ -355,6 +355,35 @@ def run_ours(args, wl):
     plz.close()
     lazy_s = max_over_ranks(sum(lz_ms) / 1e3, world, "cuda")
 
+    # --- the same seeds with layer samples drawn on C_free (rejection, Sec. III's pi_m): quality and speed
+    pfree = binding.Planner(sc.robot, M, L, H, max_obstacles=64)
+    pfree.set_scene(sc)
+    binding.gtmp_set_sampler(pfree.ctx, binding.SAMPLER_FREE, 64)
+    for s in range(args.warmup):
+        binding.gtmp_sample_layers(pfree.ctx, seed0 + 10_000 + s, M)
+        binding.gtmp_solve(pfree.ctx, lz_path, lz_cost)
+    pfree.synchronize()
+    fr_ms, fr_costs, un_costs = [], [], []
+    for s in range(args.steps):
+        flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        binding.gtmp_sample_layers(pfree.ctx, seed0 + s, M)
+        binding.gtmp_solve(pfree.ctx, lz_path, lz_cost)
+        a1.record(stream)
+        binding.gtmp_sample_layers(p.ctx, seed0 + s, M)
+        binding.gtmp_solve(p.ctx, ref_path, ref_cost)
+        torch.cuda.synchronize()
+        fr_ms.append(a0.elapsed_time(a1))
+        fr_costs.append(float(lz_cost.cpu()[0]))
+        un_costs.append(float(ref_cost.cpu()[0]))
+    pfree.close()
+    fin = [(a, b) for a, b in zip(fr_costs, un_costs) if math.isfinite(a) and math.isfinite(b)]
+    free_sampling = {"solves_per_s": args.steps / (sum(fr_ms) / 1e3), "ms_per_step": sum(fr_ms) / len(fr_ms),
+                     "feasible": sum(math.isfinite(c) for c in fr_costs), "feasible_uniform": sum(math.isfinite(c) for c in un_costs),
+                     "mean_cost_ratio_free_over_uniform": (sum(a / b for a, b in fin) / len(fin)) if fin else None,
+                     "note": "same seeds; samples redrawn on C_free (first free of up to 64 attempts)"}
+
     # --- roofline of the fused kernel in full-evaluation mode (data-independent FP32 work)
     pf = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_FULL)
     pf.set_scene(sc)
@@ -435,6 +464,7 @@ def run_ours(args, wl):
                          "fused_ms_per_solve": fprof["fused_ms"] / full_steps},
             "fused_ms_per_solve_early_exit": prof["fused_ms"] / args.steps,
             "roofline_unfused_minplus": unfused,
+            "free_sampling": free_sampling,
             "lazy": {"solves_per_s": solves / lazy_s, "ms_per_step": sum(lz_ms) / len(lz_ms),
                      "same_paths_and_costs_as_early_exit": lz_same,
                      "note": "exact mode GTMP_EVAL_LAZY: an edge is realised only if c(u,v)+J(v) beats its row's "

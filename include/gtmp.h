@@ -145,6 +145,19 @@ GTMP_API gtmp_status gtmp_set_endpoints(gtmp_ctx* ctx, const float* q_start, con
  * and return GTMP_ERR_UNSUPPORTED otherwise. */
 GTMP_API gtmp_status gtmp_set_goals(gtmp_ctx* ctx, const float* goals, const float* values, int32_t G);
 
+/* Layer sampler of gtmp_sample_layers and gtmp_anytime.  GTMP_SAMPLER_UNIFORM
+ * (default; Alg. 1 samples uniformly in the joint box): word k & 3 of Philox
+ * block (i, l, restart, 1<<24 | k>>2) mapped to [lo, hi).  GTMP_SAMPLER_FREE
+ * (Sec. III: pi_m is a measure on C_free): rejection on the exact checker;
+ * attempt 0 is the uniform sample, attempt a >= 1 uses block (i, l, restart,
+ * 5<<24 | a<<2 | k>>2); the first free attempt is kept, else the last of
+ * max_attempts (its edges then collide through their endpoint).  Samples
+ * that are free under the uniform sampler are unchanged.  Uses the current
+ * obstacles (set them first). */
+#define GTMP_SAMPLER_UNIFORM 0
+#define GTMP_SAMPLER_FREE 1
+GTMP_API gtmp_status gtmp_set_sampler(gtmp_ctx* ctx, int32_t sampler, int32_t max_attempts);
+
 /* The goal vertex (index into the goal set) that graph `graph`'s best chain
  * reaches, -1 if infeasible: dev_goal device [1] int32.  Enqueued after the
  * solve on the context's stream. */

@@ -109,6 +109,7 @@ _SIGNATURES = {
     "gtmp_batch_set_eval_mode": [_vp, _i32],
     "gtmp_solve_classes": [_vp, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32)],
     "gtmp_set_goals": [_vp, _fp, _fp, _i32],
+    "gtmp_set_sampler": [_vp, _i32, _i32],
     "gtmp_get_goal_reached": [_vp, _i32, _vp],
     "gtmp_surrogate_train": [_vp, ctypes.POINTER(GtmpSurrogateConfig), ctypes.POINTER(GtmpSurrogateStats)],
     "gtmp_surrogate_predict": [_vp, _vp, _i32, _vp],
@@ -484,6 +485,13 @@ def gtmp_batch_get_tiling(b):
     t, c = _i32(), _i32()
     _bcheck(b, lib().gtmp_batch_get_tiling(b, ctypes.byref(t), ctypes.byref(c)))
     return t.value, c.value
+
+
+SAMPLER_UNIFORM, SAMPLER_FREE = 0, 1
+
+
+def gtmp_set_sampler(ctx, sampler, max_attempts=64):
+    _check(ctx, lib().gtmp_set_sampler(ctx, sampler, max_attempts))
 
 
 def gtmp_set_goals(ctx, goals, values=None):

@@ -155,6 +155,14 @@ gtmp_status run_fused(gtmp_ctx* c, const GraphDev& g, int mode) {
   return GTMP_OK;
 }
 
+// the context's layer sampler (uniform in the joint box, or on C_free by rejection)
+cudaError_t sample_layers_of(gtmp_ctx* c, const GraphDev& g, uint64_t seed) {
+  if (c->sampler == GTMP_SAMPLER_FREE)
+    return launch_sample_free(g, c->rb, c->variant, scene(c), c->q_lo, c->q_hi, c->dof, seed, 0, c->sampler_attempts,
+                              c->stream);
+  return launch_sample_uniform(g, c->q_lo, c->q_hi, c->dof, seed, 0, c->stream);
+}
+
 gtmp_status check_ready(gtmp_ctx* c) {
   if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "endpoints not set (gtmp_set_endpoints)");
   if (c->M_active < 1) return fail(c, GTMP_ERR_NOT_READY, "no samples (gtmp_sample_layers / gtmp_set_layers)");
@@ -503,6 +511,15 @@ gtmp_status gtmp_set_goals(gtmp_ctx* c, const float* goals, const float* values,
   return GTMP_OK;
 }
 
+gtmp_status gtmp_set_sampler(gtmp_ctx* c, int32_t sampler, int32_t max_attempts) {
+  if (!c || (sampler != GTMP_SAMPLER_UNIFORM && sampler != GTMP_SAMPLER_FREE) || max_attempts < 1 ||
+      max_attempts > (1 << 20))
+    return fail(c, GTMP_ERR_INVALID_ARG, "sampler must be GTMP_SAMPLER_UNIFORM or _FREE, attempts in [1, 2^20]");
+  c->sampler = sampler;
+  c->sampler_attempts = max_attempts;
+  return GTMP_OK;
+}
+
 gtmp_status gtmp_get_goal_reached(gtmp_ctx* c, int32_t gi, int32_t* dev_goal) {
   if (!c || !dev_goal || gi < 0 || gi >= c->p.R) return fail(c, GTMP_ERR_INVALID_ARG, "bad request");
   if (c->M_active < 1) return fail(c, GTMP_ERR_NOT_READY, "no samples");
@@ -516,7 +533,7 @@ gtmp_status gtmp_sample_layers(gtmp_ctx* c, uint64_t seed, int32_t M) {
   if (!c) return GTMP_ERR_INVALID_ARG;
   if (M < 1 || M > c->p.M) return fail(c, GTMP_ERR_INVALID_ARG, "M=%d outside 1..%d", M, c->p.M);
   GraphDev g = graph(c, 1, M);
-  CUDA_TRY(c, launch_sample_uniform(g, c->q_lo, c->q_hi, c->dof, seed, 0, c->stream));
+  CUDA_TRY(c, sample_layers_of(c, g, seed));
   LAUNCHED(c, 1);
   c->M_active = M;
   return GTMP_OK;
@@ -667,7 +684,7 @@ gtmp_status gtmp_anytime(gtmp_ctx* c, uint64_t seed, int32_t restarts, int32_t* 
     return fail(c, GTMP_ERR_INVALID_ARG, "restarts=%d outside 1..%d", restarts, c->p.R);
   if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "endpoints not set");
   GraphDev g = graph(c, restarts, c->p.M);
-  CUDA_TRY(c, launch_sample_uniform(g, c->q_lo, c->q_hi, c->dof, seed, 0, c->stream));
+  CUDA_TRY(c, sample_layers_of(c, g, seed));
   LAUNCHED(c, 1);
   c->M_active = c->p.M;
   gtmp_status s = run_fused(c, g, c->p.eval_mode);

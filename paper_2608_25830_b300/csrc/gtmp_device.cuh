@@ -23,6 +23,7 @@ constexpr int kMaxSpl = 8;
 constexpr uint32_t kTagUniform = 1u;
 constexpr uint32_t kTagInformed = 2u;
 constexpr uint32_t kTagCoin = 3u;
+constexpr uint32_t kTagFree = 5u;  // rejection attempts of the free-space sampler
 constexpr unsigned long long kEmptyKey = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
 

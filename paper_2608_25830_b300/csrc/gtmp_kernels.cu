@@ -50,6 +50,54 @@ __global__ void sample_uniform_kernel(GraphDev g, Box16 box, int dof, unsigned l
   }
 }
 
+// ---------------------------------------------------------------------------
+// Layer sampling on C_free by rejection (Sec. III: pi_m is a measure on
+// C_m and C_free): thread per (r, layer 1..L, i); attempt 0 is the uniform
+// sample above, attempt a >= 1 takes word k & 3 of Philox block
+// (i, layer - 1, restart, TAG_FREE << 24 | a << 2 | k >> 2); the first
+// attempt the exact checker finds free is kept, else the last (its edges then
+// collide through their endpoint, as with uniform sampling).
+// ---------------------------------------------------------------------------
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) sample_free_kernel(GraphDev g, RobotDev rb, SceneDev sc, Box16 box,
+                                                               int dof, unsigned long long seed, int restart0,
+                                                               int max_attempts) {
+  extern __shared__ float4 s_obs[];
+  stage_obstacles_plain(s_obs, sc.obs, scene_float4s(sc));
+  __syncthreads();
+  const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long total = static_cast<long long>(g.R) * g.L * g.M;
+  if (tid >= total) return;
+  const int i = static_cast<int>(tid % g.M);
+  const int l = static_cast<int>((tid / g.M) % g.L);
+  const int r = static_cast<int>(tid / (static_cast<long long>(g.M) * g.L));
+  const uint2 key = seed_key(seed);
+  constexpr int DP = Var<VAR>::kDp;
+  float q[DP];
+  for (int a = 0; a < max_attempts; ++a) {
+    uint4 w = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      if (k >= dof) {
+        q[k] = 0.0f;
+        continue;
+      }
+      if ((k & 3) == 0) {
+        const uint32_t word3 = a == 0 ? (kTagUniform << 24) | static_cast<uint32_t>(k >> 2)
+                                      : (kTagFree << 24) | (static_cast<uint32_t>(a) << 2) | static_cast<uint32_t>(k >> 2);
+        w = philox4x32_10(make_uint4(static_cast<uint32_t>(i), static_cast<uint32_t>(l),
+                                     static_cast<uint32_t>(restart0 + r), word3),
+                          key);
+      }
+      q[k] = __fmaf_rn(word_to_unit(word_of(w, k)), __fsub_rn(box.hi[k], box.lo[k]), box.lo[k]);
+    }
+    if (!config_collides<VAR, false, false>(q, true, rb, s_obs, sc)) break;
+  }
+  float* out = g.Q + vidx(g, r, l + 1, i) * g.dp;
+#pragma unroll
+  for (int k = 0; k < DP; ++k) out[k] = q[k];
+}
+
 __global__ void init_keys_kernel(GraphDev g, int* counters, int n_counters) {
   const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long per_r = static_cast<long long>(g.L + 2) * g.M_stride;
@@ -530,6 +578,19 @@ cudaError_t by_variant(int variant, Args&&... args) {
 }
 
 template <int VAR>
+struct SampleFreeRun {
+  static cudaError_t run(const GraphDev& g, const RobotDev& rb, const SceneDev& sc, const Box16& box, int dof,
+                         unsigned long long seed, int restart0, int max_attempts, cudaStream_t st) {
+    const long long n = static_cast<long long>(g.R) * g.L * g.M;
+    if (n == 0) return cudaSuccess;
+    const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16;
+    sample_free_kernel<VAR><<<blocks_for(n, kThreads), kThreads, smem, st>>>(g, rb, sc, box, dof, seed, restart0,
+                                                                             max_attempts);
+    return cudaGetLastError();
+  }
+};
+
+template <int VAR>
 struct VertexLabelsRun {
   static cudaError_t run(const GraphDev& g, const RobotDev& rb, const SceneDev& sc, cudaStream_t st) {
     const long long n = static_cast<long long>(g.R) * (g.L + 2) * g.M_stride;
@@ -596,6 +657,9 @@ struct ConfigureRun {
       return e;
     if ((e = cudaFuncSetAttribute(vertex_labels_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_max)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(sample_free_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) !=
+        cudaSuccess)
       return e;
     return cudaFuncSetAttribute(label_configs_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   }
@@ -739,6 +803,12 @@ cudaError_t launch_sample_uniform(const GraphDev& g, const float* lo, const floa
   if (n == 0) return cudaSuccess;
   sample_uniform_kernel<<<blocks_for(n, kThreads), kThreads, 0, st>>>(g, make_box(lo, hi, dof), dof, seed, restart0);
   return cudaGetLastError();
+}
+
+cudaError_t launch_sample_free(const GraphDev& g, const RobotDev& rb, int variant, const SceneDev& sc, const float* lo,
+                               const float* hi, int dof, unsigned long long seed, int restart0, int max_attempts,
+                               cudaStream_t st) {
+  return by_variant<SampleFreeRun>(variant, g, rb, sc, make_box(lo, hi, dof), dof, seed, restart0, max_attempts, st);
 }
 
 cudaError_t launch_init_keys(const GraphDev& g, int* counters, int n_counters, cudaStream_t st) {

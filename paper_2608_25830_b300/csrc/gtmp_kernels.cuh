@@ -64,6 +64,9 @@ int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n
 double arm_reach_bound(const RobotDev& rb);
 
 cudaError_t configure_kernels(int smem_max);
+cudaError_t launch_sample_free(const GraphDev& g, const RobotDev& rb, int variant, const SceneDev& sc, const float* lo,
+                               const float* hi, int dof, unsigned long long seed, int restart0, int max_attempts,
+                               cudaStream_t st);
 cudaError_t launch_sample_uniform(const GraphDev& g, const float* lo, const float* hi, int dof,
                                   unsigned long long seed, int restart0, cudaStream_t st);
 cudaError_t launch_init_keys(const GraphDev& g, int* counters, int n_counters, cudaStream_t st);

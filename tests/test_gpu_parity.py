@@ -313,3 +313,41 @@ def test_goal_set_restarts_and_ao_guard(torch_cuda):
     t = lambda *s, d=torch.int32: torch.empty(*s, dtype=d, device="cuda")
     with pytest.raises(binding.GtmpError, match="UNSUPPORTED"):
         binding.aogtmp_expand(p2.ctx, 1, 16, t(L), t(1, d=torch.float32), t(L), t(1, d=torch.float32))
+
+
+# ---------------------------------------------------------------------------
+# layer sampling on C_free by rejection
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,dof,M,L,seed", [("point2d", 2, 64, 3, 3), ("arm", 7, 100, 3, 5), ("arm", 6, 50, 2, 9)])
+def test_free_samples_bit_exact(torch_cuda, kind, dof, M, L, seed):
+    torch = torch_cuda
+    sc = scene_for(kind, 1, dof, 30 if kind == "arm" else 14)
+    p = _planner(sc, M, L, 4)
+    binding.gtmp_set_sampler(p.ctx, binding.SAMPLER_FREE, 128)
+    p.sample_layers(seed, M)
+    Q = p.get_layers().cpu().numpy()
+    ref, used, und = oracle.sample_free(sc, seed, 0, L, M, max_attempts=128)
+    decided = ~und
+    assert decided.mean() > 0.99
+    np.testing.assert_array_equal(Q[decided].view(np.uint32), ref[decided].view(np.uint32))
+    lab = p.label_configs(torch.from_numpy(np.ascontiguousarray(Q.reshape(-1, dof))).cuda()).cpu().numpy()
+    assert np.all(lab.reshape(L, M)[used >= 0] == 0)
+    assert (used >= 1).any()       # some uniform samples collided and were redrawn
+
+
+def test_free_sampler_restarts_match_oracle(torch_cuda):
+    sc = scene_for("arm", 3, 6, 30)
+    R, M, L, H = 3, 24, 3, 16
+    p = _planner(sc, M, L, H, R=R)
+    binding.gtmp_set_sampler(p.ctx, binding.SAMPLER_FREE, 64)
+    paths, costs, best = p.anytime(33, R)
+    p.synchronize()
+    costs = costs.cpu().numpy()
+    for r in range(R):
+        Q, used, und = oracle.sample_free(sc, 33, r, L, M, max_attempts=64)
+        if und.any():
+            continue
+        sol = oracle.solve(sc, Q, H)
+        V, S = p.values(r)
+        compare_solution(sol, V.cpu().numpy(), S.cpu().numpy(), paths[r].cpu().numpy(), costs[r], f"free restart {r}")
