@@ -314,6 +314,7 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
         const float* ls = robot->link_spheres + (static_cast<size_t>(i) * robot->spheres_per_link + s) * 4;
         rb.sph[i * stride + s] = make_float4(ls[0], ls[1], ls[2], ls[3]);
       }
+    fill_link_bounds(&rb);
     c->dp = 8;
   } else {
     rb.spl = 1;
@@ -335,7 +336,7 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
   c->n_counters = (p.L + 1) * p.R;
   alloc(reinterpret_cast<void**>(&c->counters), static_cast<size_t>(c->n_counters) * sizeof(int));
   // scalar table (<= 2 float4 per obstacle) or packed tables (<= 3 (n_s + n_b) + 8 float4)
-  alloc(reinterpret_cast<void**>(&c->obs), (static_cast<size_t>(p.max_obstacles) * 3 + 8) * sizeof(float4));
+  alloc(reinterpret_cast<void**>(&c->obs), packed_table_capacity(p.max_obstacles) * sizeof(float4));
   alloc(reinterpret_cast<void**>(&c->err), sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->Q, 0, graph_vertices * c->dp * sizeof(float), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
@@ -407,7 +408,7 @@ gtmp_status gtmp_set_obstacles(gtmp_ctx* c, const float* spheres, int32_t n_s, c
     for (int o = 0; o < n_b; ++o)
       for (int k = 0; k < 3; ++k)
         if (!(boxes[6 * o + 3 + k] >= boxes[6 * o + k])) return fail(c, GTMP_ERR_INVALID_ARG, "box with hi < lo");
-    host.resize(3 * static_cast<size_t>(n_s + n_b) + 8);
+    host.resize(packed_table_capacity(n_s + n_b));
     const int n4 = build_packed_tables(spheres, n_s, boxes, n_b, c->rb.r_uniform, arm_reach_bound(c->rb),
                                        host.data(), &sc);
     host.resize(n4);

@@ -407,6 +407,7 @@ bool make_robot(const gtmp_robot& r, RobotDev* rb, int* variant, int* dp) {
       rb->sph[i * stride + s] = make_float4(ls[0], ls[1], ls[2], ls[3]);
     }
   }
+  fill_link_bounds(rb);
   return true;
 }
 
@@ -414,7 +415,7 @@ bool make_robot(const gtmp_robot& r, RobotDev* rb, int* variant, int* dp) {
 int obstacle_table(const gtmp_problem& q, const RobotDev& rb, int variant, std::vector<float4>& out, SceneDev* sc) {
   *sc = SceneDev{};
   if (variant == kVarArm6x4 || variant == kVarArm7x4) {
-    out.resize(3 * static_cast<size_t>(q.n_s + q.n_b) + 8);
+    out.resize(packed_table_capacity(q.n_s + q.n_b));
     const int n4 = build_packed_tables(q.spheres, q.n_s, q.boxes, q.n_b, rb.r_uniform, arm_reach_bound(rb),
                                        out.data(), sc);
     out.resize(n4);

@@ -45,6 +45,7 @@ struct RobotDev {
   float point_radius;
   float d[kMaxDof], a[kMaxDof], ca[kMaxDof], sa[kMaxDof], toff[kMaxDof];
   float4 sph[kMaxDof * kMaxSpl];  // x, y, z, r in the link frame
+  float4 lb[kMaxDof];              // per link: centre (link frame) and radius of a ball holding all its spheres
 };
 
 // ----------------------------------------------------------------------------
@@ -214,6 +215,32 @@ __device__ __forceinline__ bool prefilter_maybe(const float (&cx)[NS], const flo
 }
 
 // ----------------------------------------------------------------------------
+// Link cull of the early-exit mode: can any obstacle come within the link's
+// bounding ball (centre c, radius R) plus a margin?  Table pairs (three float4):
+// (-2ox_a, -2ox_b, -2oy_a, -2oy_b), (-2oz_a, -2oz_b, K_a, K_b),
+// (-2r_a, -2r_b, 0, 0) with K = |o|^2 - r_o^2 - margin (boxes: their
+// enclosing ball).  Obstacle o may reach the ball iff
+// |c|^2 - 2 o.c + K - 2 r_o R - R^2 < 0.  A link cleared here is clear: each
+// of its spheres lies inside the ball.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ bool link_cull_maybe(float cx, float cy, float cz, float R, const float4* __restrict__ cull,
+                                                int n_pairs) {
+  const float2 x2 = make_float2(cx, cx), y2 = make_float2(cy, cy), z2 = make_float2(cz, cz);
+  const float2 r2 = make_float2(R, R);
+  float m = __int_as_float(0x7f800000);
+#pragma unroll 2
+  for (int p = 0; p < n_pairs; ++p) {
+    const float4 A = cull[3 * p], B = cull[3 * p + 1], C = cull[3 * p + 2];
+    float2 t = __ffma2_rn(z2, make_float2(B.x, B.y),
+                          __ffma2_rn(y2, make_float2(A.z, A.w), __ffma2_rn(x2, make_float2(A.x, A.y), make_float2(B.z, B.w))));
+    t = __ffma2_rn(make_float2(C.x, C.y), r2, t);
+    m = fmin3(m, t.x, t.y);
+  }
+  const float c2 = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
+  return m < __fmaf_rn(R, R, -c2);
+}
+
+// ----------------------------------------------------------------------------
 // Exact test of the uniform-radius arm kernels, two obstacles per packed
 // float32x2 instruction.  Tables (negated positions, radius r of the robot
 // spheres folded into the thresholds):
@@ -297,7 +324,8 @@ template <int DOF_T, int SPL_T, bool UNIF, bool WARP_EXIT, bool FULL, bool PACKE
 __device__ __forceinline__ bool arm_config_collides(const float* q, bool active, const RobotDev& rb,
                                                     const float4* __restrict__ sph, int n_s,
                                                     const float4* __restrict__ box, int n_b,
-                                                    const float4* __restrict__ pre = nullptr, int n_pairs = 0) {
+                                                    const float4* __restrict__ pre = nullptr, int n_pairs = 0,
+                                                    const float4* __restrict__ cull = nullptr, int n_cull = 0) {
   constexpr int NS = SPL_T > 0 ? SPL_T : kMaxSpl;
   constexpr int NQ = DOF_T > 0 ? DOF_T : kMaxDof;
   const int dof = DOF_T > 0 ? DOF_T : rb.dof;
@@ -341,6 +369,18 @@ __device__ __forceinline__ bool arm_config_collides(const float* q, bool active,
     X0 = u0; X1 = u1; X2 = u2;
     Y0 = y0; Y1 = y1; Y2 = y2;
     Z0 = z0; Z1 = z1; Z2 = z2;
+    if constexpr (PACKED && !FULL) {
+      // skip the link when its bounding ball is clear of every obstacle (for every active lane)
+      if (n_cull > 0) {
+        const float4 lb = rb.lb[i];
+        const float lx = __fmaf_rn(lb.z, Z0, __fmaf_rn(lb.y, Y0, __fmaf_rn(lb.x, X0, T0)));
+        const float ly = __fmaf_rn(lb.z, Z1, __fmaf_rn(lb.y, Y1, __fmaf_rn(lb.x, X1, T1)));
+        const float lz = __fmaf_rn(lb.z, Z2, __fmaf_rn(lb.y, Y2, __fmaf_rn(lb.x, X2, T2)));
+        const bool near = link_cull_maybe(lx, ly, lz, lb.w, cull, n_cull);
+        const bool any_near = WARP_EXIT ? __any_sync(kFull, active && near) : near;
+        if (!any_near) continue;
+      }
+    }
     float cx[NS], cy[NS], cz[NS], rad[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) {

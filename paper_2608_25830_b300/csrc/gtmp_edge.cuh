@@ -115,8 +115,9 @@ __device__ __forceinline__ bool config_collides(const float* q, bool active, con
     // uniform-radius arms: packed pair tables, then the prefilter table
     const float4* boxp = s_obs + 2 * sc.n_sp;
     const float4* pre = boxp + 3 * sc.n_bp;
-    return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL, true>(q, active, rb, s_obs, sc.n_sp,
-                                                                                  boxp, sc.n_bp, pre, sc.n_pairs);
+    const float4* cull = pre + 2 * sc.n_pairs;
+    return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL, true>(
+        q, active, rb, s_obs, sc.n_sp, boxp, sc.n_bp, pre, sc.n_pairs, cull, sc.n_cull);
   } else if constexpr (V::kArm) {
     return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL>(q, active, rb, s_obs, sc.n_s,
                                                                             s_obs + sc.n_s, sc.n_b);

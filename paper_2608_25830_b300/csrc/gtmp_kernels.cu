@@ -732,6 +732,60 @@ int build_prefilter_table(const float* spheres, int n_s, const float* boxes, int
   return pairs;
 }
 
+// Link-cull table (three float4 per obstacle pair, layout of link_cull_maybe):
+// per obstacle -2o, |o|^2 - r_o^2 - margin and -2 r_o, boxes by their
+// enclosing ball; the margin covers the float32 error of the test as the
+// prefilter's does, with link balls of radius up to 1 m.
+int build_cull_table(const float* spheres, int n_s, const float* boxes, int n_b, double reach, float4* out) {
+  const int n = n_s + n_b;
+  if (n == 0) return 0;
+  std::vector<double> cx(n), cy(n), cz(n), R(n);
+  for (int o = 0; o < n_s; ++o) {
+    const float* s = spheres + 4 * o;
+    cx[o] = s[0];
+    cy[o] = s[1];
+    cz[o] = s[2];
+    R[o] = s[3];
+  }
+  for (int o = 0; o < n_b; ++o) {
+    const float* b = boxes + 6 * o;
+    const float c0 = 0.5f * (b[0] + b[3]), c1 = 0.5f * (b[1] + b[4]), c2 = 0.5f * (b[2] + b[5]);
+    const float h0 = 0.5f * (b[3] - b[0]), h1 = 0.5f * (b[4] - b[1]), h2 = 0.5f * (b[5] - b[2]);
+    cx[n_s + o] = c0;
+    cy[n_s + o] = c1;
+    cz[n_s + o] = c2;
+    R[n_s + o] = std::sqrt(double(h0) * h0 + double(h1) * h1 + double(h2) * h2) * (1.0 + 1e-6) + 1e-7;
+  }
+  double bo = 0.0, rmax = 0.0;
+  for (int o = 0; o < n; ++o) {
+    bo = std::fmax(bo, std::sqrt(cx[o] * cx[o] + cy[o] * cy[o] + cz[o] * cz[o]));
+    rmax = std::fmax(rmax, R[o]);
+  }
+  const double err = 8.0 * std::ldexp(1.0, -24) * ((reach + bo) * (reach + bo) + (rmax + 1.0) * (rmax + 1.0) + reach * reach);
+  const double margin = std::fmax(1e-3, 100.0 * err);
+  const int pairs = (n + 1) / 2;
+  for (int p = 0; p < pairs; ++p) {
+    float ax[2], ay[2], az[2], kk[2], rr[2];
+    for (int h = 0; h < 2; ++h) {
+      const int o = 2 * p + h;
+      if (o < n) {
+        ax[h] = static_cast<float>(-2.0 * cx[o]);
+        ay[h] = static_cast<float>(-2.0 * cy[o]);
+        az[h] = static_cast<float>(-2.0 * cz[o]);
+        kk[h] = static_cast<float>(cx[o] * cx[o] + cy[o] * cy[o] + cz[o] * cz[o] - R[o] * R[o] - margin);
+        rr[h] = static_cast<float>(-2.0 * R[o]);
+      } else {  // padding: never near
+        ax[h] = ay[h] = az[h] = rr[h] = 0.0f;
+        kk[h] = 1e30f;
+      }
+    }
+    out[3 * p] = make_float4(ax[0], ax[1], ay[0], ay[1]);
+    out[3 * p + 1] = make_float4(az[0], az[1], kk[0], kk[1]);
+    out[3 * p + 2] = make_float4(rr[0], rr[1], 0.0f, 0.0f);
+  }
+  return pairs;
+}
+
 int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n_b, float r, double reach,
                         float4* out, SceneDev* sc) {
   const int n_sp = (n_s + 1) / 2, n_bp = (n_b + 1) / 2;
@@ -778,13 +832,41 @@ int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n
     bo[3 * p + 2] = make_float4(v[0][4], v[1][4], v[0][5], v[1][5]);
   }
   const int n_pp = build_prefilter_table(spheres, n_s, boxes, n_b, r, reach, bo + 3 * n_bp);
+  int n_cull = 0;
+  const int base = 2 * n_sp + 3 * n_bp + 2 * n_pp;
+  if (base + 3 * ((n_s + n_b + 1) / 2) <= kMaxTableFloat4s)
+    n_cull = build_cull_table(spheres, n_s, boxes, n_b, reach, bo + 3 * n_bp + 2 * n_pp);
   sc->n_s = n_s;
   sc->n_b = n_b;
   sc->packed = 1;
   sc->n_sp = n_sp;
   sc->n_bp = n_bp;
   sc->n_pairs = n_pp;
-  return 2 * n_sp + 3 * n_bp + 2 * n_pp;
+  sc->n_cull = n_cull;
+  return base + 3 * n_cull;
+}
+
+void fill_link_bounds(RobotDev* rb) {
+  const int stride = rb->spl > 4 || rb->uniform_r == 0 ? kMaxSpl : 4;
+  for (int i = 0; i < rb->dof; ++i) {
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < rb->spl; ++k) {
+      const float4 p = rb->sph[i * stride + k];
+      c[0] += p.x;
+      c[1] += p.y;
+      c[2] += p.z;
+    }
+    for (double& v : c) v /= rb->spl;
+    const float cx = static_cast<float>(c[0]), cy = static_cast<float>(c[1]), cz = static_cast<float>(c[2]);
+    double R = 0.0;
+    for (int k = 0; k < rb->spl; ++k) {
+      const float4 p = rb->sph[i * stride + k];
+      const double dx = double(p.x) - cx, dy = double(p.y) - cy, dz = double(p.z) - cz;
+      R = std::fmax(R, std::sqrt(dx * dx + dy * dy + dz * dz) + double(p.w));
+    }
+    // enlarged by a hair, like the enclosing balls of boxes
+    rb->lb[i] = make_float4(cx, cy, cz, static_cast<float>(R * (1.0 + 1e-6) + 1e-7));
+  }
 }
 
 cudaError_t configure_kernels(int smem_max) {

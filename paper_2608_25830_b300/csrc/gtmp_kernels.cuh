@@ -40,11 +40,18 @@ struct SceneDev {
   int packed;          // 1 = packed layout
   int n_sp, n_bp;      // packed: sphere pairs, box pairs
   int n_pairs;         // packed: prefilter pairs
+  int n_cull = 0;      // packed: link-cull pairs (0: no cull)
 };
 
 __host__ __device__ inline int scene_float4s(const SceneDev& s) {
-  return s.packed ? 2 * s.n_sp + 3 * s.n_bp + 2 * s.n_pairs : s.n_s + 2 * s.n_b;
+  return s.packed ? 2 * s.n_sp + 3 * s.n_bp + 2 * s.n_pairs + 3 * s.n_cull : s.n_s + 2 * s.n_b;
 }
+
+// float4 capacity a packed obstacle table of n obstacles needs
+inline size_t packed_table_capacity(int n) { return 5 * static_cast<size_t>(n) + 16; }
+
+// largest obstacle table (float4s) the kernels stage into shared memory
+constexpr int kMaxTableFloat4s = 12800;
 
 enum EvalMode { kEvalEarlyExit = 0, kEvalFull = 1, kEvalLazy = 2 };
 
@@ -62,6 +69,8 @@ int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n
                         float4* out, SceneDev* sc);
 // Host: a bound on |c| over all robot-sphere centres of a DH arm.
 double arm_reach_bound(const RobotDev& rb);
+// per link, the centre and radius of a ball holding all its spheres (RobotDev::lb)
+void fill_link_bounds(RobotDev* rb);
 
 cudaError_t configure_kernels(int smem_max);
 cudaError_t launch_sample_free(const GraphDev& g, const RobotDev& rb, int variant, const SceneDev& sc, const float* lo,

@@ -139,6 +139,7 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
         rb.sph[i * stride + s] = make_float4(ls[0], ls[1], ls[2], ls[3]);
       }
     }
+    fill_link_bounds(&rb);
   } else {
     if (!(robot->point_radius >= 0.0f) || !std::isfinite(robot->point_radius))
       return report(err_msg, err_msg_len, bad, "bad point radius");
@@ -151,7 +152,8 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
   const size_t verts = static_cast<size_t>(L + 2) * M;
   const bool packed = variant == kVarArm6x4 || variant == kVarArm7x4;
   // float4 count of the obstacle table: packed pair tables + prefilter, or the scalar table
-  const int n4 = packed ? 2 * ((n_s + 1) / 2) + 3 * ((n_b + 1) / 2) + 2 * ((n_s + n_b + 1) / 2) : n_s + 2 * n_b;
+  // packed: sphere pairs, box pairs, prefilter pairs, link-cull pairs (256 obstacles always fit)
+  const int n4 = packed ? 2 * ((n_s + 1) / 2) + 3 * ((n_b + 1) / 2) + 5 * ((n_s + n_b + 1) / 2) : n_s + 2 * n_b;
   size_t off = 0;
   const size_t off_err = off;
   off = align256(off + sizeof(int));
@@ -171,7 +173,7 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
                   M, L, dof, off, kNoallocScratchBytes);
 
   // ---- host-side tables on the stack (no heap, no device allocation)
-  float4 obs[3 * kNoallocMaxObstacles + 8];
+  float4 obs[5 * kNoallocMaxObstacles + 16];  // packed_table_capacity(kNoallocMaxObstacles)
   SceneDev sc{};
   for (int o = 0; o < n_s; ++o)
     if (!(spheres[4 * o + 3] >= 0.0f)) return report(err_msg, err_msg_len, bad, "negative sphere radius");
