@@ -215,29 +215,33 @@ __device__ __forceinline__ bool prefilter_maybe(const float (&cx)[NS], const flo
 }
 
 // ----------------------------------------------------------------------------
-// Link cull of the early-exit mode: can any obstacle come within the link's
-// bounding ball (centre c, radius R) plus a margin?  Table pairs (three float4):
-// (-2ox_a, -2ox_b, -2oy_a, -2oy_b), (-2oz_a, -2oz_b, K_a, K_b),
-// (-2r_a, -2r_b, 0, 0) with K = |o|^2 - r_o^2 - margin (boxes: their
-// enclosing ball).  Obstacle o may reach the ball iff
-// |c|^2 - 2 o.c + K - 2 r_o R - R^2 < 0.  A link cleared here is clear: each
-// of its spheres lies inside the ball.
+// Link cull of the early-exit mode: which obstacles can come within the
+// link's bounding ball (centre c, radius R) plus a margin?  Table pairs (three
+// float4), sphere obstacles' pairs first, then box obstacles' pairs (the
+// pairing of the exact tables): (-2ox_a, -2ox_b, -2oy_a, -2oy_b),
+// (-2oz_a, -2oz_b, K_a, K_b), (-2r_a, -2r_b, 0, 0) with K = |o|^2 - r_o^2 -
+// margin (boxes: their enclosing ball).  Obstacle o may reach the ball iff
+// |c|^2 - 2 o.c + K - 2 r_o R - R^2 < 0.  Returns bit p set when pair p may
+// (pairs past 64 are all reported near); a cleared obstacle cannot touch any
+// of the link's spheres, which all lie inside the ball.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ bool link_cull_maybe(float cx, float cy, float cz, float R, const float4* __restrict__ cull,
-                                                int n_pairs) {
+__device__ __forceinline__ unsigned long long link_cull_mask(float cx, float cy, float cz, float R,
+                                                             const float4* __restrict__ cull, int n_pairs) {
   const float2 x2 = make_float2(cx, cx), y2 = make_float2(cy, cy), z2 = make_float2(cz, cz);
   const float2 r2 = make_float2(R, R);
-  float m = __int_as_float(0x7f800000);
+  const float c2 = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
+  const float thr = __fmaf_rn(R, R, -c2);
+  unsigned long long mask = n_pairs > 64 ? ~0ull : 0ull;
+  const int n = n_pairs < 64 ? n_pairs : 64;
 #pragma unroll 2
-  for (int p = 0; p < n_pairs; ++p) {
+  for (int p = 0; p < n; ++p) {
     const float4 A = cull[3 * p], B = cull[3 * p + 1], C = cull[3 * p + 2];
     float2 t = __ffma2_rn(z2, make_float2(B.x, B.y),
                           __ffma2_rn(y2, make_float2(A.z, A.w), __ffma2_rn(x2, make_float2(A.x, A.y), make_float2(B.z, B.w))));
     t = __ffma2_rn(make_float2(C.x, C.y), r2, t);
-    m = fmin3(m, t.x, t.y);
+    if (fminf(t.x, t.y) < thr) mask |= 1ull << p;
   }
-  const float c2 = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
-  return m < __fmaf_rn(R, R, -c2);
+  return mask;
 }
 
 // ----------------------------------------------------------------------------
@@ -284,6 +288,62 @@ __device__ __forceinline__ bool exact_packed_hit(const float (&cx)[NS], const fl
   const float2 nr2 = make_float2(neg_r2, neg_r2);
 #pragma unroll 1
   for (int p = 0; p < n_bp; ++p) {
+    const float4 B0 = boxp[3 * p];
+    const float4 B1 = boxp[3 * p + 1];
+    const float4 B2 = boxp[3 * p + 2];
+    const float2 nbx = make_float2(B0.x, B0.y), nby = make_float2(B0.z, B0.w), nbz = make_float2(B1.x, B1.y);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const float2 ux = __fadd2_rn(x2[k], nbx);
+      const float2 uy = __fadd2_rn(y2[k], nby);
+      const float2 uz = __fadd2_rn(z2[k], nbz);
+      const float2 px = make_float2(fmaxf(__fadd_rn(fabsf(ux.x), B1.z), 0.0f), fmaxf(__fadd_rn(fabsf(ux.y), B1.w), 0.0f));
+      const float2 py = make_float2(fmaxf(__fadd_rn(fabsf(uy.x), B2.x), 0.0f), fmaxf(__fadd_rn(fabsf(uy.y), B2.y), 0.0f));
+      const float2 pz = make_float2(fmaxf(__fadd_rn(fabsf(uz.x), B2.z), 0.0f), fmaxf(__fadd_rn(fabsf(uz.y), B2.w), 0.0f));
+      const float2 t = __ffma2_rn(pz, pz, __ffma2_rn(py, py, __ffma2_rn(px, px, nr2)));
+      m[k] = fmin3(m[k], t.x, t.y);
+    }
+  }
+  bool hit = false;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) hit |= m[k] < 0.0f;
+  return hit;
+}
+
+// The exact test restricted to the sphere pairs set in smask and the box pairs
+// set in bmask (pairs a link cull could not clear); same arithmetic per pair.
+template <int NS>
+__device__ __forceinline__ bool exact_packed_hit_masked(const float (&cx)[NS], const float (&cy)[NS],
+                                                        const float (&cz)[NS], const float4* __restrict__ sphp,
+                                                        const float4* __restrict__ boxp, float neg_r2,
+                                                        unsigned smask, unsigned bmask) {
+  float2 x2[NS], y2[NS], z2[NS];
+  float m[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    x2[k] = make_float2(cx[k], cx[k]);
+    y2[k] = make_float2(cy[k], cy[k]);
+    z2[k] = make_float2(cz[k], cz[k]);
+    m[k] = __int_as_float(0x7f800000);
+  }
+  for (unsigned sm = smask; sm; sm &= sm - 1) {
+    const int p = __ffs(sm) - 1;
+    const float4 P0 = sphp[2 * p];
+    const float4 P1 = sphp[2 * p + 1];
+    const float2 nx = make_float2(P0.x, P0.y), ny = make_float2(P0.z, P0.w);
+    const float2 nz = make_float2(P1.x, P1.y), nt = make_float2(P1.z, P1.w);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const float2 dx = __fadd2_rn(x2[k], nx);
+      const float2 dy = __fadd2_rn(y2[k], ny);
+      const float2 dz = __fadd2_rn(z2[k], nz);
+      const float2 t = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, nt)));
+      m[k] = fmin3(m[k], t.x, t.y);
+    }
+  }
+  const float2 nr2 = make_float2(neg_r2, neg_r2);
+  for (unsigned bm = bmask; bm; bm &= bm - 1) {
+    const int p = __ffs(bm) - 1;
     const float4 B0 = boxp[3 * p];
     const float4 B1 = boxp[3 * p + 1];
     const float4 B2 = boxp[3 * p + 2];
@@ -369,16 +429,27 @@ __device__ __forceinline__ bool arm_config_collides(const float* q, bool active,
     X0 = u0; X1 = u1; X2 = u2;
     Y0 = y0; Y1 = y1; Y2 = y2;
     Z0 = z0; Z1 = z1; Z2 = z2;
+    // obstacle pairs a link cull could not clear (sphere pairs, box pairs)
+    unsigned near_s = 0xffffffffu, near_b = 0xffffffffu;
     if constexpr (PACKED && !FULL) {
-      // skip the link when its bounding ball is clear of every obstacle (for every active lane)
+      // skip the link when its bounding ball is clear of every obstacle (for
+      // every active lane), else test only the obstacles near the ball
       if (n_cull > 0) {
         const float4 lb = rb.lb[i];
         const float lx = __fmaf_rn(lb.z, Z0, __fmaf_rn(lb.y, Y0, __fmaf_rn(lb.x, X0, T0)));
         const float ly = __fmaf_rn(lb.z, Z1, __fmaf_rn(lb.y, Y1, __fmaf_rn(lb.x, X1, T1)));
         const float lz = __fmaf_rn(lb.z, Z2, __fmaf_rn(lb.y, Y2, __fmaf_rn(lb.x, X2, T2)));
-        const bool near = link_cull_maybe(lx, ly, lz, lb.w, cull, n_cull);
-        const bool any_near = WARP_EXIT ? __any_sync(kFull, active && near) : near;
-        if (!any_near) continue;
+        unsigned long long near = active ? link_cull_mask(lx, ly, lz, lb.w, cull, n_cull) : 0ull;
+        if (WARP_EXIT) {
+          const unsigned lo = __reduce_or_sync(kFull, static_cast<unsigned>(near));
+          const unsigned hi = __reduce_or_sync(kFull, static_cast<unsigned>(near >> 32));
+          near = (static_cast<unsigned long long>(hi) << 32) | lo;
+        }
+        if (near == 0ull) continue;
+        if (n_cull <= 64 && n_s <= 32 && n_b <= 32) {
+          near_s = static_cast<unsigned>(near & (n_s >= 32 ? 0xffffffffull : (1ull << n_s) - 1ull));
+          near_b = static_cast<unsigned>(near >> n_s);
+        }
       }
     }
     float cx[NS], cy[NS], cz[NS], rad[NS];
@@ -394,14 +465,19 @@ __device__ __forceinline__ bool arm_config_collides(const float* q, bool active,
     if constexpr (PACKED && FULL) {
       hit |= exact_packed_hit<NS>(cx, cy, cz, sph, n_s, box, n_b, -r2u);
     } else if constexpr (PACKED) {
-      // exact tests only where the prefilter could not clear the link
-      const bool maybe = prefilter_maybe<NS>(cx, cy, cz, pre, n_pairs);
-      bool run_exact;
-      if constexpr (WARP_EXIT)
-        run_exact = __any_sync(kFull, active && maybe);
-      else
-        run_exact = maybe;
-      if (run_exact) hit |= exact_packed_hit<NS>(cx, cy, cz, sph, n_s, box, n_b, -r2u);
+      if (n_cull > 0 && n_cull <= 64 && n_s <= 32 && n_b <= 32) {
+        // exact tests against the obstacles the link cull kept
+        hit |= exact_packed_hit_masked<NS>(cx, cy, cz, sph, box, -r2u, near_s, near_b);
+      } else {
+        // exact tests only where the prefilter could not clear the link
+        const bool maybe = prefilter_maybe<NS>(cx, cy, cz, pre, n_pairs);
+        bool run_exact;
+        if constexpr (WARP_EXIT)
+          run_exact = __any_sync(kFull, active && maybe);
+        else
+          run_exact = maybe;
+        if (run_exact) hit |= exact_packed_hit<NS>(cx, cy, cz, sph, n_s, box, n_b, -r2u);
+      }
     } else {
       hit |= spheres_hit<NS, UNIF, false>(cx, cy, cz, rad, spl, sph, n_s, box, n_b, r2u);
     }

@@ -732,10 +732,12 @@ int build_prefilter_table(const float* spheres, int n_s, const float* boxes, int
   return pairs;
 }
 
-// Link-cull table (three float4 per obstacle pair, layout of link_cull_maybe):
-// per obstacle -2o, |o|^2 - r_o^2 - margin and -2 r_o, boxes by their
-// enclosing ball; the margin covers the float32 error of the test as the
-// prefilter's does, with link balls of radius up to 1 m.
+// Link-cull table (three float4 per obstacle pair, layout of link_cull_mask):
+// the sphere obstacles' pairs, then the box obstacles' pairs, paired like the
+// exact tables so that pair p's bit selects the same obstacles there; per
+// obstacle -2o, |o|^2 - r_o^2 - margin and -2 r_o, boxes by their enclosing
+// ball; the margin covers the float32 error of the test as the prefilter's
+// does, with link balls of radius up to 1 m.
 int build_cull_table(const float* spheres, int n_s, const float* boxes, int n_b, double reach, float4* out) {
   const int n = n_s + n_b;
   if (n == 0) return 0;
@@ -763,12 +765,16 @@ int build_cull_table(const float* spheres, int n_s, const float* boxes, int n_b,
   }
   const double err = 8.0 * std::ldexp(1.0, -24) * ((reach + bo) * (reach + bo) + (rmax + 1.0) * (rmax + 1.0) + reach * reach);
   const double margin = std::fmax(1e-3, 100.0 * err);
-  const int pairs = (n + 1) / 2;
-  for (int p = 0; p < pairs; ++p) {
+  const int n_sp = (n_s + 1) / 2, n_bp = (n_b + 1) / 2;
+  for (int p = 0; p < n_sp + n_bp; ++p) {
+    // pair p: spheres 2p, 2p+1, or boxes 2(p - n_sp), 2(p - n_sp)+1
+    const bool sph = p < n_sp;
+    const int first = sph ? 2 * p : n_s + 2 * (p - n_sp);
+    const int end = sph ? n_s : n;
     float ax[2], ay[2], az[2], kk[2], rr[2];
     for (int h = 0; h < 2; ++h) {
-      const int o = 2 * p + h;
-      if (o < n) {
+      const int o = first + h;
+      if (o < end) {
         ax[h] = static_cast<float>(-2.0 * cx[o]);
         ay[h] = static_cast<float>(-2.0 * cy[o]);
         az[h] = static_cast<float>(-2.0 * cz[o]);
@@ -783,7 +789,7 @@ int build_cull_table(const float* spheres, int n_s, const float* boxes, int n_b,
     out[3 * p + 1] = make_float4(az[0], az[1], kk[0], kk[1]);
     out[3 * p + 2] = make_float4(rr[0], rr[1], 0.0f, 0.0f);
   }
-  return pairs;
+  return n_sp + n_bp;
 }
 
 int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n_b, float r, double reach,
@@ -834,7 +840,7 @@ int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n
   const int n_pp = build_prefilter_table(spheres, n_s, boxes, n_b, r, reach, bo + 3 * n_bp);
   int n_cull = 0;
   const int base = 2 * n_sp + 3 * n_bp + 2 * n_pp;
-  if (base + 3 * ((n_s + n_b + 1) / 2) <= kMaxTableFloat4s)
+  if (base + 3 * (n_sp + n_bp) <= kMaxTableFloat4s)
     n_cull = build_cull_table(spheres, n_s, boxes, n_b, reach, bo + 3 * n_bp + 2 * n_pp);
   sc->n_s = n_s;
   sc->n_b = n_b;

@@ -153,7 +153,7 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
   const bool packed = variant == kVarArm6x4 || variant == kVarArm7x4;
   // float4 count of the obstacle table: packed pair tables + prefilter, or the scalar table
   // packed: sphere pairs, box pairs, prefilter pairs, link-cull pairs (256 obstacles always fit)
-  const int n4 = packed ? 2 * ((n_s + 1) / 2) + 3 * ((n_b + 1) / 2) + 5 * ((n_s + n_b + 1) / 2) : n_s + 2 * n_b;
+  const int n4 = packed ? 5 * ((n_s + 1) / 2) + 6 * ((n_b + 1) / 2) + 2 * ((n_s + n_b + 1) / 2) : n_s + 2 * n_b;
   size_t off = 0;
   const size_t off_err = off;
   off = align256(off + sizeof(int));
