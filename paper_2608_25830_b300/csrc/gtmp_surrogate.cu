@@ -470,6 +470,7 @@ struct ScoreArgs {
   const __nv_bfloat16* W1b;
   const __nv_bfloat16* W2b;
   const __nv_bfloat16* W3b;
+  const uint8_t* Wimg;     // W1 (64 KB) then the eight 256 x 64 chunks of W2, W3 (32 KB each), in shared-memory layout
   const float* P;          // fp32 parameters (biases, w4, b4)
   uint8_t* prune;
   unsigned long long* n_pruned;
@@ -501,6 +502,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Weight images for the scoring kernel: W1 [256 x 128] and the chunks
+// c = 0..7 (W2 then W3, input columns [64 (c & 3), + 64)) laid out in global
+// memory exactly as their shared-memory tiles (canonical K-major), so that one
+// bulk copy moves each.  Thread per 16-byte segment.
+__global__ void weight_images_kernel(const __nv_bfloat16* W1b, const __nv_bfloat16* W2b, const __nv_bfloat16* W3b,
+                                     uint8_t* img) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 256 * 16) {
+    const int n = t >> 4, kc = t & 15;
+    *reinterpret_cast<uint4*>(img + canon(n, kc * 8, 128)) =
+        *reinterpret_cast<const uint4*>(W1b + static_cast<size_t>(n) * kFeat + kc * 8);
+    return;
+  }
+  const int u = t - 256 * 16;
+  if (u >= 8 * 256 * 8) return;
+  const int c = u >> 11, n = (u >> 3) & 255, kc = u & 7;
+  const __nv_bfloat16* W = c < 4 ? W2b : W3b;
+  *reinterpret_cast<uint4*>(img + kSmemW1 + c * kSmemS + canon(n, kc * 8, 64)) =
+      *reinterpret_cast<const uint4*>(W + static_cast<size_t>(n) * kHid + (c & 3) * 64 + kc * 8);
+}
+
 // the features of one query half: frequencies [32 HF, 32 HF + 32); DOF > 0
 // gives compile-time indices (B from the parameter bank, q in registers)
 template <int DOF, int HF>
@@ -528,6 +550,8 @@ template <int DOF>
 __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs a, FourierDev f) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar_w[3];  // weight buffers 0, 1 and the resident W1
+  __shared__ int s_abort;
   __shared__ uint32_t tmem_base;
   __shared__ float s_part[2][128];
   __shared__ float s_logit[128];
@@ -543,16 +567,27 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   const float* w4 = b3 + kHid;
   const float b4 = w4[kHid];
 
-  // weight chunk c: 0..3 = W2 columns [64c, 64c+64), 4..7 = W3 columns [64(c-4), ...)
+  // weight chunk c (0..3 = W2 columns [64c, 64c+64), 4..7 = W3 columns [64(c-4), ...)) into buffer
+  // `buf`: one bulk copy of its image, completing on that buffer's barrier (thread 0 only)
+  uint32_t wphase[2] = {0u, 0u};
   auto load_chunk = [&](int c, int buf) {
-    const __nv_bfloat16* W = c < 4 ? a.W2b : a.W3b;
-    const int k0 = (c & 3) * 64;
-    const uint32_t dst = s_u32(sS + buf * kSmemS);
-    for (int t = tid; t < 256 * 8; t += kScoreThreads) {
-      const int n = t >> 3, kc = t & 7;
-      cp_async16(dst + canon(n, kc * 8, 64), W + static_cast<size_t>(n) * kHid + k0 + kc * 8, 16u);
+    if (tid != 0) return;
+    const uint32_t bar = s_u32(&mbar_w[buf]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kSmemS) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     s_u32(sS + buf * kSmemS)),
+                 "l"(a.Wimg + kSmemW1 + static_cast<size_t>(c) * kSmemS), "r"(kSmemS), "r"(bar)
+                 : "memory");
+  };
+  // thread 0: wait (bounded) for buffer `buf`'s copy; on timeout release the others through the MMA barrier
+  auto wait_chunk = [&](int buf) -> bool {
+    const bool got = mbar_wait_parity(s_u32(&mbar_w[buf]), wphase[buf], kMbarLimit);
+    wphase[buf] ^= 1u;
+    if (!got) {
+      s_abort = 1;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    return got;
   };
   auto wait_mma = [&](uint32_t& phase) -> bool {
     const bool ok = mbar_wait_parity(mb, phase, kMbarLimit);
@@ -568,17 +603,21 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
+    s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    for (int k = 0; k < 3; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_w[k])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // resident W1: one bulk copy of its image
+    const uint32_t bar = s_u32(&mbar_w[2]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kSmemW1) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     s_u32(sW1)),
+                 "l"(a.Wimg), "r"(kSmemW1), "r"(bar)
+                 : "memory");
   }
-  // resident W1
-  for (int t = tid; t < 256 * 16; t += kScoreThreads) {
-    const int n = t >> 4, kc = t & 15;
-    cp_async16(s_u32(sW1) + canon(n, kc * 8, 128), a.W1b + static_cast<size_t>(n) * kFeat + kc * 8, 16u);
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  bool w1_ready = false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (256u >> 3 << 17) | (128u >> 4 << 24);
@@ -625,18 +664,33 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
             *reinterpret_cast<const uint4*>(cv + g8 * 8);
       }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");  // W1 (first tile) and chunk 0
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // X (generic writes) -> MMA reads
     __syncthreads();
     // layer 1: D = X W1^T
     if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int kk = 0; kk < 8; ++kk)
-        issue_mma(tmem, smem_desc(s_u32(sX) + kk * 256, 128, 2048), smem_desc(s_u32(sW1) + kk * 256, 128, 2048), idesc,
-                  kk > 0);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+      bool go = true;
+      if (!w1_ready) {
+        go = mbar_wait_parity(s_u32(&mbar_w[2]), 0u, kMbarLimit);
+        w1_ready = true;
+        if (!go) {
+          s_abort = 1;
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+        }
+      }
+      if (go) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kk = 0; kk < 8; ++kk)
+          issue_mma(tmem, smem_desc(s_u32(sX) + kk * 256, 128, 2048), smem_desc(s_u32(sW1) + kk * 256, 128, 2048),
+                    idesc, kk > 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                     : "memory");
+      }
     }
-    if (!(ok = wait_mma(phase))) break;
+    ok = wait_mma(phase);
+    if (!ok || s_abort) {
+      ok = false;
+      break;
+    }
     for (int c = 0; c <= 8 && ok; ++c) {
       // epilogue of the previous layer: TMEM -> relu(acc + b) -> bf16 -> H (after layer 1 and layer 2)
       if (c == 0 || c == 4) {
@@ -653,14 +707,13 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
             *reinterpret_cast<uint4*>(sH + canon(row, n0 + g8 * 8, 256)) = *reinterpret_cast<const uint4*>(h);
           }
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // H (generic writes) -> MMA reads
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
       }
       if (c == 8) break;
-      asm volatile("cp.async.wait_all;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
       if (c + 1 < 8) load_chunk(c + 1, (c + 1) & 1);  // that buffer's MMAs finished last iteration
-      if (tid == 0) {
+      if (tid == 0 && wait_chunk(c & 1)) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t sb = s_u32(sS + (c & 1) * kSmemS);
         const int kc = c & 3;
@@ -670,7 +723,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
                      : "memory");
       }
-      ok = wait_mma(phase);
+      ok = wait_mma(phase) && !s_abort;
     }
     if (!ok) break;
     // head: relu(acc + b3) . w4 + b4, per query; then the edge's max against the cut
@@ -701,8 +754,12 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     }
     __syncthreads();
   }
-  if (!ok && tid == 0) atomicOr(a.err, kErrWaitTimeout);
-  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (!ok && tid == 0) {
+    atomicOr(a.err, kErrWaitTimeout);
+    // let copies still in flight land before the block exits (bounded)
+    for (int b = 0; b < 2; ++b) mbar_wait_parity(s_u32(&mbar_w[b]), wphase[b], kMbarLimit);
+    if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w[2]), 0u, kMbarLimit);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
@@ -723,6 +780,7 @@ struct SurrogateState {
   double* loss = nullptr;
   unsigned long long* counter = nullptr;
   int* live = nullptr;  // live rows / columns of the transition being scored: [2 + 2 * live_cap]
+  uint8_t* wimg = nullptr;  // weight images of the scoring kernel (W1, then 8 chunks of W2 / W3)
   int live_cap = 0;
   bool trained = false;
   long long steps = 0;
@@ -732,7 +790,7 @@ void surrogate_free(SurrogateState* s) {
   if (!s) return;
   void* bufs[] = {s->P,   s->G,   s->Mm,  s->Vv,  s->W1b, s->W1bT,   s->W2b,     s->W2bT, s->W3b,
                   s->W3bT, s->X,  s->XT,  s->H1,  s->H1T, s->H2,     s->H2T,     s->H3,   s->H3T,
-                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter, s->live};
+                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter, s->live, s->wimg};
   for (void* b : bufs) cudaFree(b);
   delete s;
 }
@@ -1134,6 +1192,10 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
   cudaEventCreate(&e1);
   cudaEventCreate(&e2);
   float score_ms = 0.0f, solve_ms = 0.0f;
+  // the current weights as the scoring kernel's shared-memory images (one bulk copy each)
+  if (!s->wimg) SUR_TRY(c, cudaMalloc(&s->wimg, static_cast<size_t>(kSmemW1) + 8 * static_cast<size_t>(kSmemS)));
+  weight_images_kernel<<<(256 * 16 + 8 * 256 * 8 + 255) / 256, 256, 0, st>>>(s->W1b, s->W2b, s->W3b, s->wimg);
+  SUR_TRY(c, cudaGetLastError());
   SUR_TRY(c, cudaMemsetAsync(s->counter, 0, sizeof(unsigned long long), st));
   SUR_TRY(c, launch_init_keys(g, c->counters, L + 1, st));
   SUR_TRY(c, launch_vertex_labels(g, c->rb, c->variant, ctx_scene(c), st));
@@ -1155,6 +1217,7 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     sa.W1b = s->W1b;
     sa.W2b = s->W2b;
     sa.W3b = s->W3b;
+    sa.Wimg = s->wimg;
     sa.P = s->P;
     sa.prune = c->prune;
     sa.n_pruned = s->counter;
