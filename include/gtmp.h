@@ -68,8 +68,11 @@ enum { GTMP_ROBOT_POINT = 0, GTMP_ROBOT_DH_ARM = 1 };
 
 /* Edge evaluation mode of the fused solver.  All give the same values,
  * minimisers and paths, bit for bit.
- * EARLY_EXIT leaves an edge at its first colliding link and skips edges that
- * cannot lie on a finite chain; FULL evaluates every interior waypoint of
+ * EARLY_EXIT leaves an edge at its first colliding link, skips edges that
+ * cannot lie on a finite chain and, for the uniform-radius 6/7-DoF arms,
+ * tests each link only against the obstacles that can reach a ball enclosing
+ * its spheres (a conservative cull; results unchanged); FULL evaluates every
+ * interior waypoint of
  * every candidate edge (data-independent work, used to measure the kernel);
  * LAZY checks an edge only if its cost c(u,v) + J_{l+1}(v) is below the best
  * realised edge of its row found so far, visiting each block of 32 columns in

@@ -412,11 +412,13 @@ constexpr int kParamCount = kNW1 + kHid + kNW2 + kHid + kNW3 + kHid + kHid + 1;
 // in one persistent kernel (one CTA per SM, 8 warps).  Shared memory (bytes,
 // canonical K-major no-swizzle layouts): W1 [256 x 128] resident (64 K), the
 // tile's features X [128 x 128] (32 K), hidden activations H [128 x 256] (64 K,
-// reused by every layer), two 32 K stream buffers for 256 x 64 K-chunks of W2
-// and W3 fetched from L2 with cp.async.  TMEM: one 128 x 256 fp32 accumulator.
-// A tile is 128 queries: Q = 128 / kw edges with kw waypoints each (t = 1/2
-// for kw = 1; 1/4, 1/2, 3/4 for kw = 3); an edge is pruned when its largest
-// logit exceeds `cut`.
+// reused by every layer), two 32 K buffers for the 256 x 64 K-chunks of W2 and
+// W3.  The weights arrive as pre-arranged images of these tiles (one
+// cp.async.bulk each, completing on the buffer's mbarrier; W1 once per CTA).
+// TMEM: one 128 x 256 fp32 accumulator.  A tile is 128 queries: Q = 128 / kw
+// edges with kw waypoints each (t = 1/2 for kw = 1; 1/4, 1/2, 3/4 for kw = 3);
+// an edge is pruned when its largest logit exceeds `cut`.  Only live edges are
+// scored (compacted row and column lists).
 // ---------------------------------------------------------------------------
 // Live rows (vertex free) and live columns (vertex free, finite cost-to-go)
 // of a transition, in increasing order: one block, ballot + prefix per warp.
