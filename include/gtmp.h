@@ -72,8 +72,8 @@ enum { GTMP_ROBOT_POINT = 0, GTMP_ROBOT_DH_ARM = 1 };
  * cannot lie on a finite chain and, for the uniform-radius 6/7-DoF arms,
  * tests each link only against the obstacles that can reach a ball enclosing
  * its spheres (a conservative cull; results unchanged); FULL evaluates every
- * interior waypoint of
- * every candidate edge (data-independent work, used to measure the kernel);
+ * interior waypoint of every candidate edge against every obstacle
+ * (data-independent work, used to measure the kernel);
  * LAZY checks an edge only if its cost c(u,v) + J_{l+1}(v) is below the best
  * realised edge of its row found so far, visiting each block of 32 columns in
  * ascending order of that bound (most edges are never realised). */
