@@ -216,42 +216,6 @@ __global__ void features_kernel(const float* q, int n, FourierDev f, __nv_bfloat
   }
 }
 
-// edges e in [e0, e0 + ne) of the transition (row-major over rows x cols),
-// waypoints t = 1/4, 1/2, 3/4 -> X rows 3 (e - e0) + w
-__global__ void edge_features_kernel(GraphDev g, int layer, long long e0, long long ne, FourierDev f,
-                                     __nv_bfloat16* X) {
-  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= 3 * ne) return;
-  const long long e = e0 + t / 3;
-  const int w = static_cast<int>(t % 3);
-  const int cols = layer_size(g, layer + 1);
-  const int i = static_cast<int>(e / cols), j = static_cast<int>(e % cols);
-  const float* u = g.Q + vidx(g, 0, layer, i) * g.dp;
-  const float* v = g.Q + vidx(g, 0, layer + 1, j) * g.dp;
-  const float tw = 0.25f * static_cast<float>(w + 1);
-  float q[kMaxDof];
-  for (int d = 0; d < f.dof; ++d) q[d] = __fmaf_rn(tw, __fsub_rn(v[d], u[d]), u[d]);
-  __nv_bfloat16 row[128];
-  fourier_row(q, f, row);
-  uint4* dst = reinterpret_cast<uint4*>(X + static_cast<size_t>(t) * 128);
-  const uint4* src = reinterpret_cast<const uint4*>(row);
-  for (int k = 0; k < 16; ++k) dst[k] = src[k];
-}
-
-// prune[e] = max over the edge's 3 waypoint logits > cut
-__global__ void prune_mask_kernel(const float* logits, long long e0, long long ne, float cut, uint8_t* prune,
-                                  unsigned long long* n_pruned) {
-  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  bool p = false;
-  if (t < ne) {
-    const float z = fmaxf(logits[3 * t], fmaxf(logits[3 * t + 1], logits[3 * t + 2]));
-    p = z > cut;
-    prune[e0 + t] = p ? 1 : 0;
-  }
-  const unsigned b = __ballot_sync(kFull, p);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_pruned, static_cast<unsigned long long>(__popc(b)));
-}
-
 // ---------------------------------------------------------------------------
 // training pieces
 // ---------------------------------------------------------------------------
