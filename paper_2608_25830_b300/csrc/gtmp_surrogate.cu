@@ -666,11 +666,20 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
           const int n0 = half * 128 + cc * 32;
           uint32_t v[32];
           tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + n0, v);
+#pragma unroll
           for (int g8 = 0; g8 < 4; ++g8) {
-            __align__(16) __nv_bfloat16 h[8];
-            for (int j = 0; j < 8; ++j)
-              h[j] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[g8 * 8 + j]) + bias[n0 + g8 * 8 + j], 0.0f));
-            *reinterpret_cast<uint4*>(sH + canon(row, n0 + g8 * 8, 256)) = *reinterpret_cast<const uint4*>(h);
+            const float4 ba = __ldg(reinterpret_cast<const float4*>(bias + n0 + g8 * 8));
+            const float4 bb = __ldg(reinterpret_cast<const float4*>(bias + n0 + g8 * 8 + 4));
+            const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const __nv_bfloat162 h2 =
+                  __floats2bfloat162_rn(fmaxf(__uint_as_float(v[g8 * 8 + 2 * j]) + bv[2 * j], 0.0f),
+                                        fmaxf(__uint_as_float(v[g8 * 8 + 2 * j + 1]) + bv[2 * j + 1], 0.0f));
+              w[j] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            *reinterpret_cast<uint4*>(sH + canon(row, n0 + g8 * 8, 256)) = make_uint4(w[0], w[1], w[2], w[3]);
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // H (generic writes) -> MMA reads
@@ -699,7 +708,18 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
       const int n0 = half * 128 + cc * 32;
       uint32_t v[32];
       tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + n0, v);
-      for (int j = 0; j < 32; ++j) dot = __fmaf_rn(fmaxf(__uint_as_float(v[j]) + b3[n0 + j], 0.0f), w4[n0 + j], dot);
+      // four partial sums: a short dependency chain
+      float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int j4 = 0; j4 < 8; ++j4) {
+        const float4 bb = __ldg(reinterpret_cast<const float4*>(b3 + n0 + 4 * j4));
+        const float4 ww = __ldg(reinterpret_cast<const float4*>(w4 + n0 + 4 * j4));
+        part[0] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4]) + bb.x, 0.0f), ww.x, part[0]);
+        part[1] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 1]) + bb.y, 0.0f), ww.y, part[1]);
+        part[2] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 2]) + bb.z, 0.0f), ww.z, part[2]);
+        part[3] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 3]) + bb.w, 0.0f), ww.w, part[3]);
+      }
+      dot += (part[0] + part[1]) + (part[2] + part[3]);
     }
     s_part[half][row] = dot;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

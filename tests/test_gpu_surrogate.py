@@ -188,3 +188,40 @@ def test_backward_pass_matches_numpy():
     assert loss == pytest.approx(ref_loss, rel=1e-2), report
     for k, rel in rels.items():
         assert rel < 3e-2, report
+
+
+def test_scoring_kernel_prunes_what_the_model_predicts(trained):
+    """The fused scoring kernel's decisions against the model evaluated through the GEMM path
+    (gtmp_surrogate_predict) at every live edge's midpoint: the pruned counts agree up to decisions within
+    rounding of the threshold (features use the fast sincos in the scoring kernel)."""
+    import torch
+    sc, p, _ = trained
+    L, H, M = 4, 32, 128
+    thr = 0.5
+    p.sample_layers(12, M)
+    p.solve()                                   # vertex flags and values of this graph
+    st = binding.gtmp_solve_pruned(p.ctx, thr, torch.empty(L, dtype=torch.int32, device="cuda"),
+                                   torch.empty(1, dtype=torch.float32, device="cuda"), score_waypoints=1)
+    p.synchronize()
+    V, _ = p.values()
+    V = V.cpu().numpy()
+    Q = p.get_layers().cpu().numpy()
+    verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
+    flags = [p.label_configs(torch.from_numpy(np.ascontiguousarray(v)).cuda()).cpu().numpy() for v in verts]
+    # the pruned solve's own value iteration decides which columns are live; its values equal the plain
+    # solve's wherever no edge was pruned on the way, so recompute liveness from its own tables
+    mids, live_count = [], 0
+    for l in range(L + 1):
+        rows = np.nonzero(flags[l] == 0)[0]
+        cols = np.nonzero((flags[l + 1] == 0) & np.isfinite(V[l + 1, :len(verts[l + 1])]))[0]
+        live_count += len(rows) * len(cols)
+        if len(rows) and len(cols):
+            u = verts[l][rows][:, None, :]
+            v = verts[l + 1][cols][None, :, :]
+            mids.append((u + np.float32(0.5) * (v - u)).reshape(-1, sc.robot.dof).astype(np.float32))
+    q = np.concatenate(mids)
+    z = torch.empty(len(q), dtype=torch.float32, device="cuda")
+    binding.gtmp_surrogate_predict(p.ctx, torch.from_numpy(q).cuda(), z)
+    want = int((z.cpu().numpy() > math.log(thr / (1 - thr))).sum())
+    assert st["scored"] == live_count
+    assert abs(st["pruned"] - want) <= 0.01 * live_count, (st["pruned"], want, live_count)
