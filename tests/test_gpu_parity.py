@@ -351,3 +351,53 @@ def test_free_sampler_restarts_match_oracle(torch_cuda):
         sol = oracle.solve(sc, Q, H)
         V, S = p.values(r)
         compare_solution(sol, V.cpu().numpy(), S.cpu().numpy(), paths[r].cpu().numpy(), costs[r], f"free restart {r}")
+
+
+# ---------------------------------------------------------------------------
+# obstacle counts around the checker's table limits: the link cull with its
+# masked exact tests (<= 32 sphere pairs and <= 32 box pairs), the per-sphere
+# prefilter it falls back to beyond that, and no cull table at all when the
+# tables would not fit in shared memory
+# ---------------------------------------------------------------------------
+
+def _many_obstacles_scene(n_s, n_b, n_far, seed):
+    """n_s spheres and n_b boxes around the arm (outside a 0.4 m ball about its base), plus n_far small
+    spheres beyond its reach: they fill the tables without blocking every path."""
+    base = scene_for("arm", 7, 7, 0)
+    rng = np.random.default_rng(seed)
+    cs = rng.uniform(-0.75, 0.75, (8 * n_s + 8, 3))
+    cs = cs[np.linalg.norm(cs, axis=1) > 0.4][:n_s]
+    spheres = np.concatenate([cs, rng.uniform(0.01, 0.025, (len(cs), 1))], 1)
+    d = rng.normal(size=(n_far, 3))
+    far = d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(3.0, 4.0, (n_far, 1))
+    spheres = np.concatenate([spheres, np.concatenate([far, np.full((n_far, 1), 0.01)], 1)]).astype(np.float32)
+    cb = rng.uniform(-0.75, 0.75, (8 * n_b + 8, 3))
+    cb = cb[np.linalg.norm(cb, axis=1) > 0.45][:n_b]
+    h = rng.uniform(0.01, 0.03, (len(cb), 3))
+    boxes = np.concatenate([cb - h, cb + h], 1).astype(np.float32)
+    assert len(spheres) == n_s + n_far and len(boxes) == n_b
+    sc = scenes.Scene(base.robot, spheres, boxes, base.q_start, base.q_goal, base.candidates)
+    return scenes.pick_endpoints(sc, lambda q: oracle.config_free(sc, q))
+
+
+@pytest.mark.parametrize("n_s,n_b,n_far,M,L,H", [
+    (64, 60, 0, 48, 2, 16),         # 32 sphere pairs, 30 box pairs: the full 32-bit sphere mask
+    (80, 30, 0, 48, 2, 16),         # 40 sphere pairs: per-sphere prefilter
+    (40, 20, 1200, 12, 2, 8),       # cull table built, more than 64 pairs: prefilter
+    (40, 20, 3800, 8, 2, 8),        # tables too large for a cull table
+])
+def test_obstacle_counts_around_table_limits(torch_cuda, n_s, n_b, n_far, M, L, H):
+    sc = _many_obstacles_scene(n_s, n_b, n_far, n_s + n_b + n_far)
+    n = len(sc.spheres) + len(sc.boxes)
+    outs = []
+    for mode in (binding.EVAL_EARLY_EXIT, binding.EVAL_FULL, binding.EVAL_LAZY):
+        p = _planner(sc, M, L, H, mode=mode, max_obstacles=max(64, n))
+        p.sample_layers(3, M)
+        outs.append(_gpu_solution(p))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[0], outs[0][0])
+        np.testing.assert_array_equal(o[2], outs[0][2])
+    Q = oracle.sample_uniform(3, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    sol = oracle.solve(sc, Q, H)
+    V, S, path, cost = outs[0]
+    compare_solution(sol, V, S, path, cost, f"{n} obstacles")
