@@ -231,6 +231,19 @@ __device__ __forceinline__ unsigned long long link_cull_mask(float cx, float cy,
   const float2 r2 = make_float2(R, R);
   const float c2 = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
   const float thr = __fmaf_rn(R, R, -c2);
+  if (n_pairs <= 32) {
+    // one 32-bit word and a running bit: no 64-bit shifts in the loop
+    unsigned mask = 0u, bit = 1u;
+#pragma unroll 2
+    for (int p = 0; p < n_pairs; ++p, bit <<= 1) {
+      const float4 A = cull[3 * p], B = cull[3 * p + 1], C = cull[3 * p + 2];
+      float2 t = __ffma2_rn(z2, make_float2(B.x, B.y),
+                            __ffma2_rn(y2, make_float2(A.z, A.w), __ffma2_rn(x2, make_float2(A.x, A.y), make_float2(B.z, B.w))));
+      t = __ffma2_rn(make_float2(C.x, C.y), r2, t);
+      if (fminf(t.x, t.y) < thr) mask |= bit;
+    }
+    return mask;
+  }
   unsigned long long mask = n_pairs > 64 ? ~0ull : 0ull;
   const int n = n_pairs < 64 ? n_pairs : 64;
 #pragma unroll 2
@@ -442,7 +455,7 @@ __device__ __forceinline__ bool arm_config_collides(const float* q, bool active,
         unsigned long long near = active ? link_cull_mask(lx, ly, lz, lb.w, cull, n_cull) : 0ull;
         if (WARP_EXIT) {
           const unsigned lo = __reduce_or_sync(kFull, static_cast<unsigned>(near));
-          const unsigned hi = __reduce_or_sync(kFull, static_cast<unsigned>(near >> 32));
+          const unsigned hi = n_cull > 32 ? __reduce_or_sync(kFull, static_cast<unsigned>(near >> 32)) : 0u;
           near = (static_cast<unsigned long long>(hi) << 32) | lo;
         }
         if (near == 0ull) continue;
