@@ -81,7 +81,11 @@ def _declare(L):
     L.orc_edge_length.argtypes = [ctypes.c_int, _f32p, _f32p]
     L.orc_edge_length.restype = ctypes.c_double
     L.orc_edge_block.argtypes = [_P(OrcScene), _f32p, ctypes.c_int, _f32p, ctypes.c_int, ctypes.c_int,
-                                 ctypes.c_double, ctypes.c_double, _i8p, _f64p]
+                                 ctypes.c_double, ctypes.c_double, _f64p, ctypes.c_int, _i8p, _f64p]
+    L.orc_weight.argtypes = [ctypes.c_int, _f64p, _f64p, ctypes.c_int]
+    L.orc_weight.restype = ctypes.c_double
+    L.orc_weighted_length.argtypes = [ctypes.c_int, _f32p, _f32p, ctypes.c_int, _f64p, ctypes.c_int]
+    L.orc_weighted_length.restype = ctypes.c_double
     L.orc_edge_margins.argtypes = [_P(OrcScene), _f32p, _f32p, ctypes.c_int, _f64p]
     L.orc_informed_params.argtypes = [ctypes.c_int, _f32p, _f32p, ctypes.c_float, _P(OrcEllipsoid)]
     L.orc_informed_attempt.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -193,16 +197,44 @@ def config_free(scene, Q, eps=EPS_DEFAULT):
     return labels == FREE
 
 
-def edge_block(scene, A, B, H: int, eps=EPS_DEFAULT, max_len=math.inf):
-    """Labels int8 [na][nb] and FP64 costs of every edge A[a] -> B[b]."""
+def _bumps(bumps, dof):
+    """Weight bumps as float64 [K][dof + 2] (centre, radius s, amplitude a); K = 0 when None."""
+    if bumps is None:
+        return np.zeros((0, dof + 2)), 0
+    b = _c64(bumps).reshape(-1, dof + 2)
+    return b, b.shape[0]
+
+
+def edge_block(scene, A, B, H: int, eps=EPS_DEFAULT, max_len=math.inf, bumps=None):
+    """Labels int8 [na][nb] and FP64 costs of every edge A[a] -> B[b].
+
+    Cost: the length, or with weight bumps the weighted length of App.
+    "General Costs" (trapezoid rule on the H waypoints; see weighted_length).
+    """
     h = _SceneHandle(scene)
     A = _c32(A).reshape(-1, h.dof)
     B = _c32(B).reshape(-1, h.dof)
     labels = np.zeros((A.shape[0], B.shape[0]), np.int8)
     costs = np.zeros((A.shape[0], B.shape[0]))
+    wb, K = _bumps(bumps, h.dof)
     lib().orc_edge_block(h.ref, _ptr(A, _f32p), A.shape[0], _ptr(B, _f32p), B.shape[0], H, eps, max_len,
-                         _ptr(labels, _i8p), _ptr(costs, _f64p))
+                         _ptr(wb, _f64p), K, _ptr(labels, _i8p), _ptr(costs, _f64p))
     return labels, costs
+
+
+def weight(q, bumps) -> float:
+    """w(q) = 1 + sum_b a_b max(0, 1 - |q - c_b|^2 / s_b^2) (App. "General Costs": 1 <= w <= W, Lipschitz)."""
+    q = _c64(q)
+    wb, K = _bumps(bumps, q.shape[0])
+    return lib().orc_weight(q.shape[0], _ptr(q, _f64p), _ptr(wb, _f64p), K)
+
+
+def weighted_length(u, v, H: int, bumps) -> float:
+    """Integral of w along the straight edge u -> v by the trapezoid rule on its H waypoints:
+    |v - u| / (H - 1) * (w_0 / 2 + w_1 + ... + w_{H-2} + w_{H-1} / 2)."""
+    u, v = _c32(u), _c32(v)
+    wb, K = _bumps(bumps, u.shape[0])
+    return lib().orc_weighted_length(u.shape[0], _ptr(u, _f32p), _ptr(v, _f32p), H, _ptr(wb, _f64p), K)
 
 
 def edge_margins(scene, u, v, H: int) -> np.ndarray:
@@ -257,9 +289,9 @@ def layer_vertices(Q, q0, qg):
     return [_c32(q0)[None, :]] + [_c32(Q[l]) for l in range(Q.shape[0])] + [goals]
 
 
-def realize_edges(scene, verts, H, eps=EPS_DEFAULT, max_len=math.inf):
+def realize_edges(scene, verts, H, eps=EPS_DEFAULT, max_len=math.inf, bumps=None):
     """Labels and costs of every transition l -> l+1, l = 0..L."""
-    return [edge_block(scene, verts[l], verts[l + 1], H, eps, max_len) for l in range(len(verts) - 1)]
+    return [edge_block(scene, verts[l], verts[l + 1], H, eps, max_len, bumps) for l in range(len(verts) - 1)]
 
 
 def value_iteration(edges, ambiguous_free: bool, terminal=None):
@@ -320,31 +352,33 @@ class Solution:
     verts: list
 
 
-def solve(scene, Q, H: int, eps=EPS_DEFAULT, max_len=math.inf, goals=None, goal_values=None) -> Solution:
+def solve(scene, Q, H: int, eps=EPS_DEFAULT, max_len=math.inf, goals=None, goal_values=None,
+          bumps=None) -> Solution:
     """gtmp of Alg. 1 for given samples Q float32 [L][M][dof]; the goal set G with terminal values V_g
-    (`goals` [G][dof], `goal_values` [G]) replaces the scene's goal when given."""
+    (`goals` [G][dof], `goal_values` [G]) replaces the scene's goal when given; `bumps` makes the edge
+    cost the weighted length."""
     verts = layer_vertices(Q, scene.q_start, scene.q_goal if goals is None else goals)
-    edges = realize_edges(scene, verts, H, eps, max_len)
+    edges = realize_edges(scene, verts, H, eps, max_len, bumps)
     V_lo, sig_lo, sec_lo = value_iteration(edges, ambiguous_free=True, terminal=goal_values)
     V_hi, _, _ = value_iteration(edges, ambiguous_free=False, terminal=goal_values)
     path = extract_path(sig_lo)
     return Solution(V_lo, V_hi, sig_lo, sec_lo, path, float(V_lo[0][0]), float(V_hi[0][0]), edges, verts)
 
 
-def path_cost(scene, Q, path, H: int):
+def path_cost(scene, Q, path, H: int, bumps=None):
     """FP64 cost of the chain q0 -> Q[l][path[l]] -> qg and its worst waypoint margin."""
     verts = [_c32(scene.q_start)] + [_c32(Q[l, int(path[l])]) for l in range(Q.shape[0])] + [_c32(scene.q_goal)]
     total = 0.0
     worst = math.inf
     for a, b in zip(verts[:-1], verts[1:]):
-        total += lib().orc_edge_length(a.shape[0], _ptr(a, _f32p), _ptr(b, _f32p))
+        total += weighted_length(a, b, H, bumps)
         worst = min(worst, float(edge_margins(scene, a, b, H).min()))
     return total, worst
 
 
-def anytime(scene, seed, R, L, M, H, eps=EPS_DEFAULT):
+def anytime(scene, seed, R, L, M, H, eps=EPS_DEFAULT, bumps=None):
     """anytime-gtmp of Alg. 1 with R restarts (single class): per-restart solutions."""
-    return [solve(scene, sample_uniform(seed, r, L, M, scene.robot.q_lo, scene.robot.q_hi), H, eps)
+    return [solve(scene, sample_uniform(seed, r, L, M, scene.robot.q_lo, scene.robot.q_hi), H, eps, bumps=bumps)
             for r in range(R)]
 
 

@@ -279,9 +279,54 @@ double orc_edge_length(int dof, const float* u, const float* v) {
     return sqrt(s);
 }
 
-/* All edges between vertex set A (na rows) and vertex set B (nb rows). */
+/* ------------------------------------------------------------------------ */
+/* Weighted length (App. "General Costs": any additive cost that dominates  */
+/* length and is Lipschitz; a weighted length with 1 <= w <= W is the       */
+/* example).  Weight field: w(q) = 1 + sum_b a_b max(0, 1 - |q - c_b|^2 /   */
+/* s_b^2), bump b given as [c_b (dof values), s_b, a_b], a_b >= 0.  The     */
+/* edge cost is the integral of w along the straight edge, taken by the     */
+/* trapezoid rule on the planner's own H waypoints (the same float32        */
+/* configurations that are collision-checked):                              */
+/*   cost = |v - u| / (H - 1) * (w_0 / 2 + w_1 + ... + w_{H-2} + w_{H-1} / 2) */
+/* With no bump (K = 0) the cost is the length itself.                      */
+/* ------------------------------------------------------------------------ */
+double orc_weight(int dof, const double* q, const double* bumps, int K) {
+    double w = 1.0;
+    for (int b = 0; b < K; ++b) {
+        const double* c = bumps + (size_t)b * (dof + 2);
+        double d2 = 0.0;
+        for (int d = 0; d < dof; ++d) d2 += (q[d] - c[d]) * (q[d] - c[d]);
+        const double s = c[dof], a = c[dof + 1];
+        const double u = 1.0 - d2 / (s * s);
+        if (u > 0.0) w += a * u;
+    }
+    return w;
+}
+
+double orc_weighted_length(int dof, const float* u, const float* v, int H, const double* bumps, int K) {
+    const double len = orc_edge_length(dof, u, v);
+    if (K == 0) return len;
+    double q[64], sum = 0.0;
+    for (int k = 0; k < H; ++k) {
+        if (k == 0) {
+            for (int d = 0; d < dof; ++d) q[d] = (double)u[d];
+        } else if (k == H - 1) {
+            for (int d = 0; d < dof; ++d) q[d] = (double)v[d];
+        } else {
+            const float t = (float)k / (float)(H - 1);
+            for (int d = 0; d < dof; ++d) q[d] = (double)fmaf(t, v[d] - u[d], u[d]);
+        }
+        const double w = orc_weight(dof, q, bumps, K);
+        sum += (k == 0 || k == H - 1) ? 0.5 * w : w;
+    }
+    return len * sum / (double)(H - 1);
+}
+
+/* All edges between vertex set A (na rows) and vertex set B (nb rows); the */
+/* edge-length limit applies to the length, the cost is the weighted length */
+/* (the length itself when K = 0).                                          */
 void orc_edge_block(const orc_scene* sc, const float* A, int na, const float* B, int nb, int H,
-                    double eps, double max_len, int8_t* labels /* [na][nb] */,
+                    double eps, double max_len, const double* bumps, int K, int8_t* labels /* [na][nb] */,
                     double* costs /* [na][nb] */) {
     const int dof = sc->dof;
 #pragma omp parallel for schedule(dynamic, 1) collapse(2)
@@ -291,7 +336,7 @@ void orc_edge_block(const orc_scene* sc, const float* A, int na, const float* B,
             const float* v = B + (size_t)b * dof;
             const size_t e = (size_t)a * nb + b;
             const double len = orc_edge_length(dof, u, v);
-            costs[e] = len;
+            costs[e] = K > 0 ? orc_weighted_length(dof, u, v, H, bumps, K) : len;
             if (len > max_len) {
                 labels[e] = ORC_COLLIDE;
                 continue;

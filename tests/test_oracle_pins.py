@@ -635,3 +635,106 @@ def test_free_sampler_is_uniform_on_the_free_space():
     assert 0.1 < frac_coll < 0.7
     for k in range(2):
         assert stats.ks_2samp(X[:, k], Y[:, k]).pvalue > 1e-3, k
+
+
+# ---------------------------------------------------------------------------
+# Weighted length (App. "General Costs"): w(q) = 1 + sum_b a_b max(0, 1 -
+# |q - c_b|^2 / s_b^2), edge cost = trapezoid rule of w on the H waypoints
+# ---------------------------------------------------------------------------
+
+def test_weight_field_hand_values():
+    b = np.array([[0.0, 0.0, 2.0, 3.0],          # centre (0, 0), s = 2, a = 3
+                  [1.0, 0.0, 1.0, 0.5]])         # centre (1, 0), s = 1, a = 0.5
+    assert oracle.weight([0.0, 0.0], b[:1]) == 4.0                 # centre: 1 + a
+    assert oracle.weight([1.0, 0.0], b[:1]) == 1.0 + 3.0 * 0.75    # |q - c| = s / 2
+    assert oracle.weight([0.0, 2.0], b[:1]) == 1.0                 # on the support's boundary
+    assert oracle.weight([0.0, -5.0], b[:1]) == 1.0                # outside: the clamp, not a negative bump
+    assert oracle.weight([1.0, 0.0], b) == 1.0 + 3.0 * 0.75 + 0.5  # overlapping bumps add
+    assert oracle.weight([0.0, 0.0], np.zeros((0, 4))) == 1.0
+
+
+def test_weighted_length_without_weight_is_the_length():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        u, v = rng.uniform(-1, 1, (2, 7)).astype(np.float32)
+        length = oracle.lib().orc_edge_length(7, oracle._ptr(u, oracle._f32p), oracle._ptr(v, oracle._f32p))
+        assert oracle.weighted_length(u, v, 32, None) == length
+        zero = np.concatenate([rng.uniform(-1, 1, 7), [0.7, 0.0]])[None, :]    # amplitude 0
+        assert oracle.weighted_length(u, v, 32, zero) == pytest.approx(length, rel=1e-15)
+        far = np.concatenate([np.full(7, 9.0), [0.5, 4.0]])[None, :]           # support away from the edge
+        assert oracle.weighted_length(u, v, 32, far) == pytest.approx(length, rel=1e-15)
+
+
+@pytest.mark.parametrize("H", [2, 3, 17])
+def test_weighted_length_of_a_quadratic_weight_closed_form(H):
+    """Inside one bump w(u + t e) = f(t) is a quadratic in t; the composite
+    trapezoid rule with n = H - 1 intervals then errs by exactly
+    (f'(1) - f'(0)) h^2 / 12 = f'' h^2 / 12, h = 1/n (Euler-Maclaurin ends at
+    the first derivative term).  Dyadic endpoints make every waypoint exact."""
+    u = np.array([-0.25, 0.125], np.float32)
+    v = np.array([0.5, -0.375], np.float32)
+    c, s, a = np.array([0.0625, 0.0]), 2.0, 3.0
+    e, p = v.astype(np.float64) - u, u.astype(np.float64) - c
+    integral = 1.0 + a * (1.0 - (p @ p + p @ e + (e @ e) / 3.0) / s ** 2)
+    f2 = -2.0 * a * (e @ e) / s ** 2
+    h = 1.0 / (H - 1)
+    expect = math.sqrt(e @ e) * (integral + f2 * h * h / 12.0)
+    got = oracle.weighted_length(u, v, H, np.concatenate([c, [s, a]])[None, :])
+    assert got == pytest.approx(expect, rel=1e-13)
+
+
+def test_weighted_length_converges_to_the_exact_integral():
+    """An edge that crosses a bump's support: the exact integral is the
+    closed form of the quadratic over the chord [t1, t2]; the trapezoid rule
+    on the waypoints approaches it as H grows."""
+    u = np.array([-0.8, 0.1], np.float32)
+    v = np.array([0.7, 0.35], np.float32)
+    c, s, a = np.array([0.05, 0.3]), 0.45, 2.5
+    e, p = v.astype(np.float64) - u, u.astype(np.float64) - c
+    A, B, C0 = e @ e, 2.0 * (p @ e), p @ p - s * s
+    r = math.sqrt(B * B - 4.0 * A * C0)
+    t1, t2 = max((-B - r) / (2 * A), 0.0), min((-B + r) / (2 * A), 1.0)
+    bump = a * ((t2 - t1) * (1.0 - (p @ p) / s ** 2) - (p @ e) / s ** 2 * (t2 ** 2 - t1 ** 2)
+                - A / (3.0 * s ** 2) * (t2 ** 3 - t1 ** 3))
+    exact = math.sqrt(A) * (1.0 + bump)
+    b = np.concatenate([c, [s, a]])[None, :]
+    assert abs(oracle.weighted_length(u, v, 17, b) / exact - 1.0) < 1e-3
+    assert abs(oracle.weighted_length(u, v, 16385, b) / exact - 1.0) < 1e-7
+
+
+def test_weighted_length_is_between_length_and_w_max_times_length():
+    rng = np.random.default_rng(11)
+    b = np.concatenate([rng.uniform(-1, 1, (6, 3)), rng.uniform(0.2, 1.0, (6, 1)), rng.uniform(0, 2, (6, 1))], axis=1)
+    w_max = 1.0 + b[:, 4].sum()
+    for _ in range(50):
+        u, v = rng.uniform(-1, 1, (2, 3)).astype(np.float32)
+        length = float(np.linalg.norm(v.astype(np.float64) - u))
+        wl = oracle.weighted_length(u, v, 24, b)
+        assert length * (1 - 1e-15) <= wl <= w_max * length * (1 + 1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_weighted_value_iteration_equals_brute_force(seed):
+    sc, Q = _small_problem(seed, M=4, L=3, n_obs=6 + seed)
+    H = 16
+    rng = np.random.default_rng(100 + seed)
+    b = np.concatenate([rng.uniform(-1, 1, (3, 2)), rng.uniform(0.3, 0.8, (3, 1)), rng.uniform(0.5, 3, (3, 1))], axis=1)
+    sol = oracle.solve(sc, Q, H, bumps=b)
+    verts = sol.verts
+    best, best_chain = math.inf, None
+    for chain in itertools.product(range(4), repeat=3):
+        idx = (0,) + chain + (0,)
+        total = 0.0
+        for l in range(4):
+            lab, _ = sol.edges[l]
+            if lab[idx[l], idx[l + 1]] != oracle.FREE:
+                total = math.inf
+                break
+            total += oracle.weighted_length(verts[l][idx[l]], verts[l + 1][idx[l + 1]], H, b)
+        if total < best:
+            best, best_chain = total, chain
+    assert sol.cost_lo == pytest.approx(best, rel=1e-12) if math.isfinite(best) else math.isinf(sol.cost_lo)
+    if math.isfinite(best):
+        assert tuple(sol.path) == best_chain
+        total, _ = oracle.path_cost(sc, Q, sol.path, H, bumps=b)
+        assert total == pytest.approx(best, rel=1e-12)
