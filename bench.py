@@ -384,6 +384,33 @@ def run_ours(args, wl):
                      "mean_cost_ratio_free_over_uniform": (sum(a / b for a, b in fin) / len(fin)) if fin else None,
                      "note": "same seeds; samples redrawn on C_free (first free of up to 64 attempts)"}
 
+    # --- the same seeds with weighted-length edge costs (App. "General Costs"): speed and cost
+    pw = binding.Planner(sc.robot, M, L, H, max_obstacles=64)
+    pw.set_scene(sc)
+    bumps = scenes.weight_bumps(sc, wl["seed"])
+    pw.set_cost_weight(bumps)
+    for s in range(args.warmup):
+        binding.gtmp_sample_layers(pw.ctx, seed0 + 10_000 + s, M)
+        binding.gtmp_solve(pw.ctx, lz_path, lz_cost)
+    pw.synchronize()
+    w_ms, w_costs = [], []
+    for s in range(args.steps):
+        flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        binding.gtmp_sample_layers(pw.ctx, seed0 + s, M)
+        binding.gtmp_solve(pw.ctx, lz_path, lz_cost)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        w_ms.append(a0.elapsed_time(a1))
+        w_costs.append(float(lz_cost.cpu()[0]))
+    pw.close()
+    finw = [(a, b) for a, b in zip(w_costs, un_costs) if math.isfinite(a) and math.isfinite(b)]
+    weighted = {"solves_per_s": args.steps / (sum(w_ms) / 1e3), "ms_per_step": sum(w_ms) / len(w_ms),
+                "bumps": int(bumps.shape[0]), "w_max": float(1.0 + bumps[:, -1].astype(np.float64).sum()),
+                "mean_cost_ratio_weighted_over_length": (sum(a / b for a, b in finw) / len(finw)) if finw else None,
+                "note": "same seeds as the timed plans; edge cost = trapezoid rule of the weight on the H waypoints"}
+
     # --- roofline of the fused kernel in full-evaluation mode (data-independent FP32 work)
     pf = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_FULL)
     pf.set_scene(sc)
@@ -404,6 +431,7 @@ def run_ours(args, wl):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak_tflops = sms * 128 * 2 * 2.032e9 / 1e12
     achieved = full_flops / (fprof["fused_ms"] / 1e3) / 1e12
+    ffma_tflops = binding.gtmp_fp32_fma_peak(torch.cuda.current_stream().cuda_stream)
 
     # --- unfused variant: the min-plus sweep over stored cost matrices, at M = 4096 (C = 470 MB >> L2)
     unfused = None
@@ -460,11 +488,14 @@ def run_ours(args, wl):
                          "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one 1024 x 1024 transition "
                                          "launch (ncu), unchanged kernel",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock)",
+                         "ffma_measured": ffma_tflops, "frac_of_ffma_measured": achieved / ffma_tflops,
+                         "ffma_note": "gtmp_fp32_fma_peak: independent FMA chains on every SM, best of 6 launches",
                          "flops_per_waypoint": fpw,
                          "fused_ms_per_solve": fprof["fused_ms"] / full_steps},
             "fused_ms_per_solve_early_exit": prof["fused_ms"] / args.steps,
             "roofline_unfused_minplus": unfused,
             "free_sampling": free_sampling,
+            "weighted_length": weighted,
             "lazy": {"solves_per_s": solves / lazy_s, "ms_per_step": sum(lz_ms) / len(lz_ms),
                      "same_paths_and_costs_as_early_exit": lz_same,
                      "note": "exact mode GTMP_EVAL_LAZY: an edge is realised only if c(u,v)+J(v) beats its row's "

@@ -161,6 +161,24 @@ GTMP_API gtmp_status gtmp_set_goals(gtmp_ctx* ctx, const float* goals, const flo
 #define GTMP_SAMPLER_FREE 1
 GTMP_API gtmp_status gtmp_set_sampler(gtmp_ctx* ctx, int32_t sampler, int32_t max_attempts);
 
+/* Weighted-length edge cost (App. "General Costs": any additive cost that
+ * dominates length and is Lipschitz in the edge's endpoints keeps the
+ * guarantees; a weighted length with 1 <= w <= W is the example).  Weight
+ * field w(q) = 1 + sum_b a_b max(0, 1 - |q - c_b|^2 / s_b^2) of K bumps,
+ * bumps host [K][dof + 2] = (c_b[0..dof-1], s_b, a_b) with c_b finite,
+ * s_b > 0, a_b >= 0, 0 <= K <= GTMP_MAX_WEIGHT_BUMPS; K = 0 (bumps may be
+ * NULL) restores the plain length.  The cost of a free edge u -> v is the
+ * trapezoid rule of w on its H checked waypoints,
+ *   |v - u| / (H - 1) * (w_0 / 2 + w_1 + ... + w_{H-2} + w_{H-1} / 2),
+ * in float32, summed in waypoint order (the same bits in every mode).  The
+ * edge-length limit still applies to |v - u|.  Copied (the call returns
+ * after the copy); used by gtmp_solve (all modes), gtmp_solve_unfused,
+ * gtmp_get_edge_costs, gtmp_anytime, aogtmp_expand (its informed set stays
+ * valid: w >= 1), gtmp_solve_pruned and gtmp_solve_classes.  The batched and
+ * allocation-free solvers keep the plain length. */
+#define GTMP_MAX_WEIGHT_BUMPS 16
+GTMP_API gtmp_status gtmp_set_cost_weight(gtmp_ctx* ctx, const float* bumps, int32_t K);
+
 /* The goal vertex (index into the goal set) that graph `graph`'s best chain
  * reaches, -1 if infeasible: dev_goal device [1] int32.  Enqueued after the
  * solve on the context's stream. */
@@ -442,6 +460,15 @@ GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* ctx, const float* dev_q,
  * mask on first use. */
 GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* ctx, float threshold, int32_t score_waypoints, int32_t* dev_path,
                                        float* dev_cost, gtmp_prune_stats* stats);
+
+/* Calibration, no counterpart in the paper: the FP32 FMA throughput of the
+ * current device in TFLOP/s (FMA = 2 flops), from a kernel of independent
+ * FMA chains filling every SM, launched 8 times on cuda_stream (NULL = legacy
+ * default stream); *tflops receives the best of the last 6.  Synchronises the
+ * stream.  The fused edge kernels are FP32-pipe bound; this is the ceiling a
+ * pure FMA stream reaches at the clocks and power state of the moment.
+ * GTMP_ERR_CUDA if a launch fails. */
+GTMP_API gtmp_status gtmp_fp32_fma_peak(void* cuda_stream, double* tflops);
 
 /* The surrogate's tensor-core GEMM on its own: C[m][n] = sum_k A[m][k] B[n][k]
  * with A device [M][lda] and B device [N][ldb] bf16 (K contiguous; lda, ldb

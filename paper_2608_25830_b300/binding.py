@@ -110,6 +110,8 @@ _SIGNATURES = {
     "gtmp_solve_classes": [_vp, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32)],
     "gtmp_set_goals": [_vp, _fp, _fp, _i32],
     "gtmp_set_sampler": [_vp, _i32, _i32],
+    "gtmp_set_cost_weight": [_vp, _fp, _i32],
+    "gtmp_fp32_fma_peak": [_vp, ctypes.POINTER(ctypes.c_double)],
     "gtmp_get_goal_reached": [_vp, _i32, _vp],
     "gtmp_surrogate_train": [_vp, ctypes.POINTER(GtmpSurrogateConfig), ctypes.POINTER(GtmpSurrogateStats)],
     "gtmp_surrogate_predict": [_vp, _vp, _i32, _vp],
@@ -347,6 +349,9 @@ class Planner:
         self.n_obstacles = int(np.asarray(scene.spheres).shape[0] + np.asarray(scene.boxes).shape[0])
         gtmp_set_endpoints(self.ctx, scene.q_start, scene.q_goal)
 
+    def set_cost_weight(self, bumps):
+        gtmp_set_cost_weight(self.ctx, bumps)
+
     def sample_layers(self, seed, M=None):
         gtmp_sample_layers(self.ctx, seed, M or self.M)
 
@@ -498,6 +503,28 @@ def gtmp_set_goals(ctx, goals, values=None):
     g = _f32(goals)
     v = None if values is None else _f32(values)
     _check(ctx, lib().gtmp_set_goals(ctx, _ptr(g), None if v is None else _ptr(v), g.shape[0]))
+
+
+def gtmp_fp32_fma_peak(stream=None):
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    out = ctypes.c_double()
+    st = lib().gtmp_fp32_fma_peak(stream, ctypes.byref(out))
+    if st != 0:
+        raise RuntimeError(f"gtmp_fp32_fma_peak: {STATUS.get(st, st)}")
+    return out.value
+
+
+MAX_WEIGHT_BUMPS = 16
+
+
+def gtmp_set_cost_weight(ctx, bumps):
+    """Weighted-length edge cost: bumps [K][dof + 2] = (centre, radius s, amplitude a); None or K = 0: length."""
+    if bumps is None or np.asarray(bumps).size == 0:
+        _check(ctx, lib().gtmp_set_cost_weight(ctx, None, 0))
+        return
+    b = _f32(bumps)
+    b = b[None, :] if b.ndim == 1 else b
+    _check(ctx, lib().gtmp_set_cost_weight(ctx, _ptr(b), b.shape[0]))
 
 
 def gtmp_get_goal_reached(ctx, graph, dev_goal):

@@ -55,6 +55,8 @@ GraphDev graph(gtmp_ctx* c, int R, int M) {
   g.max_edge_len = c->p.max_edge_len;
   g.G = c->G;
   g.gval = c->goal_values ? c->gval : nullptr;
+  g.wb = c->wb;
+  g.n_wb = c->n_wb;
   return g;
 }
 
@@ -367,6 +369,7 @@ gtmp_status gtmp_destroy(gtmp_ctx* c) {
   cudaFree(c->C);
   cudaFree(c->cls);
   cudaFree(c->gval);
+  cudaFree(c->wb);
   cudaFree(c->prune);
   surrogate_free(c->sur);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -509,6 +512,37 @@ gtmp_status gtmp_set_goals(gtmp_ctx* c, const float* goals, const float* values,
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->G = G;
   c->goal_values = values != nullptr;
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_set_cost_weight(gtmp_ctx* c, const float* bumps, int32_t K) {
+  if (!c) return GTMP_ERR_INVALID_ARG;
+  if (K < 0 || K > GTMP_MAX_WEIGHT_BUMPS || (K > 0 && !bumps))
+    return fail(c, GTMP_ERR_INVALID_ARG, "bump count %d outside [0, %d] or NULL bumps", K, GTMP_MAX_WEIGHT_BUMPS);
+  const int stride = c->dp / 4 + 1;  // float4 per bump: centre (dp floats), then (1 / s^2, a, 0, 0)
+  std::vector<float4> img(static_cast<size_t>(K) * stride, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+  double w_max = 1.0;
+  for (int b = 0; b < K; ++b) {
+    const float* p = bumps + static_cast<size_t>(b) * (c->dof + 2);
+    if (!finite_all(p, c->dof + 2)) return fail(c, GTMP_ERR_INVALID_ARG, "bump %d has a non-finite value", b);
+    const double s = p[c->dof], a = p[c->dof + 1];
+    const float inv_s2 = static_cast<float>(1.0 / (s * s));
+    if (!(s > 0.0) || !std::isfinite(inv_s2) || !(a >= 0.0))
+      return fail(c, GTMP_ERR_INVALID_ARG, "bump %d needs radius > 0 (1/s^2 finite) and amplitude >= 0", b);
+    w_max += a;
+    float* cen = reinterpret_cast<float*>(&img[static_cast<size_t>(b) * stride]);
+    for (int k = 0; k < c->dof; ++k) cen[k] = p[k];
+    img[static_cast<size_t>(b) * stride + stride - 1] = make_float4(inv_s2, static_cast<float>(a), 0.0f, 0.0f);
+  }
+  if (!std::isfinite(static_cast<float>(w_max)))
+    return fail(c, GTMP_ERR_INVALID_ARG, "the weight's maximum 1 + sum a_b overflows float32");
+  if (K > 0) {
+    if (!c->wb)
+      CUDA_TRY(c, cudaMalloc(&c->wb, static_cast<size_t>(GTMP_MAX_WEIGHT_BUMPS) * stride * sizeof(float4)));
+    CUDA_TRY(c, cudaMemcpyAsync(c->wb, img.data(), img.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  c->n_wb = K;
   return GTMP_OK;
 }
 

@@ -43,6 +43,9 @@ struct gtmp_ctx {
   int G = 1;
   float* gval = nullptr;  // [p.M] device, valid when goal_values is set
   bool goal_values = false;
+  // weighted-length edge cost: n_wb bumps in the GraphDev layout (null/0: plain length)
+  float4* wb = nullptr;
+  int n_wb = 0;
   // layer sampler: GTMP_SAMPLER_UNIFORM or GTMP_SAMPLER_FREE (rejection on C_free, bounded attempts)
   int sampler = 0;
   int sampler_attempts = 64;

@@ -145,6 +145,90 @@ __device__ __forceinline__ void load_vertex(float (&q)[DP], const float* p, int 
 }
 
 // ---------------------------------------------------------------------------
+// Weighted length (App. "General Costs"): w(q) = 1 + sum_b a_b max(0, 1 -
+// |q - c_b|^2 / s_b^2) (1 <= w <= 1 + sum a_b, Lipschitz).  The cost of a
+// free edge is the trapezoid rule of w on its H waypoints,
+//   |v - u| / (H - 1) * (w_0 / 2 + w_1 + ... + w_{H-2} + w_{H-1} / 2),
+// summed in waypoint order in float32, so the lane-per-waypoint and the
+// lane-per-edge forms below give the same bits.  Waypoints are the checked
+// ones: the endpoints themselves, fma(t_k, v - u, u) in between.
+// ---------------------------------------------------------------------------
+template <int DP>
+__device__ __forceinline__ float weight_at(const float (&q)[DP], const float4* wb, int n_wb) {
+  constexpr int kStride = DP / 4 + 1;
+  float w = 1.0f;
+  for (int b = 0; b < n_wb; ++b) {
+    const float4* p = wb + b * kStride;
+    float d2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DP; d += 4) {
+      const float4 c = __ldg(p + d / 4);
+      float e = __fsub_rn(q[d], c.x);
+      d2 = __fmaf_rn(e, e, d2);
+      e = __fsub_rn(q[d + 1], c.y);
+      d2 = __fmaf_rn(e, e, d2);
+      e = __fsub_rn(q[d + 2], c.z);
+      d2 = __fmaf_rn(e, e, d2);
+      e = __fsub_rn(q[d + 3], c.w);
+      d2 = __fmaf_rn(e, e, d2);
+    }
+    const float4 par = __ldg(p + DP / 4);
+    w = __fmaf_rn(par.y, fmaxf(__fmaf_rn(-d2, par.x, 1.0f), 0.0f), w);
+  }
+  return w;
+}
+
+// The edge kernels take the weighted cost as a template parameter, so the
+// collision loops of the plain-length kernels keep their register allocation.
+
+// one thread, one edge qi -> qj of length len
+template <int DP>
+__device__ __forceinline__ float weighted_cost_thread(const float (&qi)[DP], const float (&qj)[DP], float len,
+                                                      const GraphDev& g) {
+  float dq[DP];
+#pragma unroll
+  for (int d = 0; d < DP; ++d) dq[d] = __fsub_rn(qj[d], qi[d]);
+  const float steps = static_cast<float>(g.H - 1);
+  float sum = __fmul_rn(0.5f, weight_at<DP>(qi, g.wb, g.n_wb));
+  for (int k = 1; k <= g.H - 2; ++k) {
+    const float t = __fdiv_rn(static_cast<float>(k), steps);
+    float q[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
+    sum = __fadd_rn(sum, weight_at<DP>(q, g.wb, g.n_wb));
+  }
+  sum = __fadd_rn(sum, __fmul_rn(0.5f, weight_at<DP>(qj, g.wb, g.n_wb)));
+  return __fmul_rn(len, __fdiv_rn(sum, steps));
+}
+
+// one warp, one edge: lane k evaluates interior waypoint kb + k, every lane
+// then adds the values in waypoint order (all 32 lanes must be converged);
+// dq = qj - qi as the collision loop computed it, qj read back from qj_ptr
+template <int DP>
+__device__ __forceinline__ float weighted_cost_warp(const float (&qi)[DP], const float* qj_ptr, int dp,
+                                                    const float (&dq)[DP], float len, const GraphDev& g, int lane) {
+  const float steps = static_cast<float>(g.H - 1);
+  float sum = __fmul_rn(0.5f, weight_at<DP>(qi, g.wb, g.n_wb));
+  for (int kb = 1; kb <= g.H - 2; kb += 32) {
+    const int k = kb + lane;
+    float w = 0.0f;
+    if (k <= g.H - 2) {
+      const float t = __fdiv_rn(static_cast<float>(k), steps);
+      float q[DP];
+#pragma unroll
+      for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
+      w = weight_at<DP>(q, g.wb, g.n_wb);
+    }
+    const int n = min(32, g.H - 1 - kb);
+    for (int m = 0; m < n; ++m) sum = __fadd_rn(sum, __shfl_sync(kFull, w, m));
+  }
+  float qj[DP];
+  load_vertex<DP>(qj, qj_ptr, dp);
+  sum = __fadd_rn(sum, __fmul_rn(0.5f, weight_at<DP>(qj, g.wb, g.n_wb)));
+  return __fmul_rn(len, __fdiv_rn(sum, steps));
+}
+
+// ---------------------------------------------------------------------------
 // One warp, one row i of the transition layer -> layer + 1 of graph r, columns
 // [j0, j1): the 32 lanes carry the H-2 interior waypoints of one edge at a
 // time (endpoint labels are the vertex flags), the warp leaves an edge at its
@@ -155,7 +239,7 @@ __device__ __forceinline__ void load_vertex(float (&q)[DP], const float* p, int 
 // ---------------------------------------------------------------------------
 // Point robots: one waypoint test is a handful of flops, so the 32 lanes take
 // 32 columns (edges) at a time and each lane walks its own edge's waypoints.
-template <bool FULL>
+template <bool FULL, bool WEIGHTED = false>
 __device__ __forceinline__ unsigned long long point_row_chunk_best(const GraphDev& g, int r, int layer, int i,
                                                                    int j0, int j1, const float* s_V,
                                                                    const RobotDev& rb, const float4* s_obs,
@@ -197,7 +281,11 @@ __device__ __forceinline__ unsigned long long point_row_chunk_best(const GraphDe
           if (!FULL && hit) break;
         }
       }
-      if (!hit && !skip) key = make_key(__fadd_rn(len, Vj), static_cast<uint32_t>(j));
+      if (!hit && !skip) {
+        float cost = len;
+        if constexpr (WEIGHTED) cost = weighted_cost_thread<DP>(qi, qj, len, g);
+        key = make_key(__fadd_rn(cost, Vj), static_cast<uint32_t>(j));
+      }
     }
     key = warp_min_u64(key);
     best = key < best ? key : best;
@@ -205,12 +293,12 @@ __device__ __forceinline__ unsigned long long point_row_chunk_best(const GraphDe
   return best;
 }
 
-template <int VAR, bool FULL>
+template <int VAR, bool FULL, bool WEIGHTED = false>
 __device__ __forceinline__ unsigned long long row_chunk_best(const GraphDev& g, int r, int layer, int i, int j0,
                                                              int j1, const float* s_V, const RobotDev& rb,
                                                              const float4* s_obs, const SceneDev& sc, int lane) {
   if constexpr (VAR == kVarPoint) {
-    return point_row_chunk_best<FULL>(g, r, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
+    return point_row_chunk_best<FULL, WEIGHTED>(g, r, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
   }
   using V = Var<VAR>;
   constexpr int DP = V::kDp;
@@ -251,7 +339,10 @@ __device__ __forceinline__ unsigned long long row_chunk_best(const GraphDev& g, 
       if (!FULL && hit) break;
     }
     if (!hit && !too_long && !row_hit && Vj < kInf) {
-      const unsigned long long key = make_key(__fadd_rn(len, Vj), static_cast<uint32_t>(j));
+      float cost = len;
+      if constexpr (WEIGHTED)
+        cost = weighted_cost_warp<DP>(qi, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp, dq, len, g, lane);
+      const unsigned long long key = make_key(__fadd_rn(cost, Vj), static_cast<uint32_t>(j));
       best = key < best ? key : best;
     }
   }
@@ -289,7 +380,7 @@ __device__ __forceinline__ unsigned long long warp_sort32_u64(unsigned long long
   return key;
 }
 
-template <int VAR>
+template <int VAR, bool WEIGHTED = false>
 __device__ __forceinline__ void lazy_block(const GraphDev& g, int r, int layer, int i, int j0, int j_end,
                                            const float* s_V, const RobotDev& rb, const float4* s_obs,
                                            const SceneDev& sc, int lane) {
@@ -318,7 +409,11 @@ __device__ __forceinline__ void lazy_block(const GraphDev& g, int r, int layer, 
         s2 = __fmaf_rn(e, e, s2);
       }
       const float len = __fsqrt_rn(s2);
-      if (!(len > g.max_edge_len)) key = make_key(__fadd_rn(len, Vj), static_cast<uint32_t>(jl));
+      if (!(len > g.max_edge_len)) {
+        float cost = len;
+        if constexpr (WEIGHTED) cost = weighted_cost_thread<DP>(qi, qj, len, g);
+        key = make_key(__fadd_rn(cost, Vj), static_cast<uint32_t>(jl));
+      }
     }
   }
   if (key >= bound) key = kEmptyKey;

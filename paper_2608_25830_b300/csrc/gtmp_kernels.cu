@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) label_configs_kernel(const float* q_
 // Shared memory: obstacles (bulk copy) and the column layer's cost-to-go,
 // +inf where that vertex collides or reaches no goal.
 // ---------------------------------------------------------------------------
-template <int VAR, int MODE>
+template <int VAR, int MODE, bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) fused_transition_kernel(GraphDev g, int layer, RobotDev rb, SceneDev sc,
                                                                     int* counters, int chunk, int* err) {
   constexpr bool FULL = MODE == kEvalFull;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) fused_transition_ke
       c = __shfl_sync(kFull, c, 0);
       if (c >= n_units) break;
       const int b = c / n_rows;
-      lazy_block<VAR>(g, r, layer, c - b * n_rows, b * 32, n_cols, s_V, rb, s_obs, sc, lane);
+      lazy_block<VAR, WEIGHTED>(g, r, layer, c - b * n_rows, b * 32, n_cols, s_V, rb, s_obs, sc, lane);
     }
   } else {
     while (true) {
@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) fused_transition_ke
       const int j0 = (c - i * cpr) * chunk;
       const int j1 = min(j0 + chunk, n_cols);
       const size_t vi = vidx(g, r, layer, i);
-      const unsigned long long best = row_chunk_best<VAR, FULL>(g, r, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
+      const unsigned long long best =
+          row_chunk_best<VAR, FULL, WEIGHTED>(g, r, layer, i, j0, j1, s_V, rb, s_obs, sc, lane);
       if (lane == 0 && best != kEmptyKey) atomicMin(&g.keys[vi], best);
     }
   }
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) fused_transition_ke
 // ---------------------------------------------------------------------------
 // Unfused variant, step 1: C[i][j] (row stride cs) = ||q_j - q_i|| or +inf.
 // ---------------------------------------------------------------------------
-template <int VAR>
+template <int VAR, bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) edge_costs_kernel(GraphDev g, int layer, RobotDev rb, SceneDev sc,
                                                               float* C, int cs, int* counter, int chunk, int* err) {
   using V = Var<VAR>;
@@ -264,7 +265,10 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) edge_costs_kernel(G
             hit |= config_collides<VAR, true, false>(q, k <= H - 2, rb, s_obs, sc);
             if (hit) break;
           }
-          if (!hit) out = len;
+          if (!hit) {
+            out = len;
+            if constexpr (WEIGHTED) out = weighted_cost_warp<DP>(qi, g.Q + vj * g.dp, g.dp, dq, len, g, lane);
+          }
         }
       }
       if (lane == 0) C[static_cast<size_t>(i) * cs + j] = out;
@@ -555,7 +559,12 @@ template <int VAR, int MODE>
 cudaError_t fused_dispatch_mode(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int* counters,
                                 int grid_x, int chunk, int* err, cudaStream_t st) {
   const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16 + static_cast<size_t>(g.M_stride) * 4;
-  fused_transition_kernel<VAR, MODE><<<dim3(grid_x, g.R), kThreads, smem, st>>>(g, layer, rb, sc, counters, chunk, err);
+  if (g.n_wb > 0)
+    fused_transition_kernel<VAR, MODE, true>
+        <<<dim3(grid_x, g.R), kThreads, smem, st>>>(g, layer, rb, sc, counters, chunk, err);
+  else
+    fused_transition_kernel<VAR, MODE, false>
+        <<<dim3(grid_x, g.R), kThreads, smem, st>>>(g, layer, rb, sc, counters, chunk, err);
   return cudaGetLastError();
 }
 
@@ -623,7 +632,10 @@ struct EdgeCostsRun {
   static cudaError_t run(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, float* C, int cs,
                          int* counter, int grid_x, int chunk, int* err, cudaStream_t st) {
     const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16;
-    edge_costs_kernel<VAR><<<grid_x, kThreads, smem, st>>>(g, layer, rb, sc, C, cs, counter, chunk, err);
+    if (g.n_wb > 0)
+      edge_costs_kernel<VAR, true><<<grid_x, kThreads, smem, st>>>(g, layer, rb, sc, C, cs, counter, chunk, err);
+    else
+      edge_costs_kernel<VAR, false><<<grid_x, kThreads, smem, st>>>(g, layer, rb, sc, C, cs, counter, chunk, err);
     return cudaGetLastError();
   }
 };
@@ -632,10 +644,10 @@ template <int VAR>
 struct OccupancyRun {
   static cudaError_t run(int mode, int* out) {
     if (mode == kEvalFull)
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fused_transition_kernel<VAR, kEvalFull>, kThreads,
-                                                           16 * 1024);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fused_transition_kernel<VAR, kEvalEarlyExit>, kThreads,
-                                                         16 * 1024);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fused_transition_kernel<VAR, kEvalFull, false>,
+                                                           kThreads, 16 * 1024);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fused_transition_kernel<VAR, kEvalEarlyExit, false>,
+                                                         kThreads, 16 * 1024);
   }
 };
 
@@ -643,18 +655,17 @@ template <int VAR>
 struct ConfigureRun {
   static cudaError_t run(int smem_max) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(fused_transition_kernel<VAR, kEvalFull>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(fused_transition_kernel<VAR, kEvalEarlyExit>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(fused_transition_kernel<VAR, kEvalLazy>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(edge_costs_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) !=
-        cudaSuccess)
-      return e;
+    const void* fns[] = {
+        reinterpret_cast<const void*>(fused_transition_kernel<VAR, kEvalFull, false>),
+        reinterpret_cast<const void*>(fused_transition_kernel<VAR, kEvalEarlyExit, false>),
+        reinterpret_cast<const void*>(fused_transition_kernel<VAR, kEvalLazy, false>),
+        reinterpret_cast<const void*>(fused_transition_kernel<VAR, kEvalFull, true>),
+        reinterpret_cast<const void*>(fused_transition_kernel<VAR, kEvalEarlyExit, true>),
+        reinterpret_cast<const void*>(fused_transition_kernel<VAR, kEvalLazy, true>),
+        reinterpret_cast<const void*>(edge_costs_kernel<VAR, false>),
+        reinterpret_cast<const void*>(edge_costs_kernel<VAR, true>)};
+    for (const void* f : fns)
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(vertex_labels_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_max)) != cudaSuccess)
       return e;

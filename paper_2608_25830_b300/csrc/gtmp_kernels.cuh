@@ -21,6 +21,10 @@ struct GraphDev {
   const uint8_t* prune = nullptr;  // [rows][cols] of the transition being run; 1 = edge dropped before checking
   int G = 1;                       // goal vertices (layer L+1)
   const float* gval = nullptr;     // [G] terminal values V_g (null: all 0)
+  // weighted-length edge cost: n_wb bumps of dp / 4 + 1 float4 each, the
+  // centre (dp floats, zero-padded), then (1 / s^2, a, 0, 0); n_wb = 0: length
+  const float4* wb = nullptr;
+  int n_wb = 0;
 };
 
 __host__ __device__ inline size_t vidx(const GraphDev& g, int r, int layer, int i) {

@@ -170,6 +170,24 @@ def pick_endpoints(scene: Scene, config_free) -> Scene:
     return scene.with_endpoints(int(ok[0]))
 
 
+def weight_bumps(scene: Scene, seed: int = 0, K: int = 6, amin: float = 0.5, amax: float = 3.0,
+                 smin: float = 0.3, smax: float = 0.6) -> np.ndarray:
+    """Seeded weight field for weighted-length costs: float32 [K][dof + 2] rows
+    (centre, radius s, amplitude a).  Bump 0 sits at the midpoint of the
+    scene's start and goal (so the straight connection is penalised), the rest
+    uniformly in the joint box; radii are U[smin, smax] times half the box
+    diagonal, amplitudes U[amin, amax]."""
+    lo = scene.robot.q_lo.astype(np.float64)
+    hi = scene.robot.q_hi.astype(np.float64)
+    rng = np.random.default_rng([seed, 6, scene.robot.dof, K])
+    half_diag = 0.5 * float(np.linalg.norm(hi - lo))
+    cen = rng.uniform(lo, hi, (K, lo.shape[0]))
+    cen[0] = 0.5 * (scene.q_start.astype(np.float64) + scene.q_goal)
+    rad = rng.uniform(smin, smax, K) * half_diag
+    amp = rng.uniform(amin, amax, K)
+    return _f32(np.concatenate([cen, rad[:, None], amp[:, None]], axis=1))
+
+
 # ---------------------------------------------------------------------------
 # Workload descriptions (sizes of the five evaluated configurations)
 # ---------------------------------------------------------------------------

@@ -74,4 +74,5 @@ def test_null_context_calls_fail_cleanly():
     assert L.gtmp_destroy(None) == 0
     assert L.gtmp_synchronize(None) == 1
     assert L.gtmp_solve(None, None, None) == 1
+    assert L.gtmp_set_cost_weight(None, None, 0) == 1
     assert L.gtmp_last_error(None).decode() == "null context"

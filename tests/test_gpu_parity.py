@@ -401,3 +401,12 @@ def test_obstacle_counts_around_table_limits(torch_cuda, n_s, n_b, n_far, M, L, 
     sol = oracle.solve(sc, Q, H)
     V, S, path, cost = outs[0]
     compare_solution(sol, V, S, path, cost, f"{n} obstacles")
+
+
+def test_fp32_fma_calibration_is_plausible(torch_cuda):
+    """The measured FMA rate is positive and cannot exceed SMs x 128 lanes x 2 flops x the top clock."""
+    torch = torch_cuda
+    props = torch.cuda.get_device_properties(0)
+    r = binding.gtmp_fp32_fma_peak()
+    ceiling = props.multi_processor_count * 128 * 2 * 2.2e9 / 1e12
+    assert 0.25 * ceiling < r < ceiling
