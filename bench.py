@@ -986,6 +986,33 @@ def run_ao(args, wl):
         run_schedule(rank_seed_base(rank) + 50_000 + s)
     curves = [run_schedule(rank_seed_base(rank) + s) for s in range(args.steps)]
     total_s = max_over_ranks(sum(c[-1][0] for c in curves) / 1e3, world, "cuda")
+
+    # --- epochs (Sec. IV-D): layer count grown by the layer rule and by saturation, edge limit l_M(r)
+    ep = wl.get("epochs")
+    epochs = None
+    if ep is not None:
+        pe = binding.Planner(sc.robot, ep["M_max"], ep["L_cap"], H, max_obstacles=64,
+                             eval_mode=binding.EVAL_LAZY if args.lazy else binding.EVAL_EARLY_EXIT)
+        pe.set_scene(sc)
+        kw = {k: ep[k] for k in ("L0", "M0", "M_max", "stages", "reach", "r", "varsigma", "limit_edges")}
+        pe.ao_run(rank_seed_base(rank) + 50_000, **kw)          # warm-up
+        pe.synchronize()
+        runs = []
+        for s in range(min(3, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, cost_e, log, best_layers = pe.ao_run(rank_seed_base(rank) + s, **kw)
+            pe.synchronize()
+            runs.append((time.perf_counter() - t0, log, best_layers))
+        pe.close()
+        wall, log, best_layers = runs[0]
+        epochs = {"schedule": ep, "wall_ms_per_run": [round(r[0] * 1e3, 3) for r in runs],
+                  "best_cost_per_run": [r[1][-1]["best_cost"] for r in runs],
+                  "best_chain_layers": best_layers,
+                  "stages": [[r["epoch"], r["L"], r["M"], round(r["edge_limit"], 5), r["stage_cost"], r["best_cost"]]
+                             for r in log],
+                  "note": "host wall time (the driver reads the best cost back after every stage); stages = "
+                          "[epoch, L, M, edge limit, stage cost, best cost]"}
     checks = sum(H * (2 * M + (L - 1) * M * M) for M in sizes)
     if rank == 0:
         print(json.dumps({
@@ -995,7 +1022,8 @@ def run_ao(args, wl):
             "config": {"workload": args.workload, "M_stages": sizes, "L": L, "H": H, "dof": wl["dof"],
                        "eval_mode": "lazy" if args.lazy else "early_exit",
                        "checks_per_schedule": checks, "l2": "not flushed inside a schedule (stages are sequential)"},
-            "best_cost_vs_time_ms": [[round(t, 3), c] for t, c in curves[0]]}), flush=True)
+            "best_cost_vs_time_ms": [[round(t, 3), c] for t, c in curves[0]],
+            "epochs": epochs}), flush=True)
 
 
 def main():

@@ -272,6 +272,60 @@ GTMP_API gtmp_status gtmp_anytime(gtmp_ctx* ctx, uint64_t seed, int32_t restarts
 GTMP_API gtmp_status aogtmp_expand(gtmp_ctx* ctx, uint64_t seed, int32_t M_new, int32_t* dev_stage_path,
                           float* dev_stage_cost, int32_t* dev_best_path, float* dev_best_cost);
 
+/* Active layer count (Sec. IV-D: AO-GTMP runs in epochs, each with its own
+ * number of layers): 1 <= L <= the L given to gtmp_create (the capacity).
+ * Drops the current samples (the next solve needs new ones), re-places the
+ * start and the goal set for the new layout and discards stored cost
+ * matrices.  Synchronous. */
+GTMP_API gtmp_status gtmp_set_num_layers(gtmp_ctx* ctx, int32_t L);
+
+/* Edge-length limit l of later solves (Sec. III-B: edges longer than l are
+ * rejected; Sec. V's l_M(r)): > 0, +INFINITY = none. */
+GTMP_API gtmp_status gtmp_set_max_edge_len(gtmp_ctx* ctx, float max_edge_len);
+
+/* AO-GTMP with epochs (Sec. IV-D).  Within an epoch the layer count L is
+ * fixed and each stage doubles the samples per layer (M0, 2 M0, ... up to
+ * M_max) through aogtmp_expand; the informed bound c (the best cost so far)
+ * carries over from epoch to epoch.  A new epoch starts with fresh samples
+ * (Philox seed + epoch) and
+ *   L' = max(L + 1, ceil(c / (reach - 2 r - varsigma)) - 1)  if the layer rule
+ *        L + 1 >= c / (reach - 2 r - varsigma) fails (finite c and reach),
+ *   L' = L + 1                                                if M reached M_max,
+ * clamped to the capacity (at the capacity only saturation starts an epoch,
+ * again with fresh samples).  With limit_edges, a stage's edge-length limit is
+ * l = min(l_0, c / (L + 1) + 2 r + varsigma) in double, rounded to float,
+ * with the best cost c in place of the reference length (Sec. V's l_M(r);
+ * l_0 = the limit on entry, restored on return); before the first solution
+ * l = l_0. */
+typedef struct {
+  int32_t L0;          /* layers of the first epoch, 1..capacity */
+  int32_t M0;          /* samples per layer at each epoch's first stage, >= 1 */
+  int32_t M_max;       /* per-epoch sample cap, M0..capacity */
+  int32_t stages;      /* stages in all, >= 1 */
+  float reach;         /* Lambda_s(tau): the longest edge the planner connects reliably; +INFINITY: no layer rule */
+  float r;             /* waypoint-ball radius r >= 0 */
+  float varsigma;      /* margin varsigma >= 0; reach > 2 r + varsigma */
+  int32_t limit_edges; /* 1: per-stage edge-length limit from the best cost (above); 0: keep the context's */
+} gtmp_ao_schedule;
+
+/* One stage of aogtmp_run: its epoch, layer count, samples per layer, edge
+ * limit, own cost and the best cost after it (+inf while infeasible). */
+typedef struct {
+  int32_t epoch, L, M;
+  float edge_limit, stage_cost, best_cost;
+} gtmp_ao_stage;
+
+/* Runs the schedule from scratch (c = +inf) on graph 0 (single goal).
+ * dev_best_chain device [capacity + 2][dof] float32 receives the best chain
+ * as configurations q0, ..., qg (rows past qg NaN; the epoch that found it
+ * may have fewer layers than the last one), dev_best_cost device [1] its
+ * cost, log host [stages] one record per stage, *best_layers host the layer
+ * count of the best chain (0 if none).  Reads the best cost back after every
+ * stage (the epoch rule needs it); leaves the context at the last epoch's
+ * layer count and samples. */
+GTMP_API gtmp_status aogtmp_run(gtmp_ctx* ctx, uint64_t seed, const gtmp_ao_schedule* schedule, float* dev_best_chain,
+                                float* dev_best_cost, gtmp_ao_stage* log, int32_t* best_layers);
+
 /* Launch accounting and kernel timing (library instrumentation; the paper
  * reports no such facility).  Every kernel the context enqueues increments
  * `launches`.  While timing is enabled, CUDA events bracket each fused

@@ -383,6 +383,74 @@ def anytime(scene, seed, R, L, M, H, eps=EPS_DEFAULT, bumps=None):
 
 
 # ---------------------------------------------------------------------------
+# AO-GTMP epochs (Sec. IV-D) and the edge-length limit l_M(r) (Sec. V).
+# Within an epoch the layer count is fixed and the samples per layer double
+# each stage up to a cap; a new epoch (fresh samples, Philox seed + epoch)
+# starts when the layer rule L + 1 >= c / (reach - 2r - varsigma) fails for
+# the best cost c, or when the samples have reached their cap.  The limit of
+# a stage is l = L_ref / (L + 1) + 2r + varsigma with the best cost so far
+# standing in for the reference length.  The float32 values that decide
+# edges (the limit) or samples (the informed bound) are formed exactly as the
+# CUDA driver forms them: double arithmetic, one rounding to float32.
+# ---------------------------------------------------------------------------
+
+def _margin(r, varsigma):
+    return 2.0 * float(np.float32(r)) + float(np.float32(varsigma))
+
+
+def ao_edge_limit(c_best, L, r, varsigma, base=math.inf):
+    """Edge-length limit of a stage with L layers (L + 1 edges per chain): l_M(r) of Sec. V, capped by `base`;
+    `base` itself while no chain has been found."""
+    base = np.float32(base)
+    if not math.isfinite(float(c_best)):
+        return base
+    l = np.float32(float(np.float32(c_best)) / (L + 1) + _margin(r, varsigma))
+    return l if l < base else base
+
+
+def ao_next(L, M, c_best, L_cap, M0, M_max, reach, r, varsigma):
+    """(L', M', new_epoch) after a stage: the layer rule of Sec. IV-D first, then saturation of the samples,
+    else the samples double."""
+    c = float(np.float32(c_best))
+    if math.isfinite(float(np.float32(reach))) and math.isfinite(c) and L < L_cap:
+        need = math.ceil(c / (float(np.float32(reach)) - _margin(r, varsigma))) - 1
+        if need > L:
+            return min(max(need, L + 1), L_cap), M0, True
+    if M >= M_max:
+        return min(L + 1, L_cap), M0, True
+    return L, min(2 * M, M_max), False
+
+
+def ao_run(scene, seed, L0, M0, M_max, stages, H, L_cap, reach=math.inf, r=0.0, varsigma=0.0, limit_edges=False,
+           base_limit=math.inf, best_feed=None):
+    """AO-GTMP with epochs on the oracle's own solves.  `best_feed[k]` (float32 best cost after stage k, e.g.
+    the GPU's) replaces the oracle's own running best where given, so both sides draw the same informed
+    samples; the log records what the oracle computed."""
+    dof = scene.robot.dof
+    log = []
+    epoch, L, M = 0, L0, M0
+    Q = np.zeros((L, 0, dof), np.float32)
+    best_own = math.inf
+    c_before = np.float32(np.inf)
+    for k in range(stages):
+        limit = ao_edge_limit(c_before, L, r, varsigma, base_limit) if limit_edges else np.float32(base_limit)
+        st, Q = expand_layers((seed + epoch) % (1 << 64), Q, M, scene.q_start, scene.q_goal, scene.robot.q_lo,
+                              scene.robot.q_hi, np.float32(c_before))
+        sol = solve(scene, Q, H, max_len=float(limit))
+        best_own = min(best_own, sol.cost_lo)
+        c_after = np.float32(best_feed[k]) if best_feed is not None else np.float32(best_own)
+        log.append(dict(epoch=epoch, L=L, M=M, edge_limit=limit, status=st, solution=sol, Q=Q,
+                        stage_cost=sol.cost_lo, stage_cost_hi=sol.cost_hi, best_cost=best_own))
+        L2, M2, new = ao_next(L, M, c_after, L_cap, M0, M_max, reach, r, varsigma)
+        if new:
+            epoch += 1
+            Q = np.zeros((L2, 0, dof), np.float32)
+        L, M = L2, M2
+        c_before = c_after
+    return log
+
+
+# ---------------------------------------------------------------------------
 # Class-augmented value iteration (Prop. 1; Alg. 1 with a class-indexed archive)
 # for planar scenes.  Label of a start-to-goal chain: the winding numbers of
 # the closed loop (chain, then the straight segment qg -> q0) about every

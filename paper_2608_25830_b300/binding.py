@@ -72,6 +72,17 @@ class GtmpPruneStats(ctypes.Structure):
                 ("solve_ms", ctypes.c_float), ("scored", ctypes.c_double)]
 
 
+class GtmpAoSchedule(ctypes.Structure):
+    _fields_ = [("L0", ctypes.c_int32), ("M0", ctypes.c_int32), ("M_max", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("reach", ctypes.c_float), ("r", ctypes.c_float), ("varsigma", ctypes.c_float),
+                ("limit_edges", ctypes.c_int32)]
+
+
+class GtmpAoStage(ctypes.Structure):
+    _fields_ = [("epoch", ctypes.c_int32), ("L", ctypes.c_int32), ("M", ctypes.c_int32), ("edge_limit", ctypes.c_float),
+                ("stage_cost", ctypes.c_float), ("best_cost", ctypes.c_float)]
+
+
 class GtmpProblem(ctypes.Structure):
     _fields_ = [("robot", GtmpRobot), ("spheres", _fp), ("n_s", ctypes.c_int32), ("boxes", _fp),
                 ("n_b", ctypes.c_int32), ("q_start", _fp), ("q_goal", _fp), ("M", ctypes.c_int32),
@@ -94,6 +105,10 @@ _SIGNATURES = {
     "gtmp_get_edge_costs": [_vp, _i32, _vp],
     "gtmp_anytime": [_vp, _u64, _i32, _vp, _vp, _vp],
     "aogtmp_expand": [_vp, _u64, _i32, _vp, _vp, _vp, _vp],
+    "gtmp_set_num_layers": [_vp, _i32],
+    "gtmp_set_max_edge_len": [_vp, ctypes.c_float],
+    "aogtmp_run": [_vp, _u64, ctypes.POINTER(GtmpAoSchedule), _vp, _vp, ctypes.POINTER(GtmpAoStage),
+                   ctypes.POINTER(_i32)],
     "gtmp_get_M": [_vp, ctypes.POINTER(_i32)],
     "gtmp_profile_enable": [_vp, _i32],
     "gtmp_profile_read": [_vp, ctypes.POINTER(GtmpProfile)],
@@ -281,6 +296,26 @@ def aogtmp_expand(ctx, seed, M_new, dev_stage_path, dev_stage_cost, dev_best_pat
                                     _dev(dev_best_cost, torch.float32)))
 
 
+def gtmp_set_num_layers(ctx, L):
+    _check(ctx, lib().gtmp_set_num_layers(ctx, L))
+
+
+def gtmp_set_max_edge_len(ctx, max_edge_len):
+    _check(ctx, lib().gtmp_set_max_edge_len(ctx, max_edge_len))
+
+
+def aogtmp_run(ctx, seed, schedule, dev_best_chain, dev_best_cost):
+    """AO-GTMP with epochs; returns (per-stage records as dicts, layer count of the best chain)."""
+    import torch
+    log = (GtmpAoStage * schedule.stages)()
+    best_layers = _i32()
+    _check(ctx, lib().aogtmp_run(ctx, seed, ctypes.byref(schedule), _dev(dev_best_chain, torch.float32),
+                                 _dev(dev_best_cost, torch.float32), log, ctypes.byref(best_layers)))
+    recs = [dict(epoch=x.epoch, L=x.L, M=x.M, edge_limit=x.edge_limit, stage_cost=x.stage_cost,
+                 best_cost=x.best_cost) for x in log]
+    return recs, best_layers.value
+
+
 def gtmp_profile_enable(ctx, enable=True):
     _check(ctx, lib().gtmp_profile_enable(ctx, 1 if enable else 0))
 
@@ -330,6 +365,7 @@ class Planner:
                  max_edge_len=math.inf):
         import torch
         self.robot, self.M, self.L, self.H, self.R = robot, M, L, H, R
+        self.L_cap = L   # capacity; self.L follows gtmp_set_num_layers
         self.dev = torch.device("cuda")
         self.ctx = gtmp_create(robot, M, L, H, R, max_obstacles, eval_mode, max_edge_len)
 
@@ -348,6 +384,21 @@ class Planner:
         gtmp_set_obstacles(self.ctx, scene.spheres, scene.boxes)
         self.n_obstacles = int(np.asarray(scene.spheres).shape[0] + np.asarray(scene.boxes).shape[0])
         gtmp_set_endpoints(self.ctx, scene.q_start, scene.q_goal)
+
+    def ao_run(self, seed, L0, M0, M_max, stages, reach=math.inf, r=0.0, varsigma=0.0, limit_edges=False):
+        """AO-GTMP with epochs: (best chain [L capacity + 2][dof] device, best cost device [1], stage log,
+        layer count of the best chain)."""
+        import torch
+        sched = GtmpAoSchedule(L0, M0, M_max, stages, reach, r, varsigma, 1 if limit_edges else 0)
+        chain = torch.empty((self.L_cap + 2, self.robot.dof), dtype=torch.float32, device="cuda")
+        cost = torch.empty(1, dtype=torch.float32, device="cuda")
+        log, best_layers = aogtmp_run(self.ctx, seed, sched, chain, cost)
+        self.L = log[-1]["L"]
+        return chain, cost, log, best_layers
+
+    def set_num_layers(self, L):
+        gtmp_set_num_layers(self.ctx, L)
+        self.L = L
 
     def set_cost_weight(self, bumps):
         gtmp_set_cost_weight(self.ctx, bumps)

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -64,6 +65,26 @@ SceneDev scene(gtmp_ctx* c) {
   SceneDev s = c->sc;
   s.obs = c->obs;
   return s;
+}
+
+// q0 into layer 0 and the goal set into layer L + 1 of every graph, from the
+// host copies (called again when the layer count changes)
+gtmp_status upload_terminals(gtmp_ctx* c) {
+  const int G = c->G;
+  std::vector<float> s(static_cast<size_t>(c->p.R) * c->dp, 0.0f), g(static_cast<size_t>(c->p.R) * G * c->dp, 0.0f);
+  for (int r = 0; r < c->p.R; ++r) {
+    for (int k = 0; k < c->dof; ++k) s[static_cast<size_t>(r) * c->dp + k] = c->host_start[k];
+    for (int i = 0; i < G; ++i)
+      for (int k = 0; k < c->dof; ++k)
+        g[(static_cast<size_t>(r) * G + i) * c->dp + k] = c->host_goals[static_cast<size_t>(i) * c->dof + k];
+  }
+  const size_t graph_stride = static_cast<size_t>(c->p.L + 2) * c->p.M * c->dp * sizeof(float);
+  const size_t row = c->dp * sizeof(float), width = static_cast<size_t>(G) * row;
+  CUDA_TRY(c, cudaMemcpy2DAsync(c->Q, graph_stride, s.data(), row, row, c->p.R, cudaMemcpyHostToDevice, c->stream));
+  float* dst = c->Q + static_cast<size_t>(c->p.L + 1) * c->p.M * c->dp;
+  CUDA_TRY(c, cudaMemcpy2DAsync(dst, graph_stride, g.data(), width, width, c->p.R, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return GTMP_OK;
 }
 
 bool uses_prefilter(int variant) { return variant == kVarArm6x4 || variant == kVarArm7x4; }
@@ -270,6 +291,7 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
 
   gtmp_ctx* c = new gtmp_ctx();
   c->p = p;
+  c->L_cap = p.L;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->dof = robot->dof;
   // --- robot constants
@@ -370,6 +392,7 @@ gtmp_status gtmp_destroy(gtmp_ctx* c) {
   cudaFree(c->cls);
   cudaFree(c->gval);
   cudaFree(c->wb);
+  cudaFree(c->ao_scratch);
   cudaFree(c->prune);
   surrogate_free(c->sur);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -462,25 +485,13 @@ gtmp_status gtmp_set_endpoints(gtmp_ctx* c, const float* q_start, const float* q
     if (q_start[k] < c->q_lo[k] || q_start[k] > c->q_hi[k] || q_goal[k] < c->q_lo[k] || q_goal[k] > c->q_hi[k])
       return fail(c, GTMP_ERR_INVALID_ARG, "endpoint outside the joint box (coordinate %d)", k);
   }
-  std::vector<float> s(static_cast<size_t>(c->p.R) * c->dp, 0.0f), g(s.size(), 0.0f);
-  for (int r = 0; r < c->p.R; ++r)
-    for (int k = 0; k < c->dof; ++k) {
-      s[static_cast<size_t>(r) * c->dp + k] = q_start[k];
-      g[static_cast<size_t>(r) * c->dp + k] = q_goal[k];
-    }
-  const size_t graph_stride = static_cast<size_t>(c->p.L + 2) * c->p.M * c->dp * sizeof(float);
-  const size_t row = c->dp * sizeof(float);
-  for (int which = 0; which < 2; ++which) {
-    const int layer = which == 0 ? 0 : c->p.L + 1;
-    float* dst = c->Q + static_cast<size_t>(layer) * c->p.M * c->dp;
-    CUDA_TRY(c, cudaMemcpy2DAsync(dst, graph_stride, which == 0 ? s.data() : g.data(), row, row, c->p.R,
-                                  cudaMemcpyHostToDevice, c->stream));
-  }
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  c->have_endpoints = true;
+  c->host_start.assign(q_start, q_start + c->dof);
+  c->host_goals.assign(q_goal, q_goal + c->dof);
   c->G = 1;
   c->goal_values = false;
-  return GTMP_OK;
+  gtmp_status st = upload_terminals(c);
+  if (st == GTMP_OK) c->have_endpoints = true;
+  return st;
 }
 
 gtmp_status gtmp_set_goals(gtmp_ctx* c, const float* goals, const float* values, int32_t G) {
@@ -496,22 +507,34 @@ gtmp_status gtmp_set_goals(gtmp_ctx* c, const float* goals, const float* values,
     if (values && !(std::isfinite(values[i]) && values[i] >= 0.0f))
       return fail(c, GTMP_ERR_INVALID_ARG, "goal value %d must be finite and >= 0", i);
   }
-  std::vector<float> g(static_cast<size_t>(c->p.R) * G * c->dp, 0.0f);
-  for (int r = 0; r < c->p.R; ++r)
-    for (int i = 0; i < G; ++i)
-      for (int k = 0; k < c->dof; ++k)
-        g[(static_cast<size_t>(r) * G + i) * c->dp + k] = goals[static_cast<size_t>(i) * c->dof + k];
-  const size_t graph_stride = static_cast<size_t>(c->p.L + 2) * c->p.M * c->dp * sizeof(float);
-  const size_t width = static_cast<size_t>(G) * c->dp * sizeof(float);
-  float* dst = c->Q + static_cast<size_t>(c->p.L + 1) * c->p.M * c->dp;
-  CUDA_TRY(c, cudaMemcpy2DAsync(dst, graph_stride, g.data(), width, width, c->p.R, cudaMemcpyHostToDevice, c->stream));
   if (values) {
     if (!c->gval) CUDA_TRY(c, cudaMalloc(&c->gval, static_cast<size_t>(c->p.M) * sizeof(float)));
     CUDA_TRY(c, cudaMemcpyAsync(c->gval, values, G * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   }
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->host_goals.assign(goals, goals + static_cast<size_t>(G) * c->dof);
   c->G = G;
   c->goal_values = values != nullptr;
+  return upload_terminals(c);
+}
+
+gtmp_status gtmp_set_num_layers(gtmp_ctx* c, int32_t L) {
+  if (!c) return GTMP_ERR_INVALID_ARG;
+  if (L < 1 || L > c->L_cap) return fail(c, GTMP_ERR_INVALID_ARG, "layer count %d outside [1, %d]", L, c->L_cap);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->p.L = L;
+  c->M_active = 0;  // the samples of the old layout are gone
+  cudaFree(c->C);   // stored cost matrices are laid out per transition
+  c->C = nullptr;
+  c->c_off.clear();
+  c->c_cs.clear();
+  return c->have_endpoints ? upload_terminals(c) : GTMP_OK;
+}
+
+gtmp_status gtmp_set_max_edge_len(gtmp_ctx* c, float max_edge_len) {
+  if (!c) return GTMP_ERR_INVALID_ARG;
+  if (std::isnan(max_edge_len) || !(max_edge_len > 0.0f))
+    return fail(c, GTMP_ERR_INVALID_ARG, "edge-length limit must be > 0 (+inf: none)");
+  c->p.max_edge_len = max_edge_len;
   return GTMP_OK;
 }
 
@@ -750,6 +773,92 @@ gtmp_status aogtmp_expand(gtmp_ctx* c, uint64_t seed, int32_t M_new, int32_t* de
   CUDA_TRY(c, launch_update_best(c->p.L, dev_stage_path, dev_stage_cost, dev_best_path, dev_best_cost, c->stream));
   LAUNCHED(c, 2);
   return GTMP_OK;
+}
+
+gtmp_status aogtmp_run(gtmp_ctx* c, uint64_t seed, const gtmp_ao_schedule* sch, float* dev_best_chain,
+                       float* dev_best_cost, gtmp_ao_stage* log, int32_t* best_layers) {
+  if (!c || !sch || !dev_best_chain || !dev_best_cost || !log || !best_layers)
+    return fail(c, GTMP_ERR_INVALID_ARG, "NULL argument");
+  const gtmp_ao_schedule S = *sch;
+  const double margin = 2.0 * static_cast<double>(S.r) + static_cast<double>(S.varsigma);
+  if (S.L0 < 1 || S.L0 > c->L_cap || S.M0 < 1 || S.M_max < S.M0 || S.M_max > c->p.M || S.stages < 1 ||
+      std::isnan(S.reach) || !(S.r >= 0.0f) || !(S.varsigma >= 0.0f) || !std::isfinite(S.r) ||
+      !std::isfinite(S.varsigma) || !(static_cast<double>(S.reach) > margin))
+    return fail(c, GTMP_ERR_INVALID_ARG, "schedule outside its ranges (L0 1..%d, M0 <= M_max <= %d, reach > 2r + "
+                "varsigma)", c->L_cap, c->p.M);
+  if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "endpoints not set");
+  if (c->G != 1) return fail(c, GTMP_ERR_UNSUPPORTED, "informed expansion is defined for a single goal");
+  if (!c->ao_scratch) CUDA_TRY(c, cudaMalloc(&c->ao_scratch, (2 * static_cast<size_t>(c->L_cap) + 2) * sizeof(int32_t)));
+  int32_t* stage_path = c->ao_scratch;
+  int32_t* best_path = c->ao_scratch + c->L_cap;
+  float* stage_cost = reinterpret_cast<float*>(c->ao_scratch + 2 * c->L_cap);
+  const float inf = std::numeric_limits<float>::infinity();
+  const float limit0 = c->p.max_edge_len;
+  const int rows = c->L_cap + 2;
+  CUDA_TRY(c, cudaMemcpyAsync(dev_best_cost, &inf, sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  *best_layers = 0;
+  double best = std::numeric_limits<double>::infinity();
+  int epoch = 0, L = S.L0, M = S.M0;
+  gtmp_status st = gtmp_set_num_layers(c, L);
+  for (int stage = 0; st == GTMP_OK && stage < S.stages; ++stage) {
+    float limit = limit0;
+    if (S.limit_edges && std::isfinite(best)) {
+      const float l = static_cast<float>(best / (L + 1) + margin);
+      limit = l < limit0 ? l : limit0;
+    }
+    c->p.max_edge_len = limit;
+    st = aogtmp_expand(c, seed + static_cast<uint64_t>(epoch), M, stage_path, stage_cost, best_path, dev_best_cost);
+    if (st != GTMP_OK) break;
+    float h[2];
+    if (cudaMemcpyAsync(&h[0], stage_cost, sizeof(float), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&h[1], dev_best_cost, sizeof(float), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      st = fail(c, GTMP_ERR_CUDA, "reading the stage cost back failed");
+      break;
+    }
+    if (static_cast<double>(h[0]) < best) {  // this stage found the new best chain: keep its configurations
+      GraphDev g = graph(c, 1, M);
+      if (launch_gather_chain(g, stage_path, dev_best_chain, c->dof, rows, c->stream) != cudaSuccess) {
+        st = fail(c, GTMP_ERR_CUDA, "chain gather launch failed");
+        break;
+      }
+      LAUNCHED(c, 1);
+      *best_layers = L;
+    }
+    best = h[1];
+    log[stage] = gtmp_ao_stage{epoch, L, M, limit, h[0], h[1]};
+    // next stage: the layer rule, then saturation, else double the samples
+    int L_next = L;
+    bool new_epoch = false;
+    if (std::isfinite(S.reach) && std::isfinite(best) && L < c->L_cap) {
+      const double need = std::ceil(best / (static_cast<double>(S.reach) - margin)) - 1.0;
+      if (need > L) {
+        L_next = need > L + 1 ? (need < c->L_cap ? static_cast<int>(need) : c->L_cap) : L + 1;
+        new_epoch = true;
+      }
+    }
+    if (!new_epoch && M >= S.M_max) {
+      L_next = L + 1;
+      new_epoch = true;
+    }
+    if (new_epoch) {
+      L = L_next < c->L_cap ? L_next : c->L_cap;
+      M = S.M0;
+      ++epoch;
+      if (stage + 1 < S.stages) st = gtmp_set_num_layers(c, L);
+    } else {
+      M = 2 * M < S.M_max ? 2 * M : S.M_max;
+    }
+  }
+  c->p.max_edge_len = limit0;
+  if (st == GTMP_OK && *best_layers == 0) {
+    // no feasible chain: every row NaN
+    std::vector<float> nan(static_cast<size_t>(rows) * c->dof, std::numeric_limits<float>::quiet_NaN());
+    CUDA_TRY(c, cudaMemcpyAsync(dev_best_chain, nan.data(), nan.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  return st;
 }
 
 }  // extern "C"

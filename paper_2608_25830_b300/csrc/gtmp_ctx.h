@@ -43,6 +43,12 @@ struct gtmp_ctx {
   int G = 1;
   float* gval = nullptr;  // [p.M] device, valid when goal_values is set
   bool goal_values = false;
+  // layer capacity (gtmp_create's L); p.L is the active layer count (gtmp_set_num_layers)
+  int L_cap = 0;
+  // host copies of the start and the goal set, re-uploaded when the layer count changes
+  std::vector<float> host_start, host_goals;
+  // aogtmp_run scratch (device): stage path, best path [L_cap] int32, stage cost, best cost
+  int32_t* ao_scratch = nullptr;
   // weighted-length edge cost: n_wb bumps in the GraphDev layout (null/0: plain length)
   float4* wb = nullptr;
   int n_wb = 0;

@@ -544,6 +544,24 @@ __global__ void update_best_kernel(int L, const int32_t* cand_path, const float*
   }
 }
 
+// The chain q0, Q[1][path[0]], ..., Q[L][path[L-1]], qg of graph 0 as
+// configurations: chain[row][dof], rows = L_cap + 2, rows past qg (and any
+// row of an infeasible path) NaN.
+__global__ void gather_chain_kernel(GraphDev g, const int32_t* path, float* chain, int dof, int rows) {
+  const int row = blockIdx.x, k = threadIdx.x;
+  if (row >= rows || k >= dof) return;
+  float v = __int_as_float(0x7fc00000);
+  if (row == 0) {
+    v = g.Q[vidx(g, 0, 0, 0) * g.dp + k];
+  } else if (row <= g.L) {
+    const int i = path[row - 1];
+    if (i >= 0 && i < g.M) v = g.Q[vidx(g, 0, row, i) * g.dp + k];
+  } else if (row == g.L + 1) {
+    v = g.Q[vidx(g, 0, g.L + 1, 0) * g.dp + k];
+  }
+  chain[static_cast<size_t>(row) * dof + k] = v;
+}
+
 inline int blocks_for(long long n, int threads) { return static_cast<int>((n + threads - 1) / threads); }
 
 Box16 make_box(const float* lo, const float* hi, int dof) {
@@ -989,6 +1007,12 @@ cudaError_t launch_expand(const GraphDev& g, int dof, const float* lo, const flo
   if (n <= 0) return cudaSuccess;
   expand_kernel<<<blocks_for(n, 128), 128, 0, st>>>(g, dof, make_box(lo, hi, dof), seed, M_old, M_new, c_best,
                                                     max_attempts, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_chain(const GraphDev& g, const int32_t* path, float* chain, int dof, int rows,
+                                cudaStream_t st) {
+  gather_chain_kernel<<<rows, 32, 0, st>>>(g, path, chain, dof, rows);
   return cudaGetLastError();
 }
 

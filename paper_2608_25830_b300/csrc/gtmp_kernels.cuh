@@ -100,6 +100,8 @@ cudaError_t launch_edge_costs(const GraphDev& g, int layer, const RobotDev& rb, 
 cudaError_t launch_minplus(const GraphDev& g, int layer, const float* C, int cs, int grid, cudaStream_t st);
 cudaError_t launch_expand(const GraphDev& g, int dof, const float* lo, const float* hi, unsigned long long seed,
                           int M_old, int M_new, const float* c_best, int max_attempts, int* err, cudaStream_t st);
+cudaError_t launch_gather_chain(const GraphDev& g, const int32_t* path, float* chain, int dof, int rows,
+                                cudaStream_t st);
 cudaError_t launch_update_best(int L, const int32_t* cand_path, const float* cand_cost, int32_t* best_path,
                                float* best_cost, cudaStream_t st);
 

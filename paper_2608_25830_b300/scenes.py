@@ -196,7 +196,9 @@ WORKLOADS = {
     "point2d_m32_l4_h16": dict(kind="point2d", seed=0, n_obs=10, M=32, L=4, H=16),
     "arm7_m1024_l8_h32": dict(kind="arm", dof=7, seed=0, n_obs=30, M=1024, L=8, H=32),
     "arm6_anytime_r64_m256_l6_h32": dict(kind="arm", dof=6, seed=0, n_obs=30, M=256, L=6, H=32, R=64),
-    "arm6_ao_m64to4096_l6_h32": dict(kind="arm", dof=6, seed=0, n_obs=30, M0=64, M1=4096, L=6, H=32),
+    "arm6_ao_m64to4096_l6_h32": dict(kind="arm", dof=6, seed=0, n_obs=30, M0=64, M1=4096, L=6, H=32,
+                                     epochs=dict(L0=2, L_cap=8, M0=64, M_max=2048, stages=14, reach=2.5, r=0.1,
+                                                 varsigma=0.1, limit_edges=True)),
     "arm7_m4096_l8_h32_n40": dict(kind="arm", dof=7, seed=0, n_obs=40, M=4096, L=8, H=32,
                                   n_train=1 << 21, epochs=3, sigma=0.25, threshold=0.5, score_waypoints=1),
     "batched512_h32": dict(kind="batched", seed=0, n=512, H=32),

@@ -738,3 +738,60 @@ def test_weighted_value_iteration_equals_brute_force(seed):
         assert tuple(sol.path) == best_chain
         total, _ = oracle.path_cost(sc, Q, sol.path, H, bumps=b)
         assert total == pytest.approx(best, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# AO-GTMP epochs (Sec. IV-D) and the edge limit l_M(r) (Sec. V): hand values
+# ---------------------------------------------------------------------------
+
+def test_ao_edge_limit_hand_values():
+    # c = 6 over L + 1 = 3 edges, 2r + varsigma = 1: l = 2 + 1 = 3
+    assert oracle.ao_edge_limit(6.0, 2, 0.25, 0.5) == np.float32(3.0)
+    assert oracle.ao_edge_limit(6.0, 2, 0.25, 0.5, base=2.5) == np.float32(2.5)   # the context's own limit caps it
+    assert oracle.ao_edge_limit(np.inf, 2, 0.25, 0.5, base=7.0) == np.float32(7.0)  # no chain yet
+    assert oracle.ao_edge_limit(10.0, 4, 0.0, 0.0) == np.float32(2.0)              # r = varsigma = 0: c / (L + 1)
+
+
+def test_ao_schedule_saturation_without_a_reach():
+    """reach = +inf: epochs end only when the samples reach their cap, then one more layer."""
+    seq, L, M = [], 2, 8
+    for _ in range(7):
+        seq.append((L, M))
+        L, M, _ = oracle.ao_next(L, M, 3.0, 5, 8, 32, math.inf, 0.1, 0.1)
+    assert seq == [(2, 8), (2, 16), (2, 32), (3, 8), (3, 16), (3, 32), (4, 8)]
+    assert oracle.ao_next(5, 32, 3.0, 5, 8, 32, math.inf, 0.0, 0.0) == (5, 8, True)   # at capacity: fresh epoch
+
+
+def test_ao_schedule_layer_rule_hand_values():
+    # reach 3, 2r + varsigma = 1: a chain of cost c needs L + 1 >= c / 2 edges
+    assert oracle.ao_next(2, 8, 9.0, 8, 8, 64, 3.0, 0.25, 0.5) == (4, 8, True)     # ceil(4.5) - 1 = 4 > 2
+    assert oracle.ao_next(2, 8, 5.5, 8, 8, 64, 3.0, 0.25, 0.5) == (2, 16, False)   # ceil(2.75) - 1 = 2: holds
+    assert oracle.ao_next(2, 8, 6.5, 8, 8, 64, 3.0, 0.25, 0.5) == (3, 8, True)     # ceil(3.25) - 1 = 3
+    assert oracle.ao_next(2, 8, 40.0, 6, 8, 64, 3.0, 0.25, 0.5) == (6, 8, True)    # clamped to the capacity
+    assert oracle.ao_next(6, 8, 40.0, 6, 8, 64, 3.0, 0.25, 0.5) == (6, 16, False)  # at capacity the rule rests
+    assert oracle.ao_next(2, 8, math.inf, 8, 8, 64, 3.0, 0.25, 0.5) == (2, 16, False)  # no chain yet
+
+
+def test_ao_run_epochs_on_a_planar_scene():
+    """The oracle's own run: best cost non-increasing, epochs exactly where the rules put them, every edge of
+    each stage's chain within that stage's limit, fresh samples at each epoch."""
+    sc = scenes.point2d_scene(3, 8)
+    sched = dict(L0=1, M0=4, M_max=16, stages=7, reach=1.2, r=0.05, varsigma=0.05, limit_edges=True)
+    log = oracle.ao_run(sc, 5, H=16, L_cap=5, **sched)
+    best = math.inf
+    for k, rec in enumerate(log):
+        assert rec["status"] == 0
+        assert rec["best_cost"] <= best
+        best = rec["best_cost"]
+        if k + 1 < len(log):
+            nxt = log[k + 1]
+            L2, M2, new = oracle.ao_next(rec["L"], rec["M"], np.float32(best), 5, 4, 16, 1.2, 0.05, 0.05)
+            assert (nxt["L"], nxt["M"], nxt["epoch"] == rec["epoch"] + 1) == (L2, M2, new)
+            if not new:   # within an epoch the samples are kept (nested graphs)
+                np.testing.assert_array_equal(nxt["Q"][:, :rec["M"]], rec["Q"])
+        sol = rec["solution"]
+        if math.isfinite(sol.cost_lo):
+            verts = [sc.q_start] + [rec["Q"][l, sol.path[l]] for l in range(rec["L"])] + [sc.q_goal]
+            for a, b in zip(verts[:-1], verts[1:]):
+                assert np.linalg.norm(b.astype(np.float64) - a) <= float(rec["edge_limit"]) * (1 + 1e-7)
+    assert len({r["epoch"] for r in log}) >= 2
