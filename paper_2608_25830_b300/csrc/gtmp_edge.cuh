@@ -311,42 +311,92 @@ __device__ __forceinline__ unsigned long long row_chunk_best(const GraphDev& g, 
   float qi[DP];
   load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
   const int n_cols = layer_size(g, layer + 1);
-  for (int j = j0; j < j1; ++j) {
-    const float Vj = s_V[j];
-    if (!FULL && !(Vj < kInf)) continue;
-    if (g.prune && g.prune[static_cast<size_t>(i) * n_cols + j]) continue;  // dropped by the surrogate
-    float qj[DP];
-    load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp);
-    float dq[DP];
-    float s2 = 0.0f;
+  if constexpr (FULL) {
+    // Full evaluation has no early exit, so the warp need not stay on one
+    // edge: the (edge, waypoint) items of up to 32 columns are dealt to the
+    // lanes in order (no lane idles when H - 2 is not a multiple of 32), each
+    // lane's label is OR-ed into its edge's bit, then lane e keys edge e.
+    const int nw = H - 2;
+    for (int jb = j0; jb < j1; jb += 32) {
+      const int n_edges = min(32, j1 - jb);
+      const int n_items = n_edges * nw;
+      unsigned hit_mask = 0u;
+      for (int t0 = 0; t0 < n_items; t0 += 32) {
+        const int t = t0 + lane;
+        const bool active = t < n_items;
+        const int e = active ? t / nw : 0;
+        const int k = active ? t - e * nw + 1 : 1;
+        float qj[DP];
+        load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, jb + e) * g.dp, g.dp);
+        const float tt = __fdiv_rn(static_cast<float>(k), steps);
+        float q[DP];
 #pragma unroll
-    for (int d = 0; d < DP; ++d) {
-      dq[d] = __fsub_rn(qj[d], qi[d]);
-      s2 = __fmaf_rn(dq[d], dq[d], s2);
-    }
-    const float len = __fsqrt_rn(s2);
-    const bool too_long = len > g.max_edge_len;
-    if (!FULL && too_long) continue;
-    bool hit = false;
-    for (int kb = 1; kb <= H - 2; kb += 32) {
-      const int k = kb + lane;
-      const bool active = k <= H - 2;
-      const float t = __fdiv_rn(static_cast<float>(k), steps);
-      float q[DP];
+        for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(tt, __fsub_rn(qj[d], qi[d]), qi[d]);
+        const bool h = config_collides<VAR, false, true>(q, active, rb, s_obs, sc) && active;
+        hit_mask |= __reduce_or_sync(kFull, h ? (1u << e) : 0u);
+      }
+      unsigned long long key = kEmptyKey;
+      if (lane < n_edges) {
+        const int j = jb + lane;
+        const float Vj = s_V[j];
+        float qj[DP];
+        load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp);
+        float s2 = 0.0f;
 #pragma unroll
-      for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
-      hit |= config_collides<VAR, true, FULL>(q, active, rb, s_obs, sc);
-      if (!FULL && hit) break;
-    }
-    if (!hit && !too_long && !row_hit && Vj < kInf) {
-      float cost = len;
-      if constexpr (WEIGHTED)
-        cost = weighted_cost_warp<DP>(qi, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp, dq, len, g, lane);
-      const unsigned long long key = make_key(__fadd_rn(cost, Vj), static_cast<uint32_t>(j));
+        for (int d = 0; d < DP; ++d) {
+          const float e = __fsub_rn(qj[d], qi[d]);
+          s2 = __fmaf_rn(e, e, s2);
+        }
+        const float len = __fsqrt_rn(s2);
+        const bool pruned = g.prune && g.prune[static_cast<size_t>(i) * n_cols + j];
+        if (!((hit_mask >> lane) & 1u) && !(len > g.max_edge_len) && !row_hit && Vj < kInf && !pruned) {
+          float cost = len;
+          if constexpr (WEIGHTED) cost = weighted_cost_thread<DP>(qi, qj, len, g);
+          key = make_key(__fadd_rn(cost, Vj), static_cast<uint32_t>(j));
+        }
+      }
+      key = warp_min_u64(key);
       best = key < best ? key : best;
     }
+    return best;
+  } else {
+    // early exit: the warp's lanes carry the interior waypoints of one edge
+    for (int j = j0; j < j1; ++j) {
+      const float Vj = s_V[j];
+      if (!(Vj < kInf)) continue;
+      if (g.prune && g.prune[static_cast<size_t>(i) * n_cols + j]) continue;  // dropped by the surrogate
+      float qj[DP];
+      load_vertex<DP>(qj, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp);
+      float dq[DP];
+      float s2 = 0.0f;
+#pragma unroll
+      for (int d = 0; d < DP; ++d) {
+        dq[d] = __fsub_rn(qj[d], qi[d]);
+        s2 = __fmaf_rn(dq[d], dq[d], s2);
+      }
+      const float len = __fsqrt_rn(s2);
+      if (len > g.max_edge_len) continue;
+      bool hit = false;
+      for (int kb = 1; kb <= H - 2; kb += 32) {
+        const int k = kb + lane;
+        const bool active = k <= H - 2;
+        const float t = __fdiv_rn(static_cast<float>(k), steps);
+        float q[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(t, dq[d], qi[d]);
+        hit |= config_collides<VAR, true, false>(q, active, rb, s_obs, sc);
+        if (hit) break;
+      }
+      if (!hit) {
+        float cost = len;
+        if constexpr (WEIGHTED)
+          cost = weighted_cost_warp<DP>(qi, g.Q + vidx(g, r, layer + 1, j) * g.dp, g.dp, dq, len, g, lane);
+        const unsigned long long key = make_key(__fadd_rn(cost, Vj), static_cast<uint32_t>(j));
+        best = key < best ? key : best;
+      }
+    }
+    return best;
   }
-  return best;
 }
 
 // ---------------------------------------------------------------------------
