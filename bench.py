@@ -203,7 +203,7 @@ class ClockSampler:
 # transition of this workload, from an ncu capture of this kernel (set back to None whenever the
 # kernel changes); the algorithmic bytes per launch are the two sample layers, the cost-to-go and
 # the obstacle table, about 0.1 MB, so HBM is not the bound
-FULL_MODE_DRAM_BYTES_PER_LAUNCH = 426752
+FULL_MODE_DRAM_BYTES_PER_LAUNCH = 107520
 
 
 def measured_peaks():
