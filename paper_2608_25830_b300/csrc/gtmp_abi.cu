@@ -360,7 +360,7 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
   c->n_counters = (p.L + 1) * p.R;
   alloc(reinterpret_cast<void**>(&c->counters), static_cast<size_t>(c->n_counters) * sizeof(int));
   // scalar table (<= 2 float4 per obstacle) or packed tables (<= 3 (n_s + n_b) + 8 float4)
-  alloc(reinterpret_cast<void**>(&c->obs), packed_table_capacity(p.max_obstacles) * sizeof(float4));
+  alloc(reinterpret_cast<void**>(&c->obs), (packed_table_capacity(p.max_obstacles) + kMaxGridCells / 4) * sizeof(float4));
   alloc(reinterpret_cast<void**>(&c->err), sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->Q, 0, graph_vertices * c->dp * sizeof(float), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
@@ -434,9 +434,17 @@ gtmp_status gtmp_set_obstacles(gtmp_ctx* c, const float* spheres, int32_t n_s, c
     for (int o = 0; o < n_b; ++o)
       for (int k = 0; k < 3; ++k)
         if (!(boxes[6 * o + 3 + k] >= boxes[6 * o + k])) return fail(c, GTMP_ERR_INVALID_ARG, "box with hi < lo");
-    host.resize(packed_table_capacity(n_s + n_b));
-    const int n4 = build_packed_tables(spheres, n_s, boxes, n_b, c->rb.r_uniform, arm_reach_bound(c->rb),
-                                       host.data(), &sc);
+    host.resize(packed_table_capacity(n_s + n_b) + kMaxGridCells / 4);
+    int n4 = build_packed_tables(spheres, n_s, boxes, n_b, c->rb.r_uniform, arm_reach_bound(c->rb), host.data(),
+                                 &sc);
+    // cull grid within the shared memory that keeps two edge-kernel blocks per SM
+    // (table + grid + the column layer's cost-to-go <= ~110 KB per block)
+    double R_link = 0.0;
+    for (int i = 0; i < c->dof; ++i) R_link = std::fmax(R_link, static_cast<double>(c->rb.lb[i].w));
+    const long long budget = (110LL * 1024 - 4LL * c->p.M - 16LL * n4 - 2048) / 4;
+    const int max_cells = static_cast<int>(std::min<long long>(kMaxGridCells, std::max<long long>(budget, 0)));
+    if (n4 + max_cells / 4 + 1 <= kMaxTableFloat4s)
+      n4 += build_cull_grid(spheres, n_s, boxes, n_b, R_link, max_cells, host.data() + n4, &sc);
     host.resize(n4);
   } else {
     host.resize(static_cast<size_t>(n_s) + 2 * static_cast<size_t>(n_b));

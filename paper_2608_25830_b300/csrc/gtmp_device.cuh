@@ -225,6 +225,48 @@ __device__ __forceinline__ bool prefilter_maybe(const float (&cx)[NS], const flo
 // (pairs past 64 are all reported near); a cleared obstacle cannot touch any
 // of the link's spheres, which all lie inside the ball.
 // ----------------------------------------------------------------------------
+// Uniform grid over the obstacles (see build_cull_grid): the cell holding a
+// link ball's centre gives the cull pairs that can reach the ball, a superset
+// of what link_cull_mask finds; points outside the grid reach no obstacle.
+struct CullGrid {
+  const unsigned* cells = nullptr;  // null: no grid
+  float lx = 0.0f, ly = 0.0f, lz = 0.0f, inv = 0.0f;
+  int nx = 0, ny = 0, nz = 0;
+};
+
+__device__ __forceinline__ unsigned grid_cell_mask(const CullGrid& gv, float x, float y, float z) {
+  const float fx = __fmul_rn(__fsub_rn(x, gv.lx), gv.inv);
+  const float fy = __fmul_rn(__fsub_rn(y, gv.ly), gv.inv);
+  const float fz = __fmul_rn(__fsub_rn(z, gv.lz), gv.inv);
+  if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < static_cast<float>(gv.nx) &&
+        fy < static_cast<float>(gv.ny) && fz < static_cast<float>(gv.nz)))
+    return 0u;
+  const int ix = min(static_cast<int>(fx), gv.nx - 1);
+  const int iy = min(static_cast<int>(fy), gv.ny - 1);
+  const int iz = min(static_cast<int>(fz), gv.nz - 1);
+  return gv.cells[(iz * gv.ny + iy) * gv.nx + ix];
+}
+
+// link_cull_mask restricted to the pairs set in sel (at most 32 pairs)
+__device__ __forceinline__ unsigned link_cull_mask_sel(float cx, float cy, float cz, float R,
+                                                       const float4* __restrict__ cull, unsigned sel) {
+  const float2 x2 = make_float2(cx, cx), y2 = make_float2(cy, cy), z2 = make_float2(cz, cz);
+  const float2 r2 = make_float2(R, R);
+  const float c2 = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
+  const float thr = __fmaf_rn(R, R, -c2);
+  unsigned mask = 0u;
+  while (sel) {
+    const int p = __ffs(sel) - 1;
+    sel &= sel - 1u;
+    const float4 A = cull[3 * p], B = cull[3 * p + 1], C = cull[3 * p + 2];
+    float2 t = __ffma2_rn(z2, make_float2(B.x, B.y),
+                          __ffma2_rn(y2, make_float2(A.z, A.w), __ffma2_rn(x2, make_float2(A.x, A.y), make_float2(B.z, B.w))));
+    t = __ffma2_rn(make_float2(C.x, C.y), r2, t);
+    if (fminf(t.x, t.y) < thr) mask |= 1u << p;
+  }
+  return mask;
+}
+
 __device__ __forceinline__ unsigned long long link_cull_mask(float cx, float cy, float cz, float R,
                                                              const float4* __restrict__ cull, int n_pairs) {
   const float2 x2 = make_float2(cx, cx), y2 = make_float2(cy, cy), z2 = make_float2(cz, cz);
@@ -398,7 +440,8 @@ __device__ __forceinline__ bool arm_config_collides(const float* q, bool active,
                                                     const float4* __restrict__ sph, int n_s,
                                                     const float4* __restrict__ box, int n_b,
                                                     const float4* __restrict__ pre = nullptr, int n_pairs = 0,
-                                                    const float4* __restrict__ cull = nullptr, int n_cull = 0) {
+                                                    const float4* __restrict__ cull = nullptr, int n_cull = 0,
+                                                    const CullGrid& grid = CullGrid()) {
   constexpr int NS = SPL_T > 0 ? SPL_T : kMaxSpl;
   constexpr int NQ = DOF_T > 0 ? DOF_T : kMaxDof;
   const int dof = DOF_T > 0 ? DOF_T : rb.dof;
@@ -452,11 +495,22 @@ __device__ __forceinline__ bool arm_config_collides(const float* q, bool active,
         const float lx = __fmaf_rn(lb.z, Z0, __fmaf_rn(lb.y, Y0, __fmaf_rn(lb.x, X0, T0)));
         const float ly = __fmaf_rn(lb.z, Z1, __fmaf_rn(lb.y, Y1, __fmaf_rn(lb.x, X1, T1)));
         const float lz = __fmaf_rn(lb.z, Z2, __fmaf_rn(lb.y, Y2, __fmaf_rn(lb.x, X2, T2)));
-        unsigned long long near = active ? link_cull_mask(lx, ly, lz, lb.w, cull, n_cull) : 0ull;
-        if (WARP_EXIT) {
-          const unsigned lo = __reduce_or_sync(kFull, static_cast<unsigned>(near));
-          const unsigned hi = n_cull > 32 ? __reduce_or_sync(kFull, static_cast<unsigned>(near >> 32)) : 0u;
-          near = (static_cast<unsigned long long>(hi) << 32) | lo;
+        unsigned long long near;
+        if (grid.cells != nullptr) {
+          // the grid cell first (one lookup), then the ball test on the pairs it keeps
+          unsigned sel = active ? grid_cell_mask(grid, lx, ly, lz) : 0u;
+          if (WARP_EXIT) sel = __reduce_or_sync(kFull, sel);
+          if (sel == 0u) continue;
+          unsigned m = active ? link_cull_mask_sel(lx, ly, lz, lb.w, cull, sel) : 0u;
+          if (WARP_EXIT) m = __reduce_or_sync(kFull, m);
+          near = m;
+        } else {
+          near = active ? link_cull_mask(lx, ly, lz, lb.w, cull, n_cull) : 0ull;
+          if (WARP_EXIT) {
+            const unsigned lo = __reduce_or_sync(kFull, static_cast<unsigned>(near));
+            const unsigned hi = n_cull > 32 ? __reduce_or_sync(kFull, static_cast<unsigned>(near >> 32)) : 0u;
+            near = (static_cast<unsigned long long>(hi) << 32) | lo;
+          }
         }
         if (near == 0ull) continue;
         if (n_cull <= 64 && n_s <= 32 && n_b <= 32) {

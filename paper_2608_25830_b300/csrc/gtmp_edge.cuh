@@ -116,8 +116,19 @@ __device__ __forceinline__ bool config_collides(const float* q, bool active, con
     const float4* boxp = s_obs + 2 * sc.n_sp;
     const float4* pre = boxp + 3 * sc.n_bp;
     const float4* cull = pre + 2 * sc.n_pairs;
+    CullGrid grid;
+    if (sc.gnx > 0) {
+      grid.cells = reinterpret_cast<const unsigned*>(s_obs + sc.g_off);
+      grid.lx = sc.glx;
+      grid.ly = sc.gly;
+      grid.lz = sc.glz;
+      grid.inv = sc.ginv;
+      grid.nx = sc.gnx;
+      grid.ny = sc.gny;
+      grid.nz = sc.gnz;
+    }
     return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL, true>(
-        q, active, rb, s_obs, sc.n_sp, boxp, sc.n_bp, pre, sc.n_pairs, cull, sc.n_cull);
+        q, active, rb, s_obs, sc.n_sp, boxp, sc.n_bp, pre, sc.n_pairs, cull, sc.n_cull, grid);
   } else if constexpr (V::kArm) {
     return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL>(q, active, rb, s_obs, sc.n_s,
                                                                             s_obs + sc.n_s, sc.n_b);

@@ -14,6 +14,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "gtmp_edge.cuh"
@@ -879,6 +880,94 @@ int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n
   sc->n_pairs = n_pp;
   sc->n_cull = n_cull;
   return base + 3 * n_cull;
+}
+
+int build_cull_grid(const float* spheres, int n_s, const float* boxes, int n_b, double R_link, int max_cells,
+                    float4* out, SceneDev* sc) {
+  sc->gnx = sc->gny = sc->gnz = 0;
+  const int n_sp = (n_s + 1) / 2, n_pairs = n_sp + (n_b + 1) / 2;
+  if (n_s + n_b == 0 || n_pairs > 32 || sc->n_cull != n_pairs || max_cells < 64) return 0;
+  // each obstacle as (lo, hi, reach): a sphere is its centre with reach
+  // R_link + r_obs, a box its extent with reach R_link; margin over float32
+  // rounding of the lookup (cell index of a point within ~1e-6 m of a face)
+  const double margin = 2e-3;
+  const int n = n_s + n_b;
+  std::vector<double> lo(3 * n), hi(3 * n), reach(n);
+  std::vector<int> bit(n);
+  for (int o = 0; o < n_s; ++o) {
+    for (int k = 0; k < 3; ++k) lo[3 * o + k] = hi[3 * o + k] = spheres[4 * o + k];
+    reach[o] = R_link + spheres[4 * o + 3] + margin;
+    bit[o] = o / 2;
+  }
+  for (int o = 0; o < n_b; ++o) {
+    for (int k = 0; k < 3; ++k) {
+      lo[3 * (n_s + o) + k] = boxes[6 * o + k];
+      hi[3 * (n_s + o) + k] = boxes[6 * o + 3 + k];
+    }
+    reach[n_s + o] = R_link + margin;
+    bit[n_s + o] = n_sp + o / 2;
+  }
+  double glo[3], ghi[3];
+  for (int k = 0; k < 3; ++k) {
+    glo[k] = 1e300;
+    ghi[k] = -1e300;
+    for (int o = 0; o < n; ++o) {
+      glo[k] = std::fmin(glo[k], lo[3 * o + k] - reach[o] - margin);
+      ghi[k] = std::fmax(ghi[k], hi[3 * o + k] + reach[o] + margin);
+    }
+  }
+  const double ex = ghi[0] - glo[0], ey = ghi[1] - glo[1], ez = ghi[2] - glo[2];
+  double h = std::cbrt(ex * ey * ez / max_cells);
+  int nx, ny, nz;
+  for (;;) {
+    nx = std::max(1, static_cast<int>(std::ceil(ex / h)));
+    ny = std::max(1, static_cast<int>(std::ceil(ey / h)));
+    nz = std::max(1, static_cast<int>(std::ceil(ez / h)));
+    if (static_cast<long long>(nx) * ny * nz <= max_cells) break;
+    h *= 1.02;
+  }
+  // the lookup uses 1 / h in float32: take h as the float it implies
+  const float inv = static_cast<float>(1.0 / h);
+  h = 1.0 / static_cast<double>(inv);
+  const int cells = nx * ny * nz;
+  std::vector<uint32_t> mask(static_cast<size_t>(cells) + 3, 0u);
+  // the squared distance between a cell and an obstacle's extent separates by
+  // axis: per obstacle, the squared gap of every cell row along each axis
+  std::vector<double> g2[3];
+  for (int k = 0; k < 3; ++k) g2[k].resize(k == 0 ? nx : k == 1 ? ny : nz);
+  for (int o = 0; o < n; ++o) {
+    int c0[3], c1[3];
+    for (int k = 0; k < 3; ++k) {
+      const int nk = k == 0 ? nx : k == 1 ? ny : nz;
+      c0[k] = std::max(0, static_cast<int>(std::floor((lo[3 * o + k] - reach[o] - glo[k]) / h)) - 1);
+      c1[k] = std::min(nk - 1, static_cast<int>(std::floor((hi[3 * o + k] + reach[o] - glo[k]) / h)) + 1);
+      for (int i = c0[k]; i <= c1[k]; ++i) {
+        const double a = glo[k] + i * h, b = a + h;
+        const double gap = std::fmax(std::fmax(lo[3 * o + k] - b, a - hi[3 * o + k]), 0.0);
+        g2[k][i] = gap * gap;
+      }
+    }
+    const double r2 = reach[o] * reach[o];
+    const uint32_t b = 1u << bit[o];
+    for (int iz = c0[2]; iz <= c1[2]; ++iz)
+      for (int iy = c0[1]; iy <= c1[1]; ++iy) {
+        const double dyz = g2[2][iz] + g2[1][iy];
+        if (dyz >= r2) continue;
+        uint32_t* row = mask.data() + (static_cast<size_t>(iz) * ny + iy) * nx;
+        for (int ix = c0[0]; ix <= c1[0]; ++ix)
+          if (dyz + g2[0][ix] < r2) row[ix] |= b;
+      }
+  }
+  std::memcpy(out, mask.data(), static_cast<size_t>((cells + 3) / 4) * sizeof(float4));
+  sc->gnx = nx;
+  sc->gny = ny;
+  sc->gnz = nz;
+  sc->glx = static_cast<float>(glo[0]);
+  sc->gly = static_cast<float>(glo[1]);
+  sc->glz = static_cast<float>(glo[2]);
+  sc->ginv = inv;
+  sc->g_off = 2 * sc->n_sp + 3 * sc->n_bp + 2 * sc->n_pairs + 3 * sc->n_cull;
+  return (cells + 3) / 4;
 }
 
 void fill_link_bounds(RobotDev* rb) {

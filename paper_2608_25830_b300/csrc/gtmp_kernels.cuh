@@ -45,11 +45,21 @@ struct SceneDev {
   int n_sp, n_bp;      // packed: sphere pairs, box pairs
   int n_pairs;         // packed: prefilter pairs
   int n_cull = 0;      // packed: link-cull pairs (0: no cull)
+  // packed, at most 32 cull pairs: uniform grid over the obstacles, per cell
+  // the 32-bit mask of the cull pairs that can reach a link ball centred in
+  // it (nx = 0: no grid); cells stored as uint32 from float4 offset g_off
+  int g_off = 0;
+  int gnx = 0, gny = 0, gnz = 0;
+  float glx = 0.0f, gly = 0.0f, glz = 0.0f, ginv = 0.0f;  // lower corner, 1 / cell size
 };
 
 __host__ __device__ inline int scene_float4s(const SceneDev& s) {
-  return s.packed ? 2 * s.n_sp + 3 * s.n_bp + 2 * s.n_pairs + 3 * s.n_cull : s.n_s + 2 * s.n_b;
+  return s.packed ? 2 * s.n_sp + 3 * s.n_bp + 2 * s.n_pairs + 3 * s.n_cull + (s.gnx * s.gny * s.gnz + 3) / 4
+                  : s.n_s + 2 * s.n_b;
 }
+
+// largest cull grid (cells; 64 KB of masks)
+constexpr int kMaxGridCells = 16384;
 
 // float4 capacity a packed obstacle table of n obstacles needs
 inline size_t packed_table_capacity(int n) { return 5 * static_cast<size_t>(n) + 16; }
@@ -71,6 +81,14 @@ int build_prefilter_table(const float* spheres, int n_s, const float* boxes, int
 // the float4 count written to out (capacity 3 * (n_s + n_b) + 8 float4).
 int build_packed_tables(const float* spheres, int n_s, const float* boxes, int n_b, float r, double reach,
                         float4* out, SceneDev* sc);
+// Host: the cull grid appended after the packed tables (sc's counts set by
+// build_packed_tables, at most 32 cull pairs): cells of the obstacles' region
+// dilated by R_link, at most max_cells of them; cell mask bit p set when
+// pair p's sphere comes within R_link + r_obs (box: R_link) of the cell, plus
+// a margin.  Writes the float4s at out and the grid fields of sc; returns
+// their count (0: no grid).
+int build_cull_grid(const float* spheres, int n_s, const float* boxes, int n_b, double R_link, int max_cells,
+                    float4* out, SceneDev* sc);
 // Host: a bound on |c| over all robot-sphere centres of a DH arm.
 double arm_reach_bound(const RobotDev& rb);
 // per link, the centre and radius of a ball holding all its spheres (RobotDev::lb)
