@@ -411,13 +411,20 @@ bool make_robot(const gtmp_robot& r, RobotDev* rb, int* variant, int* dp) {
   return true;
 }
 
+constexpr int kBatchGridCells = 4096;
+
 // scalar or packed obstacle table of one problem (the layout gtmp_set_obstacles writes)
 int obstacle_table(const gtmp_problem& q, const RobotDev& rb, int variant, std::vector<float4>& out, SceneDev* sc) {
   *sc = SceneDev{};
   if (variant == kVarArm6x4 || variant == kVarArm7x4) {
-    out.resize(packed_table_capacity(q.n_s + q.n_b));
-    const int n4 = build_packed_tables(q.spheres, q.n_s, q.boxes, q.n_b, rb.r_uniform, arm_reach_bound(rb),
-                                       out.data(), sc);
+    out.resize(packed_table_capacity(q.n_s + q.n_b) + kBatchGridCells / 4 + 1);
+    int n4 = build_packed_tables(q.spheres, q.n_s, q.boxes, q.n_b, rb.r_uniform, arm_reach_bound(rb), out.data(),
+                                 sc);
+    // a small cull grid: items re-stage their problem's table, so it stays at 16 KB
+    double R_link = 0.0;
+    for (int i = 0; i < rb.dof; ++i) R_link = std::fmax(R_link, static_cast<double>(rb.lb[i].w));
+    if (n4 + kBatchGridCells / 4 + 1 <= kMaxTableFloat4s)
+      n4 += build_cull_grid(q.spheres, q.n_s, q.boxes, q.n_b, R_link, kBatchGridCells, out.data() + n4, sc);
     out.resize(n4);
     return n4;
   }
