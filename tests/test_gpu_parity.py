@@ -410,3 +410,23 @@ def test_fp32_fma_calibration_is_plausible(torch_cuda):
     r = binding.gtmp_fp32_fma_peak()
     ceiling = props.multi_processor_count * 128 * 2 * 2.2e9 / 1e12
     assert 0.25 * ceiling < r < ceiling
+
+
+def test_anytime_corridor_coverage_frequency(torch_cuda):
+    """Sec. V's coverage probability on the appendix's layerwise-hitting
+    instance (a walled strip |y| < w): a restart finds a chain iff every layer
+    has a sample in the strip, Pr = (1 - (1 - w)^N)^L; 2048 restarts of the GPU
+    anytime solver reproduce it, and the first 300 agree with the oracle."""
+    w, N, L, H, R = 0.1, 12, 3, 16, 2048
+    sc = scenes.corridor_scene(w, 0.3)
+    p = _planner(sc, N, L, H, R=R)
+    paths, costs, best = p.anytime(77, R)
+    p.synchronize()
+    costs = costs.cpu().numpy()
+    freq = float(np.isfinite(costs).mean())
+    expect = (1.0 - (1.0 - w) ** N) ** L
+    assert abs(freq - expect) < 4.5 * math.sqrt(expect * (1 - expect) / R), (freq, expect)
+    for r in range(300):
+        Q = oracle.sample_uniform(77, r, L, N, sc.robot.q_lo, sc.robot.q_hi)
+        sol = oracle.solve(sc, Q, H)
+        assert math.isfinite(sol.cost_lo) == bool(np.isfinite(costs[r])), r

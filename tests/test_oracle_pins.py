@@ -795,3 +795,35 @@ def test_ao_run_epochs_on_a_planar_scene():
             for a, b in zip(verts[:-1], verts[1:]):
                 assert np.linalg.norm(b.astype(np.float64) - a) <= float(rec["edge_limit"]) * (1 + 1e-7)
     assert len({r["epoch"] for r in log}) >= 2
+
+
+# ---------------------------------------------------------------------------
+# Coverage probability (Sec. V): the layerwise-hitting instance of the
+# appendix's proposition, where the bound holds with equality
+# ---------------------------------------------------------------------------
+
+def corridor_cover_probability(w, N, L):
+    """A free strip |y| < w of the box [-1, 1]^2 (uniform samples land in it with
+    probability tau = w), convex, walled off from the rest: a chain exists iff
+    every layer has a sample in the strip, so Pr[cover] = (1 - (1 - w)^N)^L."""
+    return (1.0 - (1.0 - w) ** N) ** L
+
+
+def test_corridor_coverage_frequency_matches_the_closed_form():
+    w, N, L, H, K = 0.1, 12, 3, 16, 600
+    sc = scenes.corridor_scene(w, 0.3)
+    hits = 0
+    for r in range(K):
+        Q = oracle.sample_uniform(77, r, L, N, sc.robot.q_lo, sc.robot.q_hi)
+        sol = oracle.solve(sc, Q, H)
+        if math.isfinite(sol.cost_lo):
+            hits += 1
+            # every vertex of the returned chain lies in the strip
+            assert all(abs(float(Q[l, sol.path[l], 1])) < w for l in range(L))
+    p = corridor_cover_probability(w, N, L)
+    sigma = math.sqrt(p * (1 - p) / K)
+    assert abs(hits / K - p) < 4.5 * sigma, (hits / K, p)
+    # the proposition's upper bound (1 - (1 - tau)^N)^M with tau = w is attained here; the theorem's lower
+    # bound 1 - L (1 - p_m)^N with waypoint balls of radius w is below it
+    p_m = math.pi * w * w / 4.0
+    assert 1.0 - L * (1.0 - p_m) ** N <= p
