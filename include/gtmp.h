@@ -71,7 +71,8 @@ enum { GTMP_ROBOT_POINT = 0, GTMP_ROBOT_DH_ARM = 1 };
  * EARLY_EXIT leaves an edge at its first colliding link, skips edges that
  * cannot lie on a finite chain and, for the uniform-radius 6/7-DoF arms,
  * tests each link only against the obstacles that can reach a ball enclosing
- * its spheres (a conservative cull; results unchanged); FULL evaluates every
+ * its spheres, found through a uniform grid over the obstacles built by
+ * gtmp_set_obstacles (a conservative cull; results unchanged); FULL evaluates every
  * interior waypoint of every candidate edge against every obstacle
  * (data-independent work, used to measure the kernel);
  * LAZY checks an edge only if its cost c(u,v) + J_{l+1}(v) is below the best
@@ -132,7 +133,10 @@ GTMP_API gtmp_status gtmp_synchronize(gtmp_ctx* ctx);
 
 /* Obstacle region C_coll of Sec. III: spheres host [n_s][4] (centre x, y, z,
  * radius) and axis-aligned boxes host [n_b][6] (lo x, y, z, hi x, y, z).
- * Copied (the call returns after the copy).  n_s + n_b <= max_obstacles. */
+ * Copied (the call returns after the copy).  n_s + n_b <= max_obstacles.
+ * For the uniform-radius 6/7-DoF arms with at most 32 obstacle pairs it also
+ * builds the early-exit cull grid (on the host, up to 16384 cells, sized so
+ * the edge kernels keep two blocks per SM) and uploads it with the tables. */
 GTMP_API gtmp_status gtmp_set_obstacles(gtmp_ctx* ctx, const float* spheres, int32_t n_s, const float* boxes, int32_t n_b);
 
 /* Start q0 and goal qg (host [dof] each, inside the joint box).  Sec. III.
