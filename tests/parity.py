@@ -46,7 +46,8 @@ def decisive(sol, layer):
     best = sol.V_lo[layer]
     sec = sol.second[layer]
     fin = np.isfinite(best)
-    gap = np.where(fin, sec - best, 0.0)
+    with np.errstate(invalid="ignore"):   # inf - inf where a vertex has a single finite candidate
+        gap = np.where(fin, sec - best, 0.0)
     same = np.where(fin, np.isclose(sol.V_lo[layer], sol.V_hi[layer], rtol=0, atol=0), False)
     return fin & same & (gap > REL * np.maximum(best, 1e-30))
 

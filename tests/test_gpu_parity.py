@@ -430,3 +430,36 @@ def test_anytime_corridor_coverage_frequency(torch_cuda):
         Q = oracle.sample_uniform(77, r, L, N, sc.robot.q_lo, sc.robot.q_hi)
         sol = oracle.solve(sc, Q, H)
         assert math.isfinite(sol.cost_lo) == bool(np.isfinite(costs[r])), r
+
+
+@pytest.mark.parametrize("mode", [binding.EVAL_EARLY_EXIT, binding.EVAL_LAZY])
+def test_sample_and_solve_capture_in_a_cuda_graph(torch_cuda, mode):
+    """Every step of a plan is enqueued on the context's stream with nothing
+    synchronous in between, so sampling + solving captures into one CUDA
+    graph; replays reproduce the direct calls bit for bit."""
+    import ctypes
+    torch = torch_cuda
+    sc = scene_for("arm", 1, 7, 30)
+    M, L, H = 48, 3, 32
+    p = _planner(sc, M, L, H, mode=mode)
+    s = torch.cuda.Stream()
+    binding.gtmp_set_stream(p.ctx, ctypes.c_void_p(s.cuda_stream))
+    path = torch.empty(L, dtype=torch.int32, device="cuda")
+    cost = torch.empty(1, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s):
+        binding.gtmp_sample_layers(p.ctx, 5, M)
+        binding.gtmp_solve(p.ctx, path, cost)
+    s.synchronize()
+    ref_path, ref_cost = path.clone(), cost.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        binding.gtmp_sample_layers(p.ctx, 5, M)
+        binding.gtmp_solve(p.ctx, path, cost)
+    for _ in range(3):
+        path.fill_(-5)
+        cost.fill_(-1.0)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(path, ref_path)
+        assert torch.equal(cost, ref_cost)
+    p.synchronize()
