@@ -11,6 +11,7 @@
 //   minplus             unfused variant: J_l from a stored C_l (HBM-bound)
 //   extract_paths       follow the minimisers from q0 (Alg. 1 path extraction)
 //   expand              expand-samples of Alg. 1 (AO-GTMP, Sec. IV-D)
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
