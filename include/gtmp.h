@@ -519,6 +519,20 @@ GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* ctx, const float* dev_q,
 GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* ctx, float threshold, int32_t score_waypoints, int32_t* dev_path,
                                        float* dev_cost, gtmp_prune_stats* stats);
 
+/* Inspection, no counterpart in the paper: the cull grid gtmp_set_obstacles
+ * builds for the early-exit checker of the uniform-radius arms, computed on
+ * the host for obstacles given as to gtmp_set_obstacles and a link-ball
+ * radius R_link > 0.  masks host [max_cells] uint32: cell (ix, iy, iz) at
+ * (iz * ny + iy) * nx + ix, bit p set when obstacle pair p (spheres 2p and
+ * 2p + 1, then boxes in the same way after the sphere pairs) comes within
+ * R_link + r (box: R_link) of the cell, plus a margin; dims host [3] = (nx,
+ * ny, nz), all 0 when no grid is built (no obstacle, more than 32 pairs, or
+ * max_cells < 64); origin_inv host [4] = lower corner x, y, z and 1 / cell
+ * size.  A point whose float32 cell index (x - corner) * inv falls outside
+ * the grid is farther than that from every obstacle.  Needs no GPU. */
+GTMP_API gtmp_status gtmp_cull_grid(const float* spheres, int32_t n_s, const float* boxes, int32_t n_b, float R_link,
+                                    int32_t max_cells, uint32_t* masks, int32_t* dims, float* origin_inv);
+
 /* Calibration, no counterpart in the paper: the FP32 FMA throughput of the
  * current device in TFLOP/s (FMA = 2 flops), from a kernel of independent
  * FMA chains filling every SM, launched 8 times on cuda_stream (NULL = legacy

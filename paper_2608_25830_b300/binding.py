@@ -127,6 +127,8 @@ _SIGNATURES = {
     "gtmp_set_sampler": [_vp, _i32, _i32],
     "gtmp_set_cost_weight": [_vp, _fp, _i32],
     "gtmp_fp32_fma_peak": [_vp, ctypes.POINTER(ctypes.c_double)],
+    "gtmp_cull_grid": [_fp, _i32, _fp, _i32, ctypes.c_float, _i32, ctypes.POINTER(ctypes.c_uint32),
+                       ctypes.POINTER(_i32), _fp],
     "gtmp_get_goal_reached": [_vp, _i32, _vp],
     "gtmp_surrogate_train": [_vp, ctypes.POINTER(GtmpSurrogateConfig), ctypes.POINTER(GtmpSurrogateStats)],
     "gtmp_surrogate_predict": [_vp, _vp, _i32, _vp],
@@ -563,6 +565,21 @@ def gtmp_fp32_fma_peak(stream=None):
     if st != 0:
         raise RuntimeError(f"gtmp_fp32_fma_peak: {STATUS.get(st, st)}")
     return out.value
+
+
+def gtmp_cull_grid(spheres, boxes, R_link, max_cells=16384):
+    """The early-exit cull grid for these obstacles (host only): (masks [nz][ny][nx] uint32, origin [3], inv)."""
+    sp = _f32(spheres).reshape(-1, 4)
+    bx = _f32(boxes).reshape(-1, 6)
+    masks = np.zeros(max(max_cells, 1), np.uint32)
+    dims = (_i32 * 3)()
+    oi = np.zeros(4, np.float32)
+    st = lib().gtmp_cull_grid(_ptr(sp), sp.shape[0], _ptr(bx), bx.shape[0], R_link, max_cells,
+                              masks.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), dims, _ptr(oi))
+    if st != 0:
+        raise GtmpError(st, "gtmp_cull_grid")
+    nx, ny, nz = dims[0], dims[1], dims[2]
+    return masks[:nx * ny * nz].reshape(nz, ny, nx), oi[:3].copy(), np.float32(oi[3])
 
 
 MAX_WEIGHT_BUMPS = 16

@@ -577,6 +577,30 @@ gtmp_status gtmp_set_cost_weight(gtmp_ctx* c, const float* bumps, int32_t K) {
   return GTMP_OK;
 }
 
+gtmp_status gtmp_cull_grid(const float* spheres, int32_t n_s, const float* boxes, int32_t n_b, float R_link,
+                           int32_t max_cells, uint32_t* masks, int32_t* dims, float* origin_inv) {
+  if (n_s < 0 || n_b < 0 || (n_s > 0 && !spheres) || (n_b > 0 && !boxes) || !masks || !dims || !origin_inv ||
+      !(R_link > 0.0f) || !std::isfinite(R_link) || max_cells < 0 || max_cells > kMaxGridCells || n_s + n_b > 4096)
+    return GTMP_ERR_INVALID_ARG;
+  if ((n_s > 0 && !finite_all(spheres, static_cast<size_t>(n_s) * 4)) ||
+      (n_b > 0 && !finite_all(boxes, static_cast<size_t>(n_b) * 6)))
+    return GTMP_ERR_INVALID_ARG;
+  SceneDev sc{};
+  std::vector<float4> host(packed_table_capacity(n_s + n_b) + kMaxGridCells / 4 + 1);
+  const int n4 = build_packed_tables(spheres, n_s, boxes, n_b, 0.0f, 4.0, host.data(), &sc);
+  const int g4 = build_cull_grid(spheres, n_s, boxes, n_b, R_link, max_cells, host.data() + n4, &sc);
+  dims[0] = sc.gnx;
+  dims[1] = sc.gny;
+  dims[2] = sc.gnz;
+  origin_inv[0] = sc.glx;
+  origin_inv[1] = sc.gly;
+  origin_inv[2] = sc.glz;
+  origin_inv[3] = sc.ginv;
+  if (g4 > 0)
+    std::memcpy(masks, host.data() + n4, static_cast<size_t>(sc.gnx) * sc.gny * sc.gnz * sizeof(uint32_t));
+  return GTMP_OK;
+}
+
 gtmp_status gtmp_set_sampler(gtmp_ctx* c, int32_t sampler, int32_t max_attempts) {
   if (!c || (sampler != GTMP_SAMPLER_UNIFORM && sampler != GTMP_SAMPLER_FREE) || max_attempts < 1 ||
       max_attempts > (1 << 20))
