@@ -445,6 +445,16 @@ GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t
  * gtmp_batch_solve; GTMP_ERR_INVALID_ARG for any other mode. */
 GTMP_API gtmp_status gtmp_batch_set_eval_mode(gtmp_batch* b, int32_t eval_mode);
 
+/* Fault injection for tests, no counterpart in the paper: makes depth `depth`
+ * (0 <= depth < L of that problem) of problem `problem` unfinishable by
+ * raising its completion target out of reach, so in the next
+ * gtmp_batch_solve the items waiting on it give up after ~2 s without
+ * progress, every other wait then stops at once, the waiting items are
+ * abandoned and gtmp_batch_synchronize reports GTMP_ERR_TIMEOUT; nothing
+ * faults and the GPU stays usable.  problem < 0 restores every target (the
+ * next solve is exact again).  Synchronous; host-side only. */
+GTMP_API gtmp_status gtmp_batch_inject_stall(gtmp_batch* b, int32_t problem, int32_t depth);
+
 /* ---------------------------------------------------------------------------
  * Learned collision surrogate and surrogate-pruned solve (serving pattern; the
  * paper has no surrogate and names lazy edge realisation as future work,

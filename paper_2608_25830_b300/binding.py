@@ -122,6 +122,7 @@ _SIGNATURES = {
     "gtmp_batch_get_tiling": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "gtmp_batch_autotune": [_vp, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_float)],
     "gtmp_batch_set_eval_mode": [_vp, _i32],
+    "gtmp_batch_inject_stall": [_vp, _i32, _i32],
     "gtmp_solve_classes": [_vp, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32)],
     "gtmp_set_goals": [_vp, _fp, _fp, _i32],
     "gtmp_set_sampler": [_vp, _i32, _i32],

@@ -768,6 +768,21 @@ GTMP_API gtmp_status gtmp_batch_set_eval_mode(gtmp_batch* b, int32_t eval_mode) 
   return GTMP_OK;
 }
 
+GTMP_API gtmp_status gtmp_batch_inject_stall(gtmp_batch* b, int32_t problem, int32_t depth) {
+  if (!b) return GTMP_ERR_INVALID_ARG;
+  BATCH_TRY(b, cudaStreamSynchronize(b->stream));
+  if (problem < 0) {
+    BATCH_TRY(b, cudaMemcpy(b->d_need, b->need.data(), b->need.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return GTMP_OK;
+  }
+  if (problem >= b->n || depth < 0 || depth >= b->probs[problem].g.L)
+    return bfail(b, GTMP_ERR_INVALID_ARG, "stall at problem %d depth %d: outside the batch", problem, depth);
+  const int unreachable = 0x7fffffff;
+  BATCH_TRY(b, cudaMemcpy(b->d_need + b->probs[problem].need_base + depth, &unreachable, sizeof(int),
+                          cudaMemcpyHostToDevice));
+  return GTMP_OK;
+}
+
 GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t* target_edges, int32_t* chunk) {
   if (!b) return GTMP_ERR_INVALID_ARG;
   if (target_edges) *target_edges = b->target_edges;

@@ -64,6 +64,32 @@ def test_batch_equals_single_solves(mixed):
     b.close()
 
 
+def test_stalled_dependency_times_out_and_the_batch_recovers(mixed):
+    """Failure detection without a GPU fault: one dependency of the persistent
+    solve is made unreachable on the host; the waiting items give up after
+    their bounded wait (~2 s without progress), the others stop at once, the
+    error word comes back as GTMP_ERR_TIMEOUT, and after restoring the targets
+    the same batch object solves exactly again."""
+    import time
+    probs, H, singles = mixed
+    b = binding.Batch(probs, H)
+    L = binding.lib()
+    assert L.gtmp_batch_inject_stall(b.handle, 4, 0) == 0       # a 7-DoF problem, L = 3
+    t0 = time.time()
+    b.solve()
+    with pytest.raises(binding.GtmpError) as e:
+        b.synchronize()
+    assert e.value.status == 4
+    assert time.time() - t0 < 60
+    assert L.gtmp_batch_inject_stall(b.handle, 4, 3) == 1       # depth L has nothing waiting on it
+    assert L.gtmp_batch_inject_stall(b.handle, len(probs), 0) == 1
+    assert L.gtmp_batch_inject_stall(b.handle, -1, 0) == 0      # restore
+    b.solve()
+    b.synchronize()
+    _check_against_singles(b, probs, singles)
+    b.close()
+
+
 @pytest.mark.parametrize("target,chunk", [(1, 1), (64, 3), (100, 8), (4096, 16), (1 << 20, 64)])
 def test_every_tiling_gives_the_same_plans(mixed, target, chunk):
     probs, H, singles = mixed
