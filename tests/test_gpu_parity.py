@@ -463,3 +463,47 @@ def test_sample_and_solve_capture_in_a_cuda_graph(torch_cuda, mode):
         assert torch.equal(path, ref_path)
         assert torch.equal(cost, ref_cost)
     p.synchronize()
+
+
+def test_ao_checkpoint_and_resume_is_bit_identical(torch_cuda):
+    """AO-GTMP state is the samples, the best cost and the best path; Philox
+    counters depend on (slot, layer, attempt), not on history, so a run that
+    is checkpointed to the host after two stages, torn down and resumed in a
+    fresh context ends exactly where an uninterrupted run ends."""
+    torch = torch_cuda
+    sc = scene_for("arm", 4, 6, 30)
+    L, H, sizes = 4, 16, [8, 16, 32, 64]
+
+    def fresh():
+        p = _planner(sc, sizes[-1], L, H)
+        st = (torch.empty(L, dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.float32, device="cuda"))
+        return p, st
+
+    def stages(p, st, best, ms):
+        for M in ms:
+            binding.aogtmp_expand(p.ctx, 99, M, st[0], st[1], best[0], best[1])
+        p.synchronize()
+
+    p, st = fresh()
+    best = (torch.full((L,), -1, dtype=torch.int32, device="cuda"),
+            torch.full((1,), math.inf, dtype=torch.float32, device="cuda"))
+    stages(p, st, best, sizes)
+    ref = (p.get_layers().cpu().numpy(), best[0].cpu().numpy(), best[1].cpu().numpy(), st[1].cpu().numpy())
+    p.close()
+
+    p, st = fresh()
+    best = (torch.full((L,), -1, dtype=torch.int32, device="cuda"),
+            torch.full((1,), math.inf, dtype=torch.float32, device="cuda"))
+    stages(p, st, best, sizes[:2])
+    ckpt = (p.get_layers().cpu(), best[0].cpu(), best[1].cpu())   # host-side checkpoint
+    p.close()
+
+    p, st = fresh()
+    p.set_layers(ckpt[0].cuda())
+    best = (ckpt[1].cuda(), ckpt[2].cuda())
+    stages(p, st, best, sizes[2:])
+    got = (p.get_layers().cpu().numpy(), best[0].cpu().numpy(), best[1].cpu().numpy(), st[1].cpu().numpy())
+    p.close()
+    np.testing.assert_array_equal(got[0].view(np.uint32), ref[0].view(np.uint32))
+    for a, b in zip(got[1:], ref[1:]):
+        np.testing.assert_array_equal(a, b)
