@@ -419,6 +419,7 @@ gtmp_status gtmp_synchronize(gtmp_ctx* c) {
 }
 
 gtmp_status gtmp_set_obstacles(gtmp_ctx* c, const float* spheres, int32_t n_s, const float* boxes, int32_t n_b) {
+  GtmpNvtxRange nvtx_("gtmp_set_obstacles");
   if (!c) return GTMP_ERR_INVALID_ARG;
   if (n_s < 0 || n_b < 0 || n_s + n_b > c->p.max_obstacles)
     return fail(c, GTMP_ERR_INVALID_ARG, "obstacle count %d + %d exceeds capacity %d", n_s, n_b, c->p.max_obstacles);
@@ -547,6 +548,7 @@ gtmp_status gtmp_set_max_edge_len(gtmp_ctx* c, float max_edge_len) {
 }
 
 gtmp_status gtmp_set_cost_weight(gtmp_ctx* c, const float* bumps, int32_t K) {
+  GtmpNvtxRange nvtx_("gtmp_set_cost_weight");
   if (!c) return GTMP_ERR_INVALID_ARG;
   if (K < 0 || K > GTMP_MAX_WEIGHT_BUMPS || (K > 0 && !bumps))
     return fail(c, GTMP_ERR_INVALID_ARG, "bump count %d outside [0, %d] or NULL bumps", K, GTMP_MAX_WEIGHT_BUMPS);
@@ -620,6 +622,7 @@ gtmp_status gtmp_get_goal_reached(gtmp_ctx* c, int32_t gi, int32_t* dev_goal) {
 }
 
 gtmp_status gtmp_sample_layers(gtmp_ctx* c, uint64_t seed, int32_t M) {
+  GtmpNvtxRange nvtx_("gtmp_sample_layers");
   if (!c) return GTMP_ERR_INVALID_ARG;
   if (M < 1 || M > c->p.M) return fail(c, GTMP_ERR_INVALID_ARG, "M=%d outside 1..%d", M, c->p.M);
   GraphDev g = graph(c, 1, M);
@@ -698,6 +701,7 @@ gtmp_status gtmp_label_configs(gtmp_ctx* c, const float* dev_q, int32_t n, uint8
 }
 
 gtmp_status gtmp_solve(gtmp_ctx* c, int32_t* dev_path, float* dev_cost) {
+  GtmpNvtxRange nvtx_("gtmp_solve");
   if (!c || !dev_path || !dev_cost) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
   gtmp_status s = check_ready(c);
   if (s != GTMP_OK) return s;
@@ -722,6 +726,7 @@ gtmp_status gtmp_get_values(gtmp_ctx* c, int32_t gi, float* dev_V, int32_t* dev_
 }
 
 gtmp_status gtmp_solve_unfused(gtmp_ctx* c, int32_t* dev_path, float* dev_cost) {
+  GtmpNvtxRange nvtx_("gtmp_solve_unfused");
   if (!c || !dev_path || !dev_cost) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
   gtmp_status s = check_ready(c);
   if (s != GTMP_OK) return s;
@@ -769,6 +774,7 @@ gtmp_status gtmp_get_edge_costs(gtmp_ctx* c, int32_t l, float* dev_C) {
 
 gtmp_status gtmp_anytime(gtmp_ctx* c, uint64_t seed, int32_t restarts, int32_t* dev_paths, float* dev_costs,
                          int32_t* dev_best) {
+  GtmpNvtxRange nvtx_("gtmp_anytime");
   if (!c || !dev_paths || !dev_costs || !dev_best) return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
   if (restarts < 1 || restarts > c->p.R)
     return fail(c, GTMP_ERR_INVALID_ARG, "restarts=%d outside 1..%d", restarts, c->p.R);
@@ -786,6 +792,7 @@ gtmp_status gtmp_anytime(gtmp_ctx* c, uint64_t seed, int32_t restarts, int32_t* 
 
 gtmp_status aogtmp_expand(gtmp_ctx* c, uint64_t seed, int32_t M_new, int32_t* dev_stage_path, float* dev_stage_cost,
                           int32_t* dev_best_path, float* dev_best_cost) {
+  GtmpNvtxRange nvtx_("aogtmp_expand");
   if (!c || !dev_stage_path || !dev_stage_cost || !dev_best_path || !dev_best_cost)
     return fail(c, GTMP_ERR_INVALID_ARG, "NULL output");
   if (!c->have_endpoints) return fail(c, GTMP_ERR_NOT_READY, "endpoints not set");
@@ -809,6 +816,7 @@ gtmp_status aogtmp_expand(gtmp_ctx* c, uint64_t seed, int32_t M_new, int32_t* de
 
 gtmp_status aogtmp_run(gtmp_ctx* c, uint64_t seed, const gtmp_ao_schedule* sch, float* dev_best_chain,
                        float* dev_best_cost, gtmp_ao_stage* log, int32_t* best_layers) {
+  GtmpNvtxRange nvtx_("aogtmp_run");
   if (!c || !sch || !dev_best_chain || !dev_best_cost || !log || !best_layers)
     return fail(c, GTMP_ERR_INVALID_ARG, "NULL argument");
   const gtmp_ao_schedule S = *sch;

@@ -699,6 +699,7 @@ GTMP_API gtmp_status gtmp_batch_info(const gtmp_batch* b, int32_t* L_max, double
 }
 
 GTMP_API gtmp_status gtmp_batch_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
+  GtmpNvtxRange nvtx_("gtmp_batch_solve");
   if (!b || !dev_paths || !dev_costs) return bfail(b, GTMP_ERR_INVALID_ARG, "NULL output");
   return enqueue_solve(b, dev_paths, dev_costs);
 }

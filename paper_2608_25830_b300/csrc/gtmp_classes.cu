@@ -253,6 +253,7 @@ using namespace gtmp_classes_impl;
 extern "C" GTMP_API gtmp_status gtmp_solve_classes(gtmp_ctx* c, int32_t max_labels, int32_t max_classes,
                                                    int32_t* dev_paths, float* dev_costs, int8_t* dev_labels,
                                                    int32_t* n_classes) {
+  GtmpNvtxRange nvtx_("gtmp_solve_classes");
   if (!c || !dev_paths || !dev_costs || !dev_labels || !n_classes || max_classes < 1 || max_labels < 32 ||
       max_labels > 4096 || (max_labels & (max_labels - 1)) != 0)
     return cfail(c, GTMP_ERR_INVALID_ARG, "bad class request (max_labels a power of two in [32, 4096])");

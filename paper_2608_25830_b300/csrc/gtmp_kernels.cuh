@@ -3,8 +3,18 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "gtmp_device.cuh"
+
+// Scoped NVTX range around an ABI call, so Nsight timelines show the
+// planner's stages (a no-op unless a tool is attached).
+struct GtmpNvtxRange {
+  explicit GtmpNvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~GtmpNvtxRange() { nvtxRangePop(); }
+  GtmpNvtxRange(const GtmpNvtxRange&) = delete;
+  GtmpNvtxRange& operator=(const GtmpNvtxRange&) = delete;
+};
 
 namespace gtmp {
 

@@ -937,6 +937,7 @@ SceneDev ctx_scene(gtmp_ctx* c) {
 extern "C" {
 
 GTMP_API gtmp_status gtmp_surrogate_train(gtmp_ctx* c, const gtmp_surrogate_config* cfg, gtmp_surrogate_stats* out) {
+  GtmpNvtxRange nvtx_("gtmp_surrogate_train");
   if (!c || !cfg) return GTMP_ERR_INVALID_ARG;
   const int n_train = cfg->n_train, n_hold = cfg->n_holdout, batch = cfg->batch, epochs = cfg->epochs;
   if (n_train < 64 || n_train % 64 != 0 || n_hold < 0 || batch < 64 || batch % 64 != 0 || batch > n_train ||
@@ -1140,6 +1141,7 @@ GTMP_API int64_t gtmp_surrogate_param_count(void) { return kParamCount; }
 
 GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t score_waypoints, int32_t* dev_path,
                                        float* dev_cost, gtmp_prune_stats* stats) {
+  GtmpNvtxRange nvtx_("gtmp_solve_pruned");
   if (!c || !dev_path || !dev_cost || !(threshold > 0.0f && threshold < 1.0f) ||
       (score_waypoints != 1 && score_waypoints != 3))
     return sfail(c, GTMP_ERR_INVALID_ARG, "bad pruned-solve request (threshold in (0, 1), 1 or 3 waypoints)");
