@@ -531,8 +531,9 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* ctx, float threshold, int32_t s
 
 /* Inspection, no counterpart in the paper: the cull grid gtmp_set_obstacles
  * builds for the early-exit checker of the uniform-radius arms, computed on
- * the host for obstacles given as to gtmp_set_obstacles and a link-ball
- * radius R_link > 0.  masks host [max_cells] uint32: cell (ix, iy, iz) at
+ * the host for obstacles given as to gtmp_set_obstacles (n_s + n_b <= 4096)
+ * and a link-ball radius R_link > 0, with at most max_cells <= 16384 cells.
+ * masks host [max_cells] uint32: cell (ix, iy, iz) at
  * (iz * ny + iy) * nx + ix, bit p set when obstacle pair p (spheres 2p and
  * 2p + 1, then boxes in the same way after the sphere pairs) comes within
  * R_link + r (box: R_link) of the cell, plus a margin; dims host [3] = (nx,
