@@ -507,3 +507,22 @@ def test_ao_checkpoint_and_resume_is_bit_identical(torch_cuda):
     np.testing.assert_array_equal(got[0].view(np.uint32), ref[0].view(np.uint32))
     for a, b in zip(got[1:], ref[1:]):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode", [binding.EVAL_EARLY_EXIT, binding.EVAL_FULL, binding.EVAL_LAZY])
+def test_candidate_edge_count_of_a_solve(torch_cuda, mode):
+    """Sec. IV-C: one solve covers 2M + (L - 1) M^2 candidate edges (start
+    row, L - 1 interior transitions, goal column) in L + 1 fused launches,
+    whatever the mode skips inside them."""
+    sc = scene_for("arm", 2, 7, 30)
+    M, L, H = 40, 3, 16
+    p = _planner(sc, M, L, H, mode=mode)
+    p.sample_layers(3, M)
+    binding.gtmp_profile_read(p.ctx)                       # reset the counters
+    binding.gtmp_profile_enable(p.ctx, True)
+    p.solve()
+    prof = binding.gtmp_profile_read(p.ctx)
+    binding.gtmp_profile_enable(p.ctx, False)
+    assert prof["fused_edges"] == 2 * M + (L - 1) * M * M
+    assert prof["fused_launches"] == L + 1
+    assert prof["fused_ms"] > 0.0
