@@ -96,6 +96,33 @@ def oracle_rows(sc, wl, budget_s, seed=0, max_rows=None):
             return rows * len(verts[layer + 1]), el, rows
 
 
+L2_POLICY = "flushed between GPU steps"
+
+
+def workload_config(args, wl, world, n_s, n_b):
+    """The workload description both arms print (the reference arm runs the same workload on host cores)."""
+    M, L, H = wl["M"], wl["L"], wl["H"]
+    return {"workload": args.workload, "M": M, "L": L, "H": H, "dof": wl.get("dof", 2), "obstacles": [n_s, n_b],
+            "eval_mode": "early_exit", "parallelism": f"replicas x{world}", "l2": L2_POLICY,
+            "checks_per_solve": H * (2 * M + (L - 1) * M * M)}
+
+
+def cpu_baseline(sc, wl, budget_s, seed0):
+    """The oracle on whole rows of the layer-to-layer transitions: all host threads for budget_s, then one
+    thread for a third of it; checks/s extrapolated per nominal check."""
+    import oracle
+    M, H = wl["M"], wl["H"]
+    n_all = oracle.set_threads(0)
+    edges, secs, rows = oracle_rows(sc, wl, budget_s, seed=seed0)
+    oracle.set_threads(1)
+    e1, s1, r1 = oracle_rows(sc, wl, budget_s / 3, seed=seed0)
+    oracle.set_threads(n_all)
+    return {"value": edges * H / secs, "unit": "checks/s", "cores": n_all, "kind": "oracle",
+            "value_1thread": e1 * H / s1,
+            "sample": f"{rows} rows x {M} edges of the layer-to-layer transitions (H={H}) in {secs:.1f} s on "
+                      f"{n_all} threads, {r1} rows in {s1:.1f} s on 1 thread; extrapolated per nominal check"}
+
+
 def oracle_free_fn(sc):
     import oracle
     return lambda q: oracle.config_free(sc, q)
@@ -111,30 +138,31 @@ def run_reference(args, wl):
     else:
         base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
         sc = scenes.pick_endpoints(base, oracle_free_fn(base))
+    import oracle
     per_step = args.ref_budget
     for _ in range(args.warmup):
         oracle_rows(sc, wl, per_step / 4, max_rows=1)
     edges = 0
     secs = 0.0
     rows = 0
+    seed0 = rank_seed_base(0)                    # the GPU arm's seeds: step s plans seed seed0 + s
     for s in range(args.steps):
-        e, t, r = oracle_rows(sc, wl, per_step, seed=s)
+        e, t, r = oracle_rows(sc, wl, per_step, seed=seed0 + s)
         edges += e
         secs += t
         rows += r
     checks = edges * wl["H"]
     nominal_edges = 2 * wl["M"] + (wl["L"] - 1) * wl["M"] ** 2
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    cores = oracle.set_threads(0)
     value = checks / secs
     sample = (f"{rows} rows x {wl['M']} edges of the layer-to-layer transitions (H={wl['H']}), "
-              f"{args.steps} steps of ~{per_step:.0f} s, extrapolated per check")
+              f"{args.steps} steps of ~{per_step:.0f} s on {cores} threads, extrapolated per nominal check")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "solves_per_s": edges / secs / nominal_edges,
-        "config": {"workload": args.workload, "M": wl["M"], "L": wl["L"], "H": wl["H"], "dof": wl.get("dof", 2),
-                   "obstacles": wl["n_obs"], "l2": "n/a (CPU)"},
+        "config": workload_config(args, wl, world, sc.spheres.shape[0], sc.boxes.shape[0]),
         "cpu_baseline": {"value": value, "unit": "checks/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "checks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -427,6 +455,8 @@ def run_ours(args, wl):
     fprof = binding.gtmp_profile_read(pf.ctx)
     pf.close()
     fpw = flops_per_waypoint(dof, sc.robot.spheres_per_link, n_s, n_b, wl["kind"] == "arm")
+    n_sp, n_bp = (n_s + 1) // 2, (n_b + 1) // 2
+    full_alg_bytes = 2 * M * 8 * 4 + 2 * M * 8 + (5 * n_sp + 6 * n_bp + (n_s + n_b + 1) // 2 * 2) * 16
     full_flops = fprof["fused_edges"] * (H - 2) * fpw
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak_tflops = sms * 128 * 2 * 2.032e9 / 1e12
@@ -463,23 +493,28 @@ def run_ours(args, wl):
                    "note": "4 B per stored edge cost + 8 B per cost-to-go read and written; the cost matrices are "
                            "written last-layer first, so most of each sweep's reads come from HBM"}
 
+    # --- the metric's comparisons: batched (512 uneven problems) and surrogate-pruned (M = 4096) against the
+    # plain solver on the same problems and samples, and the anytime / AO forms; each with its own clock record
+    extras = {}
+    if not args.no_extras:
+        from paper_2608_25830_b300 import scenes as _sc
+        extras["batched"] = measure_batched(args, _sc.WORKLOADS["batched512_h32"], flush, 2, 1)
+        extras["surrogate"] = measure_surrogate(args, _sc.WORKLOADS["arm7_m4096_l8_h32_n40"], flush, 3, 1)
+        extras["anytime"] = measure_anytime(args, _sc.WORKLOADS["arm6_anytime_r64_m256_l6_h32"], flush, 20, 3)
+        extras["ao"] = measure_ao(args, _sc.WORKLOADS["arm6_ao_m64to4096_l6_h32"], 5, 1)
+
     out = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            edges, secs, rows = oracle_rows(sc, wl, args.cpu_budget)
-            cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
-            cpu = {"value": edges * H / secs, "unit": "checks/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{rows} rows x {M} edges of the layer-to-layer transitions (H={H}) in {secs:.1f} s, "
-                             f"extrapolated per nominal check"}
+            cpu = cpu_baseline(sc, wl, args.cpu_budget, seed0)
         out = {
             "metric": METRIC, "value": value, "unit": "checks/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene and samples)",
             "solves_per_s": solves / total_s,
-            "config": {"workload": args.workload, "M": M, "L": L, "H": H, "dof": dof, "obstacles": [n_s, n_b],
-                       "eval_mode": "early_exit", "parallelism": f"replicas x{world}", "l2": "flushed between steps",
-                       "checks_per_solve": nominal_checks, "last_cost": last_cost},
+            "config": workload_config(args, wl, world, n_s, n_b),
+            "last_cost": last_cost,
             "e2e": {"value": e2e_value, "unit": "checks/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(prof["launches"]),
             "roofline": {"bound": "alu", "kernel": "fused_transition_kernel (full-evaluation mode)",
@@ -493,6 +528,12 @@ def run_ours(args, wl):
                          "ffma_measured": ffma_tflops, "frac_of_ffma_measured": achieved / ffma_tflops,
                          "ffma_note": "gtmp_fp32_fma_peak: independent FMA chains on every SM, best of 6 launches",
                          "flops_per_waypoint": fpw,
+                         "algorithmic_bytes_per_launch": full_alg_bytes,
+                         "algorithmic_bytes_note": "rows' and columns' samples (M x 8 floats each), the columns' "
+                                                   "cost-to-go keys read and the rows' keys written (8 B each), the "
+                                                   "exact-test obstacle tables; the staged block also carries the "
+                                                   "early-exit cull grid (up to 64 KB), which full evaluation does "
+                                                   "not use",
                          "fused_ms_per_solve": fprof["fused_ms"] / full_steps},
             "fused_ms_per_solve_early_exit": prof["fused_ms"] / args.steps,
             "roofline_unfused_minplus": unfused,
@@ -505,6 +546,7 @@ def run_ours(args, wl):
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
+        out.update(extras)
         print(json.dumps(out), flush=True)
     p.close()
     if world > 1:
@@ -512,146 +554,137 @@ def run_ours(args, wl):
     return out
 
 
-def run_batched(args, wl):
-    """512 uneven problems (2D point robots and 7-DoF arms) in one persistent launch."""
+def gpu_endpoints(binding, scenes, base):
+    """Arm scene with start and goal picked by the GPU's own exact checker (first free candidate pair)."""
+    import numpy as np
+    import torch
+    probe = binding.Planner(base.robot, 8, 1, 2, max_obstacles=64)
+    binding.gtmp_set_obstacles(probe.ctx, base.spheres, base.boxes)
+    sc = scenes.pick_endpoints(base, lambda q: probe.label_configs(
+        torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
+    probe.close()
+    return sc
+
+
+def gpu_uuid(local):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        return str(local)
+
+
+def _timed_passes(fn, steps, flush, stream):
+    """Device time (ms) of `steps` calls of fn, L2 flushed before each; one event pair per call."""
+    import torch
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a0.elapsed_time(a1))
+    return ms
+
+
+def measure_batched(args, wl, flush, steps, warmup, lazy=True, breakdown=False):
+    """512 uneven problems (2D point robots and 7-DoF arms): one persistent launch per batch against the plain
+    single-problem solver running the same problems one after another, early exit and lazy."""
     import numpy as np
     import torch
 
     from paper_2608_25830_b300 import binding, scenes
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     H = wl["H"]
     base = scenes.batch_problems(wl["seed"] + rank, wl["n"], H=H)
     problems = []
     for bp in base:
         sc = bp.scene
         if sc.candidates is not None:
-            probe = binding.Planner(sc.robot, 8, 1, 2, max_obstacles=64)
-            binding.gtmp_set_obstacles(probe.ctx, sc.spheres, sc.boxes)
-            sc = scenes.pick_endpoints(sc, lambda q: probe.label_configs(
-                torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
-            probe.close()
+            sc = gpu_endpoints(binding, scenes, sc)
         problems.append((sc, bp.M, bp.L, bp.seed))
-    # tile autotuning on a fixed subset of 96 problems (untimed), applied to the whole batch
-    tune = binding.Batch(problems[::max(1, len(problems) // 96)][:96], H)
-    tune.autotune(repeats=1)
-    tiling = binding.gtmp_batch_get_tiling(tune.handle)
-    tune.close()
-    b = binding.Batch(problems, H)
-    binding.gtmp_batch_set_tiling(b.handle, *tiling)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        b.solve()
-    b.synchronize()
     stream = torch.cuda.current_stream()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
-    except Exception:
-        gpu_id = str(local)
-    torch.cuda.synchronize()
-    with ClockSampler(gpu_id) as clk:
-        for s in range(args.steps):
-            flush.zero_()
-            evs[s][0].record(stream)
-            b.solve()
-            evs[s][1].record(stream)
-        torch.cuda.synchronize()
-    b.synchronize()
-    step_ms = [a.elapsed_time(e) for a, e in evs]
-    total_s = max_over_ranks(sum(step_ms) / 1e3, world, "cuda")
-    costs = b.costs.cpu().numpy()
-    # the same problems through the plain single-problem solver, one after another
-    planners = []
-    for sc, M, L, seed in problems:
-        pl = binding.Planner(sc.robot, M, L, H, max_obstacles=64)
-        pl.set_scene(sc)
-        planners.append((pl, M, L, seed))
-    outs = [(torch.empty(L, dtype=torch.int32, device="cuda"), torch.empty(1, dtype=torch.float32, device="cuda"))
-            for _, _, L, _ in planners]
+    subset = problems[::max(1, len(problems) // 96)][:96]
 
-    def plain_pass():
-        for (pl, M, L, seed), (pa, co) in zip(planners, outs):
-            binding.gtmp_sample_layers(pl.ctx, seed, M)
-            binding.gtmp_solve(pl.ctx, pa, co)
-
-    plain_pass()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flush.zero_()
-    e0.record(stream)
-    plain_pass()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plain_s = e0.elapsed_time(e1) / 1e3
-    plain_same = all(float(co.cpu()[0]) == float(costs[k]) or (math.isinf(costs[k]) and math.isinf(float(co.cpu()[0])))
-                     for k, (_, co) in enumerate(outs))
-    for pl, _, _, _ in planners:
-        pl.close()
-    # lazy mode, both forms: one persistent launch vs the plain solver one problem after another
-    lazy = None
-    if args.lazy:
-        tune = binding.Batch(problems[::max(1, len(problems) // 96)][:96], H, eval_mode=binding.EVAL_LAZY)
+    def batched_form(mode):
+        tune = binding.Batch(subset, H, eval_mode=mode)      # tile autotuning on 96 problems, untimed
         tune.autotune(repeats=1)
-        lz_tiling = binding.gtmp_batch_get_tiling(tune.handle)
+        tiling = binding.gtmp_batch_get_tiling(tune.handle)
         tune.close()
-        bl = binding.Batch(problems, H, eval_mode=binding.EVAL_LAZY)
-        binding.gtmp_batch_set_tiling(bl.handle, *lz_tiling)
-        for _ in range(args.warmup):
-            bl.solve()
-        bl.synchronize()
-        lz_ms = []
-        for s in range(args.steps):
-            flush.zero_()
-            e0.record(stream)
-            bl.solve()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            lz_ms.append(e0.elapsed_time(e1))
-        bl.synchronize()
-        lz_costs = bl.costs.cpu().numpy()
-        bl.close()
-        lz_batched_s = max_over_ranks(sum(lz_ms) / 1e3, world, "cuda")
+        b = binding.Batch(problems, H, eval_mode=mode)
+        binding.gtmp_batch_set_tiling(b.handle, *tiling)
+        for _ in range(warmup):
+            b.solve()
+        b.synchronize()
+        return b, tiling
+
+    def plain_form(mode):
         planners = []
         for sc, M, L, seed in problems:
-            pl = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=binding.EVAL_LAZY)
+            pl = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=mode)
             pl.set_scene(sc)
-            planners.append((pl, M, L, seed))
-        plain_pass()
+            planners.append((pl, M, L, seed, torch.empty(L, dtype=torch.int32, device="cuda"),
+                             torch.empty(1, dtype=torch.float32, device="cuda")))
+
+        def run():
+            for pl, M, L, seed, pa, co in planners:
+                binding.gtmp_sample_layers(pl.ctx, seed, M)
+                binding.gtmp_solve(pl.ctx, pa, co)
+        run()
         torch.cuda.synchronize()
-        plz_ms = []
-        for s in range(args.steps):
-            flush.zero_()
-            e0.record(stream)
-            plain_pass()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            plz_ms.append(e0.elapsed_time(e1))
-        lz_same = all(float(co.cpu()[0]) == float(costs[k]) or (math.isinf(costs[k]) and math.isinf(float(co.cpu()[0])))
-                      for k, (_, co) in enumerate(outs))
-        lz_same = lz_same and bool(np.array_equal(lz_costs, costs))
-        for pl, _, _, _ in planners:
-            pl.close()
-        plz_s = max_over_ranks(sum(plz_ms) / 1e3, world, "cuda")
-        lazy = {"batched_solves_per_s": wl["n"] * args.steps * world / lz_batched_s,
-                "plain_sequential_solves_per_s": wl["n"] * args.steps * world / plz_s,
-                "batched_ms_per_batch": sum(lz_ms) / len(lz_ms), "plain_ms_per_batch": sum(plz_ms) / len(plz_ms),
-                "tiling": list(lz_tiling), "same_costs_as_early_exit": lz_same}
-    breakdown = None
-    if args.breakdown:
-        breakdown = {}
+        return planners, run
+
+    out = {"problems": wl["n"], "H": H}
+    modes = [("early_exit", binding.EVAL_EARLY_EXIT)] + ([("lazy", binding.EVAL_LAZY)] if lazy else [])
+    ref_costs = None
+    with ClockSampler(gpu_uuid(local)) as clk:
+        for name, mode in modes:
+            b, tiling = batched_form(mode)
+            b_ms = _timed_passes(b.solve, steps, flush, stream)
+            b.synchronize()
+            costs = b.costs.cpu().numpy()
+            nominal = b.nominal_checks
+            items = b.work_items
+            b.close()
+            planners, run = plain_form(mode)
+            p_ms = _timed_passes(run, steps, flush, stream)
+            plain_costs = np.array([float(co.cpu()[0]) for *_, co in planners], np.float32)
+            for pl, *_ in planners:
+                pl.close()
+            if ref_costs is None:
+                ref_costs = costs
+            b_s = max_over_ranks(sum(b_ms) / 1e3, world, "cuda")
+            p_s = max_over_ranks(sum(p_ms) / 1e3, world, "cuda")
+            out[name] = {
+                "batched_solves_per_s": wl["n"] * steps * world / b_s,
+                "plain_solves_per_s": wl["n"] * steps * world / p_s,
+                "batched_over_plain": p_s / b_s,
+                "batched_checks_per_s": nominal * steps * world / b_s,
+                "batched_ms_per_batch": sum(b_ms) / len(b_ms), "plain_ms_per_batch": sum(p_ms) / len(p_ms),
+                "tiling": list(tiling), "work_items": items, "checks_per_batch": nominal,
+                "feasible": int(np.isfinite(costs).sum()),
+                "same_costs_batched_plain": bool(np.array_equal(costs, plain_costs)),
+                "same_costs_as_early_exit": bool(np.array_equal(costs, ref_costs)),
+                "gpu_launches_per_batch": 5,
+            }
+    out["clocks"] = clk.summary()
+    out["steps"], out["warmup"] = steps, warmup
+    out["l2"] = "flushed before every batch and every plain pass"
+    out["note"] = ("plain = gtmp_sample_layers + gtmp_solve per problem, one after another on one stream; "
+                   "batched = gtmp_batch_solve (one persistent launch); same problems and seeds")
+    if breakdown:
+        out["breakdown"] = {}
+        tiling = out["early_exit"]["tiling"]
         for name, keep in (("arm", lambda sc: sc.robot.dof > 3), ("point2d", lambda sc: sc.robot.dof <= 3)):
             sub = [p for p in problems if keep(p[0])]
             sb = binding.Batch(sub, H)
             binding.gtmp_batch_set_tiling(sb.handle, *tiling)
             sb.solve()
             torch.cuda.synchronize()
-            e0.record(stream)
-            sb.solve()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_batched = e0.elapsed_time(e1) / 1e3
+            t_b = _timed_passes(sb.solve, 1, flush, stream)[0] / 1e3
             sb.close()
             pls = []
             for sc, M, L, seed in sub:
@@ -659,73 +692,62 @@ def run_batched(args, wl):
                 pl.set_scene(sc)
                 pls.append((pl, M, L, seed, torch.empty(L, dtype=torch.int32, device="cuda"),
                             torch.empty(1, dtype=torch.float32, device="cuda")))
-            for pl, M, L, seed, pa, co in pls:
-                binding.gtmp_sample_layers(pl.ctx, seed, M)
-                binding.gtmp_solve(pl.ctx, pa, co)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for pl, M, L, seed, pa, co in pls:
-                binding.gtmp_sample_layers(pl.ctx, seed, M)
-                binding.gtmp_solve(pl.ctx, pa, co)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            breakdown[name] = {"problems": len(sub), "batched_s": t_batched, "plain_s": e0.elapsed_time(e1) / 1e3}
+
+            def run_sub():
+                for pl, M, L, seed, pa, co in pls:
+                    binding.gtmp_sample_layers(pl.ctx, seed, M)
+                    binding.gtmp_solve(pl.ctx, pa, co)
+            run_sub()
+            t_p = _timed_passes(run_sub, 1, flush, stream)[0] / 1e3
+            out["breakdown"][name] = {"problems": len(sub), "batched_s": t_b, "plain_s": t_p}
             for pl, *_ in pls:
                 pl.close()
+    return out
+
+
+def run_batched(args, wl):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    r = measure_batched(args, wl, flush, args.steps, args.warmup, lazy=args.lazy, breakdown=args.breakdown)
     if rank == 0:
-        out = {
-            "metric": METRIC, "value": b.nominal_checks * args.steps * world / total_s, "unit": "checks/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scenes and samples)",
-            "solves_per_s": wl["n"] * args.steps * world / total_s,
-            "config": {"workload": args.workload, "problems": wl["n"], "H": H, "tiling": list(tiling),
-                       "work_items": b.work_items, "checks_per_batch": b.nominal_checks,
-                       "feasible": int(np.isfinite(costs).sum()), "l2": "flushed between steps"},
-            "gpu_launches": 5 * args.steps,
-            "clocks": clk.summary(),
-            "plain_sequential": {"solves_per_s": wl["n"] / plain_s, "s_per_batch": plain_s,
-                                 "same_costs_as_batched": bool(plain_same)},
-            "lazy": lazy,
-            "breakdown": breakdown,
-        }
-        print(json.dumps(out), flush=True)
-    b.close()
+        ee = r["early_exit"]
+        print(json.dumps({
+            "metric": METRIC, "value": ee["batched_checks_per_s"], "unit": "checks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ee["batched_ms_per_batch"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded scenes and samples)", "solves_per_s": ee["batched_solves_per_s"],
+            "config": {"workload": args.workload, "problems": wl["n"], "H": wl["H"], "l2": r["l2"]},
+            "gpu_launches": 5 * args.steps, "clocks": r["clocks"], "batched": r}), flush=True)
 
 
-def run_surrogate(args, wl):
-    """Surrogate-pruned solves against plain solves of the same samples, early-exit and lazy."""
+def measure_surrogate(args, wl, flush, steps, warmup, n_train=None, epochs=None):
+    """Surrogate-pruned solves against plain solves of the same samples, early exit and lazy."""
     import numpy as np
     import torch
 
     from paper_2608_25830_b300 import binding, scenes
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     M, L, H = wl["M"], wl["L"], wl["H"]
-    base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
-    probe = binding.Planner(base.robot, 8, 1, 2, max_obstacles=64)
-    binding.gtmp_set_obstacles(probe.ctx, base.spheres, base.boxes)
-    sc = scenes.pick_endpoints(base, lambda q: probe.label_configs(
-        torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
-    probe.close()
+    sc = gpu_endpoints(binding, scenes, scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"]))
     planners = {}
     for name, mode in (("early_exit", binding.EVAL_EARLY_EXIT), ("lazy", binding.EVAL_LAZY)):
         planners[name] = binding.Planner(sc.robot, M, L, H, max_obstacles=64, eval_mode=mode)
         planners[name].set_scene(sc)
-    n_train = args.sur_train or wl["n_train"]
+    n_train = n_train or wl["n_train"]
     train = binding.gtmp_surrogate_train(planners["early_exit"].ctx, n_train=n_train, n_holdout=1 << 16,
-                                         epochs=wl["epochs"] if not args.sur_train else 1, batch=1024, lr=1e-3, seed=1,
+                                         epochs=epochs or wl["epochs"], batch=1024, lr=1e-3, seed=1,
                                          fourier_sigma=wl["sigma"])
     binding.gtmp_surrogate_set_params(planners["lazy"].ctx,
                                       binding.gtmp_surrogate_get_params(planners["early_exit"].ctx, sc.robot.dof))
     thr, kw = wl["threshold"], wl["score_waypoints"]
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     path = torch.empty(L, dtype=torch.int32, device="cuda")
     cost = torch.empty(1, dtype=torch.float32, device="cuda")
     seed0 = rank_seed_base(rank)
-    steps = {k: [] for k in ("early_exit", "early_exit_pruned", "lazy", "lazy_pruned")}
+    times = {k: [] for k in ("early_exit", "early_exit_pruned", "lazy", "lazy_pruned")}
     ratios, pruned_frac, colliding_waypoints, checked = [], [], 0, 0
     score_ms, live_edges = [], []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -747,71 +769,89 @@ def run_surrogate(args, wl):
         wps = np.concatenate([u + t * (v - u) for u, v in zip(verts[:-1], verts[1:])]).astype(np.float32)
         return int(pl.label_configs(torch.from_numpy(wps).cuda()).sum()), len(wps)
 
-    for s in range(-args.warmup, args.steps):
-        seed = seed0 + (10_000 + s if s < 0 else s)
-        row = {}
-        for name, pl in planners.items():
-            pl.sample_layers(seed, M)
-            ms, _ = timed(lambda: binding.gtmp_solve(pl.ctx, path, cost))
-            c_plain = float(cost.cpu()[0])
-            msp, st = timed(lambda: binding.gtmp_solve_pruned(pl.ctx, thr, path, cost, score_waypoints=kw))
-            c_pruned = float(cost.cpu()[0])
-            row[name] = (ms, msp, c_plain, c_pruned, st)
-            if s >= 0 and math.isfinite(c_pruned):
-                bad, n = recheck(pl, path.cpu().numpy())
-                colliding_waypoints += bad
-                checked += n
-        if s < 0:
-            continue
-        for name in planners:
-            ms, msp, c_plain, c_pruned, st = row[name]
-            steps[name].append(ms)
-            steps[name + "_pruned"].append(msp)
-        ms, msp, c_plain, c_pruned, st = row["early_exit"]
-        assert row["lazy"][2] == c_plain or (math.isinf(c_plain) and math.isinf(row["lazy"][2]))
-        pruned_frac.append(st["pruned"] / st["edges"])
-        score_ms.append(st["score_ms"])
-        live_edges.append(st["scored"])
-        if math.isfinite(c_plain):
-            ratios.append(c_pruned / c_plain if math.isfinite(c_pruned) else math.inf)
-    # tensor-core roofline of the fused scoring kernel: 164 096 MAC per scored waypoint (128x256 + 2x256x256
-    # + 256), one scored waypoint per live edge; the live-edge count is measured from the same solves
-    score_roofline = None
-    if score_ms and live_edges:
-        peaks = measured_peaks()
-        tfl = 2.0 * 164096 * kw * (sum(live_edges) / len(live_edges)) / (sum(score_ms) / len(score_ms) / 1e3) / 1e12
-        pk = peaks.get("bf16_tflops")
-        score_roofline = {"bound": "tensor", "kernel": "score_edges_kernel (BF16 MLP, tcgen05)", "achieved": tfl,
-                          "peak": pk, "unit": "TFLOP/s", "frac": tfl / pk if pk else None, "traffic": None,
-                          "peak_basis": f"cuBLAS bf16 GEMM burst (bf16_tflops, {peaks['source']})",
-                          "score_ms_per_solve": sum(score_ms) / len(score_ms),
-                          "live_edges_per_solve": sum(live_edges) / len(live_edges)}
-    tot = {k: max_over_ranks(sum(v) / 1e3, world, "cuda") for k, v in steps.items()}
-    sps = {k: args.steps * world / v for k, v in tot.items()}
-    if rank == 0:
-        fin = [r for r in ratios if math.isfinite(r)]
-        print(json.dumps({
-            "metric": "solves/s, surrogate-pruned vs plain (7-DoF, M=4096, L=8, H=32, 40 obstacles)",
-            "value": sps["early_exit_pruned"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sum(steps["early_exit_pruned"]) / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 surrogate, f32 checker",
-            "data": "synthetic (seeded scene and samples)",
-            "config": {"workload": args.workload, "M": M, "L": L, "H": H, "dof": wl["dof"], "obstacles": wl["n_obs"],
-                       "threshold": thr, "score_waypoints": kw, "train_configs": n_train,
-                       "l2": "flushed between solves"},
-            "solves_per_s": sps,
-            "surrogate_over_plain": {"early_exit": sps["early_exit_pruned"] / sps["early_exit"],
-                                     "lazy": sps["lazy_pruned"] / sps["lazy"]},
-            "cost_ratio_pruned_over_plain": {"mean": float(np.mean(fin)) if fin else None,
-                                             "max": float(np.max(fin)) if fin else None,
-                                             "lost_feasibility": len(ratios) - len(fin), "solves": len(ratios)},
-            "roofline": score_roofline,
-            "pruned_edge_fraction": float(np.mean(pruned_frac)),
-            "returned_paths_recheck": {"waypoints": checked, "colliding": colliding_waypoints},
-            "training": train,
-        }), flush=True)
+    with ClockSampler(gpu_uuid(local)) as clk:
+        for s in range(-warmup, steps):
+            seed = seed0 + (10_000 + s if s < 0 else s)
+            row = {}
+            for name, pl in planners.items():
+                pl.sample_layers(seed, M)
+                ms, _ = timed(lambda: binding.gtmp_solve(pl.ctx, path, cost))
+                c_plain = float(cost.cpu()[0])
+                msp, st = timed(lambda: binding.gtmp_solve_pruned(pl.ctx, thr, path, cost, score_waypoints=kw))
+                c_pruned = float(cost.cpu()[0])
+                row[name] = (ms, msp, c_plain, c_pruned, st)
+                if s >= 0 and math.isfinite(c_pruned):
+                    bad, n = recheck(pl, path.cpu().numpy())
+                    colliding_waypoints += bad
+                    checked += n
+            if s < 0:
+                continue
+            for name in planners:
+                ms, msp, c_plain, c_pruned, st = row[name]
+                times[name].append(ms)
+                times[name + "_pruned"].append(msp)
+            ms, msp, c_plain, c_pruned, st = row["early_exit"]
+            assert row["lazy"][2] == c_plain or (math.isinf(c_plain) and math.isinf(row["lazy"][2]))
+            pruned_frac.append(st["pruned"] / st["edges"])
+            score_ms.append(st["score_ms"])
+            live_edges.append(st["scored"])
+            if math.isfinite(c_plain):
+                ratios.append(c_pruned / c_plain if math.isfinite(c_pruned) else math.inf)
     for pl in planners.values():
         pl.close()
+    # tensor-core roofline of the fused scoring kernel: 164 096 MAC per scored waypoint (128x256 + 2x256x256
+    # + 256), one scored waypoint per live edge; the live-edge count is measured from the same solves.  The
+    # kernel runs inside a solve, so the sustained bf16 rate is its peak.
+    peaks = measured_peaks()
+    tfl = 2.0 * 164096 * kw * (sum(live_edges) / len(live_edges)) / (sum(score_ms) / len(score_ms) / 1e3) / 1e12
+    pk = peaks.get("bf16_tflops_sustained")
+    roof = {"bound": "tensor", "kernel": "score_edges_kernel (BF16 MLP, tcgen05)", "achieved": tfl,
+            "peak": pk, "unit": "TFLOP/s", "frac": tfl / pk if pk else None, "traffic": None,
+            "peak_basis": f"cuBLAS bf16 GEMM sustained (bf16_tflops_sustained, {peaks['source']})",
+            "frac_of_burst": tfl / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
+            "score_ms_per_solve": sum(score_ms) / len(score_ms),
+            "live_edges_per_solve": sum(live_edges) / len(live_edges)}
+    tot = {k: max_over_ranks(sum(v) / 1e3, world, "cuda") for k, v in times.items()}
+    sps = {k: steps * world / v for k, v in tot.items()}
+    fin = [r for r in ratios if math.isfinite(r)]
+    return {
+        "workload": "7-DoF arm, 40 obstacles, M=4096, L=8, H=32; MLP Fourier(64)-256-256-256-1, bf16",
+        "M": M, "L": L, "H": H, "dof": wl["dof"], "obstacles": wl["n_obs"], "threshold": thr,
+        "score_waypoints": kw, "train_configs": n_train, "steps": steps, "warmup": warmup,
+        "solves_per_s": sps,
+        "ms_per_solve": {k: 1e3 / v for k, v in sps.items()},
+        "surrogate_over_plain": {"early_exit": sps["early_exit_pruned"] / sps["early_exit"],
+                                 "lazy": sps["lazy_pruned"] / sps["lazy"]},
+        "cost_ratio_pruned_over_plain": {"mean": float(np.mean(fin)) if fin else None,
+                                         "max": float(np.max(fin)) if fin else None,
+                                         "lost_feasibility": len(ratios) - len(fin), "solves": len(ratios)},
+        "roofline": roof,
+        "pruned_edge_fraction": float(np.mean(pruned_frac)),
+        "returned_paths_recheck": {"waypoints": checked, "colliding": colliding_waypoints},
+        "training": train,
+        "clocks": clk.summary(),
+        "l2": "flushed before every solve",
+        "note": "plain and pruned solve the same samples (seed = step) in each mode; every returned chain is "
+                "re-checked at all H waypoints of every edge by the exact checker",
+    }
+
+
+def run_surrogate(args, wl):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    r = measure_surrogate(args, wl, flush, args.steps, args.warmup,
+                          n_train=args.sur_train or None, epochs=1 if args.sur_train else None)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "solves/s, surrogate-pruned vs plain (7-DoF, M=4096, L=8, H=32, 40 obstacles)",
+            "value": r["solves_per_s"]["early_exit_pruned"], "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_solve"]["early_exit_pruned"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 surrogate, f32 checker",
+            "data": "synthetic (seeded scene and samples)",
+            "config": {"workload": args.workload, "M": wl["M"], "L": wl["L"], "H": wl["H"], "l2": r["l2"]},
+            "clocks": r["clocks"], "roofline": r["roofline"], "surrogate": r}), flush=True)
 
 
 def run_classes(args, wl):
@@ -887,85 +927,81 @@ def run_classes(args, wl):
         }), flush=True)
 
 
-def run_anytime(args, wl):
-    """Anytime-GTMP: R restarts of one problem, all in one batch of launches."""
+def measure_anytime(args, wl, flush, steps, warmup, lazy=False):
+    """Anytime-GTMP: R restarts of one problem, all in one batch of launches (restart = grid.y)."""
     import numpy as np
     import torch
 
     from paper_2608_25830_b300 import binding, scenes
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     M, L, H, R = wl["M"], wl["L"], wl["H"], wl["R"]
-    base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
-    probe = binding.Planner(base.robot, 8, 1, 2, max_obstacles=64)
-    binding.gtmp_set_obstacles(probe.ctx, base.spheres, base.boxes)
-    sc = scenes.pick_endpoints(base, lambda q: probe.label_configs(
-        torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
-    probe.close()
+    sc = gpu_endpoints(binding, scenes, scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"]))
     p = binding.Planner(sc.robot, M, L, H, R=R, max_obstacles=64,
-                        eval_mode=binding.EVAL_LAZY if args.lazy else binding.EVAL_EARLY_EXIT)
+                        eval_mode=binding.EVAL_LAZY if lazy else binding.EVAL_EARLY_EXIT)
     p.set_scene(sc)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     paths = torch.empty((R, L), dtype=torch.int32, device="cuda")
     costs = torch.empty(R, dtype=torch.float32, device="cuda")
     best = torch.empty(1, dtype=torch.int32, device="cuda")
     seed0 = rank_seed_base(rank)
-    for s in range(args.warmup):
+    for s in range(warmup):
         binding.gtmp_anytime(p.ctx, seed0 + 10_000 + s, R, paths, costs, best)
     p.synchronize()
     stream = torch.cuda.current_stream()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for s in range(args.steps):
-        flush.zero_()
-        evs[s][0].record(stream)
-        binding.gtmp_anytime(p.ctx, seed0 + s, R, paths, costs, best)
-        evs[s][1].record(stream)
-    torch.cuda.synchronize()
+    it = iter(range(steps))
+    with ClockSampler(gpu_uuid(local)) as clk:
+        ms = _timed_passes(lambda: binding.gtmp_anytime(p.ctx, seed0 + next(it), R, paths, costs, best),
+                           steps, flush, stream)
     p.synchronize()
-    total_s = max_over_ranks(sum(a.elapsed_time(e) for a, e in evs) / 1e3, world, "cuda")
+    p.close()
+    total_s = max_over_ranks(sum(ms) / 1e3, world, "cuda")
     checks = R * H * (2 * M + (L - 1) * M * M)
     c = costs.cpu().numpy()
+    b = int(best.cpu()[0])
+    return {"workload": f"{wl['dof']}-DoF arm, {wl['n_obs']} obstacles, {R} restarts, M={M}, L={L}, H={H}",
+            "restarts": R, "M": M, "L": L, "H": H, "dof": wl["dof"], "eval_mode": "lazy" if lazy else "early_exit",
+            "steps": steps, "warmup": warmup,
+            "solves_per_s": R * steps * world / total_s, "checks_per_s": checks * steps * world / total_s,
+            "ms_per_launch_batch": sum(ms) / len(ms), "checks_per_launch_batch": checks,
+            "feasible_restarts": int(np.isfinite(c).sum()), "best_cost": float(c[b]) if b >= 0 else None,
+            "clocks": clk.summary(), "l2": "flushed before every launch batch"}
+
+
+def run_anytime(args, wl):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    r = measure_anytime(args, wl, flush, args.steps, args.warmup, lazy=args.lazy)
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": checks * args.steps * world / total_s, "unit": "checks/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "metric": METRIC, "value": r["checks_per_s"], "unit": "checks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_launch_batch"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "solves_per_s": R * args.steps * world / total_s,
-            "config": {"workload": args.workload, "restarts": R, "M": M, "L": L, "H": H, "dof": wl["dof"],
-                       "eval_mode": "lazy" if args.lazy else "early_exit",
-                       "checks_per_launch_batch": checks, "feasible_restarts": int(np.isfinite(c).sum()),
-                       "best_cost": float(c[int(best.cpu()[0])]) if int(best.cpu()[0]) >= 0 else None,
-                       "l2": "flushed between steps"}}), flush=True)
-    p.close()
+            "solves_per_s": r["solves_per_s"], "config": {"workload": args.workload, "l2": r["l2"]},
+            "clocks": r["clocks"], "anytime": r}), flush=True)
 
 
-def run_ao(args, wl):
-    """AO-GTMP: M doubles from M0 to M1 (L fixed), best cost against device time."""
-    import numpy as np
+def measure_ao(args, wl, steps, warmup, lazy=False, epochs=True):
+    """AO-GTMP: M doubles from M0 to M1 (L fixed), best cost against device time; then the epoch schedule."""
     import torch
 
     from paper_2608_25830_b300 import binding, scenes
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     L, H = wl["L"], wl["H"]
     sizes = []
     m = wl["M0"]
     while m <= wl["M1"]:
         sizes.append(m)
         m *= 2
-    base = scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"])
-    probe = binding.Planner(base.robot, 8, 1, 2, max_obstacles=64)
-    binding.gtmp_set_obstacles(probe.ctx, base.spheres, base.boxes)
-    sc = scenes.pick_endpoints(base, lambda q: probe.label_configs(
-        torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy() == 0)
-    probe.close()
+    sc = gpu_endpoints(binding, scenes, scenes.arm_scene(wl["seed"], wl["dof"], wl["n_obs"]))
     stream = torch.cuda.current_stream()
+    mode = binding.EVAL_LAZY if lazy else binding.EVAL_EARLY_EXIT
 
     def run_schedule(seed):
-        p = binding.Planner(sc.robot, sizes[-1], L, H, max_obstacles=64,
-                            eval_mode=binding.EVAL_LAZY if args.lazy else binding.EVAL_EARLY_EXIT)
+        """One schedule from an empty graph (a fresh context; its creation is outside the events)."""
+        p = binding.Planner(sc.robot, sizes[-1], L, H, max_obstacles=64, eval_mode=mode)
         p.set_scene(sc)
         sp = torch.empty(L, dtype=torch.int32, device="cuda")
         scost = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -973,6 +1009,7 @@ def run_ao(args, wl):
         bc = torch.full((1,), math.inf, dtype=torch.float32, device="cuda")
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(sizes) + 1)]
         best = []
+        torch.cuda.synchronize()
         evs[0].record(stream)
         for k, M in enumerate(sizes):
             binding.aogtmp_expand(p.ctx, seed, M, sp, scost, bp, bc)
@@ -980,27 +1017,34 @@ def run_ao(args, wl):
             best.append(bc.clone())
         torch.cuda.synchronize()
         p.synchronize()
-        curve = [(evs[0].elapsed_time(evs[k + 1]), float(best[k].cpu()[0])) for k in range(len(sizes))]
         p.close()
-        return curve
+        return [(evs[0].elapsed_time(evs[k + 1]), float(best[k].cpu()[0])) for k in range(len(sizes))]
 
-    for s in range(args.warmup):
+    for s in range(warmup):
         run_schedule(rank_seed_base(rank) + 50_000 + s)
-    curves = [run_schedule(rank_seed_base(rank) + s) for s in range(args.steps)]
+    with ClockSampler(gpu_uuid(local)) as clk:
+        curves = [run_schedule(rank_seed_base(rank) + s) for s in range(steps)]
     total_s = max_over_ranks(sum(c[-1][0] for c in curves) / 1e3, world, "cuda")
-
-    # --- epochs (Sec. IV-D): layer count grown by the layer rule and by saturation, edge limit l_M(r)
+    checks = sum(H * (2 * M + (L - 1) * M * M) for M in sizes)
+    out = {"workload": f"{wl['dof']}-DoF arm, {wl['n_obs']} obstacles, AO-GTMP M {sizes[0]} -> {sizes[-1]} "
+                       f"(x2 per stage), L={L}, H={H}",
+           "M_stages": sizes, "L": L, "H": H, "dof": wl["dof"], "eval_mode": "lazy" if lazy else "early_exit",
+           "steps": steps, "warmup": warmup,
+           "ms_per_schedule": total_s * 1e3 / steps, "checks_per_s": checks * steps * world / total_s,
+           "checks_per_schedule": checks,
+           "best_cost_vs_time_ms": [[round(t, 3), c] for t, c in curves[0]],
+           "final_best_cost_per_schedule": [c[-1][1] for c in curves],
+           "clocks": clk.summary(), "l2": "not flushed inside a schedule (stages are sequential)"}
     ep = wl.get("epochs")
-    epochs = None
-    if ep is not None:
-        pe = binding.Planner(sc.robot, ep["M_max"], ep["L_cap"], H, max_obstacles=64,
-                             eval_mode=binding.EVAL_LAZY if args.lazy else binding.EVAL_EARLY_EXIT)
+    if epochs and ep is not None:
+        # epochs (Sec. IV-D): layer count grown by the layer rule and by saturation, edge limit l_M(r)
+        pe = binding.Planner(sc.robot, ep["M_max"], ep["L_cap"], H, max_obstacles=64, eval_mode=mode)
         pe.set_scene(sc)
         kw = {k: ep[k] for k in ("L0", "M0", "M_max", "stages", "reach", "r", "varsigma", "limit_edges")}
         pe.ao_run(rank_seed_base(rank) + 50_000, **kw)          # warm-up
         pe.synchronize()
         runs = []
-        for s in range(min(3, args.steps)):
+        for s in range(min(3, steps)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, cost_e, log, best_layers = pe.ao_run(rank_seed_base(rank) + s, **kw)
@@ -1008,24 +1052,27 @@ def run_ao(args, wl):
             runs.append((time.perf_counter() - t0, log, best_layers))
         pe.close()
         wall, log, best_layers = runs[0]
-        epochs = {"schedule": ep, "wall_ms_per_run": [round(r[0] * 1e3, 3) for r in runs],
-                  "best_cost_per_run": [r[1][-1]["best_cost"] for r in runs],
-                  "best_chain_layers": best_layers,
-                  "stages": [[r["epoch"], r["L"], r["M"], round(r["edge_limit"], 5), r["stage_cost"], r["best_cost"]]
-                             for r in log],
-                  "note": "host wall time (the driver reads the best cost back after every stage); stages = "
-                          "[epoch, L, M, edge limit, stage cost, best cost]"}
-    checks = sum(H * (2 * M + (L - 1) * M * M) for M in sizes)
+        out["epochs"] = {"schedule": ep, "wall_ms_per_run": [round(r[0] * 1e3, 3) for r in runs],
+                         "best_cost_per_run": [r[1][-1]["best_cost"] for r in runs],
+                         "best_chain_layers": best_layers,
+                         "stages": [[r["epoch"], r["L"], r["M"], round(r["edge_limit"], 5), r["stage_cost"],
+                                     r["best_cost"]] for r in log],
+                         "note": "host wall time (the driver reads the best cost back after every stage); stages = "
+                                 "[epoch, L, M, edge limit, stage cost, best cost]"}
+    return out
+
+
+def run_ao(args, wl):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    r = measure_ao(args, wl, args.steps, args.warmup, lazy=args.lazy)
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": checks * args.steps * world / total_s, "unit": "checks/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "metric": METRIC, "value": r["checks_per_s"], "unit": "checks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_schedule"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "M_stages": sizes, "L": L, "H": H, "dof": wl["dof"],
-                       "eval_mode": "lazy" if args.lazy else "early_exit",
-                       "checks_per_schedule": checks, "l2": "not flushed inside a schedule (stages are sequential)"},
-            "best_cost_vs_time_ms": [[round(t, 3), c] for t, c in curves[0]],
-            "epochs": epochs}), flush=True)
+            "config": {"workload": args.workload, "l2": r["l2"]}, "clocks": r["clocks"], "ao": r}), flush=True)
 
 
 def main():
@@ -1037,9 +1084,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="arm7_m1024_l8_h32", choices=sorted(scenes.WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
-    ap.add_argument("--ref-budget", type=float, default=10.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--ref-budget", type=float, default=6.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused min-plus roofline (M=4096)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the batched, surrogate, anytime and AO comparisons")
     ap.add_argument("--lazy", action="store_true",
                     help="batched workload: also time the lazy mode, both forms; anytime / AO workloads: lazy mode")
     ap.add_argument("--sur-train", type=int, default=0,

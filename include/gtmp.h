@@ -374,6 +374,9 @@ GTMP_API gtmp_status gtmp_profile_read(gtmp_ctx* ctx, gtmp_profile* out);
  * that first call before any stream capture.  Every call on a device shares
  * the one array and overwrites it, so calls whose GPU work overlaps (other
  * streams, other threads) race and give wrong results; serialise them.
+ * The host inputs (obstacle table, endpoints) travel inside the kernel
+ * parameters of the call's first launch, so the call reads no host memory
+ * after it returns and does not wait for earlier work on cuda_stream.
  * Work is enqueued on cuda_stream; outputs are valid after it completes.
  * On failure, err_msg (host, err_msg_len bytes, may be NULL) receives a
  * one-line reason. */
@@ -528,6 +531,21 @@ GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* ctx, const float* dev_q,
  * mask on first use. */
 GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* ctx, float threshold, int32_t score_waypoints, int32_t* dev_path,
                                        float* dev_cost, gtmp_prune_stats* stats);
+
+/* Inspection of the scoring step of gtmp_solve_pruned (no counterpart in the
+ * paper): the fused scoring kernel's decision for every live edge of one
+ * transition `layer` (0 = start row, L = the goal column) of graph 0, with
+ * liveness taken from the context's current vertex labels and cost-to-go (so
+ * call it after a gtmp_solve or gtmp_solve_pruned of the same samples):
+ * rows whose vertex is free, columns whose vertex is free with a finite
+ * cost-to-go.  dev_mask device [rows][cols] uint8 (rows = 1 for layer 0, else
+ * M; cols = M, or the goal count for layer L): 1 = pruned (the largest
+ * scored waypoint logit exceeds logit(threshold)), 0 = kept, 2 = not live
+ * (not scored).  host_scored (may be NULL) receives the live-edge count.
+ * Synchronous.  Errors: GTMP_ERR_NOT_READY before training or sampling,
+ * GTMP_ERR_INVALID_ARG for a bad layer, threshold or waypoint count. */
+GTMP_API gtmp_status gtmp_surrogate_score(gtmp_ctx* ctx, int32_t layer, float threshold, int32_t score_waypoints,
+                                          uint8_t* dev_mask, int64_t* host_scored);
 
 /* Inspection, no counterpart in the paper: the cull grid gtmp_set_obstacles
  * builds for the early-exit checker of the uniform-radius arms, computed on

@@ -64,6 +64,11 @@ _P = ctypes.POINTER
 _u32p, _f32p, _f64p, _i8p = _P(ctypes.c_uint32), _P(ctypes.c_float), _P(ctypes.c_double), _P(ctypes.c_int8)
 
 
+def set_threads(n: int = 0) -> int:
+    """OpenMP threads of the per-edge loops (n <= 0 leaves them); returns the count in effect."""
+    return int(lib().orc_set_threads(int(n)))
+
+
 def _declare(L):
     L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
     L.orc_sample_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
@@ -94,6 +99,8 @@ def _declare(L):
     L.orc_expand_layers.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     _f32p, _f32p, _f32p, _f32p, ctypes.c_float, ctypes.c_int, _f32p]
     L.orc_expand_layers.restype = ctypes.c_int
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_set_threads.restype = ctypes.c_int
 
 
 def _ptr(a, t):

@@ -23,6 +23,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <omp.h>
+
 #define ORC_FREE 0
 #define ORC_COLLIDE 1
 #define ORC_AMBIGUOUS 2
@@ -503,4 +505,11 @@ int orc_expand_layers(uint64_t seed, int L, int M_old, int M_new, int dof, const
         }
     }
     return status;
+}
+
+/* Thread count of the OpenMP loops above (the timing of the CPU baseline at
+ * one thread and at all threads); returns the count now in effect. */
+int orc_set_threads(int n) {
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
 }

@@ -22,6 +22,31 @@ constexpr size_t kNoallocScratchBytes = size_t(1) << 20;  // 1 MiB
 constexpr int kNoallocMaxObstacles = 256;                 // spheres + boxes
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
+// The call's host inputs (obstacle table, endpoints), carried to the device
+// inside the kernel parameters of one staging launch: nothing is read from
+// the caller's or this call's host memory after the call returns, and the
+// call does not wait for earlier work on the stream (a pageable
+// cudaMemcpyAsync would).  Kernel parameters may hold up to 32 764 bytes.
+constexpr int kNoallocTableCap = 5 * kNoallocMaxObstacles + 16;  // packed_table_capacity(256)
+struct NoallocStage {
+  float4 obs[kNoallocTableCap];
+  float ends[2][kMaxDof];  // start, goal; zero beyond dof
+  int n4;                  // float4s of obs in use
+  int dp;                  // padded coordinates per sample
+  long long goal_offset;   // float offset of the goal vertex in Q
+};
+static_assert(sizeof(NoallocStage) <= 32000, "staging parameters exceed the kernel-parameter limit");
+
+// error word = 0, obstacle table, both endpoints into Q (one block)
+__global__ void noalloc_stage_kernel(const __grid_constant__ NoallocStage s, int* err, float4* obs, float* Q) {
+  if (threadIdx.x == 0) *err = 0;
+  for (int k = threadIdx.x; k < s.n4; k += blockDim.x) obs[k] = s.obs[k];
+  if (threadIdx.x < s.dp) {
+    Q[threadIdx.x] = s.ends[0][threadIdx.x];
+    Q[s.goal_offset + threadIdx.x] = s.ends[1][threadIdx.x];
+  }
+}
+
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch per device
@@ -148,12 +173,50 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
     rb.r_uniform = robot->point_radius;
   }
 
+  // ---- host inputs for the staging launch (kernel parameters; no heap, no device allocation)
+  for (int o = 0; o < n_s; ++o)
+    if (!(spheres[4 * o + 3] >= 0.0f)) return report(err_msg, err_msg_len, bad, "negative sphere radius");
+  for (int o = 0; o < n_b; ++o)
+    for (int k = 0; k < 3; ++k)
+      if (!(boxes[6 * o + 3 + k] >= boxes[6 * o + k])) return report(err_msg, err_msg_len, bad, "box with hi < lo");
+  const bool packed = variant == kVarArm6x4 || variant == kVarArm7x4;
+  NoallocStage stage;
+  SceneDev sc{};
+  int n4 = 0;  // float4 count of the obstacle table, as its builder reports it
+  if (packed) {
+    n4 = build_packed_tables(spheres, n_s, boxes, n_b, rb.r_uniform, arm_reach_bound(rb), stage.obs, &sc);
+  } else {
+    for (int o = 0; o < n_s; ++o) {
+      const float* s = spheres + 4 * o;
+      float w = s[3];
+      if (rb.uniform_r) {
+        const float rr = s[3] + rb.r_uniform;
+        w = rr * rr;
+      }
+      stage.obs[o] = make_float4(s[0], s[1], s[2], w);
+    }
+    for (int o = 0; o < n_b; ++o) {
+      const float* b = boxes + 6 * o;
+      stage.obs[n_s + 2 * o] = make_float4(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]),
+                                           0.5f * (b[3] - b[0]));
+      stage.obs[n_s + 2 * o + 1] = make_float4(0.5f * (b[4] - b[1]), 0.5f * (b[5] - b[2]), 0.0f, 0.0f);
+    }
+    sc.n_s = n_s;
+    sc.n_b = n_b;
+    n4 = n_s + 2 * n_b;
+  }
+  if (n4 < 0 || n4 > kNoallocTableCap)
+    return report(err_msg, err_msg_len, GTMP_ERR_UNSUPPORTED, "obstacle table of %d float4 exceeds %d", n4,
+                  kNoallocTableCap);
+  stage.n4 = n4;
+  stage.dp = dp;
+  for (int k = 0; k < kMaxDof; ++k) {
+    stage.ends[0][k] = k < dof ? q_start[k] : 0.0f;
+    stage.ends[1][k] = k < dof ? q_goal[k] : 0.0f;
+  }
+
   // ---- scratch layout and the size limit
   const size_t verts = static_cast<size_t>(L + 2) * M;
-  const bool packed = variant == kVarArm6x4 || variant == kVarArm7x4;
-  // float4 count of the obstacle table: packed pair tables + prefilter, or the scalar table
-  // packed: sphere pairs, box pairs, prefilter pairs, link-cull pairs (256 obstacles always fit)
-  const int n4 = packed ? 5 * ((n_s + 1) / 2) + 6 * ((n_b + 1) / 2) + 2 * ((n_s + n_b + 1) / 2) : n_s + 2 * n_b;
   size_t off = 0;
   const size_t off_err = off;
   off = align256(off + sizeof(int));
@@ -171,41 +234,7 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
     return report(err_msg, err_msg_len, bad,
                   "M=%d, L=%d, dof=%d need %zu bytes of scratch; the no-allocation entry point has %zu",
                   M, L, dof, off, kNoallocScratchBytes);
-
-  // ---- host-side tables on the stack (no heap, no device allocation)
-  float4 obs[5 * kNoallocMaxObstacles + 16];  // packed_table_capacity(kNoallocMaxObstacles)
-  SceneDev sc{};
-  for (int o = 0; o < n_s; ++o)
-    if (!(spheres[4 * o + 3] >= 0.0f)) return report(err_msg, err_msg_len, bad, "negative sphere radius");
-  for (int o = 0; o < n_b; ++o)
-    for (int k = 0; k < 3; ++k)
-      if (!(boxes[6 * o + 3 + k] >= boxes[6 * o + k])) return report(err_msg, err_msg_len, bad, "box with hi < lo");
-  if (packed) {
-    build_packed_tables(spheres, n_s, boxes, n_b, rb.r_uniform, arm_reach_bound(rb), obs, &sc);
-  } else {
-    for (int o = 0; o < n_s; ++o) {
-      const float* s = spheres + 4 * o;
-      float w = s[3];
-      if (rb.uniform_r) {
-        const float rr = s[3] + rb.r_uniform;
-        w = rr * rr;
-      }
-      obs[o] = make_float4(s[0], s[1], s[2], w);
-    }
-    for (int o = 0; o < n_b; ++o) {
-      const float* b = boxes + 6 * o;
-      obs[n_s + 2 * o] = make_float4(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]),
-                                     0.5f * (b[3] - b[0]));
-      obs[n_s + 2 * o + 1] = make_float4(0.5f * (b[4] - b[1]), 0.5f * (b[5] - b[2]), 0.0f, 0.0f);
-    }
-    sc.n_s = n_s;
-    sc.n_b = n_b;
-  }
-  float ends[2][kMaxDof] = {};
-  for (int k = 0; k < dof; ++k) {
-    ends[0][k] = q_start[k];
-    ends[1][k] = q_goal[k];
-  }
+  stage.goal_offset = static_cast<long long>(L + 1) * M * dp;
 
   // ---- device set-up (first call on this device) and launches
   int dev = 0;
@@ -240,12 +269,10 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
       return report(err_msg, err_msg_len, GTMP_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));      \
   } while (0)
 
-  // zero what must start at zero (the error word); everything else is written before it is read
-  NA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-  if (n4 > 0) NA_TRY(cudaMemcpyAsync(d_obs, obs, static_cast<size_t>(n4) * sizeof(float4), cudaMemcpyHostToDevice, st));
-  NA_TRY(cudaMemcpyAsync(g.Q, ends[0], dp * sizeof(float), cudaMemcpyHostToDevice, st));
-  NA_TRY(cudaMemcpyAsync(g.Q + static_cast<size_t>(L + 1) * M * dp, ends[1], dp * sizeof(float),
-                         cudaMemcpyHostToDevice, st));
+  // error word (the one value that must start at zero), obstacle table and endpoints; everything
+  // else in the scratch is written before it is read
+  noalloc_stage_kernel<<<1, 256, 0, st>>>(stage, err, d_obs, g.Q);
+  NA_TRY(cudaGetLastError());
   NA_TRY(launch_pack_layers(g, const_cast<float*>(dev_Q), dof, 1, st));
   NA_TRY(launch_init_keys(g, counters, L + 1, st));
   NA_TRY(launch_vertex_labels(g, rb, variant, sc, st));

@@ -1139,18 +1139,15 @@ GTMP_API gtmp_status gtmp_surrogate_get_params(gtmp_ctx* c, float* host_params, 
 
 GTMP_API int64_t gtmp_surrogate_param_count(void) { return kParamCount; }
 
-GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t score_waypoints, int32_t* dev_path,
-                                       float* dev_cost, gtmp_prune_stats* stats) {
-  GtmpNvtxRange nvtx_("gtmp_solve_pruned");
-  if (!c || !dev_path || !dev_cost || !(threshold > 0.0f && threshold < 1.0f) ||
-      (score_waypoints != 1 && score_waypoints != 3))
-    return sfail(c, GTMP_ERR_INVALID_ARG, "bad pruned-solve request (threshold in (0, 1), 1 or 3 waypoints)");
-  if (!c->sur || !c->sur->trained) return sfail(c, GTMP_ERR_NOT_READY, "surrogate not trained");
-  if (!c->have_endpoints || c->M_active < 1) return sfail(c, GTMP_ERR_NOT_READY, "endpoints or samples missing");
+}  // extern "C"
+
+namespace {
+
+// Buffers, kernel attributes and the weight images the scoring kernel needs
+// (the images are rebuilt from the current weights on every call).
+gtmp_status prepare_scoring(gtmp_ctx* c) {
   SurrogateState* s = c->sur;
   cudaStream_t st = c->stream;
-  const int M = c->M_active, L = c->p.L;
-  if (!c->prune) SUR_TRY(c, cudaMalloc(&c->prune, static_cast<size_t>(c->p.M) * c->p.M));
   if (s->live_cap < c->p.M) {
     cudaFree(s->live);
     s->live = nullptr;
@@ -1161,30 +1158,114 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
   SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
   SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
   SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
-  const float cut = std::log(threshold / (1.0f - threshold));  // logit of the threshold
+  if (!s->wimg) SUR_TRY(c, cudaMalloc(&s->wimg, static_cast<size_t>(kSmemW1) + 8 * static_cast<size_t>(kSmemS)));
+  weight_images_kernel<<<(256 * 16 + 8 * 256 * 8 + 255) / 256, 256, 0, st>>>(s->W1b, s->W2b, s->W3b, s->wimg);
+  SUR_TRY(c, cudaGetLastError());
+  SUR_TRY(c, cudaMemsetAsync(s->counter, 0, sizeof(unsigned long long), st));
+  return GTMP_OK;
+}
+
+GraphDev pruned_graph(gtmp_ctx* c) {
   GraphDev g;
   g.Q = c->Q;
   g.vflag = c->vflag;
   g.keys = c->keys;
   g.R = 1;
-  g.L = L;
-  g.M = M;
+  g.L = c->p.L;
+  g.M = c->M_active;
   g.dp = c->dp;
   g.H = c->p.H;
   g.M_stride = c->p.M;
   g.max_edge_len = c->p.max_edge_len;
   g.G = c->G;
   g.gval = c->goal_values ? c->gval : nullptr;
+  return g;
+}
+
+// Score the live edges of transition `layer` (rows = its live vertices, columns
+// = the next layer's free vertices with a finite cost-to-go in the keys) into
+// prune[i * cols + j]: 1 = pruned, 0 = kept; other entries are not written.
+gtmp_status launch_score_transition(gtmp_ctx* c, const GraphDev& g, int layer, float cut, int kw, uint8_t* prune) {
+  SurrogateState* s = c->sur;
+  cudaStream_t st = c->stream;
+  const long long ne = static_cast<long long>(layer_size(g, layer)) * layer_size(g, layer + 1);
+  ScoreArgs sa{};
+  sa.g = g;
+  sa.layer = layer;
+  sa.live = s->live;
+  sa.cap = s->live_cap;
+  sa.kw = kw;
+  sa.cut = cut;
+  sa.W1b = s->W1b;
+  sa.W2b = s->W2b;
+  sa.W3b = s->W3b;
+  sa.Wimg = s->wimg;
+  sa.P = s->P;
+  sa.prune = prune;
+  sa.n_pruned = s->counter;
+  sa.err = c->err;
+  // the live count stays on the device: a persistent grid reads it
+  live_lists_kernel<<<1, 1024, 0, st>>>(g, layer, s->live_cap, s->live);
+  SUR_TRY(c, cudaGetLastError());
+  const long long tiles = (ne + 128 / kw - 1) / (128 / kw);
+  const int score_grid = static_cast<int>(std::min<long long>(tiles, c->num_sms));
+  if (s->four.dof == 7)
+    score_edges_kernel<7><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
+  else if (s->four.dof == 6)
+    score_edges_kernel<6><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
+  else
+    score_edges_kernel<0><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
+  SUR_TRY(c, cudaGetLastError());
+  return GTMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+GTMP_API gtmp_status gtmp_surrogate_score(gtmp_ctx* c, int32_t layer, float threshold, int32_t score_waypoints,
+                                          uint8_t* dev_mask, int64_t* host_scored) {
+  GtmpNvtxRange nvtx_("gtmp_surrogate_score");
+  if (!c || !dev_mask || !(threshold > 0.0f && threshold < 1.0f) || (score_waypoints != 1 && score_waypoints != 3))
+    return sfail(c, GTMP_ERR_INVALID_ARG, "bad scoring request (threshold in (0, 1), 1 or 3 waypoints)");
+  if (!c->sur || !c->sur->trained) return sfail(c, GTMP_ERR_NOT_READY, "surrogate not trained");
+  if (!c->have_endpoints || c->M_active < 1) return sfail(c, GTMP_ERR_NOT_READY, "endpoints or samples missing");
+  if (layer < 0 || layer > c->p.L) return sfail(c, GTMP_ERR_INVALID_ARG, "layer outside 0..L");
+  gtmp_status r = prepare_scoring(c);
+  if (r != GTMP_OK) return r;
+  const GraphDev g = pruned_graph(c);
+  const size_t n = static_cast<size_t>(layer_size(g, layer)) * layer_size(g, layer + 1);
+  SUR_TRY(c, cudaMemsetAsync(dev_mask, 2, n, c->stream));
+  r = launch_score_transition(c, g, layer, std::log(threshold / (1.0f - threshold)), score_waypoints, dev_mask);
+  if (r != GTMP_OK) return r;
+  int live_n[2] = {0, 0};
+  SUR_TRY(c, cudaMemcpyAsync(live_n, c->sur->live, sizeof(live_n), cudaMemcpyDeviceToHost, c->stream));
+  SUR_TRY(c, cudaStreamSynchronize(c->stream));
+  if (host_scored) *host_scored = static_cast<int64_t>(live_n[0]) * live_n[1];
+  return GTMP_OK;
+}
+
+GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t score_waypoints, int32_t* dev_path,
+                                       float* dev_cost, gtmp_prune_stats* stats) {
+  GtmpNvtxRange nvtx_("gtmp_solve_pruned");
+  if (!c || !dev_path || !dev_cost || !(threshold > 0.0f && threshold < 1.0f) ||
+      (score_waypoints != 1 && score_waypoints != 3))
+    return sfail(c, GTMP_ERR_INVALID_ARG, "bad pruned-solve request (threshold in (0, 1), 1 or 3 waypoints)");
+  if (!c->sur || !c->sur->trained) return sfail(c, GTMP_ERR_NOT_READY, "surrogate not trained");
+  if (!c->have_endpoints || c->M_active < 1) return sfail(c, GTMP_ERR_NOT_READY, "endpoints or samples missing");
+  SurrogateState* s = c->sur;
+  cudaStream_t st = c->stream;
+  const int L = c->p.L;
+  if (!c->prune) SUR_TRY(c, cudaMalloc(&c->prune, static_cast<size_t>(c->p.M) * c->p.M));
+  gtmp_status r = prepare_scoring(c);
+  if (r != GTMP_OK) return r;
+  const float cut = std::log(threshold / (1.0f - threshold));  // logit of the threshold
+  const GraphDev g = pruned_graph(c);
   cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventCreate(&e2);
   float score_ms = 0.0f, solve_ms = 0.0f;
-  // the current weights as the scoring kernel's shared-memory images (one bulk copy each)
-  if (!s->wimg) SUR_TRY(c, cudaMalloc(&s->wimg, static_cast<size_t>(kSmemW1) + 8 * static_cast<size_t>(kSmemS)));
-  weight_images_kernel<<<(256 * 16 + 8 * 256 * 8 + 255) / 256, 256, 0, st>>>(s->W1b, s->W2b, s->W3b, s->wimg);
-  SUR_TRY(c, cudaGetLastError());
-  SUR_TRY(c, cudaMemsetAsync(s->counter, 0, sizeof(unsigned long long), st));
   SUR_TRY(c, launch_init_keys(g, c->counters, L + 1, st));
   SUR_TRY(c, launch_vertex_labels(g, c->rb, c->variant, ctx_scene(c), st));
   const int resident = c->num_sms * c->fused_bps[0];
@@ -1194,34 +1275,9 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     const long long ne = static_cast<long long>(rows) * cols;
     edges_total += static_cast<double>(ne);
     cudaEventRecord(e0, st);
-    // score every edge of the transition with the fused tensor-core kernel
-    ScoreArgs sa{};
-    sa.g = g;
-    sa.layer = layer;
-    sa.live = s->live;
-    sa.cap = s->live_cap;
-    sa.kw = score_waypoints;
-    sa.cut = cut;
-    sa.W1b = s->W1b;
-    sa.W2b = s->W2b;
-    sa.W3b = s->W3b;
-    sa.Wimg = s->wimg;
-    sa.P = s->P;
-    sa.prune = c->prune;
-    sa.n_pruned = s->counter;
-    sa.err = c->err;
-    // the live count stays on the device: a persistent grid reads it
-    live_lists_kernel<<<1, 1024, 0, st>>>(g, layer, s->live_cap, s->live);
-    SUR_TRY(c, cudaGetLastError());
-    const long long tiles = (ne + 128 / score_waypoints - 1) / (128 / score_waypoints);
-    const int score_grid = static_cast<int>(std::min<long long>(tiles, c->num_sms));
-    if (s->four.dof == 7)
-      score_edges_kernel<7><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
-    else if (s->four.dof == 6)
-      score_edges_kernel<6><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
-    else
-      score_edges_kernel<0><<<score_grid, kScoreThreads, kScoreSmem, st>>>(sa, s->four);
-    SUR_TRY(c, cudaGetLastError());
+    // score the live edges of the transition with the fused tensor-core kernel
+    r = launch_score_transition(c, g, layer, cut, score_waypoints, c->prune);
+    if (r != GTMP_OK) return r;
     cudaEventRecord(e1, st);
     // exact realisation of the surviving edges, fused with the min-plus step
     GraphDev gp = g;
