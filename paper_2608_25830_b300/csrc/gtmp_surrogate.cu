@@ -193,12 +193,15 @@ struct FourierDev {
   int dof;
 };
 
+// The features of one configuration, computed exactly as the fused scoring
+// kernel computes them (same FMA order, the fast __sincosf), so that training,
+// prediction and scoring evaluate one and the same model.
 __device__ __forceinline__ void fourier_row(const float* q, const FourierDev& f, __nv_bfloat16* out) {
   for (int k = 0; k < 64; ++k) {
     float z = 0.0f;
     for (int d = 0; d < f.dof; ++d) z = __fmaf_rn(f.B[k * f.dof + d], q[d], z);
     float s, c;
-    sincosf(z, &s, &c);
+    __sincosf(z, &s, &c);
     out[k] = __float2bfloat16_rn(s);
     out[64 + k] = __float2bfloat16_rn(c);
   }
