@@ -377,12 +377,16 @@ constexpr int kParamCount = kNW1 + kHid + kNW2 + kHid + kNW3 + kHid + kHid + 1;
 // ---------------------------------------------------------------------------
 // Fused surrogate scoring of edges: features -> 3 layers -> head -> prune mask
 // in one persistent kernel (one CTA per SM, 8 warps).  Shared memory (bytes,
-// canonical K-major no-swizzle layouts): W1 [256 x 128] resident (64 K), the
-// tile's features X [128 x 128] (32 K), hidden activations H [128 x 256] (64 K,
-// reused by every layer), two 32 K buffers for the 256 x 64 K-chunks of W2 and
-// W3.  The weights arrive as pre-arranged images of these tiles (one
-// cp.async.bulk each, completing on the buffer's mbarrier; W1 once per CTA).
-// TMEM: one 128 x 256 fp32 accumulator.  A tile is 128 queries: Q = 128 / kw
+// canonical K-major no-swizzle layouts): W1 [256 x 128] resident (64 K, one
+// bulk copy per CTA); the tile's activations (64 K): the features X
+// [128 x 128] first, then H [128 x 256], written over X once layer 1's MMAs
+// have completed and reused by every layer; three 32 K buffers for the
+// 256 x 64 K-chunks of W2 and W3, pre-arranged in global memory as images of
+// their shared-memory tiles.  Every thread copies its 128 bytes of a chunk
+// with cp.async, two chunks ahead of the MMAs (chunk numbers run on across a
+// CTA's tiles, so the next tile's first chunks load during this tile's head);
+// measured on B300, cp.async from all threads moves ~49 B per cycle per SM and
+// one bulk copy engine ~16.  TMEM: one 128 x 256 fp32 accumulator.  A tile is 128 queries: Q = 128 / kw
 // edges with kw waypoints each (t = 1/2 for kw = 1; 1/4, 1/2, 3/4 for kw = 3);
 // an edge is pruned when its largest logit exceeds `cut`.  Only live edges are
 // scored (compacted row and column lists).
@@ -426,8 +430,9 @@ __global__ void __launch_bounds__(1024) live_lists_kernel(GraphDev g, int layer,
 }
 
 constexpr int kScoreThreads = 256;
-constexpr int kSmemW1 = 256 * 128 * 2, kSmemX = 128 * 128 * 2, kSmemH = 128 * 256 * 2, kSmemS = 256 * 64 * 2;
-constexpr int kScoreSmem = kSmemW1 + kSmemX + kSmemH + 2 * kSmemS;
+constexpr int kSmemW1 = 256 * 128 * 2, kSmemH = 128 * 256 * 2, kSmemS = 256 * 64 * 2;
+constexpr int kChunkBufs = 3;                      // stream buffers: one being read, two loading
+constexpr int kScoreSmem = kSmemW1 + kSmemH + kChunkBufs * kSmemS;
 
 struct ScoreArgs {
   GraphDev g;
@@ -519,15 +524,15 @@ template <int DOF>
 __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs a, FourierDev f) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar;
-  __shared__ __align__(8) uint64_t mbar_w[3];  // weight buffers 0, 1 and the resident W1
+  __shared__ __align__(8) uint64_t mbar_w1;    // the resident W1
   __shared__ int s_abort;
   __shared__ uint32_t tmem_base;
   __shared__ float s_part[2][128];
   __shared__ float s_logit[128];
   uint8_t* sW1 = smem;
-  uint8_t* sX = sW1 + kSmemW1;
-  uint8_t* sH = sX + kSmemX;
-  uint8_t* sS = sH + kSmemH;  // two stream buffers
+  uint8_t* sH = sW1 + kSmemW1;
+  uint8_t* sX = sH;           // the features occupy H's first 32 K until layer 1 has read them
+  uint8_t* sS = sH + kSmemH;  // stream buffers
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t mb = s_u32(&mbar);
   const float* b1 = a.P + kNW1;
@@ -536,27 +541,21 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   const float* w4 = b3 + kHid;
   const float b4 = w4[kHid];
 
-  // weight chunk c (0..3 = W2 columns [64c, 64c+64), 4..7 = W3 columns [64(c-4), ...)) into buffer
-  // `buf`: one bulk copy of its image, completing on that buffer's barrier (thread 0 only)
-  uint32_t wphase[2] = {0u, 0u};
-  auto load_chunk = [&](int c, int buf) {
-    if (tid != 0) return;
-    const uint32_t bar = s_u32(&mbar_w[buf]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kSmemS) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     s_u32(sS + buf * kSmemS)),
-                 "l"(a.Wimg + kSmemW1 + static_cast<size_t>(c) * kSmemS), "r"(kSmemS), "r"(bar)
-                 : "memory");
-  };
-  // thread 0: wait (bounded) for buffer `buf`'s copy; on timeout release the others through the MMA barrier
-  auto wait_chunk = [&](int buf) -> bool {
-    const bool got = mbar_wait_parity(s_u32(&mbar_w[buf]), wphase[buf], kMbarLimit);
-    wphase[buf] ^= 1u;
-    if (!got) {
-      s_abort = 1;
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+  // weight chunk g (chunk numbers run on across this CTA's tiles; g % 8 = 0..3: W2 columns
+  // [64 (g % 4), + 64), 4..7: W3 columns) into buffer g % kChunkBufs: this thread's 128 bytes as one
+  // cp.async group (an empty group past the CTA's last chunk, so that group g always holds chunk g)
+  long long chunks_loaded = 0, chunks_used = 0;
+  auto load_chunk = [&](long long g, long long total) {
+    if (g < total) {
+      const uint8_t* src = a.Wimg + kSmemW1 + static_cast<size_t>(g % 8) * kSmemS;
+      const uint32_t dst = s_u32(sS + static_cast<int>(g % kChunkBufs) * kSmemS);
+#pragma unroll
+      for (int k = 0; k < kSmemS / 16 / kScoreThreads; ++k) {
+        const int off = (k * kScoreThreads + tid) * 16;
+        cp_async16(dst + off, src + off, 16);
+      }
     }
-    return got;
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
   auto wait_mma = [&](uint32_t& phase) -> bool {
     const bool ok = mbar_wait_parity(mb, phase, kMbarLimit);
@@ -574,10 +573,10 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   if (tid == 0) {
     s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-    for (int k = 0; k < 3; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_w[k])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_w1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // resident W1: one bulk copy of its image
-    const uint32_t bar = s_u32(&mbar_w[2]);
+    const uint32_t bar = s_u32(&mbar_w1);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kSmemW1) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      s_u32(sW1)),
@@ -603,10 +602,12 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   const int row = quarter * 32 + lane;  // TMEM lane = tile row this thread reads
   uint32_t phase = 0;
   bool ok = true;
+  const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long total_chunks = my_tiles * 8;
+  for (; chunks_loaded < kChunkBufs - 1; ++chunks_loaded) load_chunk(chunks_loaded, total_chunks);
 
   for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const long long e_first = tile * e_per_tile;
-    load_chunk(0, 0);
     // features of the tile's queries -> X: two threads per query, 32 frequencies
     // each; the fast __sincosf is ample here (|Bq| < 10, absolute error ~1e-6,
     // the features are rounded to bf16 right after)
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     if (tid == 0) {
       bool go = true;
       if (!w1_ready) {
-        go = mbar_wait_parity(s_u32(&mbar_w[2]), 0u, kMbarLimit);
+        go = mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);
         w1_ready = true;
         if (!go) {
           s_abort = 1;
@@ -690,17 +691,27 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
         __syncthreads();
       }
       if (c == 8) break;
-      if (c + 1 < 8) load_chunk(c + 1, (c + 1) & 1);  // that buffer's MMAs finished last iteration
-      if (tid == 0 && wait_chunk(c & 1)) {
+      // the buffer of chunk g + 2 last held chunk g - 1, whose MMAs every thread has seen complete
+      load_chunk(chunks_loaded++, total_chunks);
+      // this thread's part of chunk g has landed (groups g + 1 and g + 2 may be in flight): make it visible
+      // to the MMA (async proxy), then wait for every thread's part
+      asm volatile("cp.async.wait_group %0;" ::"n"(kChunkBufs - 1) : "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (warp == 0 && !s_abort) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sb = s_u32(sS + (c & 1) * kSmemS);
-        const int kc = c & 3;
-        for (int kk = 0; kk < 4; ++kk)
-          issue_mma(tmem, smem_desc(s_u32(sH) + kc * 1024 + kk * 256, 128, 4096), smem_desc(sb + kk * 256, 128, 1024),
-                    idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                     : "memory");
+        if (lane == 0) {
+          const uint32_t sb = s_u32(sS + static_cast<int>(chunks_used % kChunkBufs) * kSmemS);
+          const int kc = c & 3;
+          for (int kk = 0; kk < 4; ++kk)
+            issue_mma(tmem, smem_desc(s_u32(sH) + kc * 1024 + kk * 256, 128, 4096),
+                      smem_desc(sb + kk * 256, 128, 1024), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                       : "memory");
+        }
+        __syncwarp();
       }
+      ++chunks_used;
       ok = wait_mma(phase) && !s_abort;
     }
     if (!ok) break;
@@ -743,11 +754,10 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     }
     __syncthreads();
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies have landed
   if (!ok && tid == 0) {
     atomicOr(a.err, kErrWaitTimeout);
-    // let copies still in flight land before the block exits (bounded)
-    for (int b = 0; b < 2; ++b) mbar_wait_parity(s_u32(&mbar_w[b]), wphase[b], kMbarLimit);
-    if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w[2]), 0u, kMbarLimit);
+    if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);  // let the W1 copy land (bounded)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
