@@ -170,43 +170,17 @@ __device__ __forceinline__ void item_rows(const GraphDev& g, const SceneDev& sc,
   }
 }
 
-// one out-of-line body per robot variant and mode: the persistent loop's own
-// state stays out of the register budget of the edge code (measured faster
-// than inlining the variants into one switch, which spills); the problem's
-// graph and scene descriptors are read from shared memory, not held in
-// registers (the single-problem kernel has them in its parameter bank)
+// One persistent kernel per robot variant and mode, launched one after another
+// on the batch stream over that variant's share of the work list: each keeps
+// its edge code inlined, as the single-problem kernel does (one kernel for
+// all variants needed out-of-line bodies, which cost ~12 % per edge, or
+// spilled); the problem's graph and scene descriptors are read from shared
+// memory, the robot constants too (a batch holds a robot per problem).
 template <int VAR, bool LAZY>
-__device__ __noinline__ void item_rows_call(const GraphDev& g, const SceneDev& sc, int layer, int row0, int rows,
-                                            int col0, int cols, int chunk, const float* s_V, const RobotDev& rb,
-                                            const float4* s_obs, int* s_next) {
-  item_rows<VAR, LAZY>(g, sc, layer, row0, rows, col0, cols, chunk, s_V, rb, s_obs, s_next);
-}
-
-template <bool LAZY>
-__device__ __forceinline__ void item_dispatch(int variant, const GraphDev& g, const SceneDev& sc, int layer,
-                                              const WorkItem& w, int chunk, const float* s_V, const RobotDev& rb,
-                                              const float4* s_obs, int* s_next) {
-  switch (variant) {
-    case kVarPoint:
-      item_rows_call<kVarPoint, LAZY>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, rb, s_obs, s_next);
-      break;
-    case kVarArm6x4:
-      item_rows_call<kVarArm6x4, LAZY>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, rb, s_obs, s_next);
-      break;
-    case kVarArm7x4:
-      item_rows_call<kVarArm7x4, LAZY>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, rb, s_obs, s_next);
-      break;
-    default:
-      item_rows_call<kVarArmGeneric, LAZY>(g, sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, rb, s_obs,
-                                           s_next);
-      break;
-  }
-}
-
 __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
     batch_persistent_kernel(const ProblemDev* __restrict__ probs, const RobotDev* __restrict__ robots,
                             const WorkItem* __restrict__ items, int n_items, const int* __restrict__ need,
-                            int* done, int* next_item, int chunk, int lazy, int* err) {
+                            int* done, int* next_item, int chunk, int* err) {
   __shared__ RobotDev s_rb;
   // raw storage: the descriptor types have default member initialisers
   __shared__ __align__(16) unsigned char s_g_raw[sizeof(GraphDev)];
@@ -271,10 +245,7 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
       s_V[j] = P.g.vflag[v] ? kInf : key_value(__ldcg(P.g.keys + v));
     }
     __syncthreads();
-    if (lazy)
-      item_dispatch<true>(P.variant, s_g, s_sc, layer, w, chunk, s_V, s_rb, smem, &s_next);
-    else
-      item_dispatch<false>(P.variant, s_g, s_sc, layer, w, chunk, s_V, s_rb, smem, &s_next);
+    item_rows<VAR, LAZY>(s_g, s_sc, layer, w.row0, w.rows, w.col0, w.cols, chunk, s_V, s_rb, smem, &s_next);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(done + P.need_base + w.depth, 1);
@@ -312,7 +283,9 @@ using namespace gtmp_batch_impl;
 
 struct gtmp_batch {
   int n = 0, H = 0, L_max = 0, M_max = 0, obs4_max = 0;
-  int num_sms = 148, bps = 1;
+  int num_sms = 148;
+  int bps[4][2] = {};                    // persistent blocks per SM per variant and mode (early exit, lazy)
+  int item_begin[5] = {};                // the work list holds variant v's items in [item_begin[v], item_begin[v + 1])
   cudaStream_t stream = nullptr;
   // host copies
   std::vector<ProblemDev> probs;
@@ -329,7 +302,7 @@ struct gtmp_batch {
   RobotDev* d_robots = nullptr;
   WorkItem* d_items = nullptr;
   int* d_need = nullptr;
-  int* d_done = nullptr;  // [need.size()] done counters followed by the item counter
+  int* d_done = nullptr;  // [need.size()] done counters followed by one item counter per variant
   int* d_err = nullptr;
   float4* d_obs = nullptr;
   float* d_Q = nullptr;
@@ -411,7 +384,7 @@ bool make_robot(const gtmp_robot& r, RobotDev* rb, int* variant, int* dp) {
   return true;
 }
 
-constexpr int kBatchGridCells = 4096;
+constexpr int kBatchGridCells = 16384;
 
 // scalar or packed obstacle table of one problem (the layout gtmp_set_obstacles writes)
 int obstacle_table(const gtmp_problem& q, const RobotDev& rb, int variant, std::vector<float4>& out, SceneDev* sc) {
@@ -453,10 +426,12 @@ int obstacle_table(const gtmp_problem& q, const RobotDev& rb, int variant, std::
 gtmp_status build_items(gtmp_batch* b) {
   std::vector<WorkItem> items;
   std::fill(b->need.begin(), b->need.end(), 0);
-  for (int d = 0; d <= b->L_max; ++d)
+  for (int v = 0; v < 4; ++v) {
+   b->item_begin[v] = static_cast<int>(items.size());
+   for (int d = 0; d <= b->L_max; ++d)
     for (int p = 0; p < b->n; ++p) {
       const ProblemDev& P = b->probs[p];
-      if (d > P.g.L) continue;
+      if (P.variant != v || d > P.g.L) continue;
       const int layer = P.g.L - d;
       const int rows = layer_size(P.g, layer), cols = layer_size(P.g, layer + 1);
       // boundary transitions (start row, goal column) sit at the two ends of
@@ -489,6 +464,8 @@ gtmp_status build_items(gtmp_batch* b) {
         b->need[P.need_base + d] += 1;
       }
     }
+  }
+  b->item_begin[4] = static_cast<int>(items.size());
   b->n_items = static_cast<int>(items.size());
   cudaFree(b->d_items);
   b->d_items = nullptr;
@@ -500,7 +477,7 @@ gtmp_status build_items(gtmp_batch* b) {
 
 gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
   cudaStream_t st = b->stream;
-  const size_t n_done = b->need.size() + 1;
+  const size_t n_done = b->need.size() + 4;
   BATCH_TRY(b, cudaMemsetAsync(b->d_done, 0, n_done * sizeof(int), st));
   const int per_problem_blocks = std::max(1, std::min(64, ((b->L_max + 2) * b->M_max + kThreads - 1) / kThreads));
   batch_init_kernel<<<dim3(per_problem_blocks, b->n), kThreads, 0, st>>>(b->d_probs);
@@ -511,10 +488,31 @@ gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
                                                                                                     b->d_robots);
   BATCH_TRY(b, cudaGetLastError());
   const size_t smem = b->obs4_max * sizeof(float4) + static_cast<size_t>(b->M_max) * sizeof(float);
-  batch_persistent_kernel<<<b->num_sms * b->bps, kThreads, smem, st>>>(
-      b->d_probs, b->d_robots, b->d_items, b->n_items, b->d_need, b->d_done, b->d_done + b->need.size(), b->chunk,
-      b->eval_mode == GTMP_EVAL_LAZY ? 1 : 0, b->d_err);
-  BATCH_TRY(b, cudaGetLastError());
+  const int lazy = b->eval_mode == GTMP_EVAL_LAZY ? 1 : 0;
+  for (int v = 0; v < 4; ++v) {
+    const int n_items = b->item_begin[v + 1] - b->item_begin[v];
+    if (n_items == 0) continue;
+    const dim3 grid(b->num_sms * b->bps[v][lazy]);
+    const WorkItem* items = b->d_items + b->item_begin[v];
+    int* counter = b->d_done + b->need.size() + v;
+#define GTMP_BATCH_LAUNCH(VAR)                                                                                     \
+  if (lazy)                                                                                                        \
+    batch_persistent_kernel<VAR, true><<<grid, kThreads, smem, st>>>(b->d_probs, b->d_robots, items, n_items,      \
+                                                                     b->d_need, b->d_done, counter, b->chunk,     \
+                                                                     b->d_err);                                    \
+  else                                                                                                             \
+    batch_persistent_kernel<VAR, false><<<grid, kThreads, smem, st>>>(b->d_probs, b->d_robots, items, n_items,     \
+                                                                      b->d_need, b->d_done, counter, b->chunk,    \
+                                                                      b->d_err)
+    switch (v) {
+      case kVarPoint: GTMP_BATCH_LAUNCH(kVarPoint); break;
+      case kVarArm6x4: GTMP_BATCH_LAUNCH(kVarArm6x4); break;
+      case kVarArm7x4: GTMP_BATCH_LAUNCH(kVarArm7x4); break;
+      default: GTMP_BATCH_LAUNCH(kVarArmGeneric); break;
+    }
+#undef GTMP_BATCH_LAUNCH
+    BATCH_TRY(b, cudaGetLastError());
+  }
   batch_paths_kernel<<<(b->n + 127) / 128, 128, 0, st>>>(b->d_probs, b->n, b->L_max, dev_paths, dev_costs);
   BATCH_TRY(b, cudaGetLastError());
   return GTMP_OK;
@@ -607,17 +605,31 @@ GTMP_API gtmp_status gtmp_batch_create(const gtmp_problem* problems, int32_t n, 
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return fail_create(e);
   if ((e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return fail_create(e);
-  if ((e = cudaFuncSetAttribute(batch_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                200 * 1024)) != cudaSuccess)
-    return fail_create(e);
   if ((e = cudaFuncSetAttribute(batch_labels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) !=
       cudaSuccess)
     return fail_create(e);
   const size_t smem = b->obs4_max * sizeof(float4) + static_cast<size_t>(b->M_max) * sizeof(float);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->bps, batch_persistent_kernel, kThreads, smem)) !=
-      cudaSuccess)
-    return fail_create(e);
-  if (b->bps < 1) b->bps = 1;
+  {
+    const void* kernels[4][2] = {
+        {reinterpret_cast<const void*>(batch_persistent_kernel<kVarPoint, false>),
+         reinterpret_cast<const void*>(batch_persistent_kernel<kVarPoint, true>)},
+        {reinterpret_cast<const void*>(batch_persistent_kernel<kVarArm6x4, false>),
+         reinterpret_cast<const void*>(batch_persistent_kernel<kVarArm6x4, true>)},
+        {reinterpret_cast<const void*>(batch_persistent_kernel<kVarArm7x4, false>),
+         reinterpret_cast<const void*>(batch_persistent_kernel<kVarArm7x4, true>)},
+        {reinterpret_cast<const void*>(batch_persistent_kernel<kVarArmGeneric, false>),
+         reinterpret_cast<const void*>(batch_persistent_kernel<kVarArmGeneric, true>)}};
+    for (int v = 0; v < 4; ++v)
+      for (int m = 0; m < 2; ++m) {
+        if ((e = cudaFuncSetAttribute(kernels[v][m], cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) !=
+            cudaSuccess)
+          return fail_create(e);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->bps[v][m], kernels[v][m], kThreads, smem)) !=
+            cudaSuccess)
+          return fail_create(e);
+        if (b->bps[v][m] < 1) b->bps[v][m] = 1;
+      }
+  }
   if ((e = cudaMalloc(&b->d_Q, std::max<size_t>(q_floats, 1) * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_vflag, std::max<size_t>(verts, 1))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_keys, std::max<size_t>(verts, 1) * sizeof(unsigned long long))) != cudaSuccess ||
@@ -625,7 +637,7 @@ GTMP_API gtmp_status gtmp_batch_create(const gtmp_problem* problems, int32_t n, 
       (e = cudaMalloc(&b->d_probs, n * sizeof(ProblemDev))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_robots, n * sizeof(RobotDev))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_need, (need_total + 1) * sizeof(int))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_done, (need_total + 1) * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_done, (need_total + 4) * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess)
     return fail_create(e);
   // rebase offsets to device pointers; write endpoints and obstacle tables
