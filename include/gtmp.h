@@ -342,7 +342,9 @@ typedef struct {
   double fused_ms;         /* their summed device time (ms) */
   double fused_edges;      /* candidate edges those launches processed */
   int64_t minplus_launches;  /* min-plus launches of gtmp_solve_unfused timed */
-  double minplus_ms;         /* their summed device time (ms) */
+  double minplus_ms;         /* device time of their sweeps (ms): one event pair around each
+                                sweep of L + 1 launches, which overlap as programmatic
+                                dependent launches */
   double minplus_bytes;      /* their algorithmic HBM bytes: 4 per stored edge cost read, 8 per
                                 cost-to-go read and 8 per cost-to-go written */
 } gtmp_profile;

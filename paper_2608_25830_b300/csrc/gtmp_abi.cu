@@ -676,7 +676,7 @@ gtmp_status gtmp_profile_read(gtmp_ctx* c, gtmp_profile* out) {
     CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev_pool[pr.first], c->ev_pool[pr.second]));
     mp += t;
   }
-  out->minplus_launches = static_cast<int64_t>(c->ev_minplus.size());
+  out->minplus_launches = c->minplus_launches;
   out->minplus_ms = mp;
   out->minplus_bytes = c->minplus_bytes;
   c->launches = 0;
@@ -684,6 +684,7 @@ gtmp_status gtmp_profile_read(gtmp_ctx* c, gtmp_profile* out) {
   c->timed_edges = 0.0;
   c->ev_minplus.clear();
   c->minplus_bytes = 0.0;
+  c->minplus_launches = 0;
   return GTMP_OK;
 }
 
@@ -733,28 +734,33 @@ gtmp_status gtmp_solve_unfused(gtmp_ctx* c, int32_t* dev_path, float* dev_cost) 
   if ((s = gtmp_internal_edge_costs(c)) != GTMP_OK) return s;
   const int L = c->p.L;
   GraphDev g = graph(c, 1, c->M_active);
-  // step 2: the min-plus sweep over the stored matrices
+  // step 2: the min-plus sweep over the stored matrices, each transition a
+  // programmatic dependent of the previous one (timed as one sweep: events
+  // between the launches would serialise them)
+  size_t slot = 0;
+  if (c->timing) {
+    slot = (c->ev_used.size() + c->ev_minplus.size()) * 2;
+    cudaEvent_t e0 = nullptr;
+    CUDA_TRY(c, event_at(c, slot, &e0));
+    CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+  }
   for (int layer = L; layer >= 0; --layer) {
     int rows, cols;
     transition_shape(g, layer, &rows, &cols);
     int grid = (rows + 7) / 8;
     if (grid > c->num_sms * 8) grid = c->num_sms * 8;
-    size_t slot = 0;
-    if (c->timing) {
-      slot = (c->ev_used.size() + c->ev_minplus.size()) * 2;
-      cudaEvent_t e0 = nullptr;
-      CUDA_TRY(c, event_at(c, slot, &e0));
-      CUDA_TRY(c, cudaEventRecord(e0, c->stream));
-    }
-    CUDA_TRY(c, launch_minplus(g, layer, c->C + c->c_off[layer], c->c_cs[layer], grid, c->stream));
+    CUDA_TRY(c, launch_minplus(g, layer, c->C + c->c_off[layer], c->c_cs[layer], grid, layer < L, c->stream));
     LAUNCHED(c, 1);
     if (c->timing) {
-      cudaEvent_t e1 = nullptr;
-      CUDA_TRY(c, event_at(c, slot + 1, &e1));
-      CUDA_TRY(c, cudaEventRecord(e1, c->stream));
-      c->ev_minplus.emplace_back(static_cast<int>(slot), static_cast<int>(slot + 1));
+      c->minplus_launches += 1;
       c->minplus_bytes += 4.0 * rows * cols + 8.0 * cols + 8.0 * rows;
     }
+  }
+  if (c->timing) {
+    cudaEvent_t e1 = nullptr;
+    CUDA_TRY(c, event_at(c, slot + 1, &e1));
+    CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+    c->ev_minplus.emplace_back(static_cast<int>(slot), static_cast<int>(slot + 1));
   }
   CUDA_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, c->stream));
   LAUNCHED(c, 1);

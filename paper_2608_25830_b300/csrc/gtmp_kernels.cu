@@ -307,8 +307,14 @@ __device__ __forceinline__ void minplus_load(float4 (&c)[kMpBatch], const float4
   }
 }
 
+// Launched as a programmatic dependent of the previous transition's sweep
+// (except the first): the next launch may start as soon as this one is
+// running, its first row of C (written by kernels that completed before the
+// first sweep began) loads while this one finishes, and only the cost-to-go
+// J_{l+1} waits for the previous grid (griddepcontrol.wait).
 __global__ void __launch_bounds__(kThreads) minplus_kernel(GraphDev g, int layer, const float* __restrict__ C, int cs) {
   extern __shared__ __align__(16) float s_Vm[];
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int n_rows = layer_size(g, layer), n_cols = layer_size(g, layer + 1);
   const int lane = threadIdx.x & 31;
   const int warps_total = gridDim.x * kWarps;
@@ -316,6 +322,7 @@ __global__ void __launch_bounds__(kThreads) minplus_kernel(GraphDev g, int layer
   int i = blockIdx.x * kWarps + (threadIdx.x >> 5);
   float4 c[kMpBatch];
   if (i < n_rows) minplus_load(c, reinterpret_cast<const float4*>(C + static_cast<size_t>(i) * cs), lane, n4);
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // J_{l+1} is the previous sweep's output
   // stage J_{l+1}: all of a thread's key loads are issued before the first is used
   constexpr int kFill = 8;
   const unsigned long long* knext = g.keys + vidx(g, 0, layer + 1, 0);
@@ -1070,9 +1077,19 @@ cudaError_t launch_edge_costs(const GraphDev& g, int layer, const RobotDev& rb, 
   return by_variant<EdgeCostsRun>(variant, g, layer, rb, sc, C, cs, counter, grid_x, chunk, err, st);
 }
 
-cudaError_t launch_minplus(const GraphDev& g, int layer, const float* C, int cs, int grid, cudaStream_t st) {
-  minplus_kernel<<<grid, kThreads, static_cast<size_t>(cs) * 4, st>>>(g, layer, C, cs);
-  return cudaGetLastError();
+cudaError_t launch_minplus(const GraphDev& g, int layer, const float* C, int cs, int grid, bool dependent,
+                           cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = static_cast<size_t>(cs) * 4;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, minplus_kernel, g, layer, C, cs);
 }
 
 // goal vertex reached by graph gi's best chain (-1 if infeasible)

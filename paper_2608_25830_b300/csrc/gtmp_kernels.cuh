@@ -125,7 +125,8 @@ cudaError_t launch_get_values(const GraphDev& g, float* V, int32_t* sigma, cudaS
 cudaError_t launch_pack_layers(const GraphDev& g, float* user, int dof, int to_internal, cudaStream_t st);
 cudaError_t launch_edge_costs(const GraphDev& g, int layer, const RobotDev& rb, int variant, const SceneDev& sc,
                               float* C, int cs, int* counter, int grid_x, int chunk, int* err, cudaStream_t st);
-cudaError_t launch_minplus(const GraphDev& g, int layer, const float* C, int cs, int grid, cudaStream_t st);
+cudaError_t launch_minplus(const GraphDev& g, int layer, const float* C, int cs, int grid, bool dependent,
+                           cudaStream_t st);
 cudaError_t launch_expand(const GraphDev& g, int dof, const float* lo, const float* hi, unsigned long long seed,
                           int M_old, int M_new, const float* c_best, int max_attempts, int* err, cudaStream_t st);
 cudaError_t launch_gather_chain(const GraphDev& g, const int32_t* path, float* chain, int dof, int rows,
