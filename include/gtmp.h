@@ -339,7 +339,8 @@ GTMP_API gtmp_status aogtmp_run(gtmp_ctx* ctx, uint64_t seed, const gtmp_ao_sche
 typedef struct {
   int64_t launches;        /* kernels enqueued since the last read */
   int64_t fused_launches;  /* fused edge + min-plus launches timed */
-  double fused_ms;         /* their summed device time (ms) */
+  double fused_ms;         /* device time of their sweeps (ms): one event pair around each sweep of
+                              L + 1 launches, which overlap as programmatic dependent launches */
   double fused_edges;      /* candidate edges those launches processed */
   int64_t minplus_launches;  /* min-plus launches of gtmp_solve_unfused timed */
   double minplus_ms;         /* device time of their sweeps (ms): one event pair around each

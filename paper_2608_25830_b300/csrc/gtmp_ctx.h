@@ -68,7 +68,8 @@ struct gtmp_ctx {
   double timed_edges = 0.0;
   std::vector<std::pair<int, int>> ev_minplus;  // (start, end) indices into ev_pool
   double minplus_bytes = 0.0;
-  int64_t minplus_launches = 0;                 // min-plus launches timed (the sweeps in ev_minplus)
+  int64_t minplus_launches = 0;
+  int64_t fused_timed_launches = 0;             // fused launches timed (the sweeps in ev_used)                 // min-plus launches timed (the sweeps in ev_minplus)
   // learned collision surrogate (allocated by gtmp_surrogate_train)
   gtmp::SurrogateState* sur = nullptr;
   uint8_t* prune = nullptr;  // per-transition prune mask, M x M

@@ -172,11 +172,17 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks) fused_transition_ke
   const int r = blockIdx.y;
   const int n_rows = layer_size(g, layer), n_cols = layer_size(g, layer + 1);
 
+  // launched as a programmatic dependent of the previous transition (except the
+  // first): the obstacle table stages while that grid finishes, and only the
+  // cost-to-go J_{l+1}, its output, waits for it
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (!stage_obstacles(s_obs, sc.obs, n4, &mbar, err)) return;  // also a block barrier
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int j = threadIdx.x; j < n_cols; j += blockDim.x) {
     const size_t v = vidx(g, r, layer + 1, j);
     s_V[j] = g.vflag[v] ? kInf : key_value(g.keys[v]);
   }
-  if (!stage_obstacles(s_obs, sc.obs, n4, &mbar, err)) return;  // also a block barrier
+  __syncthreads();
 
   const int lane = threadIdx.x & 31;
   const int cpr = (n_cols + chunk - 1) / chunk;
@@ -584,23 +590,30 @@ Box16 make_box(const float* lo, const float* hi, int dof) {
 
 template <int VAR, int MODE>
 cudaError_t fused_dispatch_mode(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int* counters,
-                                int grid_x, int chunk, int* err, cudaStream_t st) {
-  const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16 + static_cast<size_t>(g.M_stride) * 4;
+                                int grid_x, int chunk, int* err, bool dependent, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_x, g.R);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = static_cast<size_t>(scene_float4s(sc)) * 16 + static_cast<size_t>(g.M_stride) * 4;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent ? 1 : 0;
   if (g.n_wb > 0)
-    fused_transition_kernel<VAR, MODE, true>
-        <<<dim3(grid_x, g.R), kThreads, smem, st>>>(g, layer, rb, sc, counters, chunk, err);
-  else
-    fused_transition_kernel<VAR, MODE, false>
-        <<<dim3(grid_x, g.R), kThreads, smem, st>>>(g, layer, rb, sc, counters, chunk, err);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, fused_transition_kernel<VAR, MODE, true>, g, layer, rb, sc, counters, chunk, err);
+  return cudaLaunchKernelEx(&cfg, fused_transition_kernel<VAR, MODE, false>, g, layer, rb, sc, counters, chunk, err);
 }
 
 template <int VAR>
 cudaError_t fused_dispatch(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int mode,
-                           int* counters, int grid_x, int chunk, int* err, cudaStream_t st) {
-  if (mode == kEvalFull) return fused_dispatch_mode<VAR, kEvalFull>(g, layer, rb, sc, counters, grid_x, chunk, err, st);
-  if (mode == kEvalLazy) return fused_dispatch_mode<VAR, kEvalLazy>(g, layer, rb, sc, counters, grid_x, chunk, err, st);
-  return fused_dispatch_mode<VAR, kEvalEarlyExit>(g, layer, rb, sc, counters, grid_x, chunk, err, st);
+                           int* counters, int grid_x, int chunk, int* err, bool dependent, cudaStream_t st) {
+  if (mode == kEvalFull)
+    return fused_dispatch_mode<VAR, kEvalFull>(g, layer, rb, sc, counters, grid_x, chunk, err, dependent, st);
+  if (mode == kEvalLazy)
+    return fused_dispatch_mode<VAR, kEvalLazy>(g, layer, rb, sc, counters, grid_x, chunk, err, dependent, st);
+  return fused_dispatch_mode<VAR, kEvalEarlyExit>(g, layer, rb, sc, counters, grid_x, chunk, err, dependent, st);
 }
 
 template <template <int> class F, typename... Args>
@@ -649,8 +662,8 @@ struct LabelConfigsRun {
 template <int VAR>
 struct FusedRun {
   static cudaError_t run(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int mode,
-                         int* counters, int grid_x, int chunk, int* err, cudaStream_t st) {
-    return fused_dispatch<VAR>(g, layer, rb, sc, mode, counters, grid_x, chunk, err, st);
+                         int* counters, int grid_x, int chunk, int* err, bool dependent, cudaStream_t st) {
+    return fused_dispatch<VAR>(g, layer, rb, sc, mode, counters, grid_x, chunk, err, dependent, st);
   }
 };
 
@@ -1044,8 +1057,9 @@ cudaError_t launch_label_configs(const float* q, int n, int dof, const RobotDev&
 }
 
 cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev& rb, int variant, const SceneDev& sc,
-                                    int mode, int* counters, int grid_x, int chunk, int* err, cudaStream_t st) {
-  return by_variant<FusedRun>(variant, g, layer, rb, sc, mode, counters, grid_x, chunk, err, st);
+                                    int mode, int* counters, int grid_x, int chunk, int* err, cudaStream_t st,
+                                    bool dependent) {
+  return by_variant<FusedRun>(variant, g, layer, rb, sc, mode, counters, grid_x, chunk, err, dependent, st);
 }
 
 int fused_max_blocks_per_sm(int variant, int mode) {

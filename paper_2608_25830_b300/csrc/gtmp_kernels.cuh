@@ -115,9 +115,11 @@ cudaError_t launch_vertex_labels(const GraphDev& g, const RobotDev& rb, int vari
                                  cudaStream_t st);
 cudaError_t launch_label_configs(const float* q, int n, int dof, const RobotDev& rb, int variant,
                                  const SceneDev& sc, uint8_t* out, cudaStream_t st);
+// dependent: launch as a programmatic dependent of the previous kernel on the
+// stream (that kernel must be the previous transition of the same sweep)
 cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev& rb, int variant,
                                     const SceneDev& sc, int mode, int* counters, int grid_x, int chunk, int* err,
-                                    cudaStream_t st);
+                                    cudaStream_t st, bool dependent = false);
 int fused_max_blocks_per_sm(int variant, int mode);
 cudaError_t launch_extract_paths(const GraphDev& g, int32_t* path, float* cost, int32_t* best, cudaStream_t st);
 cudaError_t launch_goal_reached(const GraphDev& g, int gi, int32_t* goal, cudaStream_t st);
