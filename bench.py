@@ -228,10 +228,10 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one full-evaluation launch of the fused kernel on a 1024 x 1024
-# transition of this workload, from an ncu capture of this kernel (set back to None whenever the
-# kernel changes); the algorithmic bytes per launch are the two sample layers, the cost-to-go and
-# the obstacle table, about 0.1 MB, so HBM is not the bound
-FULL_MODE_DRAM_BYTES_PER_LAUNCH = 502016
+# transition of this workload, from the ncu capture summarised in
+# profiles/fused_transition_arm7_m1024_l8_h32.md (set back to None whenever the kernel changes); the
+# algorithmic bytes per launch are reported beside it
+FULL_MODE_DRAM_BYTES_PER_LAUNCH = 172800
 
 
 def measured_peaks():
@@ -521,9 +521,9 @@ def run_ours(args, wl):
                          "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": FULL_MODE_DRAM_BYTES_PER_LAUNCH,
                          "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one 1024 x 1024 transition "
-                                         "launch (ncu --metrics capture), unchanged kernel; the algorithmic bytes "
-                                         "(two sample layers, cost-to-go, obstacle table with its cull grid) are "
-                                         "~0.15 MB, read once per launch",
+                                         "launch (ncu --set full capture of the current kernel); the staged block "
+                                         "also carries the 64 KB cull grid, so traffic is about the algorithmic "
+                                         "bytes plus the grid: each byte read once",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2032 MHz (max clock)",
                          "ffma_measured": ffma_tflops, "frac_of_ffma_measured": achieved / ffma_tflops,
                          "ffma_note": "gtmp_fp32_fma_peak: independent FMA chains on every SM, best of 6 launches",
