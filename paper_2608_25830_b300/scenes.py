@@ -170,14 +170,14 @@ def pick_endpoints(scene: Scene, config_free) -> Scene:
     return scene.with_endpoints(int(ok[0]))
 
 
-def corridor_scene(w: float = 0.1, t: float = 0.3) -> Scene:
+def corridor_scene(w: float = 0.1, t: float = 0.3, x0: float = 0.9) -> Scene:
     """2D point robot in a corridor: the free strip |y| < w, walled off by two
-    boxes of thickness t from the chambers |y| > w + t; start (-0.9, 0) and
-    goal (0.9, 0) in the strip.  Every chain must keep each layer vertex in
+    boxes of thickness t from the chambers |y| > w + t; start (-x0, 0) and
+    goal (x0, 0) in the strip.  Every chain must keep each layer vertex in
     the strip (the layerwise-hitting instance of the appendix)."""
     boxes = _f32([[-1.2, w, -1.0, 1.2, w + t, 1.0], [-1.2, -w - t, -1.0, 1.2, -w, 1.0]])
-    return Scene(point_robot_2d(), np.zeros((0, 4), np.float32), boxes, _f32([-0.9, 0.0]), _f32([0.9, 0.0]), None,
-                 f"corridor-w{w}-t{t}")
+    return Scene(point_robot_2d(), np.zeros((0, 4), np.float32), boxes, _f32([-x0, 0.0]), _f32([x0, 0.0]), None,
+                 f"corridor-w{w}-t{t}-x{x0}")
 
 
 def weight_bumps(scene: Scene, seed: int = 0, K: int = 6, amin: float = 0.5, amax: float = 3.0,

@@ -432,6 +432,37 @@ def test_anytime_corridor_coverage_frequency(torch_cuda):
         assert math.isfinite(sol.cost_lo) == bool(np.isfinite(costs[r])), r
 
 
+def test_anytime_single_class_coverage_lower_bound(torch_cuda):
+    """Thm. 1 of Sec. V on the GPU anytime solver (2048 restarts of a wide strip, L = 2, N = 256): every
+    restart whose samples hit every waypoint ball (found from the oracle's bit-identical samples) returns a
+    chain no costlier than the chain through those samples, and the coverage frequency is at least
+    1 - sum_m (1 - p_m)^N."""
+    from test_oracle_pins import TUBE, ball_chain, tube_waypoint_balls
+    cfg = TUBE
+    sc = scenes.corridor_scene(cfg["w"], cfg["t"], cfg["x0"])
+    centres, p_m = tube_waypoint_balls(cfg)
+    L, N, H, R = cfg["L"], cfg["N"], cfg["H"], 2048
+    p = _planner(sc, N, L, H, R=R)
+    paths, costs, best = p.anytime(91, R)
+    p.synchronize()
+    costs = costs.cpu().numpy()
+    all_hit = 0
+    for r in range(R):
+        Q = oracle.sample_uniform(91, r, L, N, sc.robot.q_lo, sc.robot.q_hi)
+        chain = ball_chain(Q, centres, cfg["r"])
+        if chain is None:
+            continue
+        all_hit += 1
+        total, worst = oracle.path_cost(sc, Q, np.array(chain), H)
+        assert worst > 0.0
+        assert np.isfinite(costs[r]) and costs[r] <= total * (1 + REL), (r, costs[r], total)
+    exact = (1.0 - (1.0 - p_m) ** N) ** L
+    bound = 1.0 - L * (1.0 - p_m) ** N
+    sigma = math.sqrt(exact * (1 - exact) / R)
+    assert abs(all_hit / R - exact) < 4.5 * sigma, (all_hit / R, exact)
+    assert float(np.isfinite(costs).mean()) >= bound - 4.5 * sigma
+
+
 @pytest.mark.parametrize("mode", [binding.EVAL_EARLY_EXIT, binding.EVAL_LAZY])
 def test_sample_and_solve_capture_in_a_cuda_graph(torch_cuda, mode):
     """Every step of a plan is enqueued on the context's stream with nothing

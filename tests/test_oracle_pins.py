@@ -827,3 +827,66 @@ def test_corridor_coverage_frequency_matches_the_closed_form():
     # bound 1 - L (1 - p_m)^N with waypoint balls of radius w is below it
     p_m = math.pi * w * w / 4.0
     assert 1.0 - L * (1.0 - p_m) ** N <= p
+
+
+# ---------------------------------------------------------------------------
+# Coverage of one class (Thm. 1 of Sec. V with the straight-line case of its
+# tube lemma): a lower bound from waypoint balls
+# ---------------------------------------------------------------------------
+
+TUBE = dict(w=0.45, t=0.3, x0=0.5, L=2, N=256, H=16, r=0.1)
+
+
+def tube_waypoint_balls(cfg):
+    """The reference path f = the segment q0 -> qg (length 1, clearance 0.45 in the strip and the box), its
+    layer points f(t_m), t_m = m / (L + 1), and the ball mass p_m = pi r^2 / 4 under uniform sampling of
+    [-1, 1]^2 (the balls lie inside the box and the free strip)."""
+    L, x0 = cfg["L"], cfg["x0"]
+    centres = [np.array([-x0 + 2 * x0 * m / (L + 1), 0.0]) for m in range(1, L + 1)]
+    length, clearance = 2 * x0, min(cfg["w"], 1.0 - x0)
+    # the straight-line case of the tube lemma needs length / (L + 1) + r < clearance
+    assert length / (L + 1) + cfg["r"] < clearance
+    return centres, math.pi * cfg["r"] ** 2 / 4.0
+
+
+def ball_chain(Q, centres, r):
+    """Indices of one sample per layer inside its waypoint ball (the first), or None if a layer misses."""
+    out = []
+    for l, c in enumerate(centres):
+        d = np.linalg.norm(Q[l].astype(np.float64) - c[None, :], axis=1)
+        hit = np.nonzero(d < r)[0]
+        if hit.size == 0:
+            return None
+        out.append(int(hit[0]))
+    return out
+
+
+def test_single_class_coverage_lower_bound():
+    """Thm. 1: Pr[cover] >= 1 - sum_m (1 - p_m)^N (straight-line planner: a free segment is always found, so
+    the planner term vanishes).  The free strip is simply connected, so covering f's class is finding a chain.
+    Per graph: whenever every layer has a sample in its waypoint ball, the chain through those samples is free
+    at every waypoint (the tube lemma) and the optimum costs at most as much; over 300 graphs the frequency of
+    'every layer hits' matches its exact value prod_m (1 - (1 - p_m)^N), and coverage is at least the bound."""
+    cfg = TUBE
+    sc = scenes.corridor_scene(cfg["w"], cfg["t"], cfg["x0"])
+    centres, p_m = tube_waypoint_balls(cfg)
+    L, N, H, K = cfg["L"], cfg["N"], cfg["H"], 300
+    all_hit = covered = 0
+    for k in range(K):
+        Q = oracle.sample_uniform(91, k, L, N, sc.robot.q_lo, sc.robot.q_hi)
+        sol = oracle.solve(sc, Q, H)
+        covered += math.isfinite(sol.cost_lo)
+        chain = ball_chain(Q, centres, cfg["r"])
+        if chain is None:
+            continue
+        all_hit += 1
+        total, worst = oracle.path_cost(sc, Q, np.array(chain), H)
+        assert worst > 0.0, (k, worst)                         # the ball chain is free
+        assert sol.cost_lo <= total * (1 + 1e-12), (k, sol.cost_lo, total)
+    exact = (1.0 - (1.0 - p_m) ** N) ** L
+    bound = 1.0 - L * (1.0 - p_m) ** N
+    assert bound <= exact
+    sigma = math.sqrt(exact * (1 - exact) / K)
+    assert abs(all_hit / K - exact) < 4.5 * sigma, (all_hit / K, exact)
+    assert covered / K >= bound - 4.5 * sigma, (covered / K, bound)
+    assert covered >= all_hit
