@@ -590,7 +590,7 @@ def _timed_passes(fn, steps, flush, stream):
 
 
 def measure_batched(args, wl, flush, steps, warmup, lazy=True, breakdown=False):
-    """512 uneven problems (2D point robots and 7-DoF arms): one persistent launch per batch against the plain
+    """512 uneven problems (2D point robots and 7-DoF arms): one persistent launch per robot variant against the plain
     single-problem solver running the same problems one after another, early exit and lazy."""
     import numpy as np
     import torch
@@ -607,15 +607,11 @@ def measure_batched(args, wl, flush, steps, warmup, lazy=True, breakdown=False):
             sc = gpu_endpoints(binding, scenes, sc)
         problems.append((sc, bp.M, bp.L, bp.seed))
     stream = torch.cuda.current_stream()
-    subset = problems[::max(1, len(problems) // 96)][:96]
 
     def batched_form(mode):
-        tune = binding.Batch(subset, H, eval_mode=mode)      # tile autotuning on 96 problems, untimed
-        tune.autotune(repeats=1)
-        tiling = binding.gtmp_batch_get_tiling(tune.handle)
-        tune.close()
         b = binding.Batch(problems, H, eval_mode=mode)
-        binding.gtmp_batch_set_tiling(b.handle, *tiling)
+        b.autotune(repeats=1)                                   # per-kind tile autotuning on the batch, untimed
+        tiling = binding.gtmp_batch_get_tilings(b.handle)
         for _ in range(warmup):
             b.solve()
         b.synchronize()
@@ -648,6 +644,7 @@ def measure_batched(args, wl, flush, steps, warmup, lazy=True, breakdown=False):
             costs = b.costs.cpu().numpy()
             nominal = b.nominal_checks
             items = b.work_items
+            kernels = b.kernels_per_solve
             b.close()
             planners, run = plain_form(mode)
             p_ms = _timed_passes(run, steps, flush, stream)
@@ -664,24 +661,27 @@ def measure_batched(args, wl, flush, steps, warmup, lazy=True, breakdown=False):
                 "batched_over_plain": p_s / b_s,
                 "batched_checks_per_s": nominal * steps * world / b_s,
                 "batched_ms_per_batch": sum(b_ms) / len(b_ms), "plain_ms_per_batch": sum(p_ms) / len(p_ms),
-                "tiling": list(tiling), "work_items": items, "checks_per_batch": nominal,
+                "tiling": {"point": list(tiling[binding.ROBOT_POINT]), "arm": list(tiling[binding.ROBOT_DH_ARM])},
+                "work_items": items, "checks_per_batch": nominal,
                 "feasible": int(np.isfinite(costs).sum()),
                 "same_costs_batched_plain": bool(np.array_equal(costs, plain_costs)),
                 "same_costs_as_early_exit": bool(np.array_equal(costs, ref_costs)),
-                "gpu_launches_per_batch": 5,
+                "gpu_launches_per_batch": kernels,
             }
     out["clocks"] = clk.summary()
     out["steps"], out["warmup"] = steps, warmup
     out["l2"] = "flushed before every batch and every plain pass"
     out["note"] = ("plain = gtmp_sample_layers + gtmp_solve per problem, one after another on one stream; "
-                   "batched = gtmp_batch_solve (one persistent launch); same problems and seeds")
+                   "batched = gtmp_batch_solve (one persistent launch per robot variant, tilings autotuned "
+                   "per robot kind before timing); same problems and seeds")
     if breakdown:
         out["breakdown"] = {}
-        tiling = out["early_exit"]["tiling"]
+        t = out["early_exit"]["tiling"]
+        tiling = {binding.ROBOT_POINT: t["point"], binding.ROBOT_DH_ARM: t["arm"]}
         for name, keep in (("arm", lambda sc: sc.robot.dof > 3), ("point2d", lambda sc: sc.robot.dof <= 3)):
             sub = [p for p in problems if keep(p[0])]
             sb = binding.Batch(sub, H)
-            binding.gtmp_batch_set_tiling(sb.handle, *tiling)
+            binding.gtmp_batch_set_tilings(sb.handle, tiling)
             sb.solve()
             torch.cuda.synchronize()
             t_b = _timed_passes(sb.solve, 1, flush, stream)[0] / 1e3
@@ -719,7 +719,8 @@ def run_batched(args, wl):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scenes and samples)", "solves_per_s": ee["batched_solves_per_s"],
             "config": {"workload": args.workload, "problems": wl["n"], "H": wl["H"], "l2": r["l2"]},
-            "gpu_launches": 5 * args.steps, "clocks": r["clocks"], "batched": r}), flush=True)
+            "gpu_launches": ee["gpu_launches_per_batch"] * args.steps, "clocks": r["clocks"], "batched": r}),
+              flush=True)
 
 
 def measure_surrogate(args, wl, flush, steps, warmup, n_train=None, epochs=None):

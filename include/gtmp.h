@@ -412,7 +412,11 @@ typedef struct {
 typedef struct gtmp_batch gtmp_batch;
 
 /* Copy n problems (H waypoints per edge for all) to the device and build the
- * work list (items of rows ordered by distance from the goal layer). */
+ * work list (items of rows ordered by distance from the goal layer).
+ * GTMP_ERR_INVALID_ARG for a problem outside the limits above (at most 4096
+ * obstacles); GTMP_ERR_UNSUPPORTED when one problem's obstacle table and
+ * cost-to-go row (16 B per obstacle float4, 4 B per sample) exceed the
+ * 200 KB of shared memory an item stages them in. */
 GTMP_API gtmp_status gtmp_batch_create(const gtmp_problem* problems, int32_t n, int32_t H, void* cuda_stream,
                                        gtmp_batch** out);
 GTMP_API gtmp_status gtmp_batch_destroy(gtmp_batch* b);
@@ -420,14 +424,18 @@ GTMP_API const char* gtmp_batch_last_error(const gtmp_batch* b);
 GTMP_API gtmp_status gtmp_batch_set_stream(gtmp_batch* b, void* cuda_stream);
 
 /* L_max = max L over problems; nominal_checks = sum over problems of
- * H (2M + (L-1) M^2); work_items = items in the current work list. */
+ * H (2M + (L-1) M^2); work_items = items in the current work list;
+ * kernels = kernel launches one gtmp_batch_solve enqueues (each output
+ * optional, host). */
 GTMP_API gtmp_status gtmp_batch_info(const gtmp_batch* b, int32_t* L_max, double* nominal_checks,
-                                     int32_t* work_items);
+                                     int32_t* work_items, int32_t* kernels);
 
 /* Sample, label and solve all problems: dev_paths device [n][L_max] int32
  * (problem p's layer indices in columns 0..L_p-1, -1 elsewhere or when
  * infeasible), dev_costs device [n] float32 (+inf when infeasible).  Enqueues
- * five kernels (one persistent) and a memset on the batch stream; no host
+ * a memset, three set-up kernels, one persistent kernel per robot variant in
+ * the batch (point robot, 6- and 7-joint uniform-radius arms, other arms)
+ * and a path kernel on the batch stream; no host
  * synchronisation, so the call can be captured in a CUDA graph.  Every
  * device-side dependency wait is bounded (about 2 s without progress of the
  * awaited items); a wait that gives up abandons its item and sets the error
@@ -435,13 +443,23 @@ GTMP_API gtmp_status gtmp_batch_info(const gtmp_batch* b, int32_t* L_max, double
 GTMP_API gtmp_status gtmp_batch_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs);
 GTMP_API gtmp_status gtmp_batch_synchronize(gtmp_batch* b);
 
-/* Tiling of the work list: about target_edges candidate edges per item (arm
- * edges; point-robot items hold 16 times as many; an item smaller than a row
- * is a column piece of one row), and chunk columns per warp claim.  gtmp_batch_autotune times every pair of a
- * small grid of tilings (repeats solves each, into the given buffers), keeps
- * the fastest and returns its time per solve in *best_ms (host, optional). */
+/* Tiling of the work list, per robot kind (kind = GTMP_ROBOT_POINT or
+ * GTMP_ROBOT_DH_ARM; the two kinds run in separate persistent launches): about
+ * target_edges candidate edges per item (an item smaller than a row is a
+ * column piece of one row) and chunk columns per warp claim (point robots
+ * take at least 32, one edge per lane).  gtmp_batch_set_tiling sets both
+ * kinds; every setter synchronises the batch stream and rebuilds the work
+ * list.  Defaults: 16384 edges for both kinds, chunk 32 (point) and 16
+ * (arm).  gtmp_batch_autotune times each kind's persistent launches (CUDA
+ * events around them; repeats solves per trial, into the given buffers)
+ * first over four item sizes per kind, then over chunks 4, 8, 16 and 32 at
+ * the best size, keeps each kind's fastest, and returns the time per solve
+ * of the whole batch under the tilings kept in *best_ms (host, optional).
+ * GTMP_ERR_INVALID_ARG for another kind, target_edges < 1 or a chunk outside
+ * [1, 4096]. */
 GTMP_API gtmp_status gtmp_batch_set_tiling(gtmp_batch* b, int32_t target_edges, int32_t chunk);
-GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t* target_edges, int32_t* chunk);
+GTMP_API gtmp_status gtmp_batch_set_kind_tiling(gtmp_batch* b, int32_t kind, int32_t target_edges, int32_t chunk);
+GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t kind, int32_t* target_edges, int32_t* chunk);
 GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t* dev_paths, float* dev_costs,
                                          float* best_ms);
 

@@ -115,11 +115,13 @@ _SIGNATURES = {
     "gtmp_batch_create": [ctypes.POINTER(GtmpProblem), _i32, _i32, _vp, ctypes.POINTER(_vp)],
     "gtmp_batch_destroy": [_vp],
     "gtmp_batch_set_stream": [_vp, _vp],
-    "gtmp_batch_info": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32)],
+    "gtmp_batch_info": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32),
+                        ctypes.POINTER(_i32)],
     "gtmp_batch_solve": [_vp, _vp, _vp],
     "gtmp_batch_synchronize": [_vp],
     "gtmp_batch_set_tiling": [_vp, _i32, _i32],
-    "gtmp_batch_get_tiling": [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
+    "gtmp_batch_set_kind_tiling": [_vp, _i32, _i32, _i32],
+    "gtmp_batch_get_tiling": [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "gtmp_batch_autotune": [_vp, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_float)],
     "gtmp_batch_set_eval_mode": [_vp, _i32],
     "gtmp_batch_inject_stall": [_vp, _i32, _i32],
@@ -523,9 +525,11 @@ def gtmp_batch_set_stream(b, stream=None):
 
 
 def gtmp_batch_info(b):
-    L_max, checks, items = _i32(), ctypes.c_double(), _i32()
-    _bcheck(b, lib().gtmp_batch_info(b, ctypes.byref(L_max), ctypes.byref(checks), ctypes.byref(items)))
-    return L_max.value, checks.value, items.value
+    """(L_max, nominal checks, work items, kernel launches per solve)."""
+    L_max, checks, items, kernels = _i32(), ctypes.c_double(), _i32(), _i32()
+    _bcheck(b, lib().gtmp_batch_info(b, ctypes.byref(L_max), ctypes.byref(checks), ctypes.byref(items),
+                                     ctypes.byref(kernels)))
+    return L_max.value, checks.value, items.value, kernels.value
 
 
 def gtmp_batch_solve(b, dev_paths, dev_costs):
@@ -537,14 +541,29 @@ def gtmp_batch_synchronize(b):
     _bcheck(b, lib().gtmp_batch_synchronize(b))
 
 
-def gtmp_batch_set_tiling(b, target_edges, chunk):
-    _bcheck(b, lib().gtmp_batch_set_tiling(b, target_edges, chunk))
+def gtmp_batch_set_tiling(b, target_edges, chunk, kind=None):
+    """Both robot kinds (kind None) or one (ROBOT_POINT, ROBOT_DH_ARM)."""
+    if kind is None:
+        _bcheck(b, lib().gtmp_batch_set_tiling(b, target_edges, chunk))
+    else:
+        _bcheck(b, lib().gtmp_batch_set_kind_tiling(b, kind, target_edges, chunk))
 
 
-def gtmp_batch_get_tiling(b):
+def gtmp_batch_get_tiling(b, kind):
     t, c = _i32(), _i32()
-    _bcheck(b, lib().gtmp_batch_get_tiling(b, ctypes.byref(t), ctypes.byref(c)))
+    _bcheck(b, lib().gtmp_batch_get_tiling(b, kind, ctypes.byref(t), ctypes.byref(c)))
     return t.value, c.value
+
+
+def gtmp_batch_get_tilings(b):
+    """{kind: (target_edges, chunk)} for both robot kinds."""
+    return {k: gtmp_batch_get_tiling(b, k) for k in (ROBOT_POINT, ROBOT_DH_ARM)}
+
+
+def gtmp_batch_set_tilings(b, tilings):
+    """Apply a {kind: (target_edges, chunk)} map (as gtmp_batch_get_tilings returns)."""
+    for k, (t, c) in tilings.items():
+        gtmp_batch_set_tiling(b, t, c, kind=k)
 
 
 SAMPLER_UNIFORM, SAMPLER_FREE = 0, 1
@@ -633,9 +652,17 @@ class Batch:
         self.handle = gtmp_batch_create(problems, H)
         if eval_mode is not None:
             gtmp_batch_set_eval_mode(self.handle, eval_mode)
-        self.L_max, self.nominal_checks, self.work_items = gtmp_batch_info(self.handle)
+        self.L_max, self.nominal_checks, _, _ = gtmp_batch_info(self.handle)
         self.paths = torch.empty((self.n, self.L_max), dtype=torch.int32, device="cuda")
         self.costs = torch.empty(self.n, dtype=torch.float32, device="cuda")
+
+    @property
+    def work_items(self):
+        return gtmp_batch_info(self.handle)[2]
+
+    @property
+    def kernels_per_solve(self):
+        return gtmp_batch_info(self.handle)[3]
 
     def solve(self):
         gtmp_batch_solve(self.handle, self.paths, self.costs)

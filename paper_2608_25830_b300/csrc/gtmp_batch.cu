@@ -43,7 +43,6 @@ struct WorkItem {
 };
 
 constexpr int kBoundaryItemEdges = 256;          // item size cap for the start row and the goal column
-constexpr int kPointItemScale = 16;              // point-robot items hold this many times more edges
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz without progress
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -279,6 +278,9 @@ __global__ void batch_paths_kernel(const ProblemDev* probs, int n, int L_max, in
   }
 }
 
+// robot kind of a kernel variant: 0 = point robot, 1 = DH arm
+inline int robot_kind(int variant) { return variant == kVarPoint ? GTMP_ROBOT_POINT : GTMP_ROBOT_DH_ARM; }
+
 bool finite_all(const float* v, size_t n) {
   for (size_t k = 0; k < n; ++k)
     if (!std::isfinite(v[k])) return false;
@@ -293,6 +295,8 @@ struct gtmp_batch {
   int n = 0, H = 0, L_max = 0, M_max = 0, obs4_max = 0;
   int num_sms = 148;
   int bps[4][2] = {};                    // persistent blocks per SM per variant and mode (early exit, lazy)
+  size_t smem[4] = {};                   // dynamic shared memory of variant v's persistent launch: its largest
+                                         // obstacle table and cost-to-go row
   int item_begin[5] = {};                // the work list holds variant v's items in [item_begin[v], item_begin[v + 1])
   cudaStream_t stream = nullptr;
   // host copies
@@ -300,9 +304,9 @@ struct gtmp_batch {
   std::vector<RobotDev> robots;
   std::vector<int> need;  // items per (problem, depth)
   double nominal_checks = 0.0;
-  // tiling (autotuned)
-  int target_edges = 8192;
-  int chunk = 16;
+  // tiling per robot kind (GTMP_ROBOT_POINT, GTMP_ROBOT_DH_ARM), autotuned
+  int target_edges[2] = {16384, 16384};
+  int chunk[2] = {32, 16};
   int eval_mode = GTMP_EVAL_EARLY_EXIT;
   int n_items = 0;
   // device memory
@@ -393,6 +397,7 @@ bool make_robot(const gtmp_robot& r, RobotDev* rb, int* variant, int* dp) {
 }
 
 constexpr int kBatchGridCells = 16384;
+constexpr size_t kBatchSmemMax = 200 * 1024;  // dynamic shared memory the batch kernels opt in to
 
 // scalar or packed obstacle table of one problem (the layout gtmp_set_obstacles writes)
 int obstacle_table(const gtmp_problem& q, const RobotDev& rb, int variant, std::vector<float4>& out, SceneDev* sc) {
@@ -401,7 +406,7 @@ int obstacle_table(const gtmp_problem& q, const RobotDev& rb, int variant, std::
     out.resize(packed_table_capacity(q.n_s + q.n_b) + kBatchGridCells / 4 + 1);
     int n4 = build_packed_tables(q.spheres, q.n_s, q.boxes, q.n_b, rb.r_uniform, arm_reach_bound(rb), out.data(),
                                  sc);
-    // a small cull grid: items re-stage their problem's table, so it stays at 16 KB
+    // the single-problem solver's cull grid (16384 cells, 64 KB of masks), when the table has room for it
     double R_link = 0.0;
     for (int i = 0; i < rb.dof; ++i) R_link = std::fmax(R_link, static_cast<double>(rb.lb[i].w));
     if (n4 + kBatchGridCells / 4 + 1 <= kMaxTableFloat4s)
@@ -444,8 +449,8 @@ gtmp_status build_items(gtmp_batch* b) {
       const int rows = layer_size(P.g, layer), cols = layer_size(P.g, layer + 1);
       // boundary transitions (start row, goal column) sit at the two ends of
       // every problem's dependency chain: cut them into small items
-      // a point-robot edge costs about 1/20 of an arm edge: its items hold more edges
-      const long long target = static_cast<long long>(b->target_edges) * (P.variant == kVarPoint ? kPointItemScale : 1);
+      // each robot kind has its own item size (a point-robot edge costs about 1/20 of an arm edge)
+      const long long target = b->target_edges[robot_kind(P.variant)];
       const int edges_per_item = static_cast<int>(
           (rows == 1 || cols == 1) ? std::min<long long>(target, kBoundaryItemEdges) : std::min<long long>(target, 1 << 30));
       if (rows == 1) {
@@ -483,7 +488,8 @@ gtmp_status build_items(gtmp_batch* b) {
   return GTMP_OK;
 }
 
-gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
+// ev (optional): events 2 v and 2 v + 1 are recorded around variant v's persistent launch
+gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs, cudaEvent_t* ev = nullptr) {
   cudaStream_t st = b->stream;
   const size_t n_done = b->need.size() + 4;
   BATCH_TRY(b, cudaMemsetAsync(b->d_done, 0, n_done * sizeof(int), st));
@@ -495,22 +501,24 @@ gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
   batch_labels_kernel<<<dim3(per_problem_blocks, b->n), kThreads, b->obs4_max * sizeof(float4), st>>>(b->d_probs,
                                                                                                     b->d_robots);
   BATCH_TRY(b, cudaGetLastError());
-  const size_t smem = b->obs4_max * sizeof(float4) + static_cast<size_t>(b->M_max) * sizeof(float);
   const int lazy = b->eval_mode == GTMP_EVAL_LAZY ? 1 : 0;
   for (int v = 0; v < 4; ++v) {
     const int n_items = b->item_begin[v + 1] - b->item_begin[v];
     if (n_items == 0) continue;
     const dim3 grid(b->num_sms * b->bps[v][lazy]);
+    const size_t smem = b->smem[v];
     const WorkItem* items = b->d_items + b->item_begin[v];
     int* counter = b->d_done + b->need.size() + v;
+    const int chunk = b->chunk[robot_kind(v)];
+    if (ev) BATCH_TRY(b, cudaEventRecord(ev[2 * v], st));
 #define GTMP_BATCH_LAUNCH(VAR)                                                                                     \
   if (lazy)                                                                                                        \
     batch_persistent_kernel<VAR, true><<<grid, kThreads, smem, st>>>(b->d_probs, b->d_robots, items, n_items,      \
-                                                                     b->d_need, b->d_done, counter, b->chunk,     \
+                                                                     b->d_need, b->d_done, counter, chunk,        \
                                                                      b->d_err);                                    \
   else                                                                                                             \
     batch_persistent_kernel<VAR, false><<<grid, kThreads, smem, st>>>(b->d_probs, b->d_robots, items, n_items,     \
-                                                                      b->d_need, b->d_done, counter, b->chunk,    \
+                                                                      b->d_need, b->d_done, counter, chunk,       \
                                                                       b->d_err)
     switch (v) {
       case kVarPoint: GTMP_BATCH_LAUNCH(kVarPoint); break;
@@ -520,6 +528,7 @@ gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs) {
     }
 #undef GTMP_BATCH_LAUNCH
     BATCH_TRY(b, cudaGetLastError());
+    if (ev) BATCH_TRY(b, cudaEventRecord(ev[2 * v + 1], st));
   }
   batch_paths_kernel<<<(b->n + 127) / 128, 128, 0, st>>>(b->d_probs, b->n, b->L_max, dev_paths, dev_costs);
   BATCH_TRY(b, cudaGetLastError());
@@ -601,9 +610,16 @@ GTMP_API gtmp_status gtmp_batch_create(const gtmp_problem* problems, int32_t n, 
     b->L_max = std::max(b->L_max, q.L);
     b->M_max = std::max(b->M_max, q.M);
     b->obs4_max = std::max(b->obs4_max, n4);
+    b->smem[variant] = std::max(b->smem[variant], n4 * sizeof(float4) + static_cast<size_t>(q.M) * sizeof(float));
     b->nominal_checks += static_cast<double>(H) * (2.0 * q.M + (q.L - 1.0) * q.M * q.M);
   }
   b->need.assign(need_total, 0);
+  // every item stages its problem's obstacle table and cost-to-go row in shared memory
+  if (static_cast<size_t>(b->obs4_max) * sizeof(float4) > kBatchSmemMax ||
+      *std::max_element(b->smem, b->smem + 4) > kBatchSmemMax) {
+    delete b;
+    return GTMP_ERR_UNSUPPORTED;
+  }
   auto fail_create = [&](cudaError_t e) {
     gtmp_batch_destroy(b);
     return e == cudaErrorMemoryAllocation ? GTMP_ERR_OOM : GTMP_ERR_CUDA;
@@ -613,10 +629,10 @@ GTMP_API gtmp_status gtmp_batch_create(const gtmp_problem* problems, int32_t n, 
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return fail_create(e);
   if ((e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return fail_create(e);
-  if ((e = cudaFuncSetAttribute(batch_labels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) !=
+  if ((e = cudaFuncSetAttribute(batch_labels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(kBatchSmemMax))) !=
       cudaSuccess)
     return fail_create(e);
-  const size_t smem = b->obs4_max * sizeof(float4) + static_cast<size_t>(b->M_max) * sizeof(float);
   {
     const void* kernels[4][2] = {
         {reinterpret_cast<const void*>(batch_persistent_kernel<kVarPoint, false>),
@@ -629,10 +645,12 @@ GTMP_API gtmp_status gtmp_batch_create(const gtmp_problem* problems, int32_t n, 
          reinterpret_cast<const void*>(batch_persistent_kernel<kVarArmGeneric, true>)}};
     for (int v = 0; v < 4; ++v)
       for (int m = 0; m < 2; ++m) {
-        if ((e = cudaFuncSetAttribute(kernels[v][m], cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) !=
+        if ((e = cudaFuncSetAttribute(kernels[v][m], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(kBatchSmemMax))) !=
             cudaSuccess)
           return fail_create(e);
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->bps[v][m], kernels[v][m], kThreads, smem)) !=
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->bps[v][m], kernels[v][m], kThreads,
+                                                               b->smem[v])) !=
             cudaSuccess)
           return fail_create(e);
         if (b->bps[v][m] < 1) b->bps[v][m] = 1;
@@ -710,11 +728,17 @@ GTMP_API gtmp_status gtmp_batch_set_stream(gtmp_batch* b, void* cuda_stream) {
 }
 
 GTMP_API gtmp_status gtmp_batch_info(const gtmp_batch* b, int32_t* L_max, double* nominal_checks,
-                                     int32_t* work_items) {
+                                     int32_t* work_items, int32_t* kernels) {
   if (!b) return GTMP_ERR_INVALID_ARG;
   if (L_max) *L_max = b->L_max;
   if (nominal_checks) *nominal_checks = b->nominal_checks;
   if (work_items) *work_items = b->n_items;
+  if (kernels) {
+    // init, sample, labels, one persistent launch per variant present, paths
+    int k = 4;
+    for (int v = 0; v < 4; ++v) k += b->item_begin[v + 1] > b->item_begin[v] ? 1 : 0;
+    *kernels = k;
+  }
   return GTMP_OK;
 }
 
@@ -736,50 +760,97 @@ GTMP_API gtmp_status gtmp_batch_synchronize(gtmp_batch* b) {
   return GTMP_OK;
 }
 
+GTMP_API gtmp_status gtmp_batch_set_kind_tiling(gtmp_batch* b, int32_t kind, int32_t target_edges, int32_t chunk) {
+  if (!b || (kind != GTMP_ROBOT_POINT && kind != GTMP_ROBOT_DH_ARM) || target_edges < 1 || chunk < 1 || chunk > 4096)
+    return bfail(b, GTMP_ERR_INVALID_ARG, "bad tiling");
+  BATCH_TRY(b, cudaStreamSynchronize(b->stream));
+  b->target_edges[kind] = target_edges;
+  b->chunk[kind] = chunk;
+  return build_items(b);
+}
+
 GTMP_API gtmp_status gtmp_batch_set_tiling(gtmp_batch* b, int32_t target_edges, int32_t chunk) {
   if (!b || target_edges < 1 || chunk < 1 || chunk > 4096) return bfail(b, GTMP_ERR_INVALID_ARG, "bad tiling");
   BATCH_TRY(b, cudaStreamSynchronize(b->stream));
-  b->target_edges = target_edges;
-  b->chunk = chunk;
+  for (int k = 0; k < 2; ++k) {
+    b->target_edges[k] = target_edges;
+    b->chunk[k] = chunk;
+  }
   return build_items(b);
 }
 
 GTMP_API gtmp_status gtmp_batch_autotune(gtmp_batch* b, int32_t repeats, int32_t* dev_paths, float* dev_costs,
                                          float* best_ms) {
   if (!b || repeats < 1 || !dev_paths || !dev_costs) return bfail(b, GTMP_ERR_INVALID_ARG, "bad autotune request");
-  static const int kTargets[] = {256, 1024, 4096, 16384};
-  static const int kChunks[] = {8, 16, 32, 64};
-  cudaEvent_t e0, e1;
-  BATCH_TRY(b, cudaEventCreate(&e0));
-  BATCH_TRY(b, cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_t = b->target_edges, best_c = b->chunk;
+  // candidate item sizes per kind (a point-robot edge is ~20 times cheaper), then chunks at the best size
+  static const int kTargets[2][4] = {{4096, 16384, 65536, 262144}, {1024, 4096, 16384, 65536}};
+  static const int kChunks[] = {4, 8, 16, 32};
+  cudaEvent_t ev[10] = {};
   gtmp_status s = GTMP_OK;
-  for (int t : kTargets) {
-    for (int c : kChunks) {
-      if ((s = gtmp_batch_set_tiling(b, t, c)) != GTMP_OK) break;
-      if ((s = enqueue_solve(b, dev_paths, dev_costs)) != GTMP_OK) break;  // warm-up
-      cudaEventRecord(e0, b->stream);
-      for (int r = 0; r < repeats && s == GTMP_OK; ++r) s = enqueue_solve(b, dev_paths, dev_costs);
-      cudaEventRecord(e1, b->stream);
-      if (s != GTMP_OK) break;
-      if ((s = gtmp_batch_synchronize(b)) != GTMP_OK) break;
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= repeats;
-      if (ms < best) {
-        best = ms;
-        best_t = t;
-        best_c = c;
+  for (int k = 0; k < 10 && s == GTMP_OK; ++k)
+    if (cudaEventCreate(&ev[k]) != cudaSuccess) s = bfail(b, GTMP_ERR_CUDA, "cudaEventCreate failed");
+  int best_t[2] = {b->target_edges[0], b->target_edges[1]}, best_c[2] = {b->chunk[0], b->chunk[1]};
+  float best[2] = {1e30f, 1e30f};
+  // time every kind's persistent launches under tiling (t[k], c[k]); keep each kind's fastest
+  auto trial = [&](const int* t, const int* c) -> gtmp_status {
+    for (int k = 0; k < 2; ++k) {
+      b->target_edges[k] = t[k];
+      b->chunk[k] = c[k];
+    }
+    gtmp_status r = build_items(b);
+    float ms[2] = {0.0f, 0.0f};
+    for (int rep = 0; rep < repeats && r == GTMP_OK; ++rep) {
+      if ((r = enqueue_solve(b, dev_paths, dev_costs, ev)) != GTMP_OK) break;
+      if ((r = gtmp_batch_synchronize(b)) != GTMP_OK) break;
+      for (int v = 0; v < 4; ++v) {
+        if (b->item_begin[v + 1] == b->item_begin[v]) continue;
+        float m = 0.0f;
+        cudaEventElapsedTime(&m, ev[2 * v], ev[2 * v + 1]);
+        ms[robot_kind(v)] += m / repeats;
       }
     }
-    if (s != GTMP_OK) break;
+    for (int k = 0; k < 2 && r == GTMP_OK; ++k)
+      if (ms[k] < best[k]) {
+        best[k] = ms[k];
+        best_t[k] = t[k];
+        best_c[k] = c[k];
+      }
+    return r;
+  };
+  if (s == GTMP_OK) s = build_items(b);
+  if (s == GTMP_OK) s = enqueue_solve(b, dev_paths, dev_costs);  // warm-up
+  if (s == GTMP_OK) s = gtmp_batch_synchronize(b);
+  const int c0[2] = {best_c[0], best_c[1]};
+  for (int i = 0; i < 4 && s == GTMP_OK; ++i) {
+    const int t[2] = {kTargets[0][i], kTargets[1][i]};
+    s = trial(t, c0);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (s != GTMP_OK) return s;
-  if (best_ms) *best_ms = best;
-  return gtmp_batch_set_tiling(b, best_t, best_c);
+  const int t1[2] = {best_t[0], best_t[1]};
+  for (int c : kChunks) {
+    if (s != GTMP_OK) break;
+    const int cc[2] = {c, c};
+    s = trial(t1, cc);
+  }
+  if (s == GTMP_OK) {
+    for (int k = 0; k < 2; ++k) {
+      b->target_edges[k] = best_t[k];
+      b->chunk[k] = best_c[k];
+    }
+    s = build_items(b);
+  }
+  if (s == GTMP_OK && best_ms) {
+    // one timed pass of the whole solve under the tilings kept
+    cudaEventRecord(ev[8], b->stream);
+    for (int rep = 0; rep < repeats && s == GTMP_OK; ++rep) s = enqueue_solve(b, dev_paths, dev_costs);
+    cudaEventRecord(ev[9], b->stream);
+    if (s == GTMP_OK) s = gtmp_batch_synchronize(b);
+    float ms = 0.0f;
+    if (s == GTMP_OK) cudaEventElapsedTime(&ms, ev[8], ev[9]);
+    *best_ms = ms / repeats;
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  return s;
 }
 
 GTMP_API gtmp_status gtmp_batch_set_eval_mode(gtmp_batch* b, int32_t eval_mode) {
@@ -804,10 +875,10 @@ GTMP_API gtmp_status gtmp_batch_inject_stall(gtmp_batch* b, int32_t problem, int
   return GTMP_OK;
 }
 
-GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t* target_edges, int32_t* chunk) {
-  if (!b) return GTMP_ERR_INVALID_ARG;
-  if (target_edges) *target_edges = b->target_edges;
-  if (chunk) *chunk = b->chunk;
+GTMP_API gtmp_status gtmp_batch_get_tiling(const gtmp_batch* b, int32_t kind, int32_t* target_edges, int32_t* chunk) {
+  if (!b || (kind != GTMP_ROBOT_POINT && kind != GTMP_ROBOT_DH_ARM)) return GTMP_ERR_INVALID_ARG;
+  if (target_edges) *target_edges = b->target_edges[kind];
+  if (chunk) *chunk = b->chunk[kind];
   return GTMP_OK;
 }
 

@@ -168,10 +168,10 @@ def test_batch_512_at_size():
     subset = problems[::max(1, len(problems) // 96)][:96]
     tune = binding.Batch(subset, H)
     tune.autotune(repeats=1)
-    tiling = binding.gtmp_batch_get_tiling(tune.handle)
+    tiling = binding.gtmp_batch_get_tilings(tune.handle)
     tune.close()
     b = binding.Batch(problems, H)
-    binding.gtmp_batch_set_tiling(b.handle, *tiling)
+    binding.gtmp_batch_set_tilings(b.handle, tiling)
     b.solve()
     b.synchronize()
     paths, costs = b.paths.cpu().numpy(), b.costs.cpu().numpy()

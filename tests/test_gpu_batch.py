@@ -101,6 +101,20 @@ def test_every_tiling_gives_the_same_plans(mixed, target, chunk):
     b.close()
 
 
+@pytest.mark.parametrize("point,arm", [((1, 1), (1 << 20, 64)), ((1 << 20, 32), (100, 3))])
+def test_per_kind_tilings_give_the_same_plans(mixed, point, arm):
+    probs, H, singles = mixed
+    b = binding.Batch(probs, H)
+    binding.gtmp_batch_set_tiling(b.handle, *point, kind=binding.ROBOT_POINT)
+    binding.gtmp_batch_set_tiling(b.handle, *arm, kind=binding.ROBOT_DH_ARM)
+    assert binding.gtmp_batch_get_tilings(b.handle) == {binding.ROBOT_POINT: point, binding.ROBOT_DH_ARM: arm}
+    b.solve()
+    b.synchronize()
+    _check_against_singles(b, probs, singles)
+    assert binding.lib().gtmp_batch_set_kind_tiling(b.handle, 2, 4096, 8) == 1    # no such robot kind
+    b.close()
+
+
 @pytest.mark.parametrize("target", [1, 4096, 1 << 20])
 def test_lazy_batch_gives_the_same_plans(mixed, target):
     probs, H, singles = mixed
@@ -117,6 +131,27 @@ def test_lazy_batch_gives_the_same_plans(mixed, target):
     b.close()
 
 
+def test_batch_rejects_tables_beyond_shared_memory():
+    """Every item stages its problem's obstacle table and cost-to-go row (4 B per sample) in at most 200 KB of
+    shared memory.  4096 boxes for a 7-joint arm (packed table: 2.5 float4 per box, 160 KB) at M = 16384
+    (64 KB) exceed it and are refused at create, before any launch; the same boxes for a point robot (2 float4
+    per box, 128 KB) fit and solve."""
+    import dataclasses
+    rng = np.random.default_rng(3)
+    lo = rng.uniform(-1.0, 0.9, (4096, 3))
+    boxes = np.concatenate([lo, lo + 0.01], 1).astype(np.float32)
+    none = np.zeros((0, 4), np.float32)
+    arm = dataclasses.replace(scene_for("arm", 1, 7, 4), spheres=none, boxes=boxes)
+    with pytest.raises(binding.GtmpError) as e:
+        binding.Batch([(arm, 16384, 1, 1)], 8)
+    assert e.value.status == 5     # GTMP_ERR_UNSUPPORTED
+    pt = dataclasses.replace(scenes.point2d_scene(1, 4), spheres=none, boxes=boxes)
+    b = binding.Batch([(pt, 16384, 1, 1)], 8)
+    b.solve()
+    b.synchronize()
+    b.close()
+
+
 def test_batch_rejects_full_mode(mixed):
     probs, H, _ = mixed
     b = binding.Batch(probs[:2], H)
@@ -130,8 +165,10 @@ def test_autotune_keeps_results(mixed):
     b = binding.Batch(probs, H)
     ms = b.autotune(repeats=1)
     assert ms > 0
-    t, c = binding.gtmp_batch_get_tiling(b.handle)
-    assert t in (256, 1024, 4096, 16384) and c in (8, 16, 32, 64)
+    t, c = binding.gtmp_batch_get_tiling(b.handle, binding.ROBOT_POINT)
+    assert t in (4096, 16384, 65536, 262144) and c in (4, 8, 16, 32)
+    t, c = binding.gtmp_batch_get_tiling(b.handle, binding.ROBOT_DH_ARM)
+    assert t in (1024, 4096, 16384, 65536) and c in (4, 8, 16, 32)
     b.solve()
     b.synchronize()
     _check_against_singles(b, probs, singles)
