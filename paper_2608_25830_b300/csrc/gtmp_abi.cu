@@ -304,19 +304,13 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
     }
     // sphere table laid out [link][stride] with stride = 4 for the 4-sphere
     // variants and kMaxSpl for the generic one
-    const bool four = robot->spheres_per_link == 4;
     for (int i = 0; i < robot->dof; ++i)
       for (int s = 0; s < robot->spheres_per_link; ++s) {
         const float* ls = robot->link_spheres + (static_cast<size_t>(i) * robot->spheres_per_link + s) * 4;
         if (ls[3] != r0) uniform = false;
       }
     rb.r_uniform = r0;
-    if (uniform && four && robot->dof == 6)
-      c->variant = kVarArm6x4;
-    else if (uniform && four && robot->dof == 7)
-      c->variant = kVarArm7x4;
-    else
-      c->variant = kVarArmGeneric;
+    c->variant = arm_kernel_variant(uniform, robot->spheres_per_link, robot->dof, r0);
     // the specialised kernels read inflated squared thresholds (r_obs + r)^2,
     // the generic kernel reads plain obstacle radii
     rb.uniform_r = (c->variant == kVarArmGeneric) ? 0 : 1;

@@ -373,9 +373,7 @@ bool make_robot(const gtmp_robot& r, RobotDev* rb, int* variant, int* dp) {
     if (!(r.link_spheres[s * 4 + 3] > 0.0f)) return false;
     if (r.link_spheres[s * 4 + 3] != r0) uniform = false;
   }
-  *variant = (uniform && spl == 4 && r.dof == 6) ? kVarArm6x4
-             : (uniform && spl == 4 && r.dof == 7) ? kVarArm7x4
-                                                   : kVarArmGeneric;
+  *variant = arm_kernel_variant(uniform, spl, r.dof, r0);
   const int stride = *variant == kVarArmGeneric ? kMaxSpl : 4;
   *dp = *variant == kVarArmGeneric ? kMaxDof : 8;
   rb->spl = spl;

@@ -309,9 +309,22 @@ __device__ __forceinline__ unsigned long long link_cull_mask(float cx, float cy,
 //                (-hy_a, -hy_b, -hz_a, -hz_b)   (centre b, half extents h).
 // A sphere hits iff dx^2 + dy^2 + dz^2 - T < 0 and a box iff
 // sum_k max(|c_k - b_k| - h_k, 0)^2 - r^2 < 0, each sum taken as one fma chain
-// starting from the negated threshold.  Odd counts are padded with obstacles
-// at 1e18 that never hit.
+// starting from the negated threshold (each box gap clamped as box_gap
+// states).  Odd counts are padded with obstacles at 1e18 that never hit.
 // ----------------------------------------------------------------------------
+// Gap of a box test along one axis, max(|u| - h, 0) for u the offset from the
+// box centre and neg_h = -h, clamped to at most 1 by the same instruction (a
+// saturating add, one rounding as __fadd_rn).  The clamp changes no decision
+// while the robot sphere radius r is below 1: the test is gx^2 + gy^2 + gz^2
+// - r^2 < 0, and one clamped gap alone already makes the sum at least 1 - r^2
+// > 0, as the unclamped gap does.  The packed arm kernels are therefore chosen
+// only for radii below 1 (arm_kernel_variant).
+__device__ __forceinline__ float box_gap(float u, float neg_h) {
+  float g;
+  asm("{\n\t.reg .f32 a;\n\tabs.f32 a, %1;\n\tadd.rn.sat.f32 %0, a, %2;\n\t}" : "=f"(g) : "f"(u), "f"(neg_h));
+  return g;
+}
+
 template <int NS>
 __device__ __forceinline__ bool exact_packed_hit(const float (&cx)[NS], const float (&cy)[NS], const float (&cz)[NS],
                                                  const float4* __restrict__ sphp, int n_sp,
@@ -352,9 +365,9 @@ __device__ __forceinline__ bool exact_packed_hit(const float (&cx)[NS], const fl
       const float2 ux = __fadd2_rn(x2[k], nbx);
       const float2 uy = __fadd2_rn(y2[k], nby);
       const float2 uz = __fadd2_rn(z2[k], nbz);
-      const float2 px = make_float2(fmaxf(__fadd_rn(fabsf(ux.x), B1.z), 0.0f), fmaxf(__fadd_rn(fabsf(ux.y), B1.w), 0.0f));
-      const float2 py = make_float2(fmaxf(__fadd_rn(fabsf(uy.x), B2.x), 0.0f), fmaxf(__fadd_rn(fabsf(uy.y), B2.y), 0.0f));
-      const float2 pz = make_float2(fmaxf(__fadd_rn(fabsf(uz.x), B2.z), 0.0f), fmaxf(__fadd_rn(fabsf(uz.y), B2.w), 0.0f));
+      const float2 px = make_float2(box_gap(ux.x, B1.z), box_gap(ux.y, B1.w));
+      const float2 py = make_float2(box_gap(uy.x, B2.x), box_gap(uy.y, B2.y));
+      const float2 pz = make_float2(box_gap(uz.x, B2.z), box_gap(uz.y, B2.w));
       const float2 t = __ffma2_rn(pz, pz, __ffma2_rn(py, py, __ffma2_rn(px, px, nr2)));
       m[k] = fmin3(m[k], t.x, t.y);
     }
@@ -408,9 +421,9 @@ __device__ __forceinline__ bool exact_packed_hit_masked(const float (&cx)[NS], c
       const float2 ux = __fadd2_rn(x2[k], nbx);
       const float2 uy = __fadd2_rn(y2[k], nby);
       const float2 uz = __fadd2_rn(z2[k], nbz);
-      const float2 px = make_float2(fmaxf(__fadd_rn(fabsf(ux.x), B1.z), 0.0f), fmaxf(__fadd_rn(fabsf(ux.y), B1.w), 0.0f));
-      const float2 py = make_float2(fmaxf(__fadd_rn(fabsf(uy.x), B2.x), 0.0f), fmaxf(__fadd_rn(fabsf(uy.y), B2.y), 0.0f));
-      const float2 pz = make_float2(fmaxf(__fadd_rn(fabsf(uz.x), B2.z), 0.0f), fmaxf(__fadd_rn(fabsf(uz.y), B2.w), 0.0f));
+      const float2 px = make_float2(box_gap(ux.x, B1.z), box_gap(ux.y, B1.w));
+      const float2 py = make_float2(box_gap(uy.x, B2.x), box_gap(uy.y, B2.y));
+      const float2 pz = make_float2(box_gap(uz.x, B2.z), box_gap(uz.y, B2.w));
       const float2 t = __ffma2_rn(pz, pz, __ffma2_rn(py, py, __ffma2_rn(px, px, nr2)));
       m[k] = fmin3(m[k], t.x, t.y);
     }

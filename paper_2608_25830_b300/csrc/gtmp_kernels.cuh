@@ -82,6 +82,15 @@ enum EvalMode { kEvalEarlyExit = 0, kEvalFull = 1, kEvalLazy = 2 };
 // Variant selector for the robot-specialised kernels.
 enum RobotVariant { kVarPoint = 0, kVarArm6x4 = 1, kVarArm7x4 = 2, kVarArmGeneric = 3 };
 
+// Kernel variant of a DH arm: the packed 6- and 7-joint kernels take four
+// spheres per link of one radius r < 1 (their box test clamps each axis gap
+// at 1, which decides nothing differently only while r < 1); every other arm
+// takes the generic kernel.
+inline int arm_kernel_variant(bool uniform, int spheres_per_link, int dof, float r) {
+  if (!uniform || spheres_per_link != 4 || !(r < 1.0f)) return kVarArmGeneric;
+  return dof == 6 ? kVarArm6x4 : dof == 7 ? kVarArm7x4 : kVarArmGeneric;
+}
+
 // Host: tables of the uniform-radius arm kernels (see gtmp_device.cuh).
 // Prefilter: out receives 2 * pairs float4 (pairs = ceil((n_s + n_b) / 2));
 // `reach` bounds |c| for every robot-sphere centre.  Returns the pair count.

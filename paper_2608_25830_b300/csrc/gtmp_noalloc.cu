@@ -142,12 +142,7 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
       if (!(robot->link_spheres[s * 4 + 3] > 0.0f)) return report(err_msg, err_msg_len, bad, "sphere radius <= 0");
       if (robot->link_spheres[s * 4 + 3] != r0) uniform = false;
     }
-    if (uniform && spl == 4 && dof == 6)
-      variant = kVarArm6x4;
-    else if (uniform && spl == 4 && dof == 7)
-      variant = kVarArm7x4;
-    else
-      variant = kVarArmGeneric;
+    variant = arm_kernel_variant(uniform, spl, dof, r0);
     const int stride = variant == kVarArmGeneric ? kMaxSpl : 4;
     dp = variant == kVarArmGeneric ? kMaxDof : 8;
     rb.spl = spl;
