@@ -66,6 +66,36 @@ def test_config_labels_match_outside_band(torch_cuda, kind, dof, n_obs):
     assert 0.05 < gpu.mean() < 0.95  # the scene has both free and colliding configurations
 
 
+@pytest.mark.parametrize("radius", [0.5, 0.99, 1.0, 1.5])
+def test_config_labels_with_far_boxes_and_large_spheres(torch_cuda, radius):
+    """The packed arm kernels clamp each box-axis gap at 1 (one saturating add), which decides the same as the
+    plain gap only for robot spheres of radius below 1; larger radii take the generic kernel.  Boxes r + 0.5 to
+    r + 2 m from the base make gaps above 1 common (about half the configurations collide), and the labels
+    still equal the oracle's on both sides of r = 1."""
+    import dataclasses
+    torch = torch_cuda
+    from paper_2608_25830_b300 import scenes
+    rng = np.random.default_rng(11)
+    robot = scenes.dh_arm(5, 7)
+    sph = robot.link_spheres.copy()
+    sph[:, :, 3] = radius
+    robot = dataclasses.replace(robot, link_spheres=sph)
+    d = rng.normal(size=(12, 3))
+    c = d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(radius + 0.5, radius + 2.0, (12, 1))
+    h = rng.uniform(0.05, 0.3, (12, 3))
+    boxes = np.concatenate([c - h, c + h], 1).astype(np.float32)
+    q0 = np.zeros(7, np.float32)
+    sc = scenes.Scene(robot, np.zeros((0, 4), np.float32), boxes, q0, q0)
+    p = _planner(sc, 8, 1, 4)
+    q = rng.uniform(robot.q_lo, robot.q_hi, (20000, 7)).astype(np.float32)
+    gpu = p.label_configs(torch.from_numpy(q).cuda()).cpu().numpy()
+    lab, margin = oracle.config_labels(sc, q)
+    clear = lab != oracle.AMBIGUOUS
+    np.testing.assert_array_equal(gpu[clear], (lab[clear] == oracle.COLLIDE).astype(np.uint8))
+    assert 0.2 < gpu.mean() < 0.8
+    p.close()
+
+
 # ---------------------------------------------------------------------------
 # unfused edge costs: labels and lengths per edge
 # ---------------------------------------------------------------------------
