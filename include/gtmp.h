@@ -87,7 +87,10 @@ enum { GTMP_EVAL_EARLY_EXIT = 0, GTMP_EVAL_FULL = 1, GTMP_EVAL_LAZY = 2 };
  *  kind = GTMP_ROBOT_DH_ARM: a serial arm in standard Denavit-Hartenberg form,
  *         link transform A_i = Rz(q_i + theta_i) Tz(d_i) Tx(a_i) Rx(alpha_i),
  *         base frame = world frame; link i carries spheres_per_link spheres
- *         given in the frame of link i (radius > 0).
+ *         given in the frame of link i (radius > 0).  Joint limits within
+ *         +-4096 rad and theta offsets within +-2048 rad (the range of the
+ *         kinematics' sine and cosine); gtmp_create, gtmp_batch_create and
+ *         gtmp_solve_noalloc refuse other arms with GTMP_ERR_INVALID_ARG.
  * All pointers are host pointers, copied by gtmp_create. */
 typedef struct {
   int32_t kind;
@@ -202,7 +205,9 @@ GTMP_API gtmp_status gtmp_set_layers(gtmp_ctx* ctx, const float* dev_Q, int32_t 
 GTMP_API gtmp_status gtmp_get_layers(gtmp_ctx* ctx, float* dev_Q);
 
 /* Exact configuration checker (membership in C_coll, Sec. III): dev_q device
- * [n][dof] float32 in, dev_labels device [n] uint8 out, 1 = in collision. */
+ * [n][dof] float32 in, dev_labels device [n] uint8 out, 1 = in collision.
+ * For an arm, a configuration with a coordinate beyond +-4096 rad (or NaN) is
+ * labelled 1. */
 GTMP_API gtmp_status gtmp_label_configs(gtmp_ctx* ctx, const float* dev_q, int32_t n, uint8_t* dev_labels);
 
 /* gtmp of Alg. 1 on graph 0 with the fused edge + min-plus kernels (the edge
@@ -582,6 +587,16 @@ GTMP_API gtmp_status gtmp_surrogate_score(gtmp_ctx* ctx, int32_t layer, float th
  * the grid is farther than that from every obstacle.  Needs no GPU. */
 GTMP_API gtmp_status gtmp_cull_grid(const float* spheres, int32_t n_s, const float* boxes, int32_t n_b, float R_link,
                                     int32_t max_cells, uint32_t* masks, int32_t* dims, float* origin_inv);
+
+/* The sine and cosine the arm kinematics takes of each joint angle q_i +
+ * theta_i (A_i above): Cody-Waite reduction by pi/2, then the Taylor series of
+ * sin and cos on |r| <= pi/4; within 1e-7 absolute of the exact values for
+ * |x| <= 6144 rad, the range the joint-limit and theta-offset bounds keep
+ * every argument in.  dev_x device [n] float32 in, dev_s, dev_c device [n]
+ * out; asynchronous on cuda_stream (NULL = legacy default stream).  Exposed
+ * so that the kinematics' trigonometry can be checked against FP64.
+ * GTMP_ERR_INVALID_ARG for n < 0 or a NULL pointer with n > 0. */
+GTMP_API gtmp_status gtmp_joint_sincos(const float* dev_x, int32_t n, float* dev_s, float* dev_c, void* cuda_stream);
 
 /* Calibration, no counterpart in the paper: the FP32 FMA throughput of the
  * current device in TFLOP/s (FMA = 2 flops), from a kernel of independent

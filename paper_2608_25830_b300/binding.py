@@ -130,6 +130,7 @@ _SIGNATURES = {
     "gtmp_set_sampler": [_vp, _i32, _i32],
     "gtmp_set_cost_weight": [_vp, _fp, _i32],
     "gtmp_fp32_fma_peak": [_vp, ctypes.POINTER(ctypes.c_double)],
+    "gtmp_joint_sincos": [_vp, _i32, _vp, _vp, _vp],
     "gtmp_cull_grid": [_fp, _i32, _fp, _i32, ctypes.c_float, _i32, ctypes.POINTER(ctypes.c_uint32),
                        ctypes.POINTER(_i32), _fp],
     "gtmp_get_goal_reached": [_vp, _i32, _vp],
@@ -577,6 +578,18 @@ def gtmp_set_goals(ctx, goals, values=None):
     g = _f32(goals)
     v = None if values is None else _f32(values)
     _check(ctx, lib().gtmp_set_goals(ctx, _ptr(g), None if v is None else _ptr(v), g.shape[0]))
+
+
+def gtmp_joint_sincos(x):
+    """(sin, cos) of a device float32 tensor as the arm kinematics computes them."""
+    import torch
+    x = x.contiguous()
+    s, c = torch.empty_like(x), torch.empty_like(x)
+    st = lib().gtmp_joint_sincos(_dev(x, torch.float32), x.numel(), _dev(s, torch.float32), _dev(c, torch.float32),
+                                 _stream())
+    if st != GTMP_OK:
+        raise GtmpError(st, "gtmp_joint_sincos")
+    return s, c
 
 
 def gtmp_fp32_fma_peak(stream=None):

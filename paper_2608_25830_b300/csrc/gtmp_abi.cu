@@ -261,6 +261,7 @@ gtmp_status gtmp_create(const gtmp_robot* robot, const gtmp_params* params, void
     if (!robot->dh || !robot->link_spheres) return GTMP_ERR_INVALID_ARG;
     if (robot->spheres_per_link < 1 || robot->spheres_per_link > kMaxSpl) return GTMP_ERR_INVALID_ARG;
     if (!finite_all(robot->dh, static_cast<size_t>(robot->dof) * 4)) return GTMP_ERR_INVALID_ARG;
+    if (!arm_angles_in_range(robot->q_lo, robot->q_hi, robot->dh, robot->dof)) return GTMP_ERR_INVALID_ARG;
     const size_t ns = static_cast<size_t>(robot->dof) * robot->spheres_per_link;
     if (!finite_all(robot->link_spheres, ns * 4)) return GTMP_ERR_INVALID_ARG;
     for (size_t s = 0; s < ns; ++s)
@@ -675,6 +676,13 @@ gtmp_status gtmp_get_M(const gtmp_ctx* c, int32_t* M) {
   if (!c || !M) return GTMP_ERR_INVALID_ARG;
   *M = c->M_active;
   return GTMP_OK;
+}
+
+gtmp_status gtmp_joint_sincos(const float* dev_x, int32_t n, float* dev_s, float* dev_c, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!dev_x || !dev_s || !dev_c))) return GTMP_ERR_INVALID_ARG;
+  return launch_joint_sincos(dev_x, n, dev_s, dev_c, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess
+             ? GTMP_OK
+             : GTMP_ERR_CUDA;
 }
 
 gtmp_status gtmp_label_configs(gtmp_ctx* c, const float* dev_q, int32_t n, uint8_t* dev_labels) {

@@ -365,7 +365,8 @@ bool make_robot(const gtmp_robot& r, RobotDev* rb, int* variant, int* dp) {
     return false;
   const int spl = r.spheres_per_link;
   if (!finite_all(r.dh, static_cast<size_t>(r.dof) * 4) ||
-      !finite_all(r.link_spheres, static_cast<size_t>(r.dof) * spl * 4))
+      !finite_all(r.link_spheres, static_cast<size_t>(r.dof) * spl * 4) || !r.q_lo || !r.q_hi ||
+      !arm_angles_in_range(r.q_lo, r.q_hi, r.dh, r.dof))
     return false;
   bool uniform = true;
   const float r0 = r.link_spheres[3];

@@ -177,6 +177,48 @@ __device__ __forceinline__ bool spheres_hit(const float (&cx)[NS], const float (
 // also cleared by the exact test, and the exact test is run whenever any lane
 // is not cleared.  The labels are therefore those of the exact test alone.
 // ----------------------------------------------------------------------------
+// Joint angles the arm kernels accept: |q| <= kMaxJointAngle for joint
+// limits (so for every sample, endpoint and goal, which lie in the joint box)
+// and |theta_offset| <= kMaxThetaOffset, so that every argument of
+// joint_sincos stays within 6144 rad.  gtmp_create and gtmp_batch_create
+// refuse arms outside these bounds; gtmp_label_configs labels a configuration
+// with a larger coordinate as colliding.
+constexpr float kMaxJointAngle = 4096.0f;
+constexpr float kMaxThetaOffset = 2048.0f;
+
+// Sine and cosine of a joint angle for the forward kinematics: Cody-Waite
+// reduction by pi/2 (pi/2 split into three float32 parts, the first two with
+// significands of at most 12 bits, so that k times each is exact for
+// |k| < 2^12, i.e. |x| < 6434), then the Taylor series of sin and cos about 0
+// on |r| <= pi/4 (through r^9 and r^10; the first omitted terms are below
+// 2e-9 there), then the quadrant's swap and signs.  Within 1.5 ulp of the
+// exact values for |x| <= 6144 (float32 emulation against FP64, and a GPU
+// test against FP64).  No branch: the fused kernels keep their registers.
+__device__ __forceinline__ void joint_sincos(float x, float* s_out, float* c_out) {
+  const float t = __fmaf_rn(x, 0.636619772f, 12582912.0f);  // 1.5 * 2^23 + rint(x * 2 / pi)
+  const float kf = __fsub_rn(t, 12582912.0f);
+  const int q = __float_as_int(t) & 3;                        // rint(x * 2 / pi) mod 4
+  float r = __fmaf_rn(-kf, 1.5703125f, x);
+  r = __fmaf_rn(-kf, 4.837512969970703e-4f, r);
+  r = __fmaf_rn(-kf, 7.549790126404332e-8f, r);
+  const float r2 = __fmul_rn(r, r);
+  // 1/9!, -1/7!, 1/5!, -1/3!
+  float ps = __fmaf_rn(r2, 2.75573192e-6f, -1.98412698e-4f);
+  ps = __fmaf_rn(r2, ps, 8.33333333e-3f);
+  ps = __fmaf_rn(r2, ps, -1.66666667e-1f);
+  const float sn = __fmaf_rn(__fmul_rn(r, r2), ps, r);
+  // -1/10!, 1/8!, -1/6!, 1/4!, -1/2!
+  float pc = __fmaf_rn(r2, -2.75573192e-7f, 2.48015873e-5f);
+  pc = __fmaf_rn(r2, pc, -1.38888889e-3f);
+  pc = __fmaf_rn(r2, pc, 4.16666667e-2f);
+  pc = __fmaf_rn(r2, pc, -0.5f);
+  const float cs = __fmaf_rn(r2, pc, 1.0f);
+  const float a = (q & 1) ? cs : sn;
+  const float b = (q & 1) ? sn : cs;
+  *s_out = __int_as_float(__float_as_int(a) ^ ((q & 2) << 30));
+  *c_out = __int_as_float(__float_as_int(b) ^ (((q + 1) & 2) << 30));
+}
+
 __device__ __forceinline__ float fmin3(float a, float b, float c) {
   float r;
   asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -475,7 +517,7 @@ __device__ __forceinline__ bool arm_config_collides(const float* q, bool active,
 #pragma unroll
     for (int k = 0; k + 1 < NQ; ++k) ang[k] = ang[k + 1];
     float s, c;
-    sincosf(__fadd_rn(qi, rb.toff[i]), &s, &c);
+    joint_sincos(__fadd_rn(qi, rb.toff[i]), &s, &c);
     // A_i = Rz(theta) Tz(d) Tx(a) Rx(alpha): new x axis u = c X + s Y,
     // v = -s X + c Y, new y = ca v + sa Z, new z = -sa v + ca Z,
     // new origin = T + a u + d Z.

@@ -145,7 +145,13 @@ __global__ void __launch_bounds__(kThreads) label_configs_kernel(const float* q_
   float q[DP];
 #pragma unroll
   for (int d = 0; d < DP; ++d) q[d] = d < dof ? q_in[static_cast<size_t>(t) * dof + d] : 0.0f;
-  out[t] = config_collides<VAR, false, false>(q, true, rb, s_obs, sc) ? 1 : 0;
+  // arms: a coordinate beyond the accepted joint range (or NaN) is labelled colliding
+  bool in_range = true;
+  if constexpr (VAR != kVarPoint) {
+#pragma unroll
+    for (int d = 0; d < DP; ++d) in_range = in_range && fabsf(q[d]) <= kMaxJointAngle;
+  }
+  out[t] = (!in_range || config_collides<VAR, false, false>(q, true, rb, s_obs, sc)) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1048,6 +1054,19 @@ cudaError_t launch_init_keys(const GraphDev& g, int* counters, int n_counters, c
 cudaError_t launch_vertex_labels(const GraphDev& g, const RobotDev& rb, int variant, const SceneDev& sc,
                                  cudaStream_t st) {
   return by_variant<VertexLabelsRun>(variant, g, rb, sc, st);
+}
+
+namespace {
+__global__ void joint_sincos_kernel(const float* x, int n, float* s, float* c) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) joint_sincos(x[t], s + t, c + t);
+}
+}  // namespace
+
+cudaError_t launch_joint_sincos(const float* x, int n, float* s, float* c, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  joint_sincos_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, n, s, c);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_label_configs(const float* q, int n, int dof, const RobotDev& rb, int variant, const SceneDev& sc,

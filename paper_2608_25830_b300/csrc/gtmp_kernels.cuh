@@ -1,6 +1,7 @@
 // Kernel launch interface shared by the C-ABI layer and the kernel sources.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
@@ -91,6 +92,17 @@ inline int arm_kernel_variant(bool uniform, int spheres_per_link, int dof, float
   return dof == 6 ? kVarArm6x4 : dof == 7 ? kVarArm7x4 : kVarArmGeneric;
 }
 
+// Host: an arm's joint box (hence every sample, endpoint and goal) and theta
+// offsets lie within the ranges the kinematics' joint_sincos serves
+// (|q| <= kMaxJointAngle, |theta_offset| <= kMaxThetaOffset); dh is [dof][4].
+inline bool arm_angles_in_range(const float* q_lo, const float* q_hi, const float* dh, int dof) {
+  for (int k = 0; k < dof; ++k)
+    if (!(std::fabs(q_lo[k]) <= kMaxJointAngle && std::fabs(q_hi[k]) <= kMaxJointAngle &&
+          std::fabs(dh[4 * k + 3]) <= kMaxThetaOffset))
+      return false;
+  return true;
+}
+
 // Host: tables of the uniform-radius arm kernels (see gtmp_device.cuh).
 // Prefilter: out receives 2 * pairs float4 (pairs = ceil((n_s + n_b) / 2));
 // `reach` bounds |c| for every robot-sphere centre.  Returns the pair count.
@@ -122,6 +134,8 @@ cudaError_t launch_sample_uniform(const GraphDev& g, const float* lo, const floa
 cudaError_t launch_init_keys(const GraphDev& g, int* counters, int n_counters, cudaStream_t st);
 cudaError_t launch_vertex_labels(const GraphDev& g, const RobotDev& rb, int variant, const SceneDev& sc,
                                  cudaStream_t st);
+// the kinematics' joint_sincos on n arguments (device pointers)
+cudaError_t launch_joint_sincos(const float* x, int n, float* s, float* c, cudaStream_t st);
 cudaError_t launch_label_configs(const float* q, int n, int dof, const RobotDev& rb, int variant,
                                  const SceneDev& sc, uint8_t* out, cudaStream_t st);
 // dependent: launch as a programmatic dependent of the previous kernel on the

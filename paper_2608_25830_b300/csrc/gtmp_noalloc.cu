@@ -136,6 +136,8 @@ extern "C" GTMP_API gtmp_status gtmp_solve_noalloc(const gtmp_robot* robot, cons
         !all_finite(robot->dh, static_cast<size_t>(dof) * 4) ||
         !all_finite(robot->link_spheres, static_cast<size_t>(dof) * spl * 4))
       return report(err_msg, err_msg_len, bad, "bad arm description");
+    if (!arm_angles_in_range(robot->q_lo, robot->q_hi, robot->dh, dof))
+      return report(err_msg, err_msg_len, bad, "joint limits beyond +-4096 rad or theta offset beyond +-2048 rad");
     bool uniform = true;
     const float r0 = robot->link_spheres[3];
     for (int s = 0; s < dof * spl; ++s) {

@@ -66,6 +66,52 @@ def test_config_labels_match_outside_band(torch_cuda, kind, dof, n_obs):
     assert 0.05 < gpu.mean() < 0.95  # the scene has both free and colliding configurations
 
 
+def test_joint_sincos_against_fp64(torch_cuda):
+    """The kinematics' own sine and cosine (Cody-Waite reduction by pi/2, Taylor series on |r| <= pi/4) stay
+    within 1e-7 of FP64 over the whole argument range the joint bounds allow (|x| <= 6144), including the
+    quadrant boundaries, zero and tiny arguments."""
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    k = np.arange(-3911, 3912)
+    xs = np.concatenate([rng.uniform(-8, 8, 200000), rng.uniform(-6144, 6144, 200000),
+                         k * (np.pi / 2), k * (np.pi / 2) + 1e-4, k * (np.pi / 4),
+                         [0.0, -0.0, 1e-30, -1e-30, 1e-7, 6144.0, -6144.0]]).astype(np.float32)
+    s, c = binding.gtmp_joint_sincos(torch.from_numpy(xs).cuda())
+    s, c = s.cpu().numpy().astype(np.float64), c.cpu().numpy().astype(np.float64)
+    x64 = xs.astype(np.float64)
+    assert np.abs(s - np.sin(x64)).max() <= 1e-7
+    assert np.abs(c - np.cos(x64)).max() <= 1e-7
+    assert np.all(s[xs == 0.0] == 0.0) and np.all(c[xs == 0.0] == 1.0)
+    assert binding.lib().gtmp_joint_sincos(None, -1, None, None, None) == 1
+
+
+def test_arm_angle_bounds_are_enforced(torch_cuda):
+    """Joint limits beyond +-4096 rad or a theta offset beyond +-2048 rad are refused at create; the label
+    query marks a configuration with a coordinate beyond +-4096 rad (or NaN) as colliding."""
+    import dataclasses
+    torch = torch_cuda
+    from paper_2608_25830_b300 import scenes
+    base = scenes.dh_arm(3, 7)
+    wide = dataclasses.replace(base, q_lo=np.full(7, -5000.0, np.float32), q_hi=np.full(7, 5000.0, np.float32))
+    with pytest.raises(binding.GtmpError):
+        binding.Planner(wide, 8, 1, 4)
+    dh = base.dh.copy()
+    dh[2, 3] = 3000.0
+    with pytest.raises(binding.GtmpError):
+        binding.Planner(dataclasses.replace(base, dh=dh), 8, 1, 4)
+    edge = dataclasses.replace(base, q_lo=np.full(7, -4096.0, np.float32), q_hi=np.full(7, 4096.0, np.float32))
+    q0 = np.zeros(7, np.float32)
+    sc = scenes.Scene(edge, np.zeros((0, 4), np.float32), np.zeros((0, 6), np.float32), q0, q0)
+    p = _planner(sc, 8, 1, 4)
+    q = np.zeros((4, 7), np.float32)
+    q[1, 3] = 4096.0
+    q[2, 3] = 4097.0
+    q[3, 5] = np.nan
+    lab = p.label_configs(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert lab.tolist() == [0, 0, 1, 1]   # no obstacles: only the out-of-range rows are labelled colliding
+    p.close()
+
+
 @pytest.mark.parametrize("radius", [0.5, 0.99, 1.0, 1.5])
 def test_config_labels_with_far_boxes_and_large_spheres(torch_cuda, radius):
     """The packed arm kernels clamp each box-axis gap at 1 (one saturating add), which decides the same as the
