@@ -386,7 +386,11 @@ constexpr int kParamCount = kNW1 + kHid + kNW2 + kHid + kNW3 + kHid + kHid + 1;
 // with cp.async, two chunks ahead of the MMAs (chunk numbers run on across a
 // CTA's tiles, so the next tile's first chunks load during this tile's head);
 // measured on B300, cp.async from all threads moves ~49 B per cycle per SM and
-// one bulk copy engine ~16.  TMEM: one 128 x 256 fp32 accumulator.  A tile is 128 queries: Q = 128 / kw
+// one bulk copy engine ~16.  TMEM: two 128 x 256 fp32 accumulators (all 512
+// columns), so that each layer's epilogue, taken in four 64-column chunks,
+// feeds the next layer's MMAs chunk by chunk (chunk c of layer l's output is
+// K-slice c of layer l + 1) while the epilogue of chunk c + 1 runs, and the
+// next tile's layer-1 MMAs run under this tile's head.  A tile is 128 queries: Q = 128 / kw
 // edges with kw waypoints each (t = 1/2 for kw = 1; 1/4, 1/2, 3/4 for kw = 3);
 // an edge is pruned when its largest logit exceeds `cut`.  Only live edges are
 // scored (compacted row and column lists).
@@ -523,8 +527,10 @@ __device__ __forceinline__ void score_features(const float* u, const float* v, f
 template <int DOF>
 __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs a, FourierDev f) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ __align__(8) uint64_t mbar_w1;    // the resident W1
+  __shared__ __align__(8) uint64_t mbar_layer;            // one arrival per layer's MMAs: three per tile
+  __shared__ __align__(8) uint64_t mbar_buf[kChunkBufs];  // chunk g's MMAs done: buffer g % kChunkBufs is free
+  __shared__ __align__(8) uint64_t mbar_w1;               // the resident W1
+  __shared__ __align__(8) uint64_t mbar_fin;              // every MMA of the CTA done (teardown)
   __shared__ int s_abort;
   __shared__ uint32_t tmem_base;
   __shared__ float s_part[2][128];
@@ -534,7 +540,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   uint8_t* sX = sH;           // the features occupy H's first 32 K until layer 1 has read them
   uint8_t* sS = sH + kSmemH;  // stream buffers
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t mb = s_u32(&mbar);
+  const uint32_t mbl = s_u32(&mbar_layer);
   const float* b1 = a.P + kNW1;
   const float* b2 = b1 + kHid + kNW2;
   const float* b3 = b2 + kHid + kNW3;
@@ -544,7 +550,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   // weight chunk g (chunk numbers run on across this CTA's tiles; g % 8 = 0..3: W2 columns
   // [64 (g % 4), + 64), 4..7: W3 columns) into buffer g % kChunkBufs: this thread's 128 bytes as one
   // cp.async group (an empty group past the CTA's last chunk, so that group g always holds chunk g)
-  long long chunks_loaded = 0, chunks_used = 0;
+  long long chunks_loaded = 0;
   auto load_chunk = [&](long long g, long long total) {
     if (g < total) {
       const uint8_t* src = a.Wimg + kSmemW1 + static_cast<size_t>(g % 8) * kSmemS;
@@ -557,23 +563,27 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  auto wait_mma = [&](uint32_t& phase) -> bool {
-    const bool ok = mbar_wait_parity(mb, phase, kMbarLimit);
-    if (!ok) mbar_wait_parity(mb, phase, kMbarLimit);  // let late MMAs drain before TMEM is freed
-    phase ^= 1u;
-    return __syncthreads_and(ok) != 0;
+  uint32_t ph_layer = 0;
+  // every thread waits for the next layer completion; the CTA agrees on the outcome
+  auto wait_layer = [&]() -> bool {
+    const bool w = mbar_wait_parity(mbl, ph_layer, kMbarLimit);
+    ph_layer ^= 1u;
+    return __syncthreads_and(w) != 0 && s_abort == 0;
   };
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(&tmem_base)),
-                 "r"(256)
+                 "r"(512)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
     s_abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbl) : "memory");
+    for (int k = 0; k < kChunkBufs; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_buf[k])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_w1)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_fin)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // resident W1: one bulk copy of its image
     const uint32_t bar = s_u32(&mbar_w1);
@@ -585,7 +595,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  bool w1_ready = false;
+  bool w1_ready = false, any_mma = false;  // thread 0's state
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (256u >> 3 << 17) | (128u >> 4 << 24);
@@ -600,76 +610,93 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   const int cols = layer_size(a.g, a.layer + 1);
   const int quarter = warp & 3, half = warp >> 2;
   const int row = quarter * 32 + lane;  // TMEM lane = tile row this thread reads
-  uint32_t phase = 0;
+  const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
   bool ok = true;
   const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long total_chunks = my_tiles * 8;
+  long long chunks_issued = 0;
   for (; chunks_loaded < kChunkBufs - 1; ++chunks_loaded) load_chunk(chunks_loaded, total_chunks);
 
-  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+  // features of a tile's queries -> X: two threads per query, 32 frequencies each; the fast __sincosf is
+  // ample here (|Bq| < 10, absolute error ~1e-6, the features are rounded to bf16 right after)
+  auto features = [&](long long tile) {
     const long long e_first = tile * e_per_tile;
-    // features of the tile's queries -> X: two threads per query, 32 frequencies
-    // each; the fast __sincosf is ample here (|Bq| < 10, absolute error ~1e-6,
-    // the features are rounded to bf16 right after)
-    {
-      const int qidx = tid & 127, hf = tid >> 7;
-      __align__(16) __nv_bfloat16 sv[32];
-      __align__(16) __nv_bfloat16 cv[32];
-      const long long e = e_first + qidx / a.kw;
-      if (qidx < q_per_tile && e < n_live) {
-        const int i = rows_live[e / nc], j = cols_live[e % nc];
-        const float* u = a.g.Q + vidx(a.g, 0, a.layer, i) * a.g.dp;
-        const float* v = a.g.Q + vidx(a.g, 0, a.layer + 1, j) * a.g.dp;
-        const float t = a.kw == 1 ? 0.5f : 0.25f * static_cast<float>(qidx % a.kw + 1);
-        if (hf == 0)
-          score_features<DOF, 0>(u, v, t, f, sv, cv);
-        else
-          score_features<DOF, 1>(u, v, t, f, sv, cv);
-      } else {
-        for (int k = 0; k < 32; ++k) sv[k] = cv[k] = __float2bfloat16_rn(0.0f);
-      }
-      for (int g8 = 0; g8 < 4; ++g8) {
-        *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + g8 * 8, 128)) = *reinterpret_cast<const uint4*>(sv + g8 * 8);
-        *reinterpret_cast<uint4*>(sX + canon(qidx, 64 + hf * 32 + g8 * 8, 128)) =
-            *reinterpret_cast<const uint4*>(cv + g8 * 8);
-      }
+    const int qidx = tid & 127, hf = tid >> 7;
+    __align__(16) __nv_bfloat16 sv[32];
+    __align__(16) __nv_bfloat16 cv[32];
+    const long long e = e_first + qidx / a.kw;
+    if (qidx < q_per_tile && e < n_live) {
+      const int i = rows_live[e / nc], j = cols_live[e % nc];
+      const float* u = a.g.Q + vidx(a.g, 0, a.layer, i) * a.g.dp;
+      const float* v = a.g.Q + vidx(a.g, 0, a.layer + 1, j) * a.g.dp;
+      const float t = a.kw == 1 ? 0.5f : 0.25f * static_cast<float>(qidx % a.kw + 1);
+      if (hf == 0)
+        score_features<DOF, 0>(u, v, t, f, sv, cv);
+      else
+        score_features<DOF, 1>(u, v, t, f, sv, cv);
+    } else {
+      for (int k = 0; k < 32; ++k) sv[k] = cv[k] = __float2bfloat16_rn(0.0f);
+    }
+    for (int g8 = 0; g8 < 4; ++g8) {
+      *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + g8 * 8, 128)) = *reinterpret_cast<const uint4*>(sv + g8 * 8);
+      *reinterpret_cast<uint4*>(sX + canon(qidx, 64 + hf * 32 + g8 * 8, 128)) =
+          *reinterpret_cast<const uint4*>(cv + g8 * 8);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // X (generic writes) -> MMA reads
+  };
+  // layer 1 (D = X W1^T) into the accumulator at TMEM column acc, committed to the layer barrier; on a W1
+  // timeout the barrier is released by hand and the abort flag set
+  auto issue_l1 = [&](uint32_t acc) {
+    if (tid != 0) return;
+    bool go = true;
+    if (!w1_ready) {
+      go = mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);
+      w1_ready = true;
+      if (!go) {
+        s_abort = 1;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbl) : "memory");
+      }
+    }
+    if (go) {
+      any_mma = true;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kk = 0; kk < 8; ++kk)
+        issue_mma(tmem + acc, smem_desc(s_u32(sX) + kk * 256, 128, 2048), smem_desc(s_u32(sW1) + kk * 256, 128, 2048),
+                  idesc, kk > 0);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbl)
+                   : "memory");
+    }
+  };
+
+  // Per tile: the layer-1 accumulator A (TMEM columns 0 or 256, alternating by tile) also takes layer 3,
+  // the other one, B, layer 2.  Each epilogue runs in four 64-column chunks; chunk c of layer l's
+  // output, written to H, is K-slice c of layer l + 1, whose four MMAs are issued at once and run
+  // under the epilogue of chunk c + 1.  The next tile's features and layer-1 MMAs (into B) run before
+  // this tile's head (which reads A).
+  long long tile = blockIdx.x;
+  uint32_t par = 0;
+  if (tile < n_tiles) {
+    features(tile);
     __syncthreads();
-    // layer 1: D = X W1^T
-    if (tid == 0) {
-      bool go = true;
-      if (!w1_ready) {
-        go = mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);
-        w1_ready = true;
-        if (!go) {
-          s_abort = 1;
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
-        }
+    issue_l1(0u);
+  }
+  for (; tile < n_tiles && ok; tile += gridDim.x, par ^= 1u) {
+    const uint32_t accA = par ? 256u : 0u, accB = par ? 0u : 256u;
+    ok = wait_layer();  // layer 1
+    for (int l = 0; l < 2 && ok; ++l) {
+      if (l == 1) {
+        ok = wait_layer();  // layer 2
+        if (!ok) break;
       }
-      if (go) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int kk = 0; kk < 8; ++kk)
-          issue_mma(tmem, smem_desc(s_u32(sX) + kk * 256, 128, 2048), smem_desc(s_u32(sW1) + kk * 256, 128, 2048),
-                    idesc, kk > 0);
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                     : "memory");
-      }
-    }
-    ok = wait_mma(phase);
-    if (!ok || s_abort) {
-      ok = false;
-      break;
-    }
-    for (int c = 0; c <= 8 && ok; ++c) {
-      // epilogue of the previous layer: TMEM -> relu(acc + b) -> bf16 -> H (after layer 1 and layer 2)
-      if (c == 0 || c == 4) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const float* bias = c == 0 ? b1 : b2;
-        for (int cc = 0; cc < 4; ++cc) {
-          const int n0 = half * 128 + cc * 32;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc_in = l == 0 ? accA : accB, acc_out = l == 0 ? accB : accA;
+      const float* bias = l == 0 ? b1 : b2;
+      for (int c = 0; c < 4; ++c) {
+        // epilogue chunk c: TMEM -> relu(acc + b) -> bf16 -> H columns [64 c, + 64)
+        {
+          const int n0 = c * 64 + half * 32;
           uint32_t v[32];
-          tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + n0, v);
+          tmem_ld32(lane_addr + acc_in + n0, v);
 #pragma unroll
           for (int g8 = 0; g8 < 4; ++g8) {
             const float4 ba = __ldg(reinterpret_cast<const float4*>(bias + n0 + g8 * 8));
@@ -687,41 +714,54 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // H (generic writes) -> MMA reads
+        // chunk g = chunks_issued goes to the MMAs now; the buffer of chunk g + 2 last held chunk g - 1,
+        // whose MMAs must have completed before it is overwritten
+        const long long g = chunks_issued;
+        bool free_ok = true;
+        if (g >= 1)
+          free_ok = mbar_wait_parity(s_u32(&mbar_buf[(g - 1) % kChunkBufs]),
+                                     static_cast<uint32_t>(((g - 1) / kChunkBufs) & 1), kMbarLimit);
+        load_chunk(chunks_loaded++, free_ok ? total_chunks : 0);
+        // this thread's part of chunk g has landed (groups g + 1 and g + 2 may be in flight): make it
+        // visible to the MMA (async proxy), then wait for every thread's part and epilogue chunk
+        asm volatile("cp.async.wait_group %0;" ::"n"(kChunkBufs - 1) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-      }
-      if (c == 8) break;
-      // the buffer of chunk g + 2 last held chunk g - 1, whose MMAs every thread has seen complete
-      load_chunk(chunks_loaded++, total_chunks);
-      // this thread's part of chunk g has landed (groups g + 1 and g + 2 may be in flight): make it visible
-      // to the MMA (async proxy), then wait for every thread's part
-      asm volatile("cp.async.wait_group %0;" ::"n"(kChunkBufs - 1) : "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (warp == 0 && !s_abort) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (lane == 0) {
-          const uint32_t sb = s_u32(sS + static_cast<int>(chunks_used % kChunkBufs) * kSmemS);
-          const int kc = c & 3;
+        ok = __syncthreads_and(free_ok) != 0 && s_abort == 0;
+        if (!ok) break;
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sb = s_u32(sS + static_cast<int>(g % kChunkBufs) * kSmemS);
           for (int kk = 0; kk < 4; ++kk)
-            issue_mma(tmem, smem_desc(s_u32(sH) + kc * 1024 + kk * 256, 128, 4096),
-                      smem_desc(sb + kk * 256, 128, 1024), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+            issue_mma(tmem + acc_out, smem_desc(s_u32(sH) + c * 1024 + kk * 256, 128, 4096),
+                      smem_desc(sb + kk * 256, 128, 1024), idesc, (c > 0 || kk > 0) ? 1u : 0u);
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           s_u32(&mbar_buf[g % kChunkBufs]))
                        : "memory");
+          if (c == 3)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbl)
+                         : "memory");
         }
-        __syncwarp();
+        ++chunks_issued;
       }
-      ++chunks_used;
-      ok = wait_mma(phase) && !s_abort;
     }
     if (!ok) break;
+    ok = wait_layer();  // layer 3 (accumulator A)
+    if (!ok) break;
+    // the next tile's features (H is free: layer 3 has read it) and layer-1 MMAs into B, under this head
+    const long long next = tile + gridDim.x;
+    if (next < n_tiles) {
+      features(next);
+      __syncthreads();
+      issue_l1(accB);
+    }
     // head: relu(acc + b3) . w4 + b4, per query; then the edge's max against the cut
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float dot = 0.0f;
     for (int cc = 0; cc < 4; ++cc) {
       const int n0 = half * 128 + cc * 32;
       uint32_t v[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + n0, v);
+      tmem_ld32(lane_addr + accA + n0, v);
       // four partial sums: a short dependency chain
       float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -742,6 +782,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     __syncthreads();
     if (tid < 128) {  // warps 0..3, full warps for the ballot
       bool pr = false;
+      const long long e_first = tile * e_per_tile;
       const long long e = e_first + tid;
       if (tid < e_per_tile && e < n_live) {
         float z = s_logit[tid * a.kw];
@@ -755,13 +796,23 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     __syncthreads();
   }
   asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies have landed
-  if (!ok && tid == 0) {
-    atomicOr(a.err, kErrWaitTimeout);
-    if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);  // let the W1 copy land (bounded)
+  if (tid == 0) {
+    // every MMA this CTA issued has completed before TMEM is freed (bounded)
+    bool drained = true;
+    if (any_mma) {
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       s_u32(&mbar_fin))
+                   : "memory");
+      drained = mbar_wait_parity(s_u32(&mbar_fin), 0u, kMbarLimit);
+    }
+    if (!ok || !drained) {
+      atomicOr(a.err, kErrWaitTimeout);
+      if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);  // let the W1 copy land (bounded)
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 struct SurrogateState {
