@@ -744,6 +744,9 @@ def measure_surrogate(args, wl, flush, steps, warmup, n_train=None, epochs=None)
     binding.gtmp_surrogate_set_params(planners["lazy"].ctx,
                                       binding.gtmp_surrogate_get_params(planners["early_exit"].ctx, sc.robot.dof))
     thr, kw = wl["threshold"], wl["score_waypoints"]
+    band = wl.get("protect", 0.0)   # edges within (1 + band) x their row's best bound stay exact
+    for pl in planners.values():
+        binding.gtmp_surrogate_set_protect(pl.ctx, band)
     stream = torch.cuda.current_stream()
     path = torch.empty(L, dtype=torch.int32, device="cuda")
     cost = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -818,7 +821,8 @@ def measure_surrogate(args, wl, flush, steps, warmup, n_train=None, epochs=None)
     return {
         "workload": "7-DoF arm, 40 obstacles, M=4096, L=8, H=32; MLP Fourier(64)-256-256-256-1, bf16",
         "M": M, "L": L, "H": H, "dof": wl["dof"], "obstacles": wl["n_obs"], "threshold": thr,
-        "score_waypoints": kw, "train_configs": n_train, "steps": steps, "warmup": warmup,
+        "protection_band": band, "score_waypoints": kw, "train_configs": n_train, "steps": steps,
+        "warmup": warmup,
         "solves_per_s": sps,
         "ms_per_solve": {k: 1e3 / v for k, v in sps.items()},
         "surrogate_over_plain": {"early_exit": sps["early_exit_pruned"] / sps["early_exit"],
@@ -832,8 +836,10 @@ def measure_surrogate(args, wl, flush, steps, warmup, n_train=None, epochs=None)
         "training": train,
         "clocks": clk.summary(),
         "l2": "flushed before every solve",
-        "note": "plain and pruned solve the same samples (seed = step) in each mode; every returned chain is "
-                "re-checked at all H waypoints of every edge by the exact checker",
+        "note": "plain and pruned solve the same samples (seed = step) in each mode; an edge is pruned when its "
+                "midpoint's collision probability exceeds the threshold and its bound |v - u| + J(v) lies above "
+                "(1 + protection_band) x its row's best bound; every returned chain is re-checked at all H "
+                "waypoints of every edge by the exact checker",
     }
 
 

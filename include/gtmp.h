@@ -546,7 +546,8 @@ GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* ctx, const float* dev_q,
 
 /* gtmp_solve on graph 0 in which an edge is dropped before exact checking when
  * the surrogate's collision probability at any of its scored waypoints
- * (score_waypoints = 1: t = 1/2; 3: t = 1/4, 1/2, 3/4) exceeds threshold;
+ * (score_waypoints = 1: t = 1/2; 3: t = 1/4, 1/2, 3/4) exceeds threshold and
+ * the edge lies outside the protection band (gtmp_surrogate_set_protect);
  * scoring runs in one fused tensor-core kernel per transition and covers the
  * live edges only (row vertex free, column vertex free with a finite
  * cost-to-go: the exact solve skips every other edge anyway).  Every
@@ -558,6 +559,17 @@ GTMP_API gtmp_status gtmp_surrogate_loss_grad(gtmp_ctx* ctx, const float* dev_q,
 GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* ctx, float threshold, int32_t score_waypoints, int32_t* dev_path,
                                        float* dev_cost, gtmp_prune_stats* stats);
 
+/* Protection band of the surrogate's pruning (no counterpart in the paper):
+ * with band > 0, an edge (u, v) whose bound |v - u| + J(v) (its length plus
+ * the cost-to-go of its head, a lower bound of what the edge can give the
+ * row) is at most (1 + band) times the smallest such bound of its row (over
+ * the live columns, edges beyond the edge limit left out) is never pruned,
+ * whatever its score: the edges a row's best path most likely takes stay with
+ * the exact checker, and the rest can be pruned at a lower threshold.  0 (the
+ * default) turns the band off.  Takes effect at the next gtmp_solve_pruned or
+ * gtmp_surrogate_score.  GTMP_ERR_INVALID_ARG outside [0, 16]. */
+GTMP_API gtmp_status gtmp_surrogate_set_protect(gtmp_ctx* ctx, float band);
+
 /* Inspection of the scoring step of gtmp_solve_pruned (no counterpart in the
  * paper): the fused scoring kernel's decision for every live edge of one
  * transition `layer` (0 = start row, L = the goal column) of graph 0, with
@@ -566,8 +578,8 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* ctx, float threshold, int32_t s
  * rows whose vertex is free, columns whose vertex is free with a finite
  * cost-to-go.  dev_mask device [rows][cols] uint8 (rows = 1 for layer 0, else
  * M; cols = M, or the goal count for layer L): 1 = pruned (the largest
- * scored waypoint logit exceeds logit(threshold)), 0 = kept, 2 = not live
- * (not scored).  host_scored (may be NULL) receives the live-edge count.
+ * scored waypoint logit exceeds logit(threshold) and the edge lies outside
+ * the protection band), 0 = kept, 2 = not live (not scored).  host_scored (may be NULL) receives the live-edge count.
  * Synchronous.  Errors: GTMP_ERR_NOT_READY before training or sampling,
  * GTMP_ERR_INVALID_ARG for a bad layer, threshold or waypoint count. */
 GTMP_API gtmp_status gtmp_surrogate_score(gtmp_ctx* ctx, int32_t layer, float threshold, int32_t score_waypoints,

@@ -138,6 +138,7 @@ _SIGNATURES = {
     "gtmp_surrogate_predict": [_vp, _vp, _i32, _vp],
     "gtmp_surrogate_get_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
     "gtmp_solve_pruned": [_vp, ctypes.c_float, _i32, _vp, _vp, ctypes.POINTER(GtmpPruneStats)],
+    "gtmp_surrogate_set_protect": [_vp, ctypes.c_float],
     "gtmp_surrogate_score": [_vp, _i32, ctypes.c_float, _i32, _vp, ctypes.POINTER(ctypes.c_int64)],
     "gtmp_surrogate_set_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
     "gtmp_surrogate_loss_grad": [_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _fp, ctypes.c_int64],
@@ -744,6 +745,11 @@ def gtmp_solve_pruned(ctx, threshold, dev_path, dev_cost, score_waypoints=1):
     _check(ctx, lib().gtmp_solve_pruned(ctx, threshold, score_waypoints, _dev(dev_path, torch.int32),
                                         _dev(dev_cost, torch.float32), ctypes.byref(st)))
     return dict(edges=st.edges, pruned=st.pruned, score_ms=st.score_ms, solve_ms=st.solve_ms, scored=st.scored)
+
+
+def gtmp_surrogate_set_protect(ctx, band):
+    """Protection band of the pruned solve: edges within (1 + band) x their row's best bound are never pruned."""
+    _check(ctx, lib().gtmp_surrogate_set_protect(ctx, band))
 
 
 def gtmp_surrogate_score(ctx, layer, threshold, dev_mask, score_waypoints=1):

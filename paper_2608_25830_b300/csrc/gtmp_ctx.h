@@ -72,6 +72,7 @@ struct gtmp_ctx {
   int64_t fused_timed_launches = 0;             // fused launches timed (the sweeps in ev_used)                 // min-plus launches timed (the sweeps in ev_minplus)
   // learned collision surrogate (allocated by gtmp_surrogate_train)
   gtmp::SurrogateState* sur = nullptr;
+  float sur_protect = 0.0f;  // protection band of the pruned solve (gtmp_surrogate_set_protect); 0 = off
   uint8_t* prune = nullptr;  // per-transition prune mask, M x M
   // class-augmented sweep (allocated by gtmp_solve_classes)
   void* cls = nullptr;

@@ -433,6 +433,36 @@ __global__ void __launch_bounds__(1024) live_lists_kernel(GraphDev g, int layer,
   }
 }
 
+// The smallest edge bound |v - u| + J(v) of each live row over the live
+// columns (edges longer than the edge limit left out), by row index: one warp
+// per live row, float32 as the exact kernels compute the length.
+__global__ void __launch_bounds__(256) row_min_bound_kernel(GraphDev g, int layer, const int* live, int cap,
+                                                            float* minb) {
+  const int nr = live[0], nc = live[1];
+  const int* rows_live = live + 2;
+  const int* cols_live = live + 2 + cap;
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nr) return;
+  const int i = rows_live[r];
+  const float* u = g.Q + vidx(g, 0, layer, i) * g.dp;
+  float best = kInf;
+  for (int c = lane; c < nc; c += 32) {
+    const int j = cols_live[c];
+    const size_t vj = vidx(g, 0, layer + 1, j);
+    const float* v = g.Q + vj * g.dp;
+    float s2 = 0.0f;
+    for (int d = 0; d < g.dp; ++d) {
+      const float e = __fsub_rn(v[d], u[d]);
+      s2 = __fmaf_rn(e, e, s2);
+    }
+    const float len = __fsqrt_rn(s2);
+    if (!(len > g.max_edge_len)) best = fminf(best, __fadd_rn(len, key_value(__ldcg(g.keys + vj))));
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(kFull, best, o));
+  if (lane == 0) minb[i] = best;
+}
+
 constexpr int kScoreThreads = 256;
 constexpr int kSmemW1 = 256 * 128 * 2, kSmemH = 128 * 256 * 2, kSmemS = 256 * 64 * 2;
 constexpr int kChunkBufs = 3;                      // stream buffers: one being read, two loading
@@ -453,6 +483,10 @@ struct ScoreArgs {
   uint8_t* prune;
   unsigned long long* n_pruned;
   int* err;
+  // protection band: an edge whose bound |v - u| + J(v) is at most protect times its row's smallest bound
+  // (minb, by row index) is never pruned; protect <= 0: no band
+  float protect;
+  const float* minb;
 };
 
 // byte offset of element (r, k) in a canonical K-major tile whose rows hold kdim elements
@@ -535,6 +569,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   __shared__ uint32_t tmem_base;
   __shared__ float s_part[2][128];
   __shared__ float s_logit[128];
+  __shared__ bool s_prot[2][128];  // per tile parity: the edge lies in its row's protection band
   uint8_t* sW1 = smem;
   uint8_t* sH = sW1 + kSmemW1;
   uint8_t* sX = sH;           // the features occupy H's first 32 K until layer 1 has read them
@@ -619,24 +654,39 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
 
   // features of a tile's queries -> X: two threads per query, 32 frequencies each; the fast __sincosf is
   // ample here (|Bq| < 10, absolute error ~1e-6, the features are rounded to bf16 right after)
-  auto features = [&](long long tile) {
+  auto features = [&](long long tile, uint32_t parity) {
     const long long e_first = tile * e_per_tile;
     const int qidx = tid & 127, hf = tid >> 7;
     __align__(16) __nv_bfloat16 sv[32];
     __align__(16) __nv_bfloat16 cv[32];
     const long long e = e_first + qidx / a.kw;
+    bool prot = false;
     if (qidx < q_per_tile && e < n_live) {
       const int i = rows_live[e / nc], j = cols_live[e % nc];
       const float* u = a.g.Q + vidx(a.g, 0, a.layer, i) * a.g.dp;
-      const float* v = a.g.Q + vidx(a.g, 0, a.layer + 1, j) * a.g.dp;
+      const size_t vj = vidx(a.g, 0, a.layer + 1, j);
+      const float* v = a.g.Q + vj * a.g.dp;
       const float t = a.kw == 1 ? 0.5f : 0.25f * static_cast<float>(qidx % a.kw + 1);
-      if (hf == 0)
+      if (hf == 0) {
         score_features<DOF, 0>(u, v, t, f, sv, cv);
-      else
+      } else {
         score_features<DOF, 1>(u, v, t, f, sv, cv);
+        if (a.protect > 0.0f && qidx % a.kw == 0) {
+          // the edge's bound |v - u| + J(v) against its row's smallest, as row_min_bound_kernel takes it
+          float s2 = 0.0f;
+          for (int d = 0; d < a.g.dp; ++d) {
+            const float df = __fsub_rn(v[d], u[d]);
+            s2 = __fmaf_rn(df, df, s2);
+          }
+          const float len = __fsqrt_rn(s2);
+          prot = !(len > a.g.max_edge_len) &&
+                 __fadd_rn(len, key_value(__ldcg(a.g.keys + vj))) <= __fmul_rn(a.protect, a.minb[i]);
+        }
+      }
     } else {
       for (int k = 0; k < 32; ++k) sv[k] = cv[k] = __float2bfloat16_rn(0.0f);
     }
+    if (hf == 1 && qidx % a.kw == 0) s_prot[parity][qidx / a.kw] = prot;
     for (int g8 = 0; g8 < 4; ++g8) {
       *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + g8 * 8, 128)) = *reinterpret_cast<const uint4*>(sv + g8 * 8);
       *reinterpret_cast<uint4*>(sX + canon(qidx, 64 + hf * 32 + g8 * 8, 128)) =
@@ -676,7 +726,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   long long tile = blockIdx.x;
   uint32_t par = 0;
   if (tile < n_tiles) {
-    features(tile);
+    features(tile, 0u);
     __syncthreads();
     issue_l1(0u);
   }
@@ -751,7 +801,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     // the next tile's features (H is free: layer 3 has read it) and layer-1 MMAs into B, under this head
     const long long next = tile + gridDim.x;
     if (next < n_tiles) {
-      features(next);
+      features(next, par ^ 1u);
       __syncthreads();
       issue_l1(accB);
     }
@@ -787,7 +837,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
       if (tid < e_per_tile && e < n_live) {
         float z = s_logit[tid * a.kw];
         for (int w = 1; w < a.kw; ++w) z = fmaxf(z, s_logit[tid * a.kw + w]);
-        pr = z > a.cut;
+        pr = z > a.cut && !s_prot[par][tid];
         a.prune[static_cast<size_t>(rows_live[e / nc]) * cols + cols_live[e % nc]] = pr ? 1 : 0;
       }
       const unsigned b = __ballot_sync(kFull, pr);
@@ -830,6 +880,7 @@ struct SurrogateState {
   double* loss = nullptr;
   unsigned long long* counter = nullptr;
   int* live = nullptr;  // live rows / columns of the transition being scored: [2 + 2 * live_cap]
+  float* minb = nullptr;  // per row index, the smallest edge bound of the transition (protection band) [live_cap]
   uint8_t* wimg = nullptr;  // weight images of the scoring kernel (W1, then 8 chunks of W2 / W3)
   int live_cap = 0;
   bool trained = false;
@@ -840,7 +891,7 @@ void surrogate_free(SurrogateState* s) {
   if (!s) return;
   void* bufs[] = {s->P,   s->G,   s->Mm,  s->Vv,  s->W1b, s->W1bT,   s->W2b,     s->W2bT, s->W3b,
                   s->W3bT, s->X,  s->XT,  s->H1,  s->H1T, s->H2,     s->H2T,     s->H3,   s->H3T,
-                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter, s->live, s->wimg};
+                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter, s->live, s->wimg, s->minb};
   for (void* b : bufs) cudaFree(b);
   delete s;
 }
@@ -1217,6 +1268,9 @@ gtmp_status prepare_scoring(gtmp_ctx* c) {
     s->live = nullptr;
     s->live_cap = 0;
     SUR_TRY(c, cudaMalloc(&s->live, (2 + 2 * static_cast<size_t>(c->p.M)) * sizeof(int)));
+    cudaFree(s->minb);
+    s->minb = nullptr;
+    SUR_TRY(c, cudaMalloc(&s->minb, static_cast<size_t>(c->p.M) * sizeof(float)));
     s->live_cap = c->p.M;
   }
   SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
@@ -1268,9 +1322,16 @@ gtmp_status launch_score_transition(gtmp_ctx* c, const GraphDev& g, int layer, f
   sa.prune = prune;
   sa.n_pruned = s->counter;
   sa.err = c->err;
+  sa.protect = c->sur_protect > 0.0f ? 1.0f + c->sur_protect : 0.0f;
+  sa.minb = s->minb;
   // the live count stays on the device: a persistent grid reads it
   live_lists_kernel<<<1, 1024, 0, st>>>(g, layer, s->live_cap, s->live);
   SUR_TRY(c, cudaGetLastError());
+  if (sa.protect > 0.0f) {
+    row_min_bound_kernel<<<(layer_size(g, layer) * 32 + 255) / 256, 256, 0, st>>>(g, layer, s->live, s->live_cap,
+                                                                               s->minb);
+    SUR_TRY(c, cudaGetLastError());
+  }
   const long long tiles = (ne + 128 / kw - 1) / (128 / kw);
   const int score_grid = static_cast<int>(std::min<long long>(tiles, c->num_sms));
   if (s->four.dof == 7)
@@ -1286,6 +1347,12 @@ gtmp_status launch_score_transition(gtmp_ctx* c, const GraphDev& g, int layer, f
 }  // namespace
 
 extern "C" {
+
+GTMP_API gtmp_status gtmp_surrogate_set_protect(gtmp_ctx* c, float band) {
+  if (!c || !(band >= 0.0f && band <= 16.0f)) return sfail(c, GTMP_ERR_INVALID_ARG, "protection band must be in [0, 16]");
+  c->sur_protect = band;
+  return GTMP_OK;
+}
 
 GTMP_API gtmp_status gtmp_surrogate_score(gtmp_ctx* c, int32_t layer, float threshold, int32_t score_waypoints,
                                           uint8_t* dev_mask, int64_t* host_scored) {

@@ -210,7 +210,8 @@ WORKLOADS = {
                                      epochs=dict(L0=2, L_cap=8, M0=64, M_max=2048, stages=14, reach=2.5, r=0.1,
                                                  varsigma=0.1, limit_edges=True)),
     "arm7_m4096_l8_h32_n40": dict(kind="arm", dof=7, seed=0, n_obs=40, M=4096, L=8, H=32,
-                                  n_train=1 << 21, epochs=3, sigma=0.25, threshold=0.5, score_waypoints=1),
+                                  n_train=1 << 21, epochs=3, sigma=0.25, threshold=0.1, protect=0.1,
+                                  score_waypoints=1),
     "batched512_h32": dict(kind="batched", seed=0, n=512, H=32),
     "point2d_classes_m32_l4_h16": dict(kind="classes", seed=0, n_obs=10, M=32, L=4, H=16, K=256, R=16),
     "point2d_classes_m64_l4_h16_n16": dict(kind="classes", seed=2, n_obs=16, M=64, L=4, H=16, K=1024, R=16),

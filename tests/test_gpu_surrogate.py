@@ -174,6 +174,57 @@ def _waypoints(u, v, kw):
     return [(u.astype(np.float64) + t * d).astype(np.float32) for t in ts]
 
 
+def test_protection_band_keeps_each_rows_best_bounds(trained):
+    """With a protection band b, an edge whose bound |v - u| + J(v) is at most (1 + b) times the smallest
+    bound of its row (over the live columns) is never pruned, and every other live edge keeps the decision
+    it has without the band; the band only ever removes edges from the pruned set.  Edges within 1e-5
+    relative of the band's edge are not judged (float32 bound against the host's FP64 one).  Aggressive
+    threshold 0.1, M = 120, five transitions."""
+    import torch
+    sc, p, _ = trained
+    L, M, thr, band = 4, 120, 0.1, 0.1
+    p.sample_layers(23, M)
+    p.solve()
+    V, _ = p.values()
+    V = V.cpu().numpy()
+    Q = p.get_layers().cpu().numpy()
+    verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
+    flags = [p.label_configs(torch.from_numpy(np.ascontiguousarray(v)).cuda()).cpu().numpy() for v in verts]
+    assert binding.lib().gtmp_surrogate_set_protect(p.ctx, -0.5) == 1
+    assert binding.lib().gtmp_surrogate_set_protect(p.ctx, float("nan")) == 1
+    judged = protected = 0
+    try:
+        for layer in range(L + 1):
+            nr, nc = len(verts[layer]), len(verts[layer + 1])
+            masks = []
+            for b in (0.0, band):
+                binding.gtmp_surrogate_set_protect(p.ctx, b)
+                m = torch.full((nr, nc), 7, dtype=torch.uint8, device="cuda")
+                binding.gtmp_surrogate_score(p.ctx, layer, thr, m)
+                masks.append(m.cpu().numpy())
+            off, on = masks
+            rows, cols = _live_edges(p, sc, L, V, flags, layer)
+            if len(rows) == 0 or len(cols) == 0:
+                continue
+            assert np.all(on[np.ix_(rows, cols)] <= off[np.ix_(rows, cols)]), f"layer {layer}: band added prunes"
+            u = verts[layer][rows].astype(np.float64)
+            v = verts[layer + 1][cols].astype(np.float64)
+            vj = V[layer + 1, :nc][cols].astype(np.float64)
+            bound = np.sqrt(((v[None, :, :] - u[:, None, :]) ** 2).sum(-1)) + vj[None, :]
+            lim = (1.0 + band) * bound.min(1, keepdims=True)
+            inside = bound <= lim * (1 - 1e-5)
+            outside = bound >= lim * (1 + 1e-5)
+            sub_on, sub_off = on[np.ix_(rows, cols)], off[np.ix_(rows, cols)]
+            assert np.all(sub_on[inside] == 0), f"layer {layer}: {int(np.sum(sub_on[inside]))} band edges pruned"
+            np.testing.assert_array_equal(sub_on[outside], sub_off[outside], err_msg=f"layer {layer}")
+            judged += int(inside.sum() + outside.sum())
+            protected += int(np.sum(inside & (sub_off == 1)))
+    finally:
+        binding.gtmp_surrogate_set_protect(p.ctx, 0.0)
+    assert protected > 0, "the band never overrode a prune: the test has no teeth"
+    print(f"protection band: {judged} live edges judged, {protected} prunes overridden")
+
+
 @pytest.mark.parametrize("kw", [1, 3])
 def test_scoring_kernel_decisions_elementwise(trained, kw):
     """Every live edge's prune decision from the fused scoring kernel (gtmp_surrogate_score) against
