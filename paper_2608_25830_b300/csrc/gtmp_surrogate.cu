@@ -433,11 +433,28 @@ __global__ void __launch_bounds__(1024) live_lists_kernel(GraphDev g, int layer,
   }
 }
 
-// The smallest edge bound |v - u| + J(v) of each live row over the live
-// columns (edges longer than the edge limit left out), by row index: one warp
-// per live row, float32 as the exact kernels compute the length.
-__global__ void __launch_bounds__(256) row_min_bound_kernel(GraphDev g, int layer, const int* live, int cap,
-                                                            float* minb) {
+// The protection band of a transition: per live row (one warp), the smallest
+// edge bound |v - u| + J(v) over the live columns (edges longer than the edge
+// limit left out; float32 as the exact kernels compute the length), then
+// every live edge of the row marked in the prune mask: kPruneProtected when
+// its bound is at most factor times that minimum, else 0.  The scoring
+// kernel then writes every live edge's decision, never pruning a marked one.
+constexpr uint8_t kPruneProtected = 3;
+
+__device__ __forceinline__ float edge_bound(const GraphDev& g, int layer, const float* u, int j) {
+  const size_t vj = vidx(g, 0, layer + 1, j);
+  const float* v = g.Q + vj * g.dp;
+  float s2 = 0.0f;
+  for (int d = 0; d < g.dp; ++d) {
+    const float e = __fsub_rn(v[d], u[d]);
+    s2 = __fmaf_rn(e, e, s2);
+  }
+  const float len = __fsqrt_rn(s2);
+  return len > g.max_edge_len ? kInf : __fadd_rn(len, key_value(__ldcg(g.keys + vj)));
+}
+
+__global__ void __launch_bounds__(256) protect_band_kernel(GraphDev g, int layer, const int* live, int cap,
+                                                           float factor, uint8_t* prune) {
   const int nr = live[0], nc = live[1];
   const int* rows_live = live + 2;
   const int* cols_live = live + 2 + cap;
@@ -445,22 +462,26 @@ __global__ void __launch_bounds__(256) row_min_bound_kernel(GraphDev g, int laye
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= nr) return;
   const int i = rows_live[r];
+  const int cols = layer_size(g, layer + 1);
   const float* u = g.Q + vidx(g, 0, layer, i) * g.dp;
+  // four columns per lane and trip: four independent chains of dependent loads in flight
   float best = kInf;
-  for (int c = lane; c < nc; c += 32) {
-    const int j = cols_live[c];
-    const size_t vj = vidx(g, 0, layer + 1, j);
-    const float* v = g.Q + vj * g.dp;
-    float s2 = 0.0f;
-    for (int d = 0; d < g.dp; ++d) {
-      const float e = __fsub_rn(v[d], u[d]);
-      s2 = __fmaf_rn(e, e, s2);
-    }
-    const float len = __fsqrt_rn(s2);
-    if (!(len > g.max_edge_len)) best = fminf(best, __fadd_rn(len, key_value(__ldcg(g.keys + vj))));
+  for (int c0 = lane; c0 < nc; c0 += 128) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (c0 + 32 * k < nc) best = fminf(best, edge_bound(g, layer, u, cols_live[c0 + 32 * k]));
   }
   for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(kFull, best, o));
-  if (lane == 0) minb[i] = best;
+  const float lim = __fmul_rn(factor, best);
+  uint8_t* row = prune + static_cast<size_t>(i) * cols;
+  for (int c0 = lane; c0 < nc; c0 += 128) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (c0 + 32 * k < nc) {
+        const int j = cols_live[c0 + 32 * k];
+        row[j] = edge_bound(g, layer, u, j) <= lim ? kPruneProtected : 0;
+      }
+  }
 }
 
 constexpr int kScoreThreads = 256;
@@ -483,10 +504,8 @@ struct ScoreArgs {
   uint8_t* prune;
   unsigned long long* n_pruned;
   int* err;
-  // protection band: an edge whose bound |v - u| + J(v) is at most protect times its row's smallest bound
-  // (minb, by row index) is never pruned; protect <= 0: no band
-  float protect;
-  const float* minb;
+  // protection band on: live entries of prune hold kPruneProtected (never pruned) or 0 on entry
+  int protect;
 };
 
 // byte offset of element (r, k) in a canonical K-major tile whose rows hold kdim elements
@@ -569,7 +588,6 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   __shared__ uint32_t tmem_base;
   __shared__ float s_part[2][128];
   __shared__ float s_logit[128];
-  __shared__ bool s_prot[2][128];  // per tile parity: the edge lies in its row's protection band
   uint8_t* sW1 = smem;
   uint8_t* sH = sW1 + kSmemW1;
   uint8_t* sX = sH;           // the features occupy H's first 32 K until layer 1 has read them
@@ -654,39 +672,24 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
 
   // features of a tile's queries -> X: two threads per query, 32 frequencies each; the fast __sincosf is
   // ample here (|Bq| < 10, absolute error ~1e-6, the features are rounded to bf16 right after)
-  auto features = [&](long long tile, uint32_t parity) {
+  auto features = [&](long long tile) {
     const long long e_first = tile * e_per_tile;
     const int qidx = tid & 127, hf = tid >> 7;
     __align__(16) __nv_bfloat16 sv[32];
     __align__(16) __nv_bfloat16 cv[32];
     const long long e = e_first + qidx / a.kw;
-    bool prot = false;
     if (qidx < q_per_tile && e < n_live) {
       const int i = rows_live[e / nc], j = cols_live[e % nc];
       const float* u = a.g.Q + vidx(a.g, 0, a.layer, i) * a.g.dp;
-      const size_t vj = vidx(a.g, 0, a.layer + 1, j);
-      const float* v = a.g.Q + vj * a.g.dp;
+      const float* v = a.g.Q + vidx(a.g, 0, a.layer + 1, j) * a.g.dp;
       const float t = a.kw == 1 ? 0.5f : 0.25f * static_cast<float>(qidx % a.kw + 1);
-      if (hf == 0) {
+      if (hf == 0)
         score_features<DOF, 0>(u, v, t, f, sv, cv);
-      } else {
+      else
         score_features<DOF, 1>(u, v, t, f, sv, cv);
-        if (a.protect > 0.0f && qidx % a.kw == 0) {
-          // the edge's bound |v - u| + J(v) against its row's smallest, as row_min_bound_kernel takes it
-          float s2 = 0.0f;
-          for (int d = 0; d < a.g.dp; ++d) {
-            const float df = __fsub_rn(v[d], u[d]);
-            s2 = __fmaf_rn(df, df, s2);
-          }
-          const float len = __fsqrt_rn(s2);
-          prot = !(len > a.g.max_edge_len) &&
-                 __fadd_rn(len, key_value(__ldcg(a.g.keys + vj))) <= __fmul_rn(a.protect, a.minb[i]);
-        }
-      }
     } else {
       for (int k = 0; k < 32; ++k) sv[k] = cv[k] = __float2bfloat16_rn(0.0f);
     }
-    if (hf == 1 && qidx % a.kw == 0) s_prot[parity][qidx / a.kw] = prot;
     for (int g8 = 0; g8 < 4; ++g8) {
       *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + g8 * 8, 128)) = *reinterpret_cast<const uint4*>(sv + g8 * 8);
       *reinterpret_cast<uint4*>(sX + canon(qidx, 64 + hf * 32 + g8 * 8, 128)) =
@@ -726,7 +729,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   long long tile = blockIdx.x;
   uint32_t par = 0;
   if (tile < n_tiles) {
-    features(tile, 0u);
+    features(tile);
     __syncthreads();
     issue_l1(0u);
   }
@@ -801,9 +804,18 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     // the next tile's features (H is free: layer 3 has read it) and layer-1 MMAs into B, under this head
     const long long next = tile + gridDim.x;
     if (next < n_tiles) {
-      features(next, par ^ 1u);
+      features(next);
       __syncthreads();
       issue_l1(accB);
+    }
+    // this thread's edge (threads 0..127) and its protection mark, loaded ahead of the head
+    size_t pidx = 0;
+    bool prot = false;
+    const long long e_mine = tile * e_per_tile + tid;
+    const bool mine = tid < e_per_tile && e_mine < n_live;
+    if (mine) {
+      pidx = static_cast<size_t>(rows_live[e_mine / nc]) * cols + cols_live[e_mine % nc];
+      if (a.protect) prot = a.prune[pidx] == kPruneProtected;
     }
     // head: relu(acc + b3) . w4 + b4, per query; then the edge's max against the cut
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -832,13 +844,11 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     __syncthreads();
     if (tid < 128) {  // warps 0..3, full warps for the ballot
       bool pr = false;
-      const long long e_first = tile * e_per_tile;
-      const long long e = e_first + tid;
-      if (tid < e_per_tile && e < n_live) {
+      if (mine) {
         float z = s_logit[tid * a.kw];
         for (int w = 1; w < a.kw; ++w) z = fmaxf(z, s_logit[tid * a.kw + w]);
-        pr = z > a.cut && !s_prot[par][tid];
-        a.prune[static_cast<size_t>(rows_live[e / nc]) * cols + cols_live[e % nc]] = pr ? 1 : 0;
+        pr = z > a.cut && !prot;
+        a.prune[pidx] = pr ? 1 : 0;
       }
       const unsigned b = __ballot_sync(kFull, pr);
       if (lane == 0 && b) atomicAdd(a.n_pruned, static_cast<unsigned long long>(__popc(b)));
@@ -880,7 +890,6 @@ struct SurrogateState {
   double* loss = nullptr;
   unsigned long long* counter = nullptr;
   int* live = nullptr;  // live rows / columns of the transition being scored: [2 + 2 * live_cap]
-  float* minb = nullptr;  // per row index, the smallest edge bound of the transition (protection band) [live_cap]
   uint8_t* wimg = nullptr;  // weight images of the scoring kernel (W1, then 8 chunks of W2 / W3)
   int live_cap = 0;
   bool trained = false;
@@ -891,7 +900,7 @@ void surrogate_free(SurrogateState* s) {
   if (!s) return;
   void* bufs[] = {s->P,   s->G,   s->Mm,  s->Vv,  s->W1b, s->W1bT,   s->W2b,     s->W2bT, s->W3b,
                   s->W3bT, s->X,  s->XT,  s->H1,  s->H1T, s->H2,     s->H2T,     s->H3,   s->H3T,
-                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter, s->live, s->wimg, s->minb};
+                  s->dA,  s->dAT, s->dB,  s->dBT, s->logits, s->dz, s->loss, s->counter, s->live, s->wimg};
   for (void* b : bufs) cudaFree(b);
   delete s;
 }
@@ -1268,9 +1277,6 @@ gtmp_status prepare_scoring(gtmp_ctx* c) {
     s->live = nullptr;
     s->live_cap = 0;
     SUR_TRY(c, cudaMalloc(&s->live, (2 + 2 * static_cast<size_t>(c->p.M)) * sizeof(int)));
-    cudaFree(s->minb);
-    s->minb = nullptr;
-    SUR_TRY(c, cudaMalloc(&s->minb, static_cast<size_t>(c->p.M) * sizeof(float)));
     s->live_cap = c->p.M;
   }
   SUR_TRY(c, cudaFuncSetAttribute(score_edges_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, kScoreSmem));
@@ -1322,14 +1328,13 @@ gtmp_status launch_score_transition(gtmp_ctx* c, const GraphDev& g, int layer, f
   sa.prune = prune;
   sa.n_pruned = s->counter;
   sa.err = c->err;
-  sa.protect = c->sur_protect > 0.0f ? 1.0f + c->sur_protect : 0.0f;
-  sa.minb = s->minb;
+  sa.protect = c->sur_protect > 0.0f ? 1 : 0;
   // the live count stays on the device: a persistent grid reads it
   live_lists_kernel<<<1, 1024, 0, st>>>(g, layer, s->live_cap, s->live);
   SUR_TRY(c, cudaGetLastError());
-  if (sa.protect > 0.0f) {
-    row_min_bound_kernel<<<(layer_size(g, layer) * 32 + 255) / 256, 256, 0, st>>>(g, layer, s->live, s->live_cap,
-                                                                               s->minb);
+  if (sa.protect) {
+    protect_band_kernel<<<(layer_size(g, layer) * 32 + 255) / 256, 256, 0, st>>>(g, layer, s->live, s->live_cap,
+                                                                              1.0f + c->sur_protect, prune);
     SUR_TRY(c, cudaGetLastError());
   }
   const long long tiles = (ne + 128 / kw - 1) / (128 / kw);
