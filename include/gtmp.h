@@ -513,9 +513,10 @@ typedef struct {
 typedef struct {
   double edges;     /* candidate edges of the graph */
   double pruned;    /* live edges dropped before exact checking */
-  float score_ms;   /* device time of the surrogate scoring */
+  float score_ms;   /* device time of the surrogate scoring (live lists and the scoring kernel) */
   float solve_ms;   /* device time of the exact fused transitions */
   double scored;    /* live edges scored by the surrogate (row and column live) */
+  float band_ms;    /* device time of the protection-band passes (0 without a band) */
 } gtmp_prune_stats;
 
 /* Train the context's surrogate for its robot and current obstacles

@@ -69,7 +69,7 @@ class GtmpSurrogateStats(ctypes.Structure):
 
 class GtmpPruneStats(ctypes.Structure):
     _fields_ = [("edges", ctypes.c_double), ("pruned", ctypes.c_double), ("score_ms", ctypes.c_float),
-                ("solve_ms", ctypes.c_float), ("scored", ctypes.c_double)]
+                ("solve_ms", ctypes.c_float), ("scored", ctypes.c_double), ("band_ms", ctypes.c_float)]
 
 
 class GtmpAoSchedule(ctypes.Structure):
@@ -744,7 +744,8 @@ def gtmp_solve_pruned(ctx, threshold, dev_path, dev_cost, score_waypoints=1):
     st = GtmpPruneStats()
     _check(ctx, lib().gtmp_solve_pruned(ctx, threshold, score_waypoints, _dev(dev_path, torch.int32),
                                         _dev(dev_cost, torch.float32), ctypes.byref(st)))
-    return dict(edges=st.edges, pruned=st.pruned, score_ms=st.score_ms, solve_ms=st.solve_ms, scored=st.scored)
+    return dict(edges=st.edges, pruned=st.pruned, score_ms=st.score_ms, solve_ms=st.solve_ms, scored=st.scored,
+                band_ms=st.band_ms)
 
 
 def gtmp_surrogate_set_protect(ctx, band):

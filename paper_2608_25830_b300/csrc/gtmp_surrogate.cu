@@ -1309,7 +1309,9 @@ GraphDev pruned_graph(gtmp_ctx* c) {
 // Score the live edges of transition `layer` (rows = its live vertices, columns
 // = the next layer's free vertices with a finite cost-to-go in the keys) into
 // prune[i * cols + j]: 1 = pruned, 0 = kept; other entries are not written.
-gtmp_status launch_score_transition(gtmp_ctx* c, const GraphDev& g, int layer, float cut, int kw, uint8_t* prune) {
+// band_done (optional): recorded after the protection-band pass, before the scoring kernel
+gtmp_status launch_score_transition(gtmp_ctx* c, const GraphDev& g, int layer, float cut, int kw, uint8_t* prune,
+                                    cudaEvent_t band_start = nullptr, cudaEvent_t band_done = nullptr) {
   SurrogateState* s = c->sur;
   cudaStream_t st = c->stream;
   const long long ne = static_cast<long long>(layer_size(g, layer)) * layer_size(g, layer + 1);
@@ -1332,11 +1334,13 @@ gtmp_status launch_score_transition(gtmp_ctx* c, const GraphDev& g, int layer, f
   // the live count stays on the device: a persistent grid reads it
   live_lists_kernel<<<1, 1024, 0, st>>>(g, layer, s->live_cap, s->live);
   SUR_TRY(c, cudaGetLastError());
+  if (band_start) cudaEventRecord(band_start, st);
   if (sa.protect) {
     protect_band_kernel<<<(layer_size(g, layer) * 32 + 255) / 256, 256, 0, st>>>(g, layer, s->live, s->live_cap,
                                                                               1.0f + c->sur_protect, prune);
     SUR_TRY(c, cudaGetLastError());
   }
+  if (band_done) cudaEventRecord(band_done, st);
   const long long tiles = (ne + 128 / kw - 1) / (128 / kw);
   const int score_grid = static_cast<int>(std::min<long long>(tiles, c->num_sms));
   if (s->four.dof == 7)
@@ -1397,11 +1401,13 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
   if (r != GTMP_OK) return r;
   const float cut = std::log(threshold / (1.0f - threshold));  // logit of the threshold
   const GraphDev g = pruned_graph(c);
-  cudaEvent_t e0, e1, e2;
+  cudaEvent_t e0, e1, e2, eb0, eb1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventCreate(&e2);
-  float score_ms = 0.0f, solve_ms = 0.0f;
+  cudaEventCreate(&eb0);
+  cudaEventCreate(&eb1);
+  float score_ms = 0.0f, solve_ms = 0.0f, band_ms = 0.0f;
   SUR_TRY(c, launch_init_keys(g, c->counters, L + 1, st));
   SUR_TRY(c, launch_vertex_labels(g, c->rb, c->variant, ctx_scene(c), st));
   const int resident = c->num_sms * c->fused_bps[0];
@@ -1412,7 +1418,7 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     edges_total += static_cast<double>(ne);
     cudaEventRecord(e0, st);
     // score the live edges of the transition with the fused tensor-core kernel
-    r = launch_score_transition(c, g, layer, cut, score_waypoints, c->prune);
+    r = launch_score_transition(c, g, layer, cut, score_waypoints, c->prune, eb0, eb1);
     if (r != GTMP_OK) return r;
     cudaEventRecord(e1, st);
     // exact realisation of the surviving edges, fused with the min-plus step
@@ -1441,11 +1447,13 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     cudaEventRecord(e2, st);
     SUR_TRY(c, cudaEventSynchronize(e2));
     scored_total += static_cast<double>(live_n[0]) * live_n[1];
-    float a = 0.0f, b = 0.0f;
+    float a = 0.0f, b = 0.0f, bb = 0.0f;
     cudaEventElapsedTime(&a, e0, e1);
     cudaEventElapsedTime(&b, e1, e2);
-    score_ms += a;
+    cudaEventElapsedTime(&bb, eb0, eb1);
+    score_ms += a - bb;
     solve_ms += b;
+    band_ms += bb;
   }
   SUR_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, st));
   unsigned long long pruned = 0;
@@ -1454,12 +1462,15 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
+  cudaEventDestroy(eb0);
+  cudaEventDestroy(eb1);
   if (stats) {
     stats->edges = edges_total;
     stats->pruned = static_cast<double>(pruned);
     stats->score_ms = score_ms;
     stats->solve_ms = solve_ms;
     stats->scored = scored_total;
+    stats->band_ms = band_ms;
   }
   return GTMP_OK;
 }
