@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
   SceneDev& s_sc = *reinterpret_cast<SceneDev*>(s_sc_raw);
   __shared__ int s_item, s_next, s_ok;
   extern __shared__ __align__(16) float4 smem[];
+  // the next variant's persistent launch (independent problems) may start on the SMs this one leaves
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   while (true) {
     if (threadIdx.x == 0) {
       s_item = atomicAdd(next_item, 1);
@@ -257,6 +259,9 @@ __global__ void __launch_bounds__(kThreads, kFusedMinBlocks)
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(done + P.need_base + w.depth, 1);
   }
+  // launched as a dependent of the previous variant's kernel: finish only after it has, so that the
+  // path kernel behind this one sees every variant's results
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 __global__ void batch_paths_kernel(const ProblemDev* probs, int n, int L_max, int32_t* paths, float* costs) {
@@ -487,6 +492,25 @@ gtmp_status build_items(gtmp_batch* b) {
   return GTMP_OK;
 }
 
+// one variant's persistent launch; dependent: a programmatic dependent of the previous kernel on the stream
+template <int VAR, bool LAZY>
+cudaError_t launch_persistent(dim3 grid, size_t smem, cudaStream_t st, bool dependent, const ProblemDev* probs,
+                              const RobotDev* robots, const WorkItem* items, int n_items, const int* need,
+                              int* done, int* next_item, int chunk, int* err) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, batch_persistent_kernel<VAR, LAZY>, probs, robots, items, n_items, need, done,
+                            next_item, chunk, err);
+}
+
 // ev (optional): events 2 v and 2 v + 1 are recorded around variant v's persistent launch
 gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs, cudaEvent_t* ev = nullptr) {
   cudaStream_t st = b->stream;
@@ -501,7 +525,11 @@ gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs, c
                                                                                                     b->d_robots);
   BATCH_TRY(b, cudaGetLastError());
   const int lazy = b->eval_mode == GTMP_EVAL_LAZY ? 1 : 0;
-  for (int v = 0; v < 4; ++v) {
+  // the arms first, the point robots last: their short items fill the SMs the arm kernel's last items leave
+  // (each later variant is a programmatic dependent of the one before; timed runs launch them plainly)
+  static const int kOrder[4] = {kVarArm7x4, kVarArm6x4, kVarArmGeneric, kVarPoint};
+  bool first = true;
+  for (int v : kOrder) {
     const int n_items = b->item_begin[v + 1] - b->item_begin[v];
     if (n_items == 0) continue;
     const dim3 grid(b->num_sms * b->bps[v][lazy]);
@@ -509,16 +537,15 @@ gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs, c
     const WorkItem* items = b->d_items + b->item_begin[v];
     int* counter = b->d_done + b->need.size() + v;
     const int chunk = b->chunk[robot_kind(v)];
+    const bool dependent = !first && ev == nullptr;
+    first = false;
     if (ev) BATCH_TRY(b, cudaEventRecord(ev[2 * v], st));
-#define GTMP_BATCH_LAUNCH(VAR)                                                                                     \
-  if (lazy)                                                                                                        \
-    batch_persistent_kernel<VAR, true><<<grid, kThreads, smem, st>>>(b->d_probs, b->d_robots, items, n_items,      \
-                                                                     b->d_need, b->d_done, counter, chunk,        \
-                                                                     b->d_err);                                    \
-  else                                                                                                             \
-    batch_persistent_kernel<VAR, false><<<grid, kThreads, smem, st>>>(b->d_probs, b->d_robots, items, n_items,     \
-                                                                      b->d_need, b->d_done, counter, chunk,       \
-                                                                      b->d_err)
+    cudaError_t le = cudaSuccess;
+#define GTMP_BATCH_LAUNCH(VAR)                                                                                 \
+  le = lazy ? launch_persistent<VAR, true>(grid, smem, st, dependent, b->d_probs, b->d_robots, items, n_items,  \
+                                           b->d_need, b->d_done, counter, chunk, b->d_err)                      \
+            : launch_persistent<VAR, false>(grid, smem, st, dependent, b->d_probs, b->d_robots, items, n_items, \
+                                            b->d_need, b->d_done, counter, chunk, b->d_err)
     switch (v) {
       case kVarPoint: GTMP_BATCH_LAUNCH(kVarPoint); break;
       case kVarArm6x4: GTMP_BATCH_LAUNCH(kVarArm6x4); break;
@@ -526,7 +553,7 @@ gtmp_status enqueue_solve(gtmp_batch* b, int32_t* dev_paths, float* dev_costs, c
       default: GTMP_BATCH_LAUNCH(kVarArmGeneric); break;
     }
 #undef GTMP_BATCH_LAUNCH
-    BATCH_TRY(b, cudaGetLastError());
+    BATCH_TRY(b, le);
     if (ev) BATCH_TRY(b, cudaEventRecord(ev[2 * v + 1], st));
   }
   batch_paths_kernel<<<(b->n + 127) / 128, 128, 0, st>>>(b->d_probs, b->n, b->L_max, dev_paths, dev_costs);
