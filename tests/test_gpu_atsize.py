@@ -22,10 +22,11 @@ oracle checks what it can compute in test time:
   column, Bellman rows of every layer and the returned chain.
 * The surrogate workload: 7-DoF arm, 40 obstacles, M = 4096, L = 8, H = 32,
   surrogate trained on 2^21 configurations: the plain solve (samples, goal
-  column, Bellman rows, chain) and the pruned solve, whose values must satisfy
-  Bellman's equation over the edges its scoring kernel kept (read back with
-  gtmp_surrogate_score), with oracle-realised edges, and whose chain the
-  oracle re-costs and finds free.
+  column, Bellman rows, chain) and the pruned solve at the workload's threshold
+  and protection band, whose values must satisfy Bellman's equation over the
+  edges its scoring kernel kept (read back with gtmp_surrogate_score), with
+  oracle-realised edges, whose chain the oracle re-costs and finds free, and
+  whose cost lies within 1 % of the plain one.
 """
 import math
 
@@ -238,8 +239,9 @@ def test_surrogate_workload_at_size():
     check_values(V[L, :M], lo, hi, "plain goal column")
     _bellman_rows(sc, verts, V, S, H, 2, 11, what="plain")
     _check_chain(sc, Q_ref, path, cost, H, "plain")
-    # pruned solve: Bellman over the kept edges
+    # pruned solve (the workload's threshold and protection band): Bellman over the kept edges
     thr = wl["threshold"]
+    binding.gtmp_surrogate_set_protect(p.ctx, wl.get("protect", 0.0))
     pp = torch.empty(L, dtype=torch.int32, device="cuda")
     pc = torch.empty(1, dtype=torch.float32, device="cuda")
     st = binding.gtmp_solve_pruned(p.ctx, thr, pp, pc, score_waypoints=wl["score_waypoints"])
@@ -255,4 +257,5 @@ def test_surrogate_workload_at_size():
     pc = float(pc.cpu()[0])
     _check_chain(sc, Q_ref, pp.cpu().numpy(), pc, H, "pruned")
     assert pc >= cost or (math.isinf(pc) and math.isinf(cost))
+    assert pc <= cost * 1.01 or math.isinf(cost)   # the bar for the pruned solve: cost within 1 % of plain
     p.close()
