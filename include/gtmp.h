@@ -224,6 +224,28 @@ GTMP_API gtmp_status gtmp_solve(gtmp_ctx* ctx, int32_t* dev_path, float* dev_cos
  * if none or for the goal). */
 GTMP_API gtmp_status gtmp_get_values(gtmp_ctx* ctx, int32_t g, float* dev_V, int32_t* dev_sigma);
 
+/* Path-level lazy evaluation (a lazy variant of the kind Sec. VII leaves to
+ * future work; no counterpart algorithm in the paper): on graph 0, repeat
+ * (1) the min-plus sweep over optimistic edge costs -- each edge's cost as
+ * gtmp_solve computes it, with no collision check, leaving out the edges found
+ * colliding so far and the colliding vertices -- and (2) the exact check of
+ * the chain it returns, at all H waypoints of its L + 1 edges, marking the
+ * colliding ones; stop when a chain has no colliding edge (or no chain
+ * exists).  Optimistic costs bound the true ones from below, so that chain is
+ * optimal: its cost equals gtmp_solve's (the same float operations along the
+ * same chain), its path may differ only between chains of equal cost.
+ * dev_path device [L] int32, dev_cost device [1] float32 as gtmp_solve.
+ * Synchronous (one host round trip per iteration); allocates (L + 1) M^2
+ * bits on first use.  stats (host, optional): iterations and colliding edges
+ * found.  GTMP_ERR_TIMEOUT after max_iterations without a verified chain (the
+ * outputs then hold the last, unverified chain). */
+typedef struct {
+  int32_t iterations;       /* sweeps run */
+  int64_t colliding_edges;  /* edges the chain checks found colliding (and left out) */
+} gtmp_lazy_stats;
+GTMP_API gtmp_status gtmp_solve_lazy_path(gtmp_ctx* ctx, int32_t max_iterations, int32_t* dev_path, float* dev_cost,
+                                          gtmp_lazy_stats* stats);
+
 /* Unfused variant of gtmp_solve (same result): step 1 writes every edge cost
  * matrix C_l (float32, +inf = absent) into library-owned device memory,
  * step 2 runs the min-plus sweep reading it back.  The first call allocates

@@ -72,6 +72,10 @@ class GtmpPruneStats(ctypes.Structure):
                 ("solve_ms", ctypes.c_float), ("scored", ctypes.c_double), ("band_ms", ctypes.c_float)]
 
 
+class GtmpLazyStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("colliding_edges", ctypes.c_int64)]
+
+
 class GtmpAoSchedule(ctypes.Structure):
     _fields_ = [("L0", ctypes.c_int32), ("M0", ctypes.c_int32), ("M_max", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("reach", ctypes.c_float), ("r", ctypes.c_float), ("varsigma", ctypes.c_float),
@@ -139,6 +143,7 @@ _SIGNATURES = {
     "gtmp_surrogate_get_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
     "gtmp_solve_pruned": [_vp, ctypes.c_float, _i32, _vp, _vp, ctypes.POINTER(GtmpPruneStats)],
     "gtmp_surrogate_set_protect": [_vp, ctypes.c_float],
+    "gtmp_solve_lazy_path": [_vp, _i32, _vp, _vp, ctypes.POINTER(GtmpLazyStats)],
     "gtmp_surrogate_score": [_vp, _i32, ctypes.c_float, _i32, _vp, ctypes.POINTER(ctypes.c_int64)],
     "gtmp_surrogate_set_params": [_vp, _fp, ctypes.c_int64, _fp, ctypes.c_int64],
     "gtmp_surrogate_loss_grad": [_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _fp, ctypes.c_int64],
@@ -746,6 +751,15 @@ def gtmp_solve_pruned(ctx, threshold, dev_path, dev_cost, score_waypoints=1):
                                         _dev(dev_cost, torch.float32), ctypes.byref(st)))
     return dict(edges=st.edges, pruned=st.pruned, score_ms=st.score_ms, solve_ms=st.solve_ms, scored=st.scored,
                 band_ms=st.band_ms)
+
+
+def gtmp_solve_lazy_path(ctx, dev_path, dev_cost, max_iterations=100000):
+    """Path-level lazy evaluation: optimistic min-plus sweeps, exact check of the winning chain, repeat."""
+    import torch
+    st = GtmpLazyStats()
+    _check(ctx, lib().gtmp_solve_lazy_path(ctx, max_iterations, _dev(dev_path, torch.int32),
+                                           _dev(dev_cost, torch.float32), ctypes.byref(st)))
+    return dict(iterations=st.iterations, colliding_edges=st.colliding_edges)
 
 
 def gtmp_surrogate_set_protect(ctx, band):

@@ -377,6 +377,8 @@ gtmp_status gtmp_destroy(gtmp_ctx* c) {
   cudaFree(c->wb);
   cudaFree(c->ao_scratch);
   cudaFree(c->prune);
+  cudaFree(c->lazy_bad);
+  cudaFree(c->lazy_count);
   surrogate_free(c->sur);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
@@ -701,6 +703,61 @@ gtmp_status gtmp_solve(gtmp_ctx* c, int32_t* dev_path, float* dev_cost) {
   if ((s = run_fused(c, g, c->p.eval_mode)) != GTMP_OK) return s;
   CUDA_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, c->stream));
   LAUNCHED(c, 1);
+  return GTMP_OK;
+}
+
+gtmp_status gtmp_solve_lazy_path(gtmp_ctx* c, int32_t max_iterations, int32_t* dev_path, float* dev_cost,
+                                 gtmp_lazy_stats* stats) {
+  GtmpNvtxRange nvtx_("gtmp_solve_lazy_path");
+  if (!c || !dev_path || !dev_cost || max_iterations < 1) return fail(c, GTMP_ERR_INVALID_ARG, "bad lazy request");
+  gtmp_status s = check_ready(c);
+  if (s != GTMP_OK) return s;
+  const GraphDev g = graph(c, 1, c->M_active);
+  const size_t words = (static_cast<size_t>(c->p.M) * c->p.M + 31) / 32;
+  if (c->lazy_words != words || !c->lazy_bad) {
+    cudaFree(c->lazy_bad);
+    c->lazy_bad = nullptr;
+    c->lazy_words = 0;
+    // (L_cap + 1) transitions of M x M bits
+    CUDA_TRY(c, cudaMalloc(&c->lazy_bad, (static_cast<size_t>(c->L_cap) + 1) * words * sizeof(uint32_t)));
+    c->lazy_words = words;
+  }
+  if (!c->lazy_count) CUDA_TRY(c, cudaMalloc(&c->lazy_count, sizeof(int)));
+  cudaStream_t st = c->stream;
+  CUDA_TRY(c, cudaMemsetAsync(c->lazy_bad, 0, (static_cast<size_t>(g.L) + 1) * words * sizeof(uint32_t), st));
+  CUDA_TRY(c, launch_init_keys(g, c->counters, g.L + 1, st));
+  CUDA_TRY(c, launch_vertex_labels(g, c->rb, c->variant, scene(c), st));
+  LAUNCHED(c, 2);
+  int it = 0, found = 0;
+  long long colliding = 0;
+  for (;;) {
+    if (it > 0) {
+      CUDA_TRY(c, launch_init_keys(g, c->counters, g.L + 1, st));
+      LAUNCHED(c, 1);
+    }
+    // the min-plus sweep over optimistic costs, then the exact check of the chain it returns
+    for (int layer = g.L; layer >= 0; --layer) {
+      CUDA_TRY(c, launch_optimistic_transition(g, layer, c->variant,
+                                               c->lazy_bad + static_cast<size_t>(layer) * words, st));
+      LAUNCHED(c, 1);
+    }
+    CUDA_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, st));
+    CUDA_TRY(c, cudaMemsetAsync(c->lazy_count, 0, sizeof(int), st));
+    CUDA_TRY(c, launch_check_chain(g, dev_path, c->rb, c->variant, scene(c), c->lazy_bad, words, c->lazy_count, st));
+    LAUNCHED(c, 2);
+    CUDA_TRY(c, cudaMemcpyAsync(&found, c->lazy_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    ++it;
+    colliding += found;
+    // a chain with no colliding edge (or no chain at all) is the optimum: every other chain's optimistic
+    // cost, a lower bound of its true cost, is at least this chain's true cost
+    if (found == 0 || it >= max_iterations) break;
+  }
+  if (stats) {
+    stats->iterations = it;
+    stats->colliding_edges = colliding;
+  }
+  if (found != 0) return fail(c, GTMP_ERR_TIMEOUT, "lazy evaluation: %d iterations without a verified chain", it);
   return GTMP_OK;
 }
 

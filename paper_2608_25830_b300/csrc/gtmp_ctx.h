@@ -74,6 +74,9 @@ struct gtmp_ctx {
   gtmp::SurrogateState* sur = nullptr;
   float sur_protect = 0.0f;  // protection band of the pruned solve (gtmp_surrogate_set_protect); 0 = off
   uint8_t* prune = nullptr;  // per-transition prune mask, M x M
+  uint32_t* lazy_bad = nullptr;  // path-level lazy evaluation: per transition a bit per (row, column) found colliding
+  size_t lazy_words = 0;         // 32-bit words per transition of lazy_bad
+  int* lazy_count = nullptr;     // colliding edges the last chain check found
   // class-augmented sweep (allocated by gtmp_solve_classes)
   void* cls = nullptr;
   size_t cls_bytes = 0;

@@ -401,6 +401,95 @@ __global__ void extract_paths_kernel(GraphDev g, int32_t* path, float* cost, int
   if (threadIdx.x == 0 && best) *best = s_best == kEmptyKey ? -1 : static_cast<int32_t>(s_best & 0xffffffffu);
 }
 
+// ---------------------------------------------------------------------------
+// Path-level lazy evaluation (a lazy variant of the kind Sec. VII names): the
+// min-plus step over optimistic edge costs -- each edge's cost as the exact
+// kernels compute it, with no collision check -- leaving out the edges found
+// colliding so far, and the exact check of the chain that step returns.
+// bad holds a bit per (row, column) of each transition: bit i * M_stride + j
+// of transition `layer` at word offset layer * words.
+// ---------------------------------------------------------------------------
+template <int VAR, bool WEIGHTED>
+__global__ void __launch_bounds__(kThreads) optimistic_transition_kernel(GraphDev g, int layer, const uint32_t* bad) {
+  using V = Var<VAR>;
+  constexpr int DP = V::kDp;
+  const int lane = threadIdx.x & 31;
+  const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  if (i >= layer_size(g, layer)) return;
+  const size_t vi = vidx(g, 0, layer, i);
+  if (g.vflag[vi] != 0) return;
+  const int cols = layer_size(g, layer + 1);
+  float qi[DP];
+  load_vertex<DP>(qi, g.Q + vi * g.dp, g.dp);
+  unsigned long long best = kEmptyKey;
+  for (int j = lane; j < cols; j += 32) {
+    const size_t vj = vidx(g, 0, layer + 1, j);
+    if (g.vflag[vj] != 0) continue;
+    const unsigned long long kj = __ldcg(g.keys + vj);
+    if (kj == kEmptyKey) continue;
+    const size_t bit = static_cast<size_t>(i) * g.M_stride + j;
+    if ((bad[bit >> 5] >> (bit & 31)) & 1u) continue;
+    float qj[DP];
+    load_vertex<DP>(qj, g.Q + vj * g.dp, g.dp);
+    float s2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DP; ++d) {
+      const float e = __fsub_rn(qj[d], qi[d]);
+      s2 = __fmaf_rn(e, e, s2);
+    }
+    const float len = __fsqrt_rn(s2);
+    if (len > g.max_edge_len) continue;
+    float cost = len;
+    if constexpr (WEIGHTED) cost = weighted_cost_thread<DP>(qi, qj, len, g);
+    const unsigned long long key = make_key(__fadd_rn(cost, key_value(kj)), static_cast<uint32_t>(j));
+    best = key < best ? key : best;
+  }
+  best = warp_min_u64(best);
+  if (lane == 0 && best != kEmptyKey) g.keys[vi] = best;
+}
+
+// The exact check of the chain extract_paths wrote (start, path[0..L-1], the
+// goal its last key names): one warp per edge, lanes over the interior
+// waypoints as the early-exit kernel takes them; a colliding edge sets its bit
+// in bad and counts in n_bad.  An infeasible chain (no start key) is not checked.
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) check_chain_kernel(GraphDev g, const int32_t* path, RobotDev rb,
+                                                               SceneDev sc, uint32_t* bad, size_t words,
+                                                               int* n_bad) {
+  extern __shared__ __align__(16) float4 s_obs[];
+  using V = Var<VAR>;
+  constexpr int DP = V::kDp;
+  if (g.keys[vidx(g, 0, 0, 0)] == kEmptyKey) return;
+  stage_obstacles_plain(s_obs, sc.obs, scene_float4s(sc));
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const float steps = static_cast<float>(g.H - 1);
+  for (int e = static_cast<int>(threadIdx.x >> 5); e <= g.L; e += static_cast<int>(blockDim.x >> 5)) {
+    const int a = e == 0 ? 0 : path[e - 1];
+    const int b = e < g.L ? path[e] : key_index(g.keys[vidx(g, 0, g.L, path[g.L - 1])]);
+    float qa[DP], qb[DP];
+    load_vertex<DP>(qa, g.Q + vidx(g, 0, e, a) * g.dp, g.dp);
+    load_vertex<DP>(qb, g.Q + vidx(g, 0, e + 1, b) * g.dp, g.dp);
+    float dq[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) dq[d] = __fsub_rn(qb[d], qa[d]);
+    bool hit = false;
+    for (int kb = 1; kb <= g.H - 2 && !hit; kb += 32) {
+      const int k = kb + lane;
+      const float tt = __fdiv_rn(static_cast<float>(k), steps);
+      float q[DP];
+#pragma unroll
+      for (int d = 0; d < DP; ++d) q[d] = __fmaf_rn(tt, dq[d], qa[d]);
+      hit = config_collides<VAR, true, false>(q, k <= g.H - 2, rb, s_obs, sc);
+    }
+    if (hit && lane == 0) {
+      const size_t bit = static_cast<size_t>(a) * g.M_stride + b;
+      atomicOr(bad + static_cast<size_t>(e) * words + (bit >> 5), 1u << (bit & 31));
+      atomicAdd(n_bad, 1);
+    }
+  }
+}
+
 __global__ void get_values_kernel(GraphDev g, float* V, int32_t* sigma) {
   const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long per_r = static_cast<long long>(g.L + 2) * g.M;
@@ -666,6 +755,29 @@ struct LabelConfigsRun {
 };
 
 template <int VAR>
+struct OptimisticRun {
+  static cudaError_t run(const GraphDev& g, int layer, const uint32_t* bad, cudaStream_t st) {
+    const int rows = layer_size(g, layer);
+    const int blocks = (rows + kWarps - 1) / kWarps;
+    if (g.n_wb > 0)
+      optimistic_transition_kernel<VAR, true><<<blocks, kThreads, 0, st>>>(g, layer, bad);
+    else
+      optimistic_transition_kernel<VAR, false><<<blocks, kThreads, 0, st>>>(g, layer, bad);
+    return cudaGetLastError();
+  }
+};
+
+template <int VAR>
+struct CheckChainRun {
+  static cudaError_t run(const GraphDev& g, const int32_t* path, const RobotDev& rb, const SceneDev& sc,
+                         uint32_t* bad, size_t words, int* n_bad, cudaStream_t st) {
+    const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16;
+    check_chain_kernel<VAR><<<1, kThreads, smem, st>>>(g, path, rb, sc, bad, words, n_bad);
+    return cudaGetLastError();
+  }
+};
+
+template <int VAR>
 struct FusedRun {
   static cudaError_t run(const GraphDev& g, int layer, const RobotDev& rb, const SceneDev& sc, int mode,
                          int* counters, int grid_x, int chunk, int* err, bool dependent, cudaStream_t st) {
@@ -716,6 +828,9 @@ struct ConfigureRun {
                                   smem_max)) != cudaSuccess)
       return e;
     if ((e = cudaFuncSetAttribute(sample_free_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(check_chain_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max)) !=
         cudaSuccess)
       return e;
     return cudaFuncSetAttribute(label_configs_kernel<VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
@@ -1073,6 +1188,16 @@ cudaError_t launch_label_configs(const float* q, int n, int dof, const RobotDev&
                                  uint8_t* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return by_variant<LabelConfigsRun>(variant, q, n, dof, rb, sc, out, st);
+}
+
+cudaError_t launch_optimistic_transition(const GraphDev& g, int layer, int variant, const uint32_t* bad,
+                                         cudaStream_t st) {
+  return by_variant<OptimisticRun>(variant, g, layer, bad, st);
+}
+
+cudaError_t launch_check_chain(const GraphDev& g, const int32_t* path, const RobotDev& rb, int variant,
+                               const SceneDev& sc, uint32_t* bad, size_t words, int* n_bad, cudaStream_t st) {
+  return by_variant<CheckChainRun>(variant, g, path, rb, sc, bad, words, n_bad, st);
 }
 
 cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev& rb, int variant, const SceneDev& sc,

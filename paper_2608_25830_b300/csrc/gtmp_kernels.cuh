@@ -144,6 +144,13 @@ cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev
                                     const SceneDev& sc, int mode, int* counters, int grid_x, int chunk, int* err,
                                     cudaStream_t st, bool dependent = false);
 int fused_max_blocks_per_sm(int variant, int mode);
+// path-level lazy evaluation: the min-plus step of transition `layer` over optimistic costs (no
+// collision check) without the edges marked in bad, and the exact check of the extracted chain
+// (colliding edges marked in bad, counted in n_bad); bad holds words 32-bit words per transition
+cudaError_t launch_optimistic_transition(const GraphDev& g, int layer, int variant, const uint32_t* bad,
+                                         cudaStream_t st);
+cudaError_t launch_check_chain(const GraphDev& g, const int32_t* path, const RobotDev& rb, int variant,
+                               const SceneDev& sc, uint32_t* bad, size_t words, int* n_bad, cudaStream_t st);
 cudaError_t launch_extract_paths(const GraphDev& g, int32_t* path, float* cost, int32_t* best, cudaStream_t st);
 cudaError_t launch_goal_reached(const GraphDev& g, int gi, int32_t* goal, cudaStream_t st);
 cudaError_t launch_get_values(const GraphDev& g, float* V, int32_t* sigma, cudaStream_t st);

@@ -197,6 +197,75 @@ def test_fused_solve_matches_oracle(torch_cuda, kind, dof, M, L, H, seed, mode):
         assert cost >= float(np.linalg.norm(sc.q_goal.astype(np.float64) - sc.q_start)) * (1 - REL)
 
 
+@pytest.mark.parametrize("kind,dof,M,L,H,seed", CASES)
+def test_lazy_path_solve_matches_plain_and_oracle(torch_cuda, kind, dof, M, L, H, seed):
+    """Path-level lazy evaluation (optimistic min-plus sweeps, the winning chain checked exactly, its colliding
+    edges left out, repeated): its cost equals gtmp_solve's bit for bit (optimistic costs bound the true ones
+    from below and rounding is monotone, so the verified chain's float cost is the plain optimum), lies in the
+    oracle's [V_lo, V_hi] band, and the chain it returns is free when the oracle re-checks it."""
+    torch = torch_cuda
+    sc = scene_for(kind, seed, dof, 30 if kind == "arm" else 10)
+    p = _planner(sc, M, L, H)
+    p.sample_layers(seed, M)
+    _, plain_cost = p.solve()
+    plain_cost = float(plain_cost.cpu()[0])
+    path = torch.empty(L, dtype=torch.int32, device="cuda")
+    cost = torch.empty(1, dtype=torch.float32, device="cuda")
+    st = binding.gtmp_solve_lazy_path(p.ctx, path, cost)
+    path, cost = path.cpu().numpy(), float(cost.cpu()[0])
+    assert cost == plain_cost or (math.isinf(cost) and math.isinf(plain_cost))
+    assert st["iterations"] >= 1 and st["colliding_edges"] >= st["iterations"] - 1
+    Q = oracle.sample_uniform(seed, 0, L, M, sc.robot.q_lo, sc.robot.q_hi)
+    sol = oracle.solve(sc, Q, H)
+    check_values([cost], [sol.cost_lo], [sol.cost_hi], f"{kind} M={M} L={L} lazy path")
+    if math.isfinite(cost):
+        total, worst = oracle.path_cost(sc, Q, path, H)
+        assert worst > -oracle.EPS_DEFAULT, "returned chain collides"
+        assert cost == pytest.approx(total, rel=REL)
+    else:
+        assert list(path) == [-1] * L
+    p.close()
+
+
+def test_lazy_path_weighted_goal_set_and_iteration_cap(torch_cuda):
+    """Weighted-length costs and a goal set with terminal values go through the optimistic sweep as through
+    gtmp_solve (equal costs); a cap of one iteration on a scene whose first optimistic chain collides ends
+    with GTMP_ERR_TIMEOUT."""
+    torch = torch_cuda
+    from paper_2608_25830_b300 import scenes
+    sc = scene_for("arm", 3, 7, 30)
+    M, L, H = 96, 4, 32
+    p = _planner(sc, M, L, H)
+    p.set_cost_weight(scenes.weight_bumps(sc, 3))
+    path = torch.empty(L, dtype=torch.int32, device="cuda")
+    cost = torch.empty(1, dtype=torch.float32, device="cuda")
+    capped = False
+    for seed in (5, 6, 7):
+        p.sample_layers(seed, M)
+        _, plain_cost = p.solve()
+        plain_cost = float(plain_cost.cpu()[0])
+        st = binding.gtmp_solve_lazy_path(p.ctx, path, cost)
+        assert float(cost.cpu()[0]) == plain_cost or math.isinf(plain_cost)
+        if st["iterations"] > 1:
+            with pytest.raises(binding.GtmpError) as e:
+                binding.gtmp_solve_lazy_path(p.ctx, path, cost, max_iterations=1)
+            assert e.value.status == 4   # GTMP_ERR_TIMEOUT
+            capped = True
+    assert capped, "no scene needed a second iteration: the cap is untested"
+    rng = np.random.default_rng(9)
+    goals = np.stack([sc.q_goal, sc.q_start * 0.5 + sc.q_goal * 0.5]).astype(np.float32)
+    free = p.label_configs(torch.from_numpy(goals).cuda()).cpu().numpy() == 0
+    goals = goals[free]
+    if len(goals):
+        binding.gtmp_set_goals(p.ctx, goals, rng.uniform(0.0, 0.5, len(goals)).astype(np.float32))
+        p.sample_layers(11, M)
+        _, plain_cost = p.solve()
+        binding.gtmp_solve_lazy_path(p.ctx, path, cost)
+        assert float(cost.cpu()[0]) == float(plain_cost.cpu()[0]) or math.isinf(float(plain_cost.cpu()[0]))
+    assert binding.lib().gtmp_solve_lazy_path(p.ctx, 0, None, None, None) == 1
+    p.close()
+
+
 @pytest.mark.parametrize("kind,dof,M,L,H,seed", CASES[:5])
 def test_fused_unfused_and_modes_agree_exactly(torch_cuda, kind, dof, M, L, H, seed):
     sc = scene_for(kind, seed, dof, 30 if kind == "arm" else 10)
