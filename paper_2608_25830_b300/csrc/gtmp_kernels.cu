@@ -445,13 +445,14 @@ __global__ void __launch_bounds__(kThreads) optimistic_transition_kernel(GraphDe
     best = key < best ? key : best;
   }
   best = warp_min_u64(best);
-  if (lane == 0 && best != kEmptyKey) g.keys[vi] = best;
+  if (lane == 0) g.keys[vi] = best;  // every free row rewritten: a later sweep needs no re-initialisation
 }
 
 // The exact check of the chain extract_paths wrote (start, path[0..L-1], the
 // goal its last key names): one warp per edge, lanes over the interior
 // waypoints as the early-exit kernel takes them; a colliding edge sets its bit
-// in bad and counts in n_bad.  An infeasible chain (no start key) is not checked.
+// in bad and counts in n_bad[0], and n_bad[1] keeps the highest transition
+// with a colliding edge.  An infeasible chain (no start key) is not checked.
 template <int VAR>
 __global__ void __launch_bounds__(kThreads) check_chain_kernel(GraphDev g, const int32_t* path, RobotDev rb,
                                                                SceneDev sc, uint32_t* bad, size_t words,
@@ -486,6 +487,7 @@ __global__ void __launch_bounds__(kThreads) check_chain_kernel(GraphDev g, const
       const size_t bit = static_cast<size_t>(a) * g.M_stride + b;
       atomicOr(bad + static_cast<size_t>(e) * words + (bit >> 5), 1u << (bit & 31));
       atomicAdd(n_bad, 1);
+      atomicMax(n_bad + 1, e);
     }
   }
 }
