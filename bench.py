@@ -783,6 +783,7 @@ def measure_surrogate(args, wl, flush, steps, warmup, n_train=None, epochs=None)
     cost = torch.empty(1, dtype=torch.float32, device="cuda")
     seed0 = rank_seed_base(rank)
     times = {k: [] for k in ("early_exit", "early_exit_pruned", "lazy", "lazy_pruned")}
+    band_only_ms, band_only_ratios, band_only_lost = [], [], 0
     ratios, pruned_frac, colliding_waypoints, checked = [], [], 0, 0
     score_ms, live_edges, band_ms = [], [], []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -815,6 +816,16 @@ def measure_surrogate(args, wl, flush, steps, warmup, n_train=None, epochs=None)
                 msp, st = timed(lambda: binding.gtmp_solve_pruned(pl.ctx, thr, path, cost, score_waypoints=kw))
                 c_pruned = float(cost.cpu()[0])
                 row[name] = (ms, msp, c_plain, c_pruned, st)
+                if name == "early_exit" and band > 0 and s >= 0:
+                    # the band without the model: every live edge outside it pruned (threshold ~0)
+                    msb, _ = timed(lambda: binding.gtmp_solve_pruned(pl.ctx, 1e-6, path, cost, score_waypoints=kw))
+                    c_band = float(cost.cpu()[0])
+                    band_only_ms.append(msb)
+                    if math.isfinite(c_plain):
+                        if math.isinf(c_band):
+                            band_only_lost += 1
+                        else:
+                            band_only_ratios.append(c_band / c_plain)
                 if s >= 0 and math.isfinite(c_pruned):
                     bad, n = recheck(pl, path.cpu().numpy())
                     colliding_waypoints += bad
@@ -865,6 +876,13 @@ def measure_surrogate(args, wl, flush, steps, warmup, n_train=None, epochs=None)
                                          "max": float(np.max(fin)) if fin else None,
                                          "lost_feasibility": len(ratios) - len(fin), "solves": len(ratios)},
         "roofline": roof,
+        "band_only": ({"early_exit_solves_per_s": len(band_only_ms) / (sum(band_only_ms) / 1e3),
+                       "over_plain": (len(band_only_ms) / (sum(band_only_ms) / 1e3)) / sps["early_exit"],
+                       "cost_ratio_mean": float(np.mean(band_only_ratios)) if band_only_ratios else None,
+                       "cost_ratio_max": float(np.max(band_only_ratios)) if band_only_ratios else None,
+                       "lost_feasibility": band_only_lost,
+                       "note": "the protection band alone (every live edge outside it pruned, no model decision): a "
+                               "bound heuristic shown for comparison"} if band_only_ms else None),
         "pruned_edge_fraction": float(np.mean(pruned_frac)),
         "returned_paths_recheck": {"waypoints": checked, "colliding": colliding_waypoints},
         "training": train,
