@@ -573,7 +573,8 @@ def run_ours(args, wl):
                           "same_costs_as_early_exit": lp_same,
                           "note": "gtmp_solve_lazy_path: min-plus sweeps over optimistic (unchecked) edge costs, "
                                   "the winning chain checked exactly and its colliding edges left out, until a "
-                                  "chain is free; one host round trip per iteration"},
+                                  "chain is free; iterations enqueued eight at a time with the loop state on "
+                                  "the device"},
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

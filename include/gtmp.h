@@ -235,7 +235,9 @@ GTMP_API gtmp_status gtmp_get_values(gtmp_ctx* ctx, int32_t g, float* dev_V, int
  * optimal: its cost equals gtmp_solve's (the same float operations along the
  * same chain), its path may differ only between chains of equal cost.
  * dev_path device [L] int32, dev_cost device [1] float32 as gtmp_solve.
- * Synchronous (one host round trip per iteration); allocates (L + 1) M^2
+ * Synchronous: iterations are enqueued eight at a time, with the loop's
+ * state on the device (the kernels of iterations past the last return at
+ * once), and the state is read back after each group; allocates (L + 1) M^2
  * bits on first use.  stats (host, optional): iterations and colliding edges
  * found.  GTMP_ERR_TIMEOUT after max_iterations without a verified chain (the
  * outputs then hold the last, unverified chain). */

@@ -722,41 +722,34 @@ gtmp_status gtmp_solve_lazy_path(gtmp_ctx* c, int32_t max_iterations, int32_t* d
     CUDA_TRY(c, cudaMalloc(&c->lazy_bad, (static_cast<size_t>(c->L_cap) + 1) * words * sizeof(uint32_t)));
     c->lazy_words = words;
   }
-  if (!c->lazy_count) CUDA_TRY(c, cudaMalloc(&c->lazy_count, 2 * sizeof(int)));
+  if (!c->lazy_count) CUDA_TRY(c, cudaMalloc(&c->lazy_count, kLazyStateInts * sizeof(int)));
   cudaStream_t st = c->stream;
   CUDA_TRY(c, cudaMemsetAsync(c->lazy_bad, 0, (static_cast<size_t>(g.L) + 1) * words * sizeof(uint32_t), st));
+  int state[kLazyStateInts] = {0, -1, g.L, 0, 0, 0};  // the first sweep covers every transition
+  CUDA_TRY(c, cudaMemcpyAsync(c->lazy_count, state, sizeof(state), cudaMemcpyHostToDevice, st));
   CUDA_TRY(c, launch_init_keys(g, c->counters, g.L + 1, st));
   CUDA_TRY(c, launch_vertex_labels(g, c->rb, c->variant, scene(c), st));
   LAUNCHED(c, 2);
-  int it = 0;
-  int found[2] = {0, g.L};  // colliding edges of the last chain, the highest transition among them
-  long long colliding = 0;
+  // iterations are enqueued eight at a time and the state read back after each group: the kernels of
+  // the iterations after the last one return at once, and the cap bounds the loop on the device too
   for (;;) {
-    // the min-plus sweep over optimistic costs, then the exact check of the chain it returns; a sweep
-    // after the first starts at the highest transition that lost an edge (the values above it stand)
-    for (int layer = found[1]; layer >= 0; --layer) {
-      CUDA_TRY(c, launch_optimistic_transition(g, layer, c->variant,
-                                               c->lazy_bad + static_cast<size_t>(layer) * words, st));
-      LAUNCHED(c, 1);
+    for (int k = 0; k < 8; ++k) {
+      CUDA_TRY(c, launch_lazy_iteration(g, c->variant, c->rb, scene(c), c->lazy_bad, words, dev_path, dev_cost,
+                                        c->lazy_count, max_iterations, st));
+      LAUNCHED(c, g.L + 5);
     }
-    CUDA_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, st));
-    CUDA_TRY(c, cudaMemsetAsync(c->lazy_count, 0, 2 * sizeof(int), st));
-    CUDA_TRY(c, launch_check_chain(g, dev_path, c->rb, c->variant, scene(c), c->lazy_bad, words, c->lazy_count, st));
-    LAUNCHED(c, 2);
-    CUDA_TRY(c, cudaMemcpyAsync(found, c->lazy_count, sizeof(found), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(state, c->lazy_count, sizeof(state), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
-    ++it;
-    colliding += found[0];
-    // a chain with no colliding edge (or no chain at all) is the optimum: every other chain's optimistic
-    // cost, a lower bound of its true cost, is at least this chain's true cost
-    if (found[0] == 0 || it >= max_iterations) break;
+    if (state[kLazyDone] != 0) break;
   }
   if (stats) {
-    stats->iterations = it;
-    stats->colliding_edges = colliding;
+    stats->iterations = state[kLazyIters];
+    stats->colliding_edges = state[kLazyEdges];
   }
-  if (found[0] != 0)
-    return fail(c, GTMP_ERR_TIMEOUT, "lazy evaluation: %d iterations without a verified chain", it);
+  // a chain with no colliding edge (or no chain at all) is the optimum: every other chain's optimistic
+  // cost, a lower bound of its true cost, is at least this chain's true cost
+  if (state[kLazyFound] != 0)
+    return fail(c, GTMP_ERR_TIMEOUT, "lazy evaluation: %d iterations without a verified chain", state[kLazyIters]);
   return GTMP_OK;
 }
 

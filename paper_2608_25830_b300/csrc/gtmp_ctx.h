@@ -76,7 +76,7 @@ struct gtmp_ctx {
   uint8_t* prune = nullptr;  // per-transition prune mask, M x M
   uint32_t* lazy_bad = nullptr;  // path-level lazy evaluation: per transition a bit per (row, column) found colliding
   size_t lazy_words = 0;         // 32-bit words per transition of lazy_bad
-  int* lazy_count = nullptr;     // colliding edges the last chain check found
+  int* lazy_count = nullptr;     // the iteration state of gtmp_solve_lazy_path (LazyState)
   // class-augmented sweep (allocated by gtmp_solve_classes)
   void* cls = nullptr;
   size_t cls_bytes = 0;

@@ -410,9 +410,12 @@ __global__ void extract_paths_kernel(GraphDev g, int32_t* path, float* cost, int
 // of transition `layer` at word offset layer * words.
 // ---------------------------------------------------------------------------
 template <int VAR, bool WEIGHTED>
-__global__ void __launch_bounds__(kThreads) optimistic_transition_kernel(GraphDev g, int layer, const uint32_t* bad) {
+__global__ void __launch_bounds__(kThreads) optimistic_transition_kernel(GraphDev g, int layer, const uint32_t* bad,
+                                                                       const int* state) {
   using V = Var<VAR>;
   constexpr int DP = V::kDp;
+  // a finished solve, or a transition above the highest one that lost an edge: nothing changes
+  if (state[kLazyDone] != 0 || layer > state[kLazyStart]) return;
   const int lane = threadIdx.x & 31;
   const int i = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
   if (i >= layer_size(g, layer)) return;
@@ -451,16 +454,16 @@ __global__ void __launch_bounds__(kThreads) optimistic_transition_kernel(GraphDe
 // The exact check of the chain extract_paths wrote (start, path[0..L-1], the
 // goal its last key names): one warp per edge, lanes over the interior
 // waypoints as the early-exit kernel takes them; a colliding edge sets its bit
-// in bad and counts in n_bad[0], and n_bad[1] keeps the highest transition
-// with a colliding edge.  An infeasible chain (no start key) is not checked.
+// in bad, counts in state[kLazyFound] and raises state[kLazyHigh] to its
+// transition.  An infeasible chain (no start key) is not checked.
 template <int VAR>
 __global__ void __launch_bounds__(kThreads) check_chain_kernel(GraphDev g, const int32_t* path, RobotDev rb,
                                                                SceneDev sc, uint32_t* bad, size_t words,
-                                                               int* n_bad) {
+                                                               int* state) {
   extern __shared__ __align__(16) float4 s_obs[];
   using V = Var<VAR>;
   constexpr int DP = V::kDp;
-  if (g.keys[vidx(g, 0, 0, 0)] == kEmptyKey) return;
+  if (state[kLazyDone] != 0 || g.keys[vidx(g, 0, 0, 0)] == kEmptyKey) return;
   stage_obstacles_plain(s_obs, sc.obs, scene_float4s(sc));
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -486,10 +489,31 @@ __global__ void __launch_bounds__(kThreads) check_chain_kernel(GraphDev g, const
     if (hit && lane == 0) {
       const size_t bit = static_cast<size_t>(a) * g.M_stride + b;
       atomicOr(bad + static_cast<size_t>(e) * words + (bit >> 5), 1u << (bit & 31));
-      atomicAdd(n_bad, 1);
-      atomicMax(n_bad + 1, e);
+      atomicAdd(state + kLazyFound, 1);
+      atomicMax(state + kLazyHigh, e);
     }
   }
+}
+
+// one thread: open an iteration's chain check (unless the solve has finished)
+__global__ void lazy_iteration_begin_kernel(int* state) {
+  if (state[kLazyDone] == 0) {
+    state[kLazyFound] = 0;
+    state[kLazyHigh] = -1;
+  }
+}
+
+// one thread: close an iteration: a chain with no colliding edge (or none at
+// all) finishes the solve, so does the iteration cap; otherwise the next sweep
+// starts at the highest transition that lost an edge
+__global__ void lazy_iteration_end_kernel(int* state, int max_iterations) {
+  if (state[kLazyDone] != 0) return;
+  state[kLazyIters] += 1;
+  state[kLazyEdges] += state[kLazyFound];
+  if (state[kLazyFound] == 0 || state[kLazyIters] >= max_iterations)
+    state[kLazyDone] = 1;
+  else
+    state[kLazyStart] = state[kLazyHigh];
 }
 
 __global__ void get_values_kernel(GraphDev g, float* V, int32_t* sigma) {
@@ -758,13 +782,13 @@ struct LabelConfigsRun {
 
 template <int VAR>
 struct OptimisticRun {
-  static cudaError_t run(const GraphDev& g, int layer, const uint32_t* bad, cudaStream_t st) {
+  static cudaError_t run(const GraphDev& g, int layer, const uint32_t* bad, const int* state, cudaStream_t st) {
     const int rows = layer_size(g, layer);
     const int blocks = (rows + kWarps - 1) / kWarps;
     if (g.n_wb > 0)
-      optimistic_transition_kernel<VAR, true><<<blocks, kThreads, 0, st>>>(g, layer, bad);
+      optimistic_transition_kernel<VAR, true><<<blocks, kThreads, 0, st>>>(g, layer, bad, state);
     else
-      optimistic_transition_kernel<VAR, false><<<blocks, kThreads, 0, st>>>(g, layer, bad);
+      optimistic_transition_kernel<VAR, false><<<blocks, kThreads, 0, st>>>(g, layer, bad, state);
     return cudaGetLastError();
   }
 };
@@ -772,9 +796,9 @@ struct OptimisticRun {
 template <int VAR>
 struct CheckChainRun {
   static cudaError_t run(const GraphDev& g, const int32_t* path, const RobotDev& rb, const SceneDev& sc,
-                         uint32_t* bad, size_t words, int* n_bad, cudaStream_t st) {
+                         uint32_t* bad, size_t words, int* state, cudaStream_t st) {
     const size_t smem = static_cast<size_t>(scene_float4s(sc)) * 16;
-    check_chain_kernel<VAR><<<1, kThreads, smem, st>>>(g, path, rb, sc, bad, words, n_bad);
+    check_chain_kernel<VAR><<<1, kThreads, smem, st>>>(g, path, rb, sc, bad, words, state);
     return cudaGetLastError();
   }
 };
@@ -1192,14 +1216,20 @@ cudaError_t launch_label_configs(const float* q, int n, int dof, const RobotDev&
   return by_variant<LabelConfigsRun>(variant, q, n, dof, rb, sc, out, st);
 }
 
-cudaError_t launch_optimistic_transition(const GraphDev& g, int layer, int variant, const uint32_t* bad,
-                                         cudaStream_t st) {
-  return by_variant<OptimisticRun>(variant, g, layer, bad, st);
-}
-
-cudaError_t launch_check_chain(const GraphDev& g, const int32_t* path, const RobotDev& rb, int variant,
-                               const SceneDev& sc, uint32_t* bad, size_t words, int* n_bad, cudaStream_t st) {
-  return by_variant<CheckChainRun>(variant, g, path, rb, sc, bad, words, n_bad, st);
+cudaError_t launch_lazy_iteration(const GraphDev& g, int variant, const RobotDev& rb, const SceneDev& sc,
+                                  uint32_t* bad, size_t words, int32_t* path, float* cost, int* state,
+                                  int max_iterations, cudaStream_t st) {
+  cudaError_t e;
+  for (int layer = g.L; layer >= 0; --layer)
+    if ((e = by_variant<OptimisticRun>(variant, g, layer, bad + static_cast<size_t>(layer) * words,
+                                       static_cast<const int*>(state), st)) != cudaSuccess)
+      return e;
+  if ((e = launch_extract_paths(g, path, cost, nullptr, st)) != cudaSuccess) return e;
+  lazy_iteration_begin_kernel<<<1, 1, 0, st>>>(state);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = by_variant<CheckChainRun>(variant, g, path, rb, sc, bad, words, state, st)) != cudaSuccess) return e;
+  lazy_iteration_end_kernel<<<1, 1, 0, st>>>(state, max_iterations);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev& rb, int variant, const SceneDev& sc,

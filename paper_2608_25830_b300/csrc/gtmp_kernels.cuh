@@ -144,13 +144,16 @@ cudaError_t launch_fused_transition(const GraphDev& g, int layer, const RobotDev
                                     const SceneDev& sc, int mode, int* counters, int grid_x, int chunk, int* err,
                                     cudaStream_t st, bool dependent = false);
 int fused_max_blocks_per_sm(int variant, int mode);
-// path-level lazy evaluation: the min-plus step of transition `layer` over optimistic costs (no
-// collision check) without the edges marked in bad, and the exact check of the extracted chain
-// (colliding edges marked in bad, counted in n_bad); bad holds words 32-bit words per transition
-cudaError_t launch_optimistic_transition(const GraphDev& g, int layer, int variant, const uint32_t* bad,
-                                         cudaStream_t st);
-cudaError_t launch_check_chain(const GraphDev& g, const int32_t* path, const RobotDev& rb, int variant,
-                               const SceneDev& sc, uint32_t* bad, size_t words, int* n_bad, cudaStream_t st);
+// Path-level lazy evaluation, one iteration on the stream: the min-plus sweep over optimistic
+// costs (no collision check) without the edges marked in bad (words 32-bit words per transition),
+// from transition state[kLazyStart] down, the chain extracted into path / cost, its exact check
+// (colliding edges marked in bad) and the iteration's bookkeeping in state; every kernel returns
+// at once when state[kLazyDone] is set, so iterations can be enqueued ahead of the host.
+enum LazyState { kLazyFound = 0, kLazyHigh = 1, kLazyStart = 2, kLazyDone = 3, kLazyIters = 4, kLazyEdges = 5,
+                 kLazyStateInts = 6 };
+cudaError_t launch_lazy_iteration(const GraphDev& g, int variant, const RobotDev& rb, const SceneDev& sc,
+                                  uint32_t* bad, size_t words, int32_t* path, float* cost, int* state,
+                                  int max_iterations, cudaStream_t st);
 cudaError_t launch_extract_paths(const GraphDev& g, int32_t* path, float* cost, int32_t* best, cudaStream_t st);
 cudaError_t launch_goal_reached(const GraphDev& g, int gi, int32_t* goal, cudaStream_t st);
 cudaError_t launch_get_values(const GraphDev& g, float* V, int32_t* sigma, cudaStream_t st);
