@@ -537,10 +537,11 @@ typedef struct {
 typedef struct {
   double edges;     /* candidate edges of the graph */
   double pruned;    /* live edges dropped before exact checking */
-  float score_ms;   /* device time of the surrogate scoring (live lists and the scoring kernel) */
+  float score_ms;   /* device time of the surrogate scoring kernels */
   float solve_ms;   /* device time of the exact fused transitions */
   double scored;    /* live edges scored by the surrogate (row and column live) */
   float band_ms;    /* device time of the protection-band passes (0 without a band) */
+  float lists_ms;   /* device time of the live row / column lists the scoring reads */
 } gtmp_prune_stats;
 
 /* Train the context's surrogate for its robot and current obstacles

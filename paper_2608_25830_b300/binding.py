@@ -69,7 +69,8 @@ class GtmpSurrogateStats(ctypes.Structure):
 
 class GtmpPruneStats(ctypes.Structure):
     _fields_ = [("edges", ctypes.c_double), ("pruned", ctypes.c_double), ("score_ms", ctypes.c_float),
-                ("solve_ms", ctypes.c_float), ("scored", ctypes.c_double), ("band_ms", ctypes.c_float)]
+                ("solve_ms", ctypes.c_float), ("scored", ctypes.c_double), ("band_ms", ctypes.c_float),
+                ("lists_ms", ctypes.c_float)]
 
 
 class GtmpLazyStats(ctypes.Structure):
@@ -750,7 +751,7 @@ def gtmp_solve_pruned(ctx, threshold, dev_path, dev_cost, score_waypoints=1):
     _check(ctx, lib().gtmp_solve_pruned(ctx, threshold, score_waypoints, _dev(dev_path, torch.int32),
                                         _dev(dev_cost, torch.float32), ctypes.byref(st)))
     return dict(edges=st.edges, pruned=st.pruned, score_ms=st.score_ms, solve_ms=st.solve_ms, scored=st.scored,
-                band_ms=st.band_ms)
+                band_ms=st.band_ms, lists_ms=st.lists_ms)
 
 
 def gtmp_solve_lazy_path(ctx, dev_path, dev_cost, max_iterations=100000):

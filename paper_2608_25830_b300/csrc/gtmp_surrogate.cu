@@ -376,24 +376,30 @@ constexpr int kParamCount = kNW1 + kHid + kNW2 + kHid + kNW3 + kHid + kHid + 1;
 
 // ---------------------------------------------------------------------------
 // Fused surrogate scoring of edges: features -> 3 layers -> head -> prune mask
-// in one persistent kernel (one CTA per SM, 8 warps).  Shared memory (bytes,
-// canonical K-major no-swizzle layouts): W1 [256 x 128] resident (64 K, one
-// bulk copy per CTA); the tile's activations (64 K): the features X
-// [128 x 128] first, then H [128 x 256], written over X once layer 1's MMAs
-// have completed and reused by every layer; three 32 K buffers for the
-// 256 x 64 K-chunks of W2 and W3, pre-arranged in global memory as images of
-// their shared-memory tiles.  Every thread copies its 128 bytes of a chunk
-// with cp.async, two chunks ahead of the MMAs (chunk numbers run on across a
-// CTA's tiles, so the next tile's first chunks load during this tile's head);
-// measured on B300, cp.async from all threads moves ~49 B per cycle per SM and
-// one bulk copy engine ~16.  TMEM: two 128 x 256 fp32 accumulators (all 512
-// columns), so that each layer's epilogue, taken in four 64-column chunks,
-// feeds the next layer's MMAs chunk by chunk (chunk c of layer l's output is
-// K-slice c of layer l + 1) while the epilogue of chunk c + 1 runs, and the
-// next tile's layer-1 MMAs run under this tile's head.  A tile is 128 queries: Q = 128 / kw
-// edges with kw waypoints each (t = 1/2 for kw = 1; 1/4, 1/2, 3/4 for kw = 3);
-// an edge is pruned when its largest logit exceeds `cut`.  Only live edges are
-// scored (compacted row and column lists).
+// in one persistent kernel (one CTA per SM: eight epilogue warps and one MMA
+// warp).  Shared memory (canonical K-major no-swizzle layouts): W1 [256 x 128]
+// resident (64 K, one bulk copy per CTA); the features X [128 x 128] (32 K),
+// layer 1's A operand; three 32 K buffers for the 256 x 64 K-chunks of W2 and
+// W3, pre-arranged in global memory as images of their shared-memory tiles;
+// the epilogues' biases.  Every epilogue thread copies its 128 bytes of a
+// chunk with cp.async two chunks ahead of the MMAs (chunk numbers run on
+// across a CTA's tiles, so the next tile's first chunks load during this
+// tile's head); measured on B300, cp.async from all threads moves ~49 B per
+// cycle per SM and one bulk copy engine ~16 (a bulk copy per chunk from the
+// MMA thread measured 25.4 ms of scoring per solve against 23.9).  TMEM: two
+// 128 x 256 fp32 accumulators (all 512 columns).  Each layer's epilogue runs
+// in four 64-column chunks; a warp's 32 columns of a chunk go back into the
+// first 16 of those columns as bf16 pairs, where they are the next layer's A
+// operand (tcgen05.mma reads A from tensor memory: no shared-memory
+// activations, stores or proxy fences), and the chunk's four MMAs (K-slice c
+// of layer l + 1, into the other accumulator) run under the epilogue of chunk
+// c + 1.  An MMA issue blocks its thread for about the MMA's own duration, so
+// one warp does nothing else; its chunk g queues behind chunk g - 1, and the
+// buffer of chunk g - 1 is reloaded only after that (the tensor pipe does not
+// drain between chunks).  A tile is 128 queries: Q = 128 / kw edges with kw
+// waypoints each (t = 1/2 for kw = 1; 1/4, 1/2, 3/4 for kw = 3); an edge is
+// pruned when its largest logit exceeds `cut`.  Only live edges are scored
+// (compacted row and column lists).
 // ---------------------------------------------------------------------------
 // Live rows (vertex free) and live columns (vertex free, finite cost-to-go)
 // of a transition, in increasing order: one block, ballot + prefix per warp.
@@ -484,10 +490,26 @@ __global__ void __launch_bounds__(256) protect_band_kernel(GraphDev g, int layer
   }
 }
 
-constexpr int kScoreThreads = 256;
-constexpr int kSmemW1 = 256 * 128 * 2, kSmemH = 128 * 256 * 2, kSmemS = 256 * 64 * 2;
+// eight epilogue warps (two per TMEM lane quarter), one MMA warp, whose lane 0 issues every MMA (an
+// issue blocks for about the MMA's own duration, so it has a warp of its own), and one load warp, whose
+// lane 0 streams the weight chunks; the first nine synchronise on named barrier 2
+constexpr int kEpiThreads = 256, kMmaThread = kEpiThreads, kMainThreads = kEpiThreads + 32;
+constexpr int kLoadThread = kMainThreads, kScoreThreads = kMainThreads + 32;
+
+// barrier 2 over the epilogue and MMA warps; the _and form returns whether p held in every thread
+__device__ __forceinline__ void bar_sync_main() { asm volatile("bar.sync 2, %0;" ::"n"(kMainThreads) : "memory"); }
+__device__ __forceinline__ bool bar_and_main(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 2, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(p)), "n"(kMainThreads)
+      : "memory");
+  return r != 0;
+}
+constexpr int kSmemW1 = 256 * 128 * 2, kSmemX = 128 * 128 * 2, kSmemS = 256 * 64 * 2, kSmemP = 4 * 256 * 4;
 constexpr int kChunkBufs = 3;                      // stream buffers: one being read, two loading
-constexpr int kScoreSmem = kSmemW1 + kSmemH + kChunkBufs * kSmemS;
+constexpr int kScoreSmem = kSmemW1 + kSmemX + kChunkBufs * kSmemS + kSmemP;
 
 struct ScoreArgs {
   GraphDev g;
@@ -513,6 +535,15 @@ __device__ __forceinline__ uint32_t canon(int r, int k, int kdim) {
   return static_cast<uint32_t>(((r >> 3) * (kdim >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// the same with A read from tensor memory (columns ta.., 128 lanes, two bf16 per 32-bit column)
+__device__ __forceinline__ void issue_mma_ts(uint32_t tmem, uint32_t ta, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "r"(ta), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void issue_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -531,6 +562,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 16 TMEM columns of this warp's 32 lanes, waited for
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&w)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]),
+      "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Weight images for the scoring kernel: W1 [256 x 128] and the chunks
@@ -554,26 +596,35 @@ __global__ void weight_images_kernel(const __nv_bfloat16* W1b, const __nv_bfloat
       *reinterpret_cast<const uint4*>(W + static_cast<size_t>(n) * kHid + (c & 3) * 64 + kc * 8);
 }
 
-// the features of one query half: frequencies [32 HF, 32 HF + 32); DOF > 0
-// gives compile-time indices (B from the parameter bank, q in registers)
+// the features of one query half, frequencies [32 HF, 32 HF + 32), from the
+// edge's end points u, v held in registers (DOF > 0: compile-time indices, B
+// from the parameter bank): sine and cosine rounded to bf16, packed in pairs
+// (the lower frequency in the low half)
 template <int DOF, int HF>
-__device__ __forceinline__ void score_features(const float* u, const float* v, float t, const FourierDev& f,
-                                               __nv_bfloat16 (&sv)[32], __nv_bfloat16 (&cv)[32]) {
+__device__ __forceinline__ void score_features(const float (&u)[DOF > 0 ? DOF : kMaxDof],
+                                               const float (&v)[DOF > 0 ? DOF : kMaxDof], float t,
+                                               const FourierDev& f, uint32_t (&sw)[16], uint32_t (&cw)[16]) {
   constexpr int ND = DOF > 0 ? DOF : kMaxDof;
   const int dof = DOF > 0 ? DOF : f.dof;
   float q[ND];
 #pragma unroll
   for (int d = 0; d < ND; ++d) q[d] = d < dof ? __fmaf_rn(t, __fsub_rn(v[d], u[d]), u[d]) : 0.0f;
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    float z = 0.0f;
+  for (int k2 = 0; k2 < 16; ++k2) {
+    float sn[2], cs[2];
 #pragma unroll
-    for (int d = 0; d < ND; ++d)
-      if (d < dof) z = __fmaf_rn(f.B[(HF * 32 + k) * dof + d], q[d], z);
-    float sn, cs;
-    __sincosf(z, &sn, &cs);
-    sv[k] = __float2bfloat16_rn(sn);
-    cv[k] = __float2bfloat16_rn(cs);
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * k2 + h;
+      float z = 0.0f;
+#pragma unroll
+      for (int d = 0; d < ND; ++d)
+        if (d < dof) z = __fmaf_rn(f.B[(HF * 32 + k) * dof + d], q[d], z);
+      __sincosf(z, &sn[h], &cs[h]);
+    }
+    const __nv_bfloat162 s2 = __floats2bfloat162_rn(sn[0], sn[1]);
+    const __nv_bfloat162 c2 = __floats2bfloat162_rn(cs[0], cs[1]);
+    sw[k2] = *reinterpret_cast<const uint32_t*>(&s2);
+    cw[k2] = *reinterpret_cast<const uint32_t*>(&c2);
   }
 }
 
@@ -582,6 +633,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar_layer;            // one arrival per layer's MMAs: three per tile
   __shared__ __align__(8) uint64_t mbar_buf[kChunkBufs];  // chunk g's MMAs done: buffer g % kChunkBufs is free
+  __shared__ __align__(8) uint64_t mbar_full[kChunkBufs]; // chunk g's weights have landed in its buffer
   __shared__ __align__(8) uint64_t mbar_w1;               // the resident W1
   __shared__ __align__(8) uint64_t mbar_fin;              // every MMA of the CTA done (teardown)
   __shared__ int s_abort;
@@ -589,39 +641,35 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   __shared__ float s_part[2][128];
   __shared__ float s_logit[128];
   uint8_t* sW1 = smem;
-  uint8_t* sH = sW1 + kSmemW1;
-  uint8_t* sX = sH;           // the features occupy H's first 32 K until layer 1 has read them
-  uint8_t* sS = sH + kSmemH;  // stream buffers
+  uint8_t* sX = sW1 + kSmemW1;                     // the tile's features (layer 1's A operand)
+  uint8_t* sS = sX + kSmemX;                       // stream buffers
+  float* sP = reinterpret_cast<float*>(sS + kChunkBufs * kSmemS);  // b1, b2, b3, w4
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool epi = tid < kEpiThreads;  // an epilogue thread (else the MMA warp)
   const uint32_t mbl = s_u32(&mbar_layer);
-  const float* b1 = a.P + kNW1;
-  const float* b2 = b1 + kHid + kNW2;
-  const float* b3 = b2 + kHid + kNW3;
-  const float* w4 = b3 + kHid;
-  const float b4 = w4[kHid];
-
-  // weight chunk g (chunk numbers run on across this CTA's tiles; g % 8 = 0..3: W2 columns
-  // [64 (g % 4), + 64), 4..7: W3 columns) into buffer g % kChunkBufs: this thread's 128 bytes as one
-  // cp.async group (an empty group past the CTA's last chunk, so that group g always holds chunk g)
-  long long chunks_loaded = 0;
-  auto load_chunk = [&](long long g, long long total) {
-    if (g < total) {
-      const uint8_t* src = a.Wimg + kSmemW1 + static_cast<size_t>(g % 8) * kSmemS;
-      const uint32_t dst = s_u32(sS + static_cast<int>(g % kChunkBufs) * kSmemS);
-#pragma unroll
-      for (int k = 0; k < kSmemS / 16 / kScoreThreads; ++k) {
-        const int off = (k * kScoreThreads + tid) * 16;
-        cp_async16(dst + off, src + off, 16);
-      }
+  {
+    const float* P1 = a.P + kNW1;
+    const float* P2 = P1 + kHid + kNW2;
+    const float* P3 = P2 + kHid + kNW3;
+    if (tid < kHid) {
+      sP[tid] = P1[tid];
+      sP[kHid + tid] = P2[tid];
+      sP[2 * kHid + tid] = P3[tid];
+      sP[3 * kHid + tid] = P3[kHid + tid];
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
+  }
+  const float* b1 = sP;
+  const float* b2 = sP + kHid;
+  const float* b3 = sP + 2 * kHid;
+  const float* w4 = sP + 3 * kHid;
+  const float b4 = a.P[kNW1 + kHid + kNW2 + kHid + kNW3 + kHid + kHid];
+
   uint32_t ph_layer = 0;
   // every thread waits for the next layer completion; the CTA agrees on the outcome
   auto wait_layer = [&]() -> bool {
     const bool w = mbar_wait_parity(mbl, ph_layer, kMbarLimit);
     ph_layer ^= 1u;
-    return __syncthreads_and(w) != 0 && s_abort == 0;
+    return bar_and_main(w && s_abort == 0);
   };
 
   if (warp == 0) {
@@ -633,8 +681,10 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   if (tid == 0) {
     s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbl) : "memory");
-    for (int k = 0; k < kChunkBufs; ++k)
+    for (int k = 0; k < kChunkBufs; ++k) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_buf[k])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_full[k])) : "memory");
+    }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_w1)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(&mbar_fin)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -648,7 +698,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  bool w1_ready = false, any_mma = false;  // thread 0's state
+  bool w1_ready = false, any_mma = false;  // the MMA thread's state
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (256u >> 3 << 17) | (128u >> 4 << 24);
@@ -668,39 +718,79 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   const long long my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long total_chunks = my_tiles * 8;
   long long chunks_issued = 0;
-  for (; chunks_loaded < kChunkBufs - 1; ++chunks_loaded) load_chunk(chunks_loaded, total_chunks);
 
-  // features of a tile's queries -> X: two threads per query, 32 frequencies each; the fast __sincosf is
-  // ample here (|Bq| < 10, absolute error ~1e-6, the features are rounded to bf16 right after)
-  auto features = [&](long long tile) {
-    const long long e_first = tile * e_per_tile;
-    const int qidx = tid & 127, hf = tid >> 7;
-    __align__(16) __nv_bfloat16 sv[32];
-    __align__(16) __nv_bfloat16 cv[32];
-    const long long e = e_first + qidx / a.kw;
-    if (qidx < q_per_tile && e < n_live) {
-      const int i = rows_live[e / nc], j = cols_live[e % nc];
-      const float* u = a.g.Q + vidx(a.g, 0, a.layer, i) * a.g.dp;
-      const float* v = a.g.Q + vidx(a.g, 0, a.layer + 1, j) * a.g.dp;
+  // Features of a tile's queries -> X, in stages spread over the previous tile so that their loads and
+  // arithmetic run under its layers: the query's vertex indices, then its end points, then the
+  // features, computed and stored once the previous tile's layer 1 has read X.  Two
+  // threads per query, 32 frequencies each; the fast __sincosf is ample here (|Bq| < 10, absolute error
+  // ~1e-6, the features are rounded to bf16 right after).
+  constexpr int ND = DOF > 0 ? DOF : kMaxDof;
+  const int qidx = tid & 127, hf = tid >> 7;
+  const bool small = n_live <= 0x7fffffffLL;
+  // live edge e -> (row list index, column list index)
+  auto split_edge = [&](long long e, int& r, int& cidx) {
+    if (small) {
+      const int ei = static_cast<int>(e);
+      r = ei / nc;
+      cidx = ei - r * nc;
+    } else {
+      r = static_cast<int>(e / nc);
+      cidx = static_cast<int>(e - static_cast<long long>(r) * nc);
+    }
+  };
+  int fi = 0, fj = 0;
+  bool fvalid = false;
+  float fu[ND], fv[ND];
+  uint32_t sw[16], cw[16];
+  auto feat_index = [&](long long tile_f) {
+    const long long e = tile_f * e_per_tile + qidx / a.kw;
+    fvalid = epi && qidx < q_per_tile && e < n_live;
+    if (fvalid) {
+      int r, cidx;
+      split_edge(e, r, cidx);
+      fi = rows_live[r];
+      fj = cols_live[cidx];
+    }
+  };
+  auto feat_points = [&]() {
+    if (fvalid) {
+      const int dof = DOF > 0 ? DOF : f.dof;
+      const float* u = a.g.Q + vidx(a.g, 0, a.layer, fi) * a.g.dp;
+      const float* v = a.g.Q + vidx(a.g, 0, a.layer + 1, fj) * a.g.dp;
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        fu[d] = d < dof ? u[d] : 0.0f;
+        fv[d] = d < dof ? v[d] : 0.0f;
+      }
+    }
+  };
+  auto feat_compute = [&]() {
+    if (fvalid) {
       const float t = a.kw == 1 ? 0.5f : 0.25f * static_cast<float>(qidx % a.kw + 1);
       if (hf == 0)
-        score_features<DOF, 0>(u, v, t, f, sv, cv);
+        score_features<DOF, 0>(fu, fv, t, f, sw, cw);
       else
-        score_features<DOF, 1>(u, v, t, f, sv, cv);
+        score_features<DOF, 1>(fu, fv, t, f, sw, cw);
     } else {
-      for (int k = 0; k < 32; ++k) sv[k] = cv[k] = __float2bfloat16_rn(0.0f);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) sw[k] = cw[k] = 0u;
     }
+  };
+  auto feat_store = [&]() {
+    if (!epi) return;
+#pragma unroll
     for (int g8 = 0; g8 < 4; ++g8) {
-      *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + g8 * 8, 128)) = *reinterpret_cast<const uint4*>(sv + g8 * 8);
+      *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + g8 * 8, 128)) =
+          make_uint4(sw[4 * g8], sw[4 * g8 + 1], sw[4 * g8 + 2], sw[4 * g8 + 3]);
       *reinterpret_cast<uint4*>(sX + canon(qidx, 64 + hf * 32 + g8 * 8, 128)) =
-          *reinterpret_cast<const uint4*>(cv + g8 * 8);
+          make_uint4(cw[4 * g8], cw[4 * g8 + 1], cw[4 * g8 + 2], cw[4 * g8 + 3]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // X (generic writes) -> MMA reads
   };
   // layer 1 (D = X W1^T) into the accumulator at TMEM column acc, committed to the layer barrier; on a W1
   // timeout the barrier is released by hand and the abort flag set
   auto issue_l1 = [&](uint32_t acc) {
-    if (tid != 0) return;
+    if (tid != kMmaThread) return;
     bool go = true;
     if (!w1_ready) {
       go = mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);
@@ -723,151 +813,205 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
 
   // Per tile: the layer-1 accumulator A (TMEM columns 0 or 256, alternating by tile) also takes layer 3,
   // the other one, B, layer 2.  Each epilogue runs in four 64-column chunks; chunk c of layer l's
-  // output, written to H, is K-slice c of layer l + 1, whose four MMAs are issued at once and run
-  // under the epilogue of chunk c + 1.  The next tile's features and layer-1 MMAs (into B) run before
-  // this tile's head (which reads A).
-  long long tile = blockIdx.x;
-  uint32_t par = 0;
-  if (tile < n_tiles) {
-    features(tile);
-    __syncthreads();
-    issue_l1(0u);
-  }
-  for (; tile < n_tiles && ok; tile += gridDim.x, par ^= 1u) {
-    const uint32_t accA = par ? 256u : 0u, accB = par ? 0u : 256u;
-    ok = wait_layer();  // layer 1
-    for (int l = 0; l < 2 && ok; ++l) {
-      if (l == 1) {
-        ok = wait_layer();  // layer 2
-        if (!ok) break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t acc_in = l == 0 ? accA : accB, acc_out = l == 0 ? accB : accA;
-      const float* bias = l == 0 ? b1 : b2;
-      for (int c = 0; c < 4; ++c) {
-        // epilogue chunk c: TMEM -> relu(acc + b) -> bf16 -> H columns [64 c, + 64)
-        {
-          const int n0 = c * 64 + half * 32;
-          uint32_t v[32];
-          tmem_ld32(lane_addr + acc_in + n0, v);
-#pragma unroll
-          for (int g8 = 0; g8 < 4; ++g8) {
-            const float4 ba = __ldg(reinterpret_cast<const float4*>(bias + n0 + g8 * 8));
-            const float4 bb = __ldg(reinterpret_cast<const float4*>(bias + n0 + g8 * 8 + 4));
-            const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-            uint32_t w[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const __nv_bfloat162 h2 =
-                  __floats2bfloat162_rn(fmaxf(__uint_as_float(v[g8 * 8 + 2 * j]) + bv[2 * j], 0.0f),
-                                        fmaxf(__uint_as_float(v[g8 * 8 + 2 * j + 1]) + bv[2 * j + 1], 0.0f));
-              w[j] = *reinterpret_cast<const uint32_t*>(&h2);
-            }
-            *reinterpret_cast<uint4*>(sH + canon(row, n0 + g8 * 8, 256)) = make_uint4(w[0], w[1], w[2], w[3]);
+  // output, written back to tensor memory as bf16, is K-slice c of layer l + 1's A operand, whose four
+  // MMAs are issued at once and run under the epilogue of chunk c + 1.  The next tile's features are
+  // loaded under layer 1's epilogue and computed and stored to X (free once this tile's layer 1 is
+  // done) under layer 2; its layer-1 MMAs (into B) run under this tile's head (which reads A).
+  if (tid >= kMainThreads) {
+    // The load warp: lane 0 streams chunk g into buffer g % kChunkBufs as one bulk copy completing on
+    // mbar_full, once chunk g - kChunkBufs's MMAs have freed the buffer.  It runs ahead of the MMAs by
+    // the buffers; it stops on the CTA's abort flag (polled between slices of each bounded wait).
+    if (tid == kLoadThread) {
+      auto wait_or_abort = [&](uint32_t bar, uint32_t parity) -> bool {
+        for (int slice = 0; slice < 64; ++slice) {
+          if (mbar_wait_parity(bar, parity, kMbarLimit / 64)) return true;
+          if (*static_cast<volatile int*>(&s_abort)) return false;
+        }
+        return false;
+      };
+      long long g = 0;
+      for (; g < total_chunks; ++g) {
+        const int b = static_cast<int>(g % kChunkBufs);
+        if (g >= kChunkBufs) {
+          const long long h = g - kChunkBufs;
+          if (!wait_or_abort(s_u32(&mbar_buf[b]), static_cast<uint32_t>((h / kChunkBufs) & 1))) {
+            s_abort = 1;
+            break;
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // H (generic writes) -> MMA reads
-        // chunk g = chunks_issued goes to the MMAs now; the buffer of chunk g + 2 last held chunk g - 1,
-        // whose MMAs must have completed before it is overwritten
-        const long long g = chunks_issued;
-        bool free_ok = true;
-        if (g >= 1)
-          free_ok = mbar_wait_parity(s_u32(&mbar_buf[(g - 1) % kChunkBufs]),
-                                     static_cast<uint32_t>(((g - 1) / kChunkBufs) & 1), kMbarLimit);
-        load_chunk(chunks_loaded++, free_ok ? total_chunks : 0);
-        // this thread's part of chunk g has landed (groups g + 1 and g + 2 may be in flight): make it
-        // visible to the MMA (async proxy), then wait for every thread's part and epilogue chunk
-        asm volatile("cp.async.wait_group %0;" ::"n"(kChunkBufs - 1) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        ok = __syncthreads_and(free_ok) != 0 && s_abort == 0;
-        if (!ok) break;
-        if (tid == 0) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sb = s_u32(sS + static_cast<int>(g % kChunkBufs) * kSmemS);
-          for (int kk = 0; kk < 4; ++kk)
-            issue_mma(tmem + acc_out, smem_desc(s_u32(sH) + c * 1024 + kk * 256, 128, 4096),
-                      smem_desc(sb + kk * 256, 128, 1024), idesc, (c > 0 || kk > 0) ? 1u : 0u);
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           s_u32(&mbar_buf[g % kChunkBufs]))
-                       : "memory");
-          if (c == 3)
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbl)
-                         : "memory");
-        }
-        ++chunks_issued;
+        const uint8_t* src = a.Wimg + kSmemW1 + static_cast<size_t>(g % 8) * kSmemS;
+        const uint32_t bar = s_u32(&mbar_full[b]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kSmemS) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         s_u32(sS + b * kSmemS)),
+                     "l"(src), "r"(kSmemS), "r"(bar)
+                     : "memory");
       }
+      // the last copy issued into each buffer has landed before the shared memory is released (bounded)
+      for (long long h = g > kChunkBufs ? g - kChunkBufs : 0; h < g; ++h)
+        mbar_wait_parity(s_u32(&mbar_full[h % kChunkBufs]), static_cast<uint32_t>((h / kChunkBufs) & 1), kMbarLimit);
     }
-    if (!ok) break;
-    ok = wait_layer();  // layer 3 (accumulator A)
-    if (!ok) break;
-    // the next tile's features (H is free: layer 3 has read it) and layer-1 MMAs into B, under this head
-    const long long next = tile + gridDim.x;
-    if (next < n_tiles) {
-      features(next);
-      __syncthreads();
-      issue_l1(accB);
+  } else {
+    long long tile = blockIdx.x;
+    uint32_t par = 0;
+    if (tile < n_tiles) {
+      feat_index(tile);
+      feat_points();
+      feat_compute();
+      feat_store();
+      bar_sync_main();
+      issue_l1(0u);
     }
-    // this thread's edge (threads 0..127) and its protection mark, loaded ahead of the head
-    size_t pidx = 0;
-    bool prot = false;
-    const long long e_mine = tile * e_per_tile + tid;
-    const bool mine = tid < e_per_tile && e_mine < n_live;
-    if (mine) {
-      pidx = static_cast<size_t>(rows_live[e_mine / nc]) * cols + cols_live[e_mine % nc];
-      if (a.protect) prot = a.prune[pidx] == kPruneProtected;
-    }
-    // head: relu(acc + b3) . w4 + b4, per query; then the edge's max against the cut
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float dot = 0.0f;
-    for (int cc = 0; cc < 4; ++cc) {
-      const int n0 = half * 128 + cc * 32;
-      uint32_t v[32];
-      tmem_ld32(lane_addr + accA + n0, v);
-      // four partial sums: a short dependency chain
-      float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-      for (int j4 = 0; j4 < 8; ++j4) {
-        const float4 bb = __ldg(reinterpret_cast<const float4*>(b3 + n0 + 4 * j4));
-        const float4 ww = __ldg(reinterpret_cast<const float4*>(w4 + n0 + 4 * j4));
-        part[0] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4]) + bb.x, 0.0f), ww.x, part[0]);
-        part[1] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 1]) + bb.y, 0.0f), ww.y, part[1]);
-        part[2] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 2]) + bb.z, 0.0f), ww.z, part[2]);
-        part[3] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 3]) + bb.w, 0.0f), ww.w, part[3]);
-      }
-      dot += (part[0] + part[1]) + (part[2] + part[3]);
-    }
-    s_part[half][row] = dot;
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (tid < 128) s_logit[tid] = s_part[0][tid] + s_part[1][tid] + b4;
-    __syncthreads();
-    if (tid < 128) {  // warps 0..3, full warps for the ballot
-      bool pr = false;
+    for (; tile < n_tiles && ok; tile += gridDim.x, par ^= 1u) {
+      const uint32_t accA = par ? 256u : 0u, accB = par ? 0u : 256u;
+      const long long next = tile + gridDim.x;
+      // this thread's edge of the head (threads 0..127) and the next tile's query: their index loads
+      // are issued now and used a layer later
+      size_t pidx = 0;
+      bool prot = false;
+      const long long e_mine = tile * e_per_tile + tid;
+      const bool mine = tid < e_per_tile && e_mine < n_live;
+      int hr = 0, hc = 0;
       if (mine) {
-        float z = s_logit[tid * a.kw];
-        for (int w = 1; w < a.kw; ++w) z = fmaxf(z, s_logit[tid * a.kw + w]);
-        pr = z > a.cut && !prot;
-        a.prune[pidx] = pr ? 1 : 0;
+        int r, cidx;
+        split_edge(e_mine, r, cidx);
+        hr = rows_live[r];
+        hc = cols_live[cidx];
       }
-      const unsigned b = __ballot_sync(kFull, pr);
-      if (lane == 0 && b) atomicAdd(a.n_pruned, static_cast<unsigned long long>(__popc(b)));
+      if (next < n_tiles) feat_index(next);
+      ok = wait_layer();  // layer 1
+      if (ok && next < n_tiles) feat_points();  // the next tile's end points, loaded under layer 1's epilogue
+      for (int l = 0; l < 2 && ok; ++l) {
+        if (l == 1) {
+          // the next tile's features to X (layer 1 has read this tile's) and this edge's protection mark,
+          // under layer 2
+          if (next < n_tiles) {
+            feat_compute();
+            feat_store();
+          }
+          if (mine) {
+            pidx = static_cast<size_t>(hr) * cols + hc;
+            if (a.protect) prot = a.prune[pidx] == kPruneProtected;
+          }
+          ok = wait_layer();  // layer 2
+          if (!ok) break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_in = l == 0 ? accA : accB, acc_out = l == 0 ? accB : accA;
+        const float* bias = l == 0 ? b1 : b2;
+        for (int c = 0; c < 4; ++c) {
+          // epilogue chunk c: this warp's 32 columns [n0, n0 + 32) of acc_in -> relu(acc + b) -> bf16 pairs,
+          // written back over the first 16 of those columns (read by this warp alone, and already read):
+          // there they are K-slice [n0, n0 + 32) of layer l + 1's A operand
+          if (epi) {
+            const int n0 = c * 64 + half * 32;
+            uint32_t v[32];
+            tmem_ld32(lane_addr + acc_in + n0, v);
+            uint32_t w[16];
+#pragma unroll
+            for (int g4 = 0; g4 < 8; ++g4) {
+              const float4 bb = *reinterpret_cast<const float4*>(bias + n0 + g4 * 4);
+              const __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[4 * g4]) + bb.x, 0.0f),
+                                                              fmaxf(__uint_as_float(v[4 * g4 + 1]) + bb.y, 0.0f));
+              const __nv_bfloat162 h1 = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[4 * g4 + 2]) + bb.z, 0.0f),
+                                                              fmaxf(__uint_as_float(v[4 * g4 + 3]) + bb.w, 0.0f));
+              w[2 * g4] = *reinterpret_cast<const uint32_t*>(&h0);
+              w[2 * g4 + 1] = *reinterpret_cast<const uint32_t*>(&h1);
+            }
+            tmem_st16(lane_addr + acc_in + n0, w);
+          }
+          // chunk g = chunks_issued goes to the MMAs once every epilogue chunk is in place (its tensor-memory
+          // stores completed in tmem_st16) and its weights have landed; the abort flag may be set by the MMA
+          // or load thread at any time: the threads' readings are combined, so the CTA agrees
+          const long long g = chunks_issued;
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          ok = bar_and_main(s_abort == 0);
+          if (!ok) break;
+          if (tid == kMmaThread) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sb = s_u32(sS + static_cast<int>(g % kChunkBufs) * kSmemS);
+            const bool go = mbar_wait_parity(s_u32(&mbar_full[g % kChunkBufs]),
+                                             static_cast<uint32_t>((g / kChunkBufs) & 1), kMbarLimit);
+            // K-step kk of chunk c: A columns 16 kk .. + 16 of the chunk, i.e. half kk / 2's packed
+            // columns, 8 columns per 16 K
+            if (go) {
+              for (int kk = 0; kk < 4; ++kk)
+                issue_mma_ts(tmem + acc_out, tmem + acc_in + c * 64 + (kk >> 1) * 32 + (kk & 1) * 8,
+                             smem_desc(sb + kk * 256, 128, 1024), idesc, (c > 0 || kk > 0) ? 1u : 0u);
+              // chunk g's MMAs free its buffer for chunk g + kChunkBufs (the load thread waits on this)
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                               s_u32(&mbar_buf[g % kChunkBufs]))
+                           : "memory");
+              if (c == 3)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbl)
+                             : "memory");
+            } else {
+              // a timeout: the CTA stops at its next barrier (the layer barrier is released for a waiter)
+              s_abort = 1;
+              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbl) : "memory");
+            }
+          }
+          ++chunks_issued;
+        }
+      }
+      if (!ok) break;
+      ok = wait_layer();  // layer 3 (accumulator A)
+      if (!ok) break;
+      // the next tile's layer-1 MMAs into B (its X was stored under layer 2, before this tile's last
+      // chunk barriers), under this head
+      if (next < n_tiles) issue_l1(accB);
+      // head: relu(acc + b3) . w4 + b4, per query; then the edge's max against the cut
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float dot = 0.0f;
+      for (int cc = 0; cc < 4 && epi; ++cc) {
+        const int n0 = half * 128 + cc * 32;
+        uint32_t v[32];
+        tmem_ld32(lane_addr + accA + n0, v);
+        // four partial sums: a short dependency chain
+        float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 bb = *reinterpret_cast<const float4*>(b3 + n0 + 4 * j4);
+          const float4 ww = *reinterpret_cast<const float4*>(w4 + n0 + 4 * j4);
+          part[0] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4]) + bb.x, 0.0f), ww.x, part[0]);
+          part[1] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 1]) + bb.y, 0.0f), ww.y, part[1]);
+          part[2] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 2]) + bb.z, 0.0f), ww.z, part[2]);
+          part[3] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 3]) + bb.w, 0.0f), ww.w, part[3]);
+        }
+        dot += (part[0] + part[1]) + (part[2] + part[3]);
+      }
+      if (epi) s_part[half][row] = dot;
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      bar_sync_main();
+      if (tid < 128) {  // warps 0..3, full warps for the ballot, under a barrier of their own
+        s_logit[tid] = s_part[0][tid] + s_part[1][tid] + b4;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        bool pr = false;
+        if (mine) {
+          float z = s_logit[tid * a.kw];
+          for (int w = 1; w < a.kw; ++w) z = fmaxf(z, s_logit[tid * a.kw + w]);
+          pr = z > a.cut && !prot;
+          a.prune[pidx] = pr ? 1 : 0;
+        }
+        const unsigned b = __ballot_sync(kFull, pr);
+        if (lane == 0 && b) atomicAdd(a.n_pruned, static_cast<unsigned long long>(__popc(b)));
+      }
+      // s_part and s_logit are next written after the next tile's first CTA barrier
     }
-    __syncthreads();
-  }
-  asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies have landed
-  if (tid == 0) {
-    // every MMA this CTA issued has completed before TMEM is freed (bounded)
-    bool drained = true;
-    if (any_mma) {
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       s_u32(&mbar_fin))
-                   : "memory");
-      drained = mbar_wait_parity(s_u32(&mbar_fin), 0u, kMbarLimit);
-    }
-    if (!ok || !drained) {
-      atomicOr(a.err, kErrWaitTimeout);
-      if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);  // let the W1 copy land (bounded)
+    if (!ok) s_abort = 1;  // the load thread stops streaming
+    if (tid == kMmaThread) {
+      // every MMA this CTA issued has completed before TMEM is freed (bounded)
+      bool drained = true;
+      if (any_mma) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         s_u32(&mbar_fin))
+                     : "memory");
+        drained = mbar_wait_parity(s_u32(&mbar_fin), 0u, kMbarLimit);
+      }
+      if (!ok || !drained) {
+        atomicOr(a.err, kErrWaitTimeout);
+        if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);  // let the W1 copy land (bounded)
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1309,7 +1453,8 @@ GraphDev pruned_graph(gtmp_ctx* c) {
 // Score the live edges of transition `layer` (rows = its live vertices, columns
 // = the next layer's free vertices with a finite cost-to-go in the keys) into
 // prune[i * cols + j]: 1 = pruned, 0 = kept; other entries are not written.
-// band_done (optional): recorded after the protection-band pass, before the scoring kernel
+// band_start, band_done (optional): recorded after the live lists and after the protection-band pass,
+// before the scoring kernel
 gtmp_status launch_score_transition(gtmp_ctx* c, const GraphDev& g, int layer, float cut, int kw, uint8_t* prune,
                                     cudaEvent_t band_start = nullptr, cudaEvent_t band_done = nullptr) {
   SurrogateState* s = c->sur;
@@ -1407,7 +1552,7 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
   cudaEventCreate(&e2);
   cudaEventCreate(&eb0);
   cudaEventCreate(&eb1);
-  float score_ms = 0.0f, solve_ms = 0.0f, band_ms = 0.0f;
+  float score_ms = 0.0f, solve_ms = 0.0f, band_ms = 0.0f, lists_ms = 0.0f;
   SUR_TRY(c, launch_init_keys(g, c->counters, L + 1, st));
   SUR_TRY(c, launch_vertex_labels(g, c->rb, c->variant, ctx_scene(c), st));
   const int resident = c->num_sms * c->fused_bps[0];
@@ -1447,13 +1592,16 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     cudaEventRecord(e2, st);
     SUR_TRY(c, cudaEventSynchronize(e2));
     scored_total += static_cast<double>(live_n[0]) * live_n[1];
-    float a = 0.0f, b = 0.0f, bb = 0.0f;
-    cudaEventElapsedTime(&a, e0, e1);
+    // e0 | live lists | eb0 | protection band | eb1 | scoring kernel | e1 | exact transition | e2
+    float a = 0.0f, b = 0.0f, bb = 0.0f, ll = 0.0f;
+    cudaEventElapsedTime(&a, eb1, e1);
     cudaEventElapsedTime(&b, e1, e2);
     cudaEventElapsedTime(&bb, eb0, eb1);
-    score_ms += a - bb;
+    cudaEventElapsedTime(&ll, e0, eb0);
+    score_ms += a;
     solve_ms += b;
     band_ms += bb;
+    lists_ms += ll;
   }
   SUR_TRY(c, launch_extract_paths(g, dev_path, dev_cost, nullptr, st));
   unsigned long long pruned = 0;
@@ -1471,6 +1619,7 @@ GTMP_API gtmp_status gtmp_solve_pruned(gtmp_ctx* c, float threshold, int32_t sco
     stats->solve_ms = solve_ms;
     stats->scored = scored_total;
     stats->band_ms = band_ms;
+    stats->lists_ms = lists_ms;
   }
   return GTMP_OK;
 }
