@@ -509,7 +509,8 @@ __device__ __forceinline__ bool bar_and_main(bool p) {
 }
 constexpr int kSmemW1 = 256 * 128 * 2, kSmemX = 128 * 128 * 2, kSmemS = 256 * 64 * 2, kSmemP = 4 * 256 * 4;
 constexpr int kChunkBufs = 3;                      // stream buffers: one being read, two loading
-constexpr int kScoreSmem = kSmemW1 + kSmemX + kChunkBufs * kSmemS + kSmemP;
+constexpr int kSmemF = 64 * kMaxDof * 4;           // the Fourier matrix, one padded row per frequency
+constexpr int kScoreSmem = kSmemW1 + kSmemX + kChunkBufs * kSmemS + kSmemP + kSmemF;
 
 struct ScoreArgs {
   GraphDev g;
@@ -596,29 +597,35 @@ __global__ void weight_images_kernel(const __nv_bfloat16* W1b, const __nv_bfloat
       *reinterpret_cast<const uint4*>(W + static_cast<size_t>(n) * kHid + (c & 3) * 64 + kc * 8);
 }
 
-// the features of one query half, frequencies [32 HF, 32 HF + 32), from the
-// edge's end points u, v held in registers (DOF > 0: compile-time indices, B
-// from the parameter bank): sine and cosine rounded to bf16, packed in pairs
-// (the lower frequency in the low half)
-template <int DOF, int HF>
-__device__ __forceinline__ void score_features(const float (&u)[DOF > 0 ? DOF : kMaxDof],
-                                               const float (&v)[DOF > 0 ? DOF : kMaxDof], float t,
-                                               const FourierDev& f, uint32_t (&sw)[16], uint32_t (&cw)[16]) {
+// eight features of one query: frequencies [k0, k0 + 8) of the waypoint q, the Fourier matrix rows
+// from shared memory (row k at sF + k kMaxDof; one address per warp, a broadcast): sine and cosine
+// rounded to bf16, packed in pairs (the lower frequency in the low half).  z = B_k q sums over the
+// joints in order, one FMA each, as the feature routine of training and prediction does.
+template <int DOF>
+__device__ __forceinline__ void score_features_part(const float (&q)[DOF > 0 ? DOF : kMaxDof], const float* sF,
+                                                    int dof_rt, int k0, uint32_t (&sw)[4], uint32_t (&cw)[4]) {
   constexpr int ND = DOF > 0 ? DOF : kMaxDof;
-  const int dof = DOF > 0 ? DOF : f.dof;
-  float q[ND];
+  constexpr int ND4 = (ND + 3) / 4;
+  const int dof = DOF > 0 ? DOF : dof_rt;
 #pragma unroll
-  for (int d = 0; d < ND; ++d) q[d] = d < dof ? __fmaf_rn(t, __fsub_rn(v[d], u[d]), u[d]) : 0.0f;
-#pragma unroll
-  for (int k2 = 0; k2 < 16; ++k2) {
+  for (int k2 = 0; k2 < 4; ++k2) {
     float sn[2], cs[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int k = 2 * k2 + h;
+      const float4* row = reinterpret_cast<const float4*>(sF + (k0 + 2 * k2 + h) * kMaxDof);
+      float b[4 * ND4];
+#pragma unroll
+      for (int i = 0; i < ND4; ++i) {
+        const float4 r4 = row[i];
+        b[4 * i] = r4.x;
+        b[4 * i + 1] = r4.y;
+        b[4 * i + 2] = r4.z;
+        b[4 * i + 3] = r4.w;
+      }
       float z = 0.0f;
 #pragma unroll
       for (int d = 0; d < ND; ++d)
-        if (d < dof) z = __fmaf_rn(f.B[(HF * 32 + k) * dof + d], q[d], z);
+        if (d < dof) z = __fmaf_rn(b[d], q[d], z);
       __sincosf(z, &sn[h], &cs[h]);
     }
     const __nv_bfloat162 s2 = __floats2bfloat162_rn(sn[0], sn[1]);
@@ -644,6 +651,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   uint8_t* sX = sW1 + kSmemW1;                     // the tile's features (layer 1's A operand)
   uint8_t* sS = sX + kSmemX;                       // stream buffers
   float* sP = reinterpret_cast<float*>(sS + kChunkBufs * kSmemS);  // b1, b2, b3, w4
+  float* sF = sP + 4 * kHid;                                        // B [64][kMaxDof], zero padded
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool epi = tid < kEpiThreads;  // an epilogue thread (else the MMA warp)
   const uint32_t mbl = s_u32(&mbar_layer);
@@ -656,6 +664,10 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
       sP[kHid + tid] = P2[tid];
       sP[2 * kHid + tid] = P3[tid];
       sP[3 * kHid + tid] = P3[kHid + tid];
+    }
+    for (int i = tid; i < 64 * kMaxDof; i += kScoreThreads) {
+      const int k = i / kMaxDof, d = i % kMaxDof;
+      sF[i] = d < f.dof ? f.B[k * f.dof + d] : 0.0f;
     }
   }
   const float* b1 = sP;
@@ -719,9 +731,10 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   const long long total_chunks = my_tiles * 8;
   long long chunks_issued = 0;
 
-  // Features of a tile's queries -> X, in stages spread over the previous tile so that their loads and
-  // arithmetic run under its layers: the query's vertex indices, then its end points, then the
-  // features, computed and stored once the previous tile's layer 1 has read X.  Two
+  // Features of a tile's queries -> X, in stages spread over the tiles before so that their loads and
+  // arithmetic run under their layers: the query's vertex indices (two tiles ahead), its end points
+  // (one tile ahead), then the features in four parts, one per step of layer 1's epilogue, each stored
+  // to X (free once the current tile's layer 1 has read it).  Two
   // threads per query, 32 frequencies each; the fast __sincosf is ample here (|Bq| < 10, absolute error
   // ~1e-6, the features are rounded to bf16 right after).
   constexpr int ND = DOF > 0 ? DOF : kMaxDof;
@@ -740,8 +753,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   };
   int fi = 0, fj = 0;
   bool fvalid = false;
-  float fu[ND], fv[ND];
-  uint32_t sw[16], cw[16];
+  float fu[ND], fv[ND], fq[ND];
   auto feat_index = [&](long long tile_f) {
     const long long e = tile_f * e_per_tile + qidx / a.kw;
     fvalid = epi && qidx < q_per_tile && e < n_live;
@@ -764,28 +776,25 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
       }
     }
   };
-  auto feat_compute = [&]() {
+  // the query's waypoint q = u + t (v - u) from its end points
+  auto feat_waypoint = [&]() {
     if (fvalid) {
+      const int dof = DOF > 0 ? DOF : f.dof;
       const float t = a.kw == 1 ? 0.5f : 0.25f * static_cast<float>(qidx % a.kw + 1);
-      if (hf == 0)
-        score_features<DOF, 0>(fu, fv, t, f, sw, cw);
-      else
-        score_features<DOF, 1>(fu, fv, t, f, sw, cw);
-    } else {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) sw[k] = cw[k] = 0u;
+      for (int d = 0; d < ND; ++d) fq[d] = d < dof ? __fmaf_rn(t, __fsub_rn(fv[d], fu[d]), fu[d]) : 0.0f;
     }
   };
-  auto feat_store = [&]() {
+  // part p of 4 of the features (8 of this thread's 32 frequencies) -> X; part 3 fences X for the MMAs
+  auto feat_part = [&](int p) {
     if (!epi) return;
-#pragma unroll
-    for (int g8 = 0; g8 < 4; ++g8) {
-      *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + g8 * 8, 128)) =
-          make_uint4(sw[4 * g8], sw[4 * g8 + 1], sw[4 * g8 + 2], sw[4 * g8 + 3]);
-      *reinterpret_cast<uint4*>(sX + canon(qidx, 64 + hf * 32 + g8 * 8, 128)) =
-          make_uint4(cw[4 * g8], cw[4 * g8 + 1], cw[4 * g8 + 2], cw[4 * g8 + 3]);
+    uint32_t sw[4] = {0u, 0u, 0u, 0u}, cw[4] = {0u, 0u, 0u, 0u};
+    if (fvalid) {
+      score_features_part<DOF>(fq, sF, f.dof, hf * 32 + p * 8, sw, cw);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // X (generic writes) -> MMA reads
+    *reinterpret_cast<uint4*>(sX + canon(qidx, hf * 32 + p * 8, 128)) = make_uint4(sw[0], sw[1], sw[2], sw[3]);
+    *reinterpret_cast<uint4*>(sX + canon(qidx, 64 + hf * 32 + p * 8, 128)) = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+    if (p == 3) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // X (generic writes) -> MMA reads
   };
   // layer 1 (D = X W1^T) into the accumulator at TMEM column acc, committed to the layer barrier; on a W1
   // timeout the barrier is released by hand and the abort flag set
@@ -857,10 +866,11 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
     if (tile < n_tiles) {
       feat_index(tile);
       feat_points();
-      feat_compute();
-      feat_store();
+      feat_waypoint();
+      for (int p = 0; p < 4; ++p) feat_part(p);
       bar_sync_main();
       issue_l1(0u);
+      if (tile + gridDim.x < n_tiles) feat_index(tile + gridDim.x);
     }
     for (; tile < n_tiles && ok; tile += gridDim.x, par ^= 1u) {
       const uint32_t accA = par ? 256u : 0u, accB = par ? 0u : 256u;
@@ -878,17 +888,14 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
         hr = rows_live[r];
         hc = cols_live[cidx];
       }
-      if (next < n_tiles) feat_index(next);
+      // the next tile's end points (its indices were loaded a tile earlier), used under layer 1's epilogue
+      if (next < n_tiles) feat_points();
       ok = wait_layer();  // layer 1
-      if (ok && next < n_tiles) feat_points();  // the next tile's end points, loaded under layer 1's epilogue
+      if (ok && next < n_tiles) feat_waypoint();
       for (int l = 0; l < 2 && ok; ++l) {
         if (l == 1) {
-          // the next tile's features to X (layer 1 has read this tile's) and this edge's protection mark,
-          // under layer 2
-          if (next < n_tiles) {
-            feat_compute();
-            feat_store();
-          }
+          // the indices of the tile after next, and this edge's protection mark, under layer 2
+          if (next + gridDim.x < n_tiles) feat_index(next + gridDim.x);
           if (mine) {
             pidx = static_cast<size_t>(hr) * cols + hc;
             if (a.protect) prot = a.prune[pidx] == kPruneProtected;
@@ -920,6 +927,9 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
             }
             tmem_st16(lane_addr + acc_in + n0, w);
           }
+          // a quarter of the next tile's features to X (layer 1 has read this tile's), while the MMAs of
+          // chunk c - 1 run
+          if (l == 0 && next < n_tiles) feat_part(c);
           // chunk g = chunks_issued goes to the MMAs once every epilogue chunk is in place (its tensor-memory
           // stores completed in tmem_st16) and its weights have landed; the abort flag may be set by the MMA
           // or load thread at any time: the threads' readings are combined, so the CTA agrees
