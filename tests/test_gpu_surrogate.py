@@ -290,3 +290,56 @@ def test_scoring_kernel_decisions_elementwise(trained, kw):
     assert total > 8000
     assert compared_a >= 0.999 * total, (compared_a, total)
     assert compared_b >= 0.6 * total, (compared_b, total)
+
+
+@pytest.mark.parametrize("dof", [6, 5])
+def test_scoring_kernel_other_joint_counts(dof):
+    """The scoring kernel's 6-joint instantiation and its generic one (5 joints: the joint count read at
+    run time) against the GEMM path at the same float32 waypoints, edge by edge, wherever the GEMM logit
+    is farther from the cut than two FP32 sums of the head's 256 terms can differ (the bound of
+    test_scoring_kernel_decisions_elementwise).  M = 100 (one full 128-query tile and a ragged one per
+    row block), every transition including the start row and the goal column."""
+    import torch
+    sc = scene_for("arm", 1, dof, 30)
+    L, M, thr = 3, 100, 0.5
+    cut = math.log(thr / (1 - thr))
+    p = binding.Planner(sc.robot, M, L, 16, max_obstacles=64)
+    p.set_scene(sc)
+    binding.gtmp_surrogate_train(p.ctx, n_train=1 << 16, n_holdout=1 << 12, epochs=1, batch=1024, lr=1e-3,
+                                 seed=5, fourier_sigma=0.25)
+    P = binding.gtmp_surrogate_get_params(p.ctx, dof)
+    p.sample_layers(9, M)
+    p.solve()
+    V, _ = p.values()
+    V = V.cpu().numpy()
+    Q = p.get_layers().cpu().numpy()
+    verts = oracle.layer_vertices(Q, sc.q_start, sc.q_goal)
+    flags = [p.label_configs(torch.from_numpy(np.ascontiguousarray(v)).cuda()).cpu().numpy() for v in verts]
+    compared = total = 0
+    for layer in range(L + 1):
+        nr, nc = len(verts[layer]), len(verts[layer + 1])
+        mask = torch.full((nr, nc), 7, dtype=torch.uint8, device="cuda")
+        scored = binding.gtmp_surrogate_score(p.ctx, layer, thr, mask, score_waypoints=1)
+        mask = mask.cpu().numpy()
+        rows, cols = _live_edges(p, sc, L, V, flags, layer)
+        live = np.zeros((nr, nc), bool)
+        live[np.ix_(rows, cols)] = True
+        assert scored == live.sum()
+        np.testing.assert_array_equal(mask[~live], 2, err_msg=f"layer {layer}: non-live edges written")
+        if not live.any():
+            continue
+        ii, jj = np.nonzero(live)
+        got = mask[ii, jj].astype(bool)
+        (w,) = _waypoints(verts[layer][ii], verts[layer + 1][jj], 1)
+        z = torch.empty(len(w), dtype=torch.float32, device="cuda")
+        binding.gtmp_surrogate_predict(p.ctx, torch.from_numpy(np.ascontiguousarray(w)).cuda(), z)
+        zg = z.cpu().numpy().astype(np.float64)
+        r = sb.reference(P, w)
+        hb = 2.0 * sb.gamma(256) * 1.5 * (r["h3"] @ np.abs(r["w4"])) + 1e-6
+        sure = np.abs(zg - cut) > hb
+        np.testing.assert_array_equal(got[sure], (zg > cut)[sure], err_msg=f"dof {dof} layer {layer}")
+        compared += int(sure.sum())
+        total += len(ii)
+    print(f"scoring dof={dof}: {total} live edges, {compared} compared with the GEMM path")
+    assert total > 5000
+    assert compared >= 0.999 * total, (compared, total)
