@@ -274,18 +274,20 @@ struct CullGrid {
   const unsigned* cells = nullptr;  // null: no grid
   float lx = 0.0f, ly = 0.0f, lz = 0.0f, inv = 0.0f;
   int nx = 0, ny = 0, nz = 0;
+  float fnx = 0.0f, fny = 0.0f, fnz = 0.0f;  // nx, ny, nz as floats
 };
 
+// The cell's mask of obstacle pairs (0 outside the grid).  The cell index takes floor(f) for
+// 0 <= f < 2^23 as the bits of f + 2^23 rounded down (an FP32 add, where a float-to-int conversion
+// would go to the slower conversion pipe), the grid extents as floats.
 __device__ __forceinline__ unsigned grid_cell_mask(const CullGrid& gv, float x, float y, float z) {
   const float fx = __fmul_rn(__fsub_rn(x, gv.lx), gv.inv);
   const float fy = __fmul_rn(__fsub_rn(y, gv.ly), gv.inv);
   const float fz = __fmul_rn(__fsub_rn(z, gv.lz), gv.inv);
-  if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < static_cast<float>(gv.nx) &&
-        fy < static_cast<float>(gv.ny) && fz < static_cast<float>(gv.nz)))
-    return 0u;
-  const int ix = min(static_cast<int>(fx), gv.nx - 1);
-  const int iy = min(static_cast<int>(fy), gv.ny - 1);
-  const int iz = min(static_cast<int>(fz), gv.nz - 1);
+  if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < gv.fnx && fy < gv.fny && fz < gv.fnz)) return 0u;
+  const int ix = min(__float_as_int(__fadd_rd(fx, 8388608.0f)) - 0x4B000000, gv.nx - 1);
+  const int iy = min(__float_as_int(__fadd_rd(fy, 8388608.0f)) - 0x4B000000, gv.ny - 1);
+  const int iz = min(__float_as_int(__fadd_rd(fz, 8388608.0f)) - 0x4B000000, gv.nz - 1);
   return gv.cells[(iz * gv.ny + iy) * gv.nx + ix];
 }
 

@@ -126,6 +126,9 @@ __device__ __forceinline__ bool config_collides(const float* q, bool active, con
       grid.nx = sc.gnx;
       grid.ny = sc.gny;
       grid.nz = sc.gnz;
+      grid.fnx = static_cast<float>(sc.gnx);
+      grid.fny = static_cast<float>(sc.gny);
+      grid.fnz = static_cast<float>(sc.gnz);
     }
     return arm_config_collides<V::kDof, V::kSpl, V::kUnif, WARP_EXIT, FULL, true>(
         q, active, rb, s_obs, sc.n_sp, boxp, sc.n_bp, pre, sc.n_pairs, cull, sc.n_cull, grid);
