@@ -1018,10 +1018,10 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
                      : "memory");
         drained = mbar_wait_parity(s_u32(&mbar_fin), 0u, kMbarLimit);
       }
-      if (!ok || !drained) {
-        atomicOr(a.err, kErrWaitTimeout);
-        if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);  // let the W1 copy land (bounded)
-      }
+      if (!ok || !drained) atomicOr(a.err, kErrWaitTimeout);
+      // the W1 copy has landed before the shared memory is released, also in a CTA that got no tile
+      // (the grid is sized by all edges, the tiles by the live ones) or stopped early (bounded)
+      if (!w1_ready) mbar_wait_parity(s_u32(&mbar_w1), 0u, kMbarLimit);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
