@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   float* sP = reinterpret_cast<float*>(sS + kChunkBufs * kSmemS);  // b1, b2, b3, w4
   float* sF = sP + 4 * kHid;                                        // B [64][kMaxDof], zero padded
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool epi = tid < kEpiThreads;  // an epilogue thread (else the MMA warp)
+  const bool epi = tid < kEpiThreads;  // an epilogue thread (else the MMA or the load warp)
   const uint32_t mbl = s_u32(&mbar_layer);
   {
     const float* P1 = a.P + kNW1;
@@ -734,9 +734,9 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   // Features of a tile's queries -> X, in stages spread over the tiles before so that their loads and
   // arithmetic run under their layers: the query's vertex indices (two tiles ahead), its end points
   // (one tile ahead), then the features in four parts, one per step of layer 1's epilogue, each stored
-  // to X (free once the current tile's layer 1 has read it).  Two
-  // threads per query, 32 frequencies each; the fast __sincosf is ample here (|Bq| < 10, absolute error
-  // ~1e-6, the features are rounded to bf16 right after).
+  // to X (free once the current tile's layer 1 has read it).  Two threads per query, 32 frequencies
+  // each; the fast __sincosf is ample here (|Bq| < 10, absolute error ~1e-6, the features are rounded
+  // to bf16 right after).
   constexpr int ND = DOF > 0 ? DOF : kMaxDof;
   const int qidx = tid & 127, hf = tid >> 7;
   const bool small = n_live <= 0x7fffffffLL;
@@ -823,9 +823,10 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   // Per tile: the layer-1 accumulator A (TMEM columns 0 or 256, alternating by tile) also takes layer 3,
   // the other one, B, layer 2.  Each epilogue runs in four 64-column chunks; chunk c of layer l's
   // output, written back to tensor memory as bf16, is K-slice c of layer l + 1's A operand, whose four
-  // MMAs are issued at once and run under the epilogue of chunk c + 1.  The next tile's features are
-  // loaded under layer 1's epilogue and computed and stored to X (free once this tile's layer 1 is
-  // done) under layer 2; its layer-1 MMAs (into B) run under this tile's head (which reads A).
+  // MMAs are issued at once and run under the epilogue of chunk c + 1.  The next tile's end points are
+  // loaded before this tile's layer-1 wait, and its features computed and stored to X (free once this
+  // tile's layer 1 is done) a quarter per step of layer 1's epilogue; its layer-1 MMAs (into B) run
+  // under this tile's head (which reads A).
   if (tid >= kMainThreads) {
     // The load warp: lane 0 streams chunk g into buffer g % kChunkBufs as one bulk copy completing on
     // mbar_full, once chunk g - kChunkBufs's MMAs have freed the buffer.  It runs ahead of the MMAs by
