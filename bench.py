@@ -231,7 +231,7 @@ class ClockSampler:
 # transition of this workload, from the ncu capture summarised in
 # profiles/fused_transition_arm7_m1024_l8_h32.md (set back to None whenever the kernel changes); the
 # algorithmic bytes per launch are reported beside it
-FULL_MODE_DRAM_BYTES_PER_LAUNCH = 198656
+FULL_MODE_DRAM_BYTES_PER_LAUNCH = 189696
 
 
 def measured_peaks():

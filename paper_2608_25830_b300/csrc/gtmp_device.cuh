@@ -382,7 +382,7 @@ __device__ __forceinline__ bool exact_packed_hit(const float (&cx)[NS], const fl
     z2[k] = make_float2(cz[k], cz[k]);
     m[k] = __int_as_float(0x7f800000);
   }
-#pragma unroll 2
+#pragma unroll 1
   for (int p = 0; p < n_sp; ++p) {
     const float4 P0 = sphp[2 * p];
     const float4 P1 = sphp[2 * p + 1];
