@@ -576,6 +576,24 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&w)[16
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// 64 TMEM columns of this warp's 32 lanes in one load
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+      "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+        "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
+        "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
+        "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Weight images for the scoring kernel: W1 [256 x 128] and the chunks
 // c = 0..7 (W2 then W3, input columns [64 (c & 3), + 64)) laid out in global
 // memory exactly as their shared-memory tiles (canonical K-major), so that one
@@ -974,22 +992,26 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
       // head: relu(acc + b3) . w4 + b4, per query; then the edge's max against the cut
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float dot = 0.0f;
-      for (int cc = 0; cc < 4 && epi; ++cc) {
-        const int n0 = half * 128 + cc * 32;
-        uint32_t v[32];
-        tmem_ld32(lane_addr + accA + n0, v);
-        // four partial sums: a short dependency chain
-        float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int cp = 0; cp < 2 && epi; ++cp) {
+        uint32_t v[64];
+        tmem_ld64(lane_addr + accA + half * 128 + cp * 64, v);
 #pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) {
-          const float4 bb = *reinterpret_cast<const float4*>(b3 + n0 + 4 * j4);
-          const float4 ww = *reinterpret_cast<const float4*>(w4 + n0 + 4 * j4);
-          part[0] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4]) + bb.x, 0.0f), ww.x, part[0]);
-          part[1] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 1]) + bb.y, 0.0f), ww.y, part[1]);
-          part[2] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 2]) + bb.z, 0.0f), ww.z, part[2]);
-          part[3] = __fmaf_rn(fmaxf(__uint_as_float(v[4 * j4 + 3]) + bb.w, 0.0f), ww.w, part[3]);
+        for (int c2 = 0; c2 < 2; ++c2) {
+          const int n0 = half * 128 + (2 * cp + c2) * 32;
+          // four partial sums: a short dependency chain
+          float part[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            const float4 bb = *reinterpret_cast<const float4*>(b3 + n0 + 4 * j4);
+            const float4 ww = *reinterpret_cast<const float4*>(w4 + n0 + 4 * j4);
+            const uint32_t* vv = v + 32 * c2 + 4 * j4;
+            part[0] = __fmaf_rn(fmaxf(__uint_as_float(vv[0]) + bb.x, 0.0f), ww.x, part[0]);
+            part[1] = __fmaf_rn(fmaxf(__uint_as_float(vv[1]) + bb.y, 0.0f), ww.y, part[1]);
+            part[2] = __fmaf_rn(fmaxf(__uint_as_float(vv[2]) + bb.z, 0.0f), ww.z, part[2]);
+            part[3] = __fmaf_rn(fmaxf(__uint_as_float(vv[3]) + bb.w, 0.0f), ww.w, part[3]);
+          }
+          dot += (part[0] + part[1]) + (part[2] + part[3]);
         }
-        dot += (part[0] + part[1]) + (part[2] + part[3]);
       }
       if (epi) s_part[half][row] = dot;
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
