@@ -986,8 +986,9 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
       if (!ok) break;
       ok = wait_layer();  // layer 3 (accumulator A)
       if (!ok) break;
-      // the next tile's layer-1 MMAs into B (its X was stored under layer 2, before this tile's last
-      // chunk barriers), under this head
+      // the next tile's layer-1 MMAs into B (its X was stored under layer 1's epilogue, before this
+      // tile's chunk barriers), under this head; the MMA thread issues after the barrier (issuing
+      // before it would hold every warp's head back by the ~1 k cycles the issue blocks)
       if (next < n_tiles) issue_l1(accB);
       // head: relu(acc + b3) . w4 + b4, per query; then the edge's max against the cut
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
