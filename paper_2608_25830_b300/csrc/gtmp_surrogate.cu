@@ -937,12 +937,13 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
 #pragma unroll
             for (int g4 = 0; g4 < 8; ++g4) {
               const float4 bb = *reinterpret_cast<const float4*>(bias + n0 + g4 * 4);
-              const __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[4 * g4]) + bb.x, 0.0f),
-                                                              fmaxf(__uint_as_float(v[4 * g4 + 1]) + bb.y, 0.0f));
-              const __nv_bfloat162 h1 = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[4 * g4 + 2]) + bb.z, 0.0f),
-                                                              fmaxf(__uint_as_float(v[4 * g4 + 3]) + bb.w, 0.0f));
-              w[2 * g4] = *reinterpret_cast<const uint32_t*>(&h0);
-              w[2 * g4 + 1] = *reinterpret_cast<const uint32_t*>(&h1);
+              // relu and the bf16 rounding in one conversion (the high half takes the first operand); it
+              // differs from max-then-round only in the sign of a zero, which no product sees, and in
+              // passing a NaN on (a model with NaN weights then prunes nothing: z > cut fails)
+              asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[2 * g4])
+                  : "f"(__uint_as_float(v[4 * g4 + 1]) + bb.y), "f"(__uint_as_float(v[4 * g4]) + bb.x));
+              asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[2 * g4 + 1])
+                  : "f"(__uint_as_float(v[4 * g4 + 3]) + bb.w), "f"(__uint_as_float(v[4 * g4 + 2]) + bb.z));
             }
             tmem_st16(lane_addr + acc_in + n0, w);
           }
