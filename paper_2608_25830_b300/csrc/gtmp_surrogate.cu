@@ -940,10 +940,12 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
               // relu and the bf16 rounding in one conversion (the high half takes the first operand); it
               // differs from max-then-round only in the sign of a zero, which no product sees, and in
               // passing a NaN on (a model with NaN weights then prunes nothing: z > cut fails)
-              asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[2 * g4])
-                  : "f"(__uint_as_float(v[4 * g4 + 1]) + bb.y), "f"(__uint_as_float(v[4 * g4]) + bb.x));
-              asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[2 * g4 + 1])
-                  : "f"(__uint_as_float(v[4 * g4 + 3]) + bb.w), "f"(__uint_as_float(v[4 * g4 + 2]) + bb.z));
+              const float2 a0 = __fadd2_rn(make_float2(__uint_as_float(v[4 * g4]), __uint_as_float(v[4 * g4 + 1])),
+                                           make_float2(bb.x, bb.y));
+              const float2 a1 = __fadd2_rn(make_float2(__uint_as_float(v[4 * g4 + 2]), __uint_as_float(v[4 * g4 + 3])),
+                                           make_float2(bb.z, bb.w));
+              asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[2 * g4]) : "f"(a0.y), "f"(a0.x));
+              asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(w[2 * g4 + 1]) : "f"(a1.y), "f"(a1.x));
             }
             tmem_st16(lane_addr + acc_in + n0, w);
           }
@@ -1007,10 +1009,18 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
             const float4 bb = *reinterpret_cast<const float4*>(b3 + n0 + 4 * j4);
             const float4 ww = *reinterpret_cast<const float4*>(w4 + n0 + 4 * j4);
             const uint32_t* vv = v + 32 * c2 + 4 * j4;
-            part[0] = __fmaf_rn(fmaxf(__uint_as_float(vv[0]) + bb.x, 0.0f), ww.x, part[0]);
-            part[1] = __fmaf_rn(fmaxf(__uint_as_float(vv[1]) + bb.y, 0.0f), ww.y, part[1]);
-            part[2] = __fmaf_rn(fmaxf(__uint_as_float(vv[2]) + bb.z, 0.0f), ww.z, part[2]);
-            part[3] = __fmaf_rn(fmaxf(__uint_as_float(vv[3]) + bb.w, 0.0f), ww.w, part[3]);
+            const float2 s0 = __fadd2_rn(make_float2(__uint_as_float(vv[0]), __uint_as_float(vv[1])),
+                                         make_float2(bb.x, bb.y));
+            const float2 s1 = __fadd2_rn(make_float2(__uint_as_float(vv[2]), __uint_as_float(vv[3])),
+                                         make_float2(bb.z, bb.w));
+            const float2 p01 = __ffma2_rn(make_float2(fmaxf(s0.x, 0.0f), fmaxf(s0.y, 0.0f)), make_float2(ww.x, ww.y),
+                                          make_float2(part[0], part[1]));
+            const float2 p23 = __ffma2_rn(make_float2(fmaxf(s1.x, 0.0f), fmaxf(s1.y, 0.0f)), make_float2(ww.z, ww.w),
+                                          make_float2(part[2], part[3]));
+            part[0] = p01.x;
+            part[1] = p01.y;
+            part[2] = p23.x;
+            part[3] = p23.y;
           }
           dot += (part[0] + part[1]) + (part[2] + part[3]);
         }
