@@ -729,6 +729,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   bool w1_ready = false, any_mma = false;  // the MMA thread's state
+  bool released = false;                   // the MMA thread has released the layer barrier by hand
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (256u >> 3 << 17) | (128u >> 4 << 24);
@@ -825,6 +826,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
       if (!go) {
         s_abort = 1;
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbl) : "memory");
+        released = true;
       }
     }
     if (go) {
@@ -953,17 +955,19 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
           // chunk c - 1 run
           if (l == 0 && next < n_tiles) feat_part(c);
           // chunk g = chunks_issued goes to the MMAs once every epilogue chunk is in place (its tensor-memory
-          // stores completed in tmem_st16) and its weights have landed; the abort flag may be set by the MMA
-          // or load thread at any time: the threads' readings are combined, so the CTA agrees
+          // stores completed in tmem_st16) and its weights have landed.  A plain barrier (a reducing one
+          // measured 8 % of the kernel): the abort flag, which the MMA or load thread may set at any time,
+          // is taken at the next layer wait, which combines every thread's reading of it
           const long long g = chunks_issued;
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          ok = bar_and_main(s_abort == 0);
-          if (!ok) break;
+          bar_sync_main();
           if (tid == kMmaThread) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sb = s_u32(sS + static_cast<int>(g % kChunkBufs) * kSmemS);
-            const bool go = mbar_wait_parity(s_u32(&mbar_full[g % kChunkBufs]),
-                                             static_cast<uint32_t>((g / kChunkBufs) & 1), kMbarLimit);
+            // after its own abort the MMA thread waits for nothing more (a load-thread abort shows here as
+            // a chunk that never lands, the bounded wait's timeout)
+            const bool go = !released && mbar_wait_parity(s_u32(&mbar_full[g % kChunkBufs]),
+                                                          static_cast<uint32_t>((g / kChunkBufs) & 1), kMbarLimit);
             // K-step kk of chunk c: A columns 16 kk .. + 16 of the chunk, i.e. half kk / 2's packed
             // columns, 8 columns per 16 K
             if (go) {
@@ -977,10 +981,12 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
               if (c == 3)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbl)
                              : "memory");
-            } else {
-              // a timeout: the CTA stops at its next barrier (the layer barrier is released for a waiter)
+            } else if (!released) {
+              // a timeout (here or in the load thread): the CTA stops at its next layer wait, whose
+              // barrier is released once by hand
               s_abort = 1;
               asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbl) : "memory");
+              released = true;
             }
           }
           ++chunks_issued;
