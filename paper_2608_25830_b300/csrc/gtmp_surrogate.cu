@@ -695,11 +695,12 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
   const float b4 = a.P[kNW1 + kHid + kNW2 + kHid + kNW3 + kHid + kHid];
 
   uint32_t ph_layer = 0;
-  // every thread waits for the next layer completion; the CTA agrees on the outcome
-  auto wait_layer = [&]() -> bool {
+  // every thread waits for the next layer completion; the CTA agrees on the outcome (and on an earlier
+  // wait's, passed in)
+  auto wait_layer = [&](bool earlier_ok = true) -> bool {
     const bool w = mbar_wait_parity(mbl, ph_layer, kMbarLimit);
     ph_layer ^= 1u;
-    return bar_and_main(w && s_abort == 0);
+    return bar_and_main(earlier_ok && w && s_abort == 0);
   };
 
   if (warp == 0) {
@@ -911,8 +912,12 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
       }
       // the next tile's end points (its indices were loaded a tile earlier), used under layer 1's epilogue
       if (next < n_tiles) feat_points();
-      ok = wait_layer();  // layer 1
-      if (ok && next < n_tiles) feat_waypoint();
+      // layer 1, issued under the previous tile's head, is long done: each thread waits for it on its
+      // own (the barrier's completion orders the accumulator for this thread's tensor-memory reads),
+      // and a timeout joins the CTA's decision at the layer-2 wait
+      const bool l1_ok = mbar_wait_parity(mbl, ph_layer, kMbarLimit);
+      ph_layer ^= 1u;
+      if (next < n_tiles) feat_waypoint();
       for (int l = 0; l < 2 && ok; ++l) {
         if (l == 1) {
           // the indices of the tile after next, and this edge's protection mark, under layer 2
@@ -921,7 +926,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1) score_edges_kernel(ScoreArgs
             pidx = static_cast<size_t>(hr) * cols + hc;
             if (a.protect) prot = a.prune[pidx] == kPruneProtected;
           }
-          ok = wait_layer();  // layer 2
+          ok = wait_layer(l1_ok);  // layer 2 (and layer 1's outcome)
           if (!ok) break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
